@@ -1,0 +1,336 @@
+"""Pins of the oracle's time step against closed forms and published values.
+
+* velocity/vorticity recovery: div u = 0, div omega = 0, omega_y = curl_y u;
+* h_v, h_g assembly: zero for gradient fields, unit responses otherwise;
+* nonlinear term: worked single-mode example, products computed with numpy's
+  Chebyshev-series routines; laminar Poiseuille gives H = (0, U U', 0);
+* time scheme: the discrete amplification factor
+  prod_k (1 + alpha_k dt mu) / (1 - beta_k dt mu) for eigenpairs of the
+  discrete tau operator (eigenpairs from scipy.linalg.eig);
+* Orr-Sommerfeld: Tollmien-Schlichting growth rate 0.00373967 at Re = 10^4;
+* laminar Poiseuille held steady, CFR forcing 3 nu, reward 1 - 3 Re_b / Re_tau^2;
+* opposition control (Sec. 4.1 equation) and the sensing node (Sec. 3.2).
+"""
+
+import math
+
+import numpy as np
+import numpy.polynomial.chebyshev as npc
+import pytest
+import scipy.linalg
+
+import seeded_inputs as si
+from oracle import channel, spectral as sp, stability
+
+
+def _params(nx=8, ny=33, nz=8, **kw):
+    base = dict(lx=2 * np.pi, lz=np.pi)
+    base.update(kw)
+    return channel.Params(nx=nx, ny=ny, nz=nz, **base)
+
+
+def _pad(c, n1):
+    out = np.zeros(n1, dtype=np.result_type(c, float))
+    out[: len(c)] = c
+    return out
+
+
+def _random_state(p, seed=1, amp=0.3, kmax=99):
+    return channel.new_state(si.perturbed_poiseuille(p.nx, p.ny, p.nz, seed, amp, kmax), p)
+
+
+# --------------------------------------------------------------------------
+# recovery of u, w, omega
+# --------------------------------------------------------------------------
+
+def test_recovery_divergence_free_and_curl_consistent():
+    p = _params(nx=8, ny=33, nz=6)
+    ops = channel.Operators(p)
+    st = _random_state(p)
+    # make the state generic in y as well
+    rng = np.random.default_rng(0)
+    st["v"] = st["v"] + 0.01 * (rng.standard_normal(st["v"].shape) * (st["v"] != 0))
+    f = channel.velocity_vorticity(st, ops)
+    kx, kz = ops.kx, ops.kz
+    D = lambda a: np.array([[_pad(npc.chebder(a[r, c]), ops.N + 1) for c in range(a.shape[1])]
+                            for r in range(a.shape[0])])
+    scale = max(np.abs(f[k]).max() for k in f)
+    div_u = 1j * kx * f["u"] + D(f["v"]) + 1j * kz * f["w"]
+    assert np.abs(div_u).max() < 1e-12 * scale * ops.N ** 2
+    div_w = 1j * kx * f["ox"] + D(f["oy"]) + 1j * kz * f["oz"]
+    assert np.abs(div_w).max() < 1e-12 * scale * ops.N ** 2
+    curl_y = 1j * kz * f["u"] - 1j * kx * f["w"]
+    m = np.ones(f["u"].shape[:2], bool)
+    m[0, 0] = False
+    assert np.abs((curl_y - f["oy"])[m]).max() < 1e-12 * scale
+    # x component of curl u: Dw - i kz v ; z component: i kx v - Du
+    cx = D(f["w"]) - 1j * kz * f["v"]
+    cz = 1j * kx * f["v"] - D(f["u"])
+    assert np.abs(cx - f["ox"]).max() < 1e-11 * scale * ops.N ** 2
+    assert np.abs(cz - f["oz"]).max() < 1e-11 * scale * ops.N ** 2
+
+
+def test_mean_mode_vorticity_signs():
+    p = _params()
+    ops = channel.Operators(p)
+    st = _random_state(p)
+    st["W"] = np.zeros(ops.N + 1)
+    st["W"][1] = 0.2       # W = 0.2 y
+    f = channel.velocity_vorticity(st, ops)
+    # U = 1.5(1-y^2): omega_z = -dU/dy = 3y = 3 T1 ; omega_x = dW/dy = 0.2
+    assert np.allclose(f["oz"][0, 0][:3], [0, 3.0, 0], atol=1e-14)
+    assert np.allclose(f["ox"][0, 0][:2], [0.2, 0], atol=1e-14)
+    assert np.all(f["v"][0, 0] == 0) and np.all(f["oy"][0, 0] == 0)
+
+
+# --------------------------------------------------------------------------
+# h_v, h_g assembly
+# --------------------------------------------------------------------------
+
+def test_assembly_kills_gradients():
+    """H = grad psi has curl H = 0, so h_v = h_g = 0 for every mode."""
+    p = _params(nx=8, ny=33, nz=8)
+    ops = channel.Operators(p)
+    rng = np.random.default_rng(5)
+    shape = (p.nz, p.nx // 2, ops.N + 1)
+    psi = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    psi[..., -1] = 0.0  # keep D psi exact within degree N-1
+    H = {"x": 1j * ops.kx * psi, "y": ops.d(psi), "z": 1j * ops.kz * psi}
+    hv, hg, _, _ = channel.assemble(H, ops)
+    assert np.abs(hv).max() < 1e-11 * np.abs(H["y"]).max()
+    assert np.abs(hg).max() < 1e-12 * np.abs(psi).max() * 10
+
+
+def test_assembly_unit_responses():
+    p = _params(nx=8, ny=17, nz=8)
+    ops = channel.Operators(p)
+    shape = (p.nz, p.nx // 2, ops.N + 1)
+    f = np.zeros(shape, complex)
+    f[1, 2, 3] = 1.0 + 2.0j
+    zero = np.zeros(shape, complex)
+    k2 = ops.k2[1, 2, 0]
+    hv, hg, _, _ = channel.assemble({"x": zero, "y": f, "z": zero}, ops)
+    assert np.allclose(hv, -k2 * f) and np.all(hg == 0)
+    hv, hg, _, _ = channel.assemble({"x": f, "y": zero, "z": zero}, ops)
+    assert np.allclose(hg, 1j * ops.kz[1, 0, 0] * f)
+    # h_v = -D(i kx H_x): T_3 derivative = 3 T_0 * 2/2 ... compare with chebder
+    ref = -1j * ops.kx[0, 2, 0] * _pad(npc.chebder(f[1, 2]), ops.N + 1)
+    assert np.allclose(hv[1, 2], ref)
+
+
+# --------------------------------------------------------------------------
+# nonlinear term worked examples
+# --------------------------------------------------------------------------
+
+def test_poiseuille_nonlinear_term():
+    p = _params(nx=8, ny=33, nz=8)
+    ops = channel.Operators(p)
+    st = channel.new_state(si.perturbed_poiseuille(p.nx, p.ny, p.nz, 0, 0.0), p)
+    hv, hg, Hx00, Hz00, H = channel.nonlinear(st, ops)
+    U = st["U"]
+    ref = _pad(npc.chebmul(U, npc.chebder(U)), ops.N + 1)     # U U'
+    assert np.allclose(np.real(H["y"][0, 0]), ref, atol=1e-14)
+    assert np.abs(hv).max() < 1e-14 and np.abs(hg).max() < 1e-14
+    assert np.abs(Hx00).max() < 1e-14 and np.abs(Hz00).max() < 1e-14
+    Hy = H["y"].copy()
+    Hy[0, 0] = 0
+    assert np.abs(Hy).max() < 1e-14
+
+
+def test_single_mode_products_exact():
+    """One oblique mode (kx, kz) = (1, 2): H at (2kx, 2kz) and at (0, 0).
+
+    Fields a = 2 Re(a_hat E), b = 2 Re(b_hat E) with E = exp(i(kx x + kz z))
+    give (ab)_hat = a_hat b_hat at 2k and 2 Re(a_hat conj(b_hat)) at 0.  The
+    y-polynomials are multiplied with numpy.polynomial.chebyshev.
+    """
+    p = _params(nx=8, ny=33, nz=8)       # kx = i, kz = 2 m
+    ops = channel.Operators(p)
+    N1 = ops.N + 1
+    st = channel.new_state(si.perturbed_poiseuille(p.nx, p.ny, p.nz, 0, 0.0), p)
+    st["U"][:] = 0.0
+    cv, cg = 0.3 - 0.2j, -0.1 + 0.4j
+    vhat = cv * np.array([0.375, 0, -0.5, 0, 0.125])      # cv (1-y^2)^2
+    ghat = cg * np.array([0.5, 0, -0.5])                  # cg (1-y^2)
+    st["v"][1, 1, :5] = vhat
+    st["g"][1, 1, :3] = ghat
+    kx, kz = 1.0, 2.0
+    k2 = kx * kx + kz * kz
+    C = npc
+    dv = C.chebder(vhat)
+    u = C.chebsub(1j * kx * dv, 1j * kz * ghat) / k2
+    w = C.chebadd(1j * kz * dv, 1j * kx * ghat) / k2
+    ox = C.chebsub(C.chebder(w), 1j * kz * vhat)
+    oz = C.chebsub(1j * kx * vhat, C.chebder(u))
+    oy = ghat
+    v = vhat
+
+    def mul(a, b):
+        return C.chebmul(a, b)
+
+    def two_re_conj(a, b):  # 2 Re(a conj(b)) as a real polynomial
+        return 2 * (mul(np.real(a), np.real(b)) + mul(np.imag(a), np.imag(b)))
+
+    ref2 = {"x": C.chebsub(mul(v, oz), mul(w, oy)),
+            "y": C.chebsub(mul(w, ox), mul(u, oz)),
+            "z": C.chebsub(mul(u, oy), mul(v, ox))}
+    ref0 = {"x": C.chebsub(two_re_conj(v, oz), two_re_conj(w, oy)),
+            "y": C.chebsub(two_re_conj(w, ox), two_re_conj(u, oz)),
+            "z": C.chebsub(two_re_conj(u, oy), two_re_conj(v, ox))}
+    _, _, _, _, H = channel.nonlinear(st, ops)
+    for c in "xyz":
+        assert np.allclose(H[c][2, 2], _pad(ref2[c], N1), atol=1e-14), c
+        assert np.allclose(H[c][0, 0], _pad(ref0[c], N1), atol=1e-14), c
+        other = H[c].copy()
+        other[2, 2] = 0
+        other[0, 0] = 0
+        assert np.abs(other).max() < 1e-14, c
+
+
+# --------------------------------------------------------------------------
+# time scheme
+# --------------------------------------------------------------------------
+
+def _tau_eigs(ops):
+    """Eigenpairs of the tau operator D^2 with homogeneous Dirichlet rows."""
+    N = ops.N
+    A = np.zeros((N + 1, N + 1))
+    B = np.zeros((N + 1, N + 1))
+    A[: N - 1] = ops.D2[: N - 1]
+    B[: N - 1, : N - 1] = np.eye(N - 1)
+    A[N - 1] = ops.Tp
+    A[N] = ops.Tm
+    mu, V = scipy.linalg.eig(A, B)
+    ok = np.isfinite(mu)
+    mu, V = mu[ok].real, V[:, ok].real
+    order = np.argsort(-mu)
+    return mu[order], V[:, order]
+
+
+def _factor(mu_lin, dt):
+    f = 1.0
+    for k in range(3):
+        f *= (1 + channel.ALPHA[k] * dt * mu_lin) / (1 - channel.BETA[k] * dt * mu_lin)
+    return f
+
+
+@pytest.mark.parametrize("which", [0, 1, 4])
+def test_mean_spanwise_heat_mode_amplification(which):
+    p = _params(nx=4, ny=33, nz=4)
+    ops = channel.Operators(p)
+    mu, V = _tau_eigs(ops)
+    assert abs(mu[0] + np.pi ** 2 / 4) < 1e-8     # slowest mode ~ -pi^2/4
+    st = channel.new_state(si.perturbed_poiseuille(p.nx, p.ny, p.nz, 0, 0.0), p)
+    W0 = 0.01 * V[:, which] / np.abs(V[:, which]).max()
+    st["W"] = W0.copy()
+    channel.rk3_step(st, ops, st["vw"], st["vw"], 0)
+    ref = _factor(p.nu * mu[which], p.dt) * W0
+    assert np.abs(st["W"] - ref).max() < 1e-13
+
+
+def test_vertical_vorticity_stokes_mode_amplification():
+    """kx = 0 omega_y mode in Poiseuille flow: no advection, decays as a Stokes mode."""
+    p = _params(nx=4, ny=33, nz=4)
+    ops = channel.Operators(p)
+    mu, V = _tau_eigs(ops)
+    st = channel.new_state(si.perturbed_poiseuille(p.nx, p.ny, p.nz, 0, 0.0), p)
+    eps = 1e-7
+    g0 = eps * V[:, 1] / np.abs(V[:, 1]).max()
+    st["g"][1, 0] = g0          # kz index +1
+    st["g"][3, 0] = g0          # kz index -1 (conjugate of a real profile)
+    kz2 = ops.kz[1, 0, 0] ** 2
+    channel.rk3_step(st, ops, st["vw"], st["vw"], 0)
+    ref = _factor(p.nu * (mu[1] - kz2), p.dt) * g0
+    assert np.abs(st["g"][1, 0] - ref).max() < 1e-9 * eps
+
+
+def test_orr_sommerfeld_growth_rate():
+    """Tollmien-Schlichting wave, Re_cl = 10^4, alpha = 1: amplitude growth
+    rate 0.00373967 in centre-line units.  Bulk units: U = 1.5 (1 - y^2),
+    nu = 1.5e-4, so the rate and time step scale by 1.5."""
+    c_os, v_os = stability.most_unstable(64, 1.0, 1.0e4)
+    assert abs(c_os.imag - 0.00373967) < 1e-8
+    p = channel.Params(nx=4, ny=65, nz=4, lx=2 * np.pi, lz=np.pi,
+                       re_bulk=1.0e4 / 1.5, dt=0.01 / 1.5)
+    ops = channel.Operators(p)
+    st = channel.new_state(si.perturbed_poiseuille(4, 65, 4, 0, 0.0), p)
+    st["v"][0, 1] = 1e-6 * v_os
+    n0 = np.linalg.norm(st["v"][0, 1])
+    nsteps = 150
+    for _ in range(nsteps):
+        channel.rk3_step(st, ops, st["vw"], st["vw"], 0)
+    T = nsteps * p.dt
+    sigma = math.log(np.linalg.norm(st["v"][0, 1]) / n0) / T / 1.5
+    assert abs(sigma - 0.00373967) < 1e-3 * 0.00373967, sigma
+
+
+# --------------------------------------------------------------------------
+# laminar flow, reward, opposition control, sensing plane
+# --------------------------------------------------------------------------
+
+def test_poiseuille_steady_and_laminar_reward():
+    p = _params(nx=4, ny=65, nz=4)
+    ops = channel.Operators(p)
+    st = channel.new_state(si.perturbed_poiseuille(p.nx, p.ny, p.nz, 0, 0.0), p)
+    U0 = st["U"].copy()
+    zero = np.zeros((p.nz, p.nx))
+    for _ in range(100):
+        obs, tau, reward = channel.env_step(st, ops, zero)
+    assert np.abs(st["U"] - U0).max() < 1e-12
+    assert abs(st["fx"] - 3 * p.nu) < 1e-9 * 3 * p.nu
+    assert abs(tau - 3.0 / p.re_bulk) < 1e-13
+    # relaminarisation bound (Sec. 3.2): 1 - 3 Re_b / Re_tau^2
+    assert abs(reward - (1 - 3 * p.re_bulk / p.re_tau ** 2)) < 1e-10
+    assert abs(reward - 0.7407407407) < 1e-9
+    # observation: u = U(y_s) everywhere, v = 0
+    ys = math.cos(math.pi * ops.js / ops.N)
+    assert np.allclose(obs[0], 1.5 * (1 - ys * ys), atol=1e-13)
+    assert np.abs(obs[1]).max() < 1e-15
+
+
+def test_opposition_control_law():
+    p = _params(nx=8, ny=33, nz=8, control=1, alpha=1.0)
+    ops = channel.Operators(p)
+    st = _random_state(p)
+    js = ops.js
+    vs = st["v"] @ ops.S[js]              # v(y_s) per mode
+    ys = math.cos(math.pi * js / ops.N)
+    # independent evaluation of v(y_s) per mode
+    ref = np.array([[npc.chebval(ys, st["v"][r, c]) for c in range(p.nx // 2)] for r in range(p.nz)])
+    assert np.allclose(vs, ref, atol=1e-14)
+    channel.env_step(st, ops)
+    vw = st["vw"]
+    expect = -p.alpha * ref
+    expect[0, 0] = 0.0
+    assert np.allclose(vw, expect, atol=1e-15)
+    # physical space: v_w = -alpha (v(y_s) - <v(y_s)>)
+    vphys = sp.to_physical(ref, p.nx, p.nz, p.nx, p.nz)
+    wphys = sp.to_physical(vw, p.nx, p.nz, p.nx, p.nz)
+    assert np.allclose(wphys, -p.alpha * (vphys - vphys.mean()), atol=1e-14)
+
+
+def test_action_clip_and_zero_net_mass_flux():
+    p = _params(nx=8, ny=17, nz=8)
+    ops = channel.Operators(p)
+    x = np.arange(p.nx) / p.nx
+    z = np.arange(p.nz) / p.nz
+    a = 0.2 * np.cos(2 * np.pi * x)[None, :] + 0.03 * np.sin(4 * np.pi * z)[:, None] + 0.05
+    F = channel.action_spectrum(a, ops)
+    assert F[0, 0] == 0
+    c = np.clip(a, -p.u_tau, p.u_tau)
+    # no Nyquist content in the clipped field? reconstruct and compare on kept content
+    back = sp.to_physical(F, p.nx, p.nz, p.nx, p.nz)
+    ref = sp.to_physical(sp.to_spectral(c - c.mean(), p.nx, p.nz, p.nx, p.nz), p.nx, p.nz, p.nx, p.nz)
+    assert np.allclose(back, ref, atol=1e-15)
+    assert abs(back.mean()) < 1e-16
+    assert np.abs(back).max() <= 2 * p.u_tau
+
+
+@pytest.mark.parametrize("ny,re_tau,yplus", [(65, 180, 17.2819), (129, 395, 17.01), (193, 550, 16.48)])
+def test_sensing_node_rounded_up(ny, re_tau, yplus):
+    N = ny - 1
+    j = channel.sensing_node(N, re_tau, 15.0)
+    yp = (1 + math.cos(math.pi * j / N)) * re_tau
+    assert yp >= 15.0 and abs(yp - yplus) < 0.01
+    yp_next = (1 + math.cos(math.pi * (j + 1) / N)) * re_tau
+    assert yp_next < 15.0
