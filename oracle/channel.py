@@ -214,12 +214,27 @@ def nonlinear(st: dict, ops: Operators):
     coefficients of H_x and H_z (real parts), and the three H coefficient
     fields.
     """
-    p = ops.p
     f = velocity_vorticity(st, ops)
-    names = ("u", "v", "w", "ox", "oy", "oz")
     # coefficients -> node values (last axis), then [node][nz][nxh]
-    nodes = {k: from_pencils(f[k] @ ops.S.T) for k in names}
-    phys = {k: sp.to_physical(nodes[k], p.nx, p.nz, ops.mx, ops.mz) for k in names}
+    nodes = {k: from_pencils(f[k] @ ops.S.T) for k in NODE_FIELDS}
+    Hn = nonlinear_nodes(nodes, ops)
+    H = {c: to_pencils(Hn[c]) @ ops.A.T for c in "xyz"}   # Chebyshev coefficients
+    hv, hg, Hx00, Hz00 = assemble(H, ops)
+    return hv, hg, Hx00, Hz00, H
+
+
+NODE_FIELDS = ("u", "v", "w", "ox", "oy", "oz")
+
+
+def nonlinear_nodes(nodes: dict, ops: Operators) -> dict:
+    """3/2-dealiased ``H = u x omega`` plane by plane.
+
+    ``nodes[name]``: ``[ny][nz][nx/2]`` Fourier coefficients at each node of
+    u, v, w, omega_x, omega_y, omega_z.  Returns the kept Fourier
+    coefficients of H_x, H_y, H_z at each node (same layout).
+    """
+    p = ops.p
+    phys = {k: sp.to_physical(nodes[k], p.nx, p.nz, ops.mx, ops.mz) for k in NODE_FIELDS}
     u, v, w = phys["u"], phys["v"], phys["w"]
     ox, oy, oz = phys["ox"], phys["oy"], phys["oz"]
     Hphys = {
@@ -227,12 +242,7 @@ def nonlinear(st: dict, ops: Operators):
         "y": w * ox - u * oz,
         "z": u * oy - v * ox,
     }
-    H = {}
-    for c in "xyz":
-        Hn = sp.to_spectral(Hphys[c], p.nx, p.nz, ops.mx, ops.mz)   # [node][nz][nxh]
-        H[c] = to_pencils(Hn) @ ops.A.T                            # coefficients
-    hv, hg, Hx00, Hz00 = assemble(H, ops)
-    return hv, hg, Hx00, Hz00, H
+    return {c: sp.to_spectral(Hphys[c], p.nx, p.nz, ops.mx, ops.mz) for c in "xyz"}
 
 
 def assemble(H: dict, ops: Operators):

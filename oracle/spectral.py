@@ -30,10 +30,15 @@ def cheb_nodes(N: int) -> np.ndarray:
     return np.cos(np.pi * np.arange(N + 1) / N)
 
 
+def _cos_pi_over(N: int) -> np.ndarray:
+    """C[j, n] = cos(pi j n / N), the integer argument j n reduced mod 2N first."""
+    j = np.arange(N + 1)
+    return np.cos(np.pi * (np.outer(j, j) % (2 * N)) / N)
+
+
 def cheb_synthesis(N: int) -> np.ndarray:
     """S[j, n] = T_n(y_j) = cos(pi n j / N): coefficients -> node values."""
-    j = np.arange(N + 1)
-    return np.cos(np.pi * np.outer(j, j) / N)
+    return _cos_pi_over(N)
 
 
 def cheb_analysis(N: int) -> np.ndarray:
@@ -45,9 +50,7 @@ def cheb_analysis(N: int) -> np.ndarray:
     """
     cbar = np.ones(N + 1)
     cbar[0] = cbar[N] = 2.0
-    j = np.arange(N + 1)
-    C = np.cos(np.pi * np.outer(j, j) / N)
-    return 2.0 / N * C / np.outer(cbar, cbar)
+    return 2.0 / N * _cos_pi_over(N) / np.outer(cbar, cbar)
 
 
 def cheb_diff(N: int) -> np.ndarray:
@@ -105,10 +108,10 @@ def _dft_mats(nx: int, nz: int, mx: int, mz: int):
     """Ex[a, i] = exp(2 pi i i a / mx), Ez[b, row] = exp(2 pi i m(row) b / mz)."""
     a = np.arange(mx)
     i = np.arange(nx // 2)
-    Ex = np.exp(2j * np.pi * np.outer(a, i) / mx)
+    Ex = np.exp(2j * np.pi * (np.outer(a, i) % mx) / mx)
     b = np.arange(mz)
     m = kz_index(nz)
-    Ez = np.exp(2j * np.pi * np.outer(b, m) / mz)
+    Ez = np.exp(2j * np.pi * (np.outer(b, m) % mz) / mz)
     return Ex, Ez
 
 
