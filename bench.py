@@ -1,0 +1,317 @@
+#!/usr/bin/env python3
+"""Environment-step throughput of the GPU channel-flow DNS.
+
+Workload (one GPU): the larger Re_tau = 180 channel of the paper (Sec. 3.1:
+2 pi h x 2h x pi h, 64 x 65 x 64 modes), all FP64, opposition control at the
+sensing node above y+ = 15 (Sec. 4.1), one RK3 step per environment step
+(dt = 0.005), observation = u, v planes at that node, reward from the wall
+shear.  The initial state is a seeded broadband divergence-free perturbation
+of laminar Poiseuille flow (the paper's developed-turbulence initial fields
+are not available); the per-step work of the method does not depend on the
+values.
+
+value: environment steps per second over all ranks, device-resident inputs,
+       CUDA events per step on the library's stream, L2 flushed (256 MiB
+       write) between steps outside the timed events.
+e2e:   same metric through env_step with host buffers (opposition control has
+       no per-step input; the observation planes and the two scalars are
+       copied back every step).
+--impl reference: the FP64 CPU oracle on the host cores, a bounded sample.
+
+Several GPUs: one process per GPU (torchrun), independent replicas, no
+collective on the data path.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(nx=64, ny=65, nz=64, lx=2 * math.pi, lz=math.pi, re_tau=180.0, re_bulk=2800.0,
+                dt=0.005, control=1, alpha=1.0, steps_per_action=1, y_sense_plus=15.0)
+WORKLOAD_NAME = "larger channel Re_tau=180, 64x65x64, all FP64, opposition control, 1 RK3 step per env step"
+METRIC = "env_steps_per_s"
+UNIT = "env-steps/s"
+KERNEL_CLASSES = ("recover", "cheb_synthesis", "nonlinear_plane", "cheb_analysis", "tau_solve", "per_step")
+L2_FLUSH_BYTES = 256 << 20
+
+
+def plane_kernel_flops(nx: int, ny: int, nz: int) -> float:
+    """Algorithmic FLOPs of one launch of the nonlinear plane kernel.
+
+    Per Gauss-Lobatto plane: 6 inverse and 3 forward complex FFTs along z of
+    length mz on nx/2 columns, 6 inverse and 3 forward real FFTs along x of
+    length mx on mz rows (5 n log2 n per complex, 2.5 n log2 n per real
+    transform), and the cross product (9 FLOPs per padded point)."""
+    mx, mz, nxh = 3 * nx // 2, 3 * nz // 2, nx // 2
+    z = 9 * nxh * 5.0 * mz * math.log2(mz)
+    x = 9 * mz * 2.5 * mx * math.log2(mx)
+    return ny * (z + x + 9.0 * mx * mz)
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# FP64 FMA rate: 152 SMs x 2 FP64 FMA/clk/SM x 2 FLOP x 2.07 GHz (probe-measured, see the design notes)
+FP64_PEAK_TFLOPS = 1.2586
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.out, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def oracle_sample(budget_s: float, max_steps: int):
+    """Time the FP64 oracle on the workload: whole environment steps until the budget is spent."""
+    import numpy as np  # noqa: F401
+
+    import seeded_inputs as si
+    from oracle import channel
+    keys = ("nx", "ny", "nz", "lx", "lz", "re_tau", "re_bulk", "dt", "steps_per_action",
+            "y_sense_plus", "control", "alpha")
+    op = channel.Params(**{k: WORKLOAD[k] for k in keys})
+    ops = channel.Operators(op)
+    st = channel.new_state(si.perturbed_poiseuille(op.nx, op.ny, op.nz, 0, 0.1, 99), op)
+    times = []
+    t_all = time.perf_counter()
+    while len(times) < max_steps and (time.perf_counter() - t_all) < budget_s:
+        t0 = time.perf_counter()
+        channel.env_step(st, ops)
+        times.append(time.perf_counter() - t0)
+    return times
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    budget = float(os.environ.get("CH_REFERENCE_BUDGET_S", "90"))
+    for _ in range(min(args.warmup, 1)):
+        oracle_sample(1e9, 1)
+    times = oracle_sample(budget, args.steps)
+    total = sum(times)
+    value = len(times) / total
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": len(times), "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD_NAME, "parallelism": "replicas"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{len(times)} whole environment steps of the workload (budget {budget:.0f} s)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import numpy as np
+    import torch
+
+    from paper_2301_09889_gb300 import native
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    native.load()
+    W = max(3, args.warmup)
+    K = args.steps
+    p = native.params(**WORKLOAD)
+    env = native.env_create(p)
+    info = native.env_info(env)
+    native.env_reset(env, seed=rank, amplitude=0.1, kmax=99)
+    stream = torch.cuda.current_stream()
+    native.env_set_stream(env, stream.cuda_stream)
+    nx, ny, nz = WORKLOAD["nx"], WORKLOAD["ny"], WORKLOAD["nz"]
+    out_len = 2 * nz * nx + 2
+    d_out = torch.zeros(out_len, dtype=torch.float64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    for _ in range(W):
+        native.env_step_device(env, None, d_out.data_ptr())
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    native.env_profile(env, True)
+    for i in range(K):
+        flush.zero_()
+        starts[i].record(stream)
+        native.env_step_device(env, None, d_out.data_ptr())
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    kern = {}
+    for c, name in enumerate(KERNEL_CLASSES):
+        ms, n = native.env_profile_read(env, c)
+        kern[name] = {"ms_total": ms, "launches": n}
+    native.env_profile(env, False)
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = K * world / (total_ms * 1e-3)
+    finite = bool(torch.isfinite(d_out).all().item())
+
+    # ---- end to end through the host-buffer API
+    Ke = min(K, 300)
+    obs = np.zeros((2, nz, nx))
+    tau = np.zeros(1)
+    rew = np.zeros(1)
+    for _ in range(3):
+        native.env_step(env, None, obs, tau, rew)
+    e2e_ms = []
+    for _ in range(Ke):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        native.env_step(env, None, obs, tau, rew)
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e_total = sum(e2e_ms)
+    if dist:
+        t = torch.tensor([e2e_total], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = Ke * world / (e2e_total * 1e-3)
+    native.env_destroy(env)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel
+    dom = max(kern, key=lambda k: kern[k]["ms_total"])
+    plane = kern["nonlinear_plane"]
+    avg_plane_s = plane["ms_total"] * 1e-3 / max(plane["launches"], 1)
+    flops = plane_kernel_flops(nx, ny, nz)
+    achieved = flops / avg_plane_s / 1e12
+    roofline = {
+        "kernel": "nonlinear_plane", "dominant_kernel": dom, "bound": "alu", "unit": "TFLOP/s",
+        "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "frac": achieved / FP64_PEAK_TFLOPS,
+        "peak_source": "FP64 FMA rate measured on GB300 by an FMA-chain probe (MEASURED_PEAKS.json has no FP64 figure)",
+        "flops_per_launch": flops, "avg_launch_ms": avg_plane_s * 1e3, "traffic": None,
+    }
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        times = oracle_sample(float(os.environ.get("CH_CPU_BASELINE_S", "20")), 1000)
+        cpu = {"value": len(times) / sum(times), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{len(times)} whole environment steps of the workload (about 20 s of CPU work)"}
+
+    srt = sorted(step_ms)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "grid": [nx, ny, nz], "re_tau": 180.0, "re_bulk": 2800.0,
+                   "dt": 0.005, "control": "opposition alpha=1, sensing node j=%d (y+=%.2f)" % (
+                       info.j_sense, info.y_plus_sense),
+                   "l2": "flushed between steps (256 MiB write outside the timed events)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "mpts_rk3_steps_per_s": value * nx * ny * nz / 1e6,
+        "p50_ms": srt[len(srt) // 2], "p99_ms": srt[min(len(srt) - 1, int(0.99 * len(srt)))],
+        "kernels_ms_per_step": {k: v["ms_total"] / K for k, v in kern.items()},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 8 * out_len},
+        "gpu_launches": int(sum(v["launches"] for v in kern.values())),
+        "clocks": clk,
+        "finite": finite,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,187 @@
+/*
+ * channel_dns.h -- C ABI of the GPU channel-flow environment.
+ *
+ * The library advances an incompressible plane-channel flow, simulated by a
+ * pseudo-spectral DNS (Fourier modes in x and z, Chebyshev polynomials in y;
+ * paper Sec. 3.1), under wall blowing/suction control (paper Sec. 3.2).  One
+ * environment step mirrors the paper's request cycle (Sec. 3.3): set the
+ * control (CNTRL), evolve the solver several time steps (EVOLVE), return the
+ * observation planes and the wall-shear reward (STATE); env_destroy ends it
+ * (TERMN).
+ *
+ * Numerical method (the readings of the paper that the library fixes):
+ *   - closed channel y in [-1, 1], no slip at both walls; the action is the
+ *     wall-normal velocity of the lower wall y = -1;
+ *   - velocity-vorticity (v, omega_y) form, 3/2-dealiased u x omega;
+ *   - third-order low-storage Runge-Kutta for the nonlinear term and
+ *     Crank-Nicolson for the viscous term (Sec. 3.1), coefficients
+ *     gamma = (8/15, 5/12, 3/4), zeta = (0, -17/60, -5/12),
+ *     alpha = beta = (gamma + zeta) / 2;
+ *   - Chebyshev-tau Helmholtz solves per Fourier mode with an influence-matrix
+ *     correction for the four v wall conditions;
+ *   - constant flow rate: the mean pressure gradient is set every stage so
+ *     that the bulk velocity stays 1.
+ * Units: half height 1, bulk velocity 1, nu = 1 / re_bulk,
+ * u_tau = re_tau / re_bulk.
+ *
+ * Conventions
+ *   - All functions return 0 (CH_OK) on success or a negative CH_ERR_* code;
+ *     ch_strerror() names it.  A failing call leaves no partial result the
+ *     caller must free.
+ *   - The library owns every device allocation it makes; the caller owns all
+ *     host buffers (they must stay valid until the call returns) and every
+ *     device buffer it passes in.
+ *   - One thread at a time per environment handle.
+ *   - Layouts are row-major C arrays.  Spectral arrays hold the kept
+ *     half-spectrum: kx index 0..nx/2-1 (fastest), kz rows in FFT order
+ *     0..nz/2-1, -nz/2..-1 where the -nz/2 (Nyquist) row is always zero.
+ *   - A batch of B environments with identical parameters shares every
+ *     launch; batched arrays carry a leading [B] dimension.
+ */
+#ifndef CHANNEL_DNS_H
+#define CHANNEL_DNS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------- */
+#define CH_OK              0
+#define CH_ERR_ARG        -1   /* invalid argument, size or parameter        */
+#define CH_ERR_OOM        -2   /* device or host allocation failed           */
+#define CH_ERR_BUDGET     -3   /* would exceed a memory budget               */
+#define CH_ERR_DIVERGED   -4   /* non-finite wall shear: the flow blew up     */
+#define CH_ERR_TIMEOUT    -5   /* a bounded wait ran out                     */
+#define CH_ERR_STATE      -6   /* call not valid in the handle's state       */
+#define CH_ERR_CUDA       -7   /* a CUDA runtime call failed                 */
+#define CH_ERR_UNSUPPORTED -8  /* parameter combination not built            */
+
+/* ---- parameters ---------------------------------------------------------- */
+typedef struct ch_params {
+    int nx, ny, nz;          /* Fourier modes in x, Chebyshev nodes in y, Fourier modes in z
+                                (nx, nz even >= 4; ny odd or even >= 9, <= 257)        */
+    double lx, lz;           /* box length and width in half heights                  */
+    double re_tau;           /* friction Reynolds number (sets u_tau and the sensing plane) */
+    double re_bulk;          /* bulk Reynolds number U_b h / nu (> 0)                  */
+    double dt;               /* time step in h / U_b                                   */
+    int steps_per_action;    /* solver steps per env_step (actuation interval, Sec. 3.2) */
+    double y_sense_plus;     /* sensing height in wall units; rounded up to a node (Sec. 3.2) */
+    int top_bc;              /* 0: no-slip upper wall (only value built)               */
+    int precision;           /* 0: all FP64 (only value built)                         */
+    int control;             /* 0: external action, 1: opposition control (Sec. 4.1)  */
+    double alpha;            /* opposition-control gain                                */
+    double tau_ref;          /* reward reference wall shear; <= 0 -> u_tau^2          */
+    int batch;               /* number of environments B sharing launches; <= 0 -> 1   */
+} ch_params_t;
+
+typedef struct ch_info {
+    int j_sense;             /* Gauss-Lobatto node index of the sensing plane (0 = upper wall) */
+    double y_plus_sense;     /* its height above the lower wall in wall units              */
+    double nu, u_tau, tau_ref;
+    size_t state_bytes;      /* bytes of one environment's serialised state                */
+    size_t device_bytes;     /* device memory held by the handle                           */
+    int plane_cluster;       /* CTAs cooperating on one y-plane of the nonlinear term       */
+    int launches_per_step;   /* kernels launched by one env_step                            */
+} ch_info_t;
+
+typedef struct ch_env ch_env_t;
+
+/* Fill *p with the minimal-channel defaults of the paper's first domain
+ * (16 x 65 x 16, 2.67 x 2 x 0.8, Re_tau 180, Re_b 2800, dt 0.005). */
+int ch_default_params(ch_params_t* p);
+
+/* Create B = p->batch environments on the current CUDA device.  Allocates all
+ * device state and precomputes the per-mode tau factorisations.  The flow is
+ * laminar Poiseuille with zero wall action until env_reset/env_set_state.
+ * Errors: CH_ERR_ARG (bad sizes/parameters), CH_ERR_UNSUPPORTED,
+ * CH_ERR_OOM, CH_ERR_CUDA. */
+int env_create(const ch_params_t* p, ch_env_t** out);
+
+/* Launch all further work of this handle on `stream` (a cudaStream_t; NULL
+ * selects the library's own stream). */
+int env_set_stream(ch_env_t* env, void* stream);
+
+/* Laminar Poiseuille flow plus a seeded divergence-free perturbation in every
+ * environment (environment e uses seed + e): SplitMix64 normals, v = s (a+ib)
+ * (1-y^2)^2 and omega_y = s (c+id) (1-y^2) on modes with kx and |kz| index
+ * <= kmax, s = amplitude / sqrt(#modes).  Time and wall action are zeroed. */
+int env_reset(ch_env_t* env, uint64_t seed, double amplitude, int kmax);
+
+/* One interaction for every environment of the batch, host buffers:
+ *   action     [B][nz][nx] wall-normal velocity at the lower wall (ignored and
+ *              may be NULL under opposition control); clipped to
+ *              [-u_tau, u_tau], plane mean removed, ramped linearly from the
+ *              previous action over the steps_per_action steps (Sec. 3.2);
+ *   obs        [B][2][nz][nx] u and v on the sensing plane after the steps;
+ *   wall_shear [B] nu dU/dy at the lower wall averaged over the steps;
+ *   reward     [B] 1 - wall_shear / tau_ref (Sec. 3.2).
+ * Synchronises the stream.  Returns CH_ERR_DIVERGED if any wall shear is not
+ * finite (outputs are still written). */
+int env_step(ch_env_t* env, const double* action, double* obs,
+             double* wall_shear, double* reward);
+
+/* Same as env_step with DEVICE buffers, asynchronous on the handle's stream:
+ *   d_action [B][nz][nx] (may be NULL under opposition control);
+ *   d_out    [B][2 nz nx + 2]: per environment the two observation planes,
+ *            then the mean wall shear and the reward.
+ * No host synchronisation, no divergence check. */
+int env_step_device(ch_env_t* env, const double* d_action, double* d_out);
+
+/* Serialised state of environment `e` (host buffer of info.state_bytes):
+ *   double v[ny][nz][nx/2][2]   Chebyshev coefficients of v per mode (re, im)
+ *   double g[ny][nz][nx/2][2]   same for omega_y
+ *   double U[ny], W[ny]         mean-flow Chebyshev coefficients
+ *   double vw[nz][nx/2][2]      spectrum of the last applied wall action
+ *   double t, steps             simulated time and completed solver steps */
+int env_get_state(ch_env_t* env, int e, void* buf, size_t nbytes);
+int env_set_state(ch_env_t* env, int e, const void* buf, size_t nbytes);
+
+/* Kernel timing for measurement tools.  While enabled, every launch of the
+ * handle is bracketed by a pair of CUDA events on the handle's stream and
+ * attributed to a class: 0 recover (u, w, vorticity from v, omega_y),
+ * 1 Chebyshev synthesis, 2 nonlinear plane kernel, 3 Chebyshev analysis,
+ * 4 tau solves, 5 per-step kernels (action, wall shear, observation).
+ * env_profile(env, 1) clears the totals and starts recording, (env, 0) stops.
+ * env_profile_read synchronises the stream and returns the summed device
+ * time (ms) and the launch count of one class since the last enable. */
+int env_profile(ch_env_t* env, int enable);
+int env_profile_read(ch_env_t* env, int cls, double* total_ms, int* launches);
+
+int env_info(const ch_env_t* env, ch_info_t* info);
+int env_destroy(ch_env_t* env);
+const char* ch_strerror(int code);
+
+/* Host only (no GPU): write the env_reset initial state of one environment
+ * into `buf` (same layout as env_get_state). */
+int ch_seed_state(const ch_params_t* p, uint64_t seed, double amplitude, int kmax,
+                  void* buf, size_t nbytes);
+
+/* Host only: bytes of one serialised state for these parameters. */
+size_t ch_state_bytes(const ch_params_t* p);
+
+/* ---- single stages, exposed for unit checks ---------------------------- */
+
+/* Dealiased nonlinear term of every environment of `env` on every
+ * Gauss-Lobatto plane (3/2 rule), asynchronous on the handle's stream:
+ *   d_q [B][6][ny][nz][nx/2] complex (re, im doubles): Fourier coefficients,
+ *       at each node, of u, v, w, omega_x, omega_y, omega_z;
+ *   d_h [B][3][ny][nz][nx/2] complex: Fourier coefficients of the kept modes
+ *       of H = u x omega evaluated on the 3nx/2 x 3nz/2 grid.
+ * Uses the handle's twiddle tables; allocates nothing. */
+int ch_nonlinear(ch_env_t* env, const double* d_q, double* d_h);
+
+/* Chebyshev-tau Dirichlet problems (D^2 - lam_m) f = r (coefficient rows
+ * 0..ny-3), f(+1) = top_m, f(-1) = bot_m for M independent problems:
+ *   d_lam [M] (>= 0), d_r [M][ny] complex, d_top/d_bot [M] complex,
+ *   d_f [M][ny] complex output.  Device pointers, asynchronous on `stream`. */
+int ch_tau_helmholtz(int ny, int M, const double* d_lam, const double* d_r,
+                     const double* d_top, const double* d_bot, double* d_f,
+                     void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CHANNEL_DNS_H */

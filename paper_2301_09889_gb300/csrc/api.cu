@@ -1,0 +1,744 @@
+// Host side of the C ABI declared in include/channel_dns.h: parameter checks,
+// per-grid tables (tau factorisations, influence-matrix solutions, twiddles),
+// the environment step driver and state serialisation.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/channel_dns.h"
+#include "common.cuh"
+#include "internal.h"
+
+using namespace chdns;
+
+namespace {
+
+// Low-storage RK3 (third-order Runge-Kutta for the nonlinear term,
+// Crank-Nicolson for the viscous term; paper Sec. 3.1).
+const double kGamma[3] = {8.0 / 15.0, 5.0 / 12.0, 3.0 / 4.0};
+const double kZeta[3] = {0.0, -17.0 / 60.0, -5.0 / 12.0};
+const double kCEnd[3] = {8.0 / 15.0, 2.0 / 3.0, 1.0};
+inline double rk_alpha(int k) { return 0.5 * (kGamma[k] + kZeta[k]); }
+inline double rk_beta(int k) { return 0.5 * (kGamma[k] + kZeta[k]); }
+
+// ---- host tau factorisation (same recurrences as the device solver) ------
+inline double cA(int n) { return (n == 2 ? 2.0 : 1.0) / (4.0 * n * (n - 1)); }
+inline double cB(int n, int N) { return n <= N - 2 ? 1.0 / (2.0 * ((double)n * n - 1.0)) : 0.0; }
+inline double cC(int n, int N) { return n + 2 <= N - 2 ? 1.0 / (4.0 * n * (n + 1)) : 0.0; }
+
+struct Factor {
+  std::vector<double> e, h, b, Q;
+  double isq = 0.0;
+};
+
+Factor host_factor(int N, int sig, double lam) {
+  const int M = (N - sig) / 2 + 1;
+  Factor F;
+  F.e.assign(M, 0.0);
+  F.h.assign(M, 0.0);
+  F.b.assign(M, 0.0);
+  F.Q.assign(M, 0.0);
+  double bnext = 0.0;
+  for (int i = M - 1; i >= 1; --i) {
+    const int n = 2 * i + sig;
+    const double L = -lam * cA(n);
+    const double Dg = 1.0 + lam * cB(n, N);
+    const double U = (i + 1 < M) ? -lam * cC(n, N) : 0.0;
+    const double den = Dg + U * bnext;
+    F.e[i] = 1.0 / den;
+    F.h[i] = U / den;
+    F.b[i] = -L / den;
+    bnext = F.b[i];
+  }
+  F.Q[0] = 1.0;
+  double sq = 1.0;
+  for (int i = 1; i < M; ++i) {
+    F.Q[i] = F.b[i] * F.Q[i - 1];
+    sq += F.Q[i];
+  }
+  F.isq = 1.0 / sq;
+  return F;
+}
+
+// real right-hand side r[i] = r_{2i+sig}; returns f[i]
+std::vector<double> host_solve(int N, int sig, const std::vector<double>& r, const Factor& F, double s) {
+  const int M = (N - sig) / 2 + 1;
+  std::vector<double> f(M, 0.0);
+  double anext = 0.0;
+  for (int i = M - 1; i >= 1; --i) {
+    const int n = 2 * i + sig;
+    double R = cA(n) * r[i - 1] - cB(n, N) * r[i];
+    if (i + 1 < M) R += cC(n, N) * r[i + 1];
+    const double a = F.e[i] * R - F.h[i] * anext;
+    f[i] = a;
+    anext = a;
+  }
+  double Pp = 0.0, sum = 0.0;
+  for (int i = 1; i < M; ++i) {
+    Pp = f[i] + F.b[i] * Pp;
+    f[i] = Pp;
+    sum += Pp;
+  }
+  const double f0 = F.isq * (s - sum);
+  f[0] = f0;
+  for (int i = 1; i < M; ++i) f[i] += F.Q[i] * f0;
+  return f;
+}
+
+bool fft_plan(int n, FftPlan* pl) {
+  pl->n = n;
+  pl->nst = 0;
+  int m = n;
+  while (m % 4 == 0 && pl->nst < kMaxRadixStages) { pl->radix[pl->nst++] = 4; m /= 4; }
+  while (m % 2 == 0 && pl->nst < kMaxRadixStages) { pl->radix[pl->nst++] = 2; m /= 2; }
+  while (m % 3 == 0 && pl->nst < kMaxRadixStages) { pl->radix[pl->nst++] = 3; m /= 3; }
+  return m == 1;
+}
+
+std::vector<double2> twiddles(int n) {
+  std::vector<double2> t(n);
+  for (int k = 0; k < n; ++k) {
+    const double a = 2.0 * M_PI * (double)k / (double)n;
+    t[k] = make_double2(std::cos(a), std::sin(a));
+  }
+  return t;
+}
+
+int sensing_node(int N, double re_tau, double y_plus) {
+  for (int j = N; j >= 0; --j) {
+    const double yj = std::cos(M_PI * j / N);
+    if ((1.0 + yj) * re_tau >= y_plus) return j;
+  }
+  return 0;
+}
+
+struct SplitMix64 {
+  uint64_t s;
+  uint64_t next() {
+    s += 0x9E3779B97F4A7C15ULL;
+    uint64_t z = s;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+  }
+  double uniform() { return (double)(next() >> 11) * (1.0 / 9007199254740992.0); }
+  void normal_pair(double* a, double* b) {
+    const double u1 = 1.0 - uniform();
+    const double u2 = uniform();
+    const double r = std::sqrt(-2.0 * std::log(u1));
+    const double t = 2.0 * M_PI * u2;
+    *a = r * std::cos(t);
+    *b = r * std::sin(t);
+  }
+};
+
+int check_params(const ch_params_t* p) {
+  if (!p) return CH_ERR_ARG;
+  if (p->nx < 4 || p->nz < 4 || (p->nx & 1) || (p->nz & 1)) return CH_ERR_ARG;
+  if (p->ny < 9 || p->ny > kMaxNy) return CH_ERR_ARG;
+  if (!(p->lx > 0) || !(p->lz > 0) || !(p->re_bulk > 0) || !(p->re_tau > 0) || !(p->dt > 0)) return CH_ERR_ARG;
+  if (p->steps_per_action < 1) return CH_ERR_ARG;
+  if (p->control != 0 && p->control != 1) return CH_ERR_ARG;
+  if (p->top_bc != 0 || p->precision != 0) return CH_ERR_UNSUPPORTED;
+  FftPlan a, b;
+  if (!fft_plan(3 * p->nx / 2, &a) || !fft_plan(3 * p->nz / 2, &b)) return CH_ERR_UNSUPPORTED;
+  if ((3 * p->nx / 2) % 2 || (3 * p->nz / 2) % 2) return CH_ERR_UNSUPPORTED;
+  return CH_OK;
+}
+
+}  // namespace
+
+struct ch_env {
+  ch_params_t prm;
+  Grid g;
+  int B = 1;
+  cudaStream_t stream = nullptr;
+  cudaStream_t own_stream = nullptr;
+  PencilBufs pb{};
+  DevTables tab{};
+  PlaneArgs<double> plane{};
+  size_t plane_smem = 0;
+  double* d_act = nullptr;
+  double* d_out = nullptr;
+  double* h_out = nullptr;
+  size_t out_stride = 0;
+  std::vector<void*> allocs;
+  size_t device_bytes = 0;
+  double t = 0.0, steps = 0.0;
+  int js = 0;
+  double nu = 0, u_tau = 0, tau_ref = 0;
+  int launches_per_step = 0;
+  // kernel timing (env_profile)
+  bool prof = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[6];
+  int ev_used[6] = {0, 0, 0, 0, 0, 0};
+  char err[256] = {0};
+};
+
+namespace {
+
+template <typename T>
+int dalloc(ch_env* env, T** ptr, size_t count) {
+  void* p = nullptr;
+  const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  if (cudaMalloc(&p, bytes) != cudaSuccess) return CH_ERR_OOM;
+  env->allocs.push_back(p);
+  env->device_bytes += bytes;
+  *ptr = static_cast<T*>(p);
+  return CH_OK;
+}
+
+template <typename T>
+int dupload(ch_env* env, const T** ptr, const std::vector<T>& host) {
+  T* d = nullptr;
+  int rc = dalloc(env, &d, host.size());
+  if (rc) return rc;
+  if (cudaMemcpy(d, host.data(), host.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) return CH_ERR_CUDA;
+  *ptr = d;
+  return CH_OK;
+}
+
+void free_env(ch_env* env) {
+  if (!env) return;
+  if (env->stream) cudaStreamSynchronize(env->stream);
+  for (auto& v : env->ev)
+    for (auto& pr : v) {
+      cudaEventDestroy(pr.first);
+      cudaEventDestroy(pr.second);
+    }
+  for (void* p : env->allocs) cudaFree(p);
+  if (env->h_out) cudaFreeHost(env->h_out);
+  if (env->own_stream) cudaStreamDestroy(env->own_stream);
+  delete env;
+}
+
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return CH_ERR_CUDA;     \
+  } while (0)
+
+#define RC(call)                 \
+  do {                           \
+    int r_ = (call);             \
+    if (r_ != CH_OK) return r_;  \
+  } while (0)
+
+int build_tables(ch_env* env) {
+  const Grid& g = env->g;
+  const int N = g.N, P = g.P, ny = g.ny;
+  const int Mh = N / 2 + 1;
+  const ch_params_t& p = env->prm;
+  std::vector<double> kx(g.nxh), kz(g.nz);
+  for (int i = 0; i < g.nxh; ++i) kx[i] = 2.0 * M_PI / p.lx * i;
+  for (int r = 0; r < g.nz; ++r) {
+    const int m = r < g.nz / 2 ? r : r - g.nz;
+    kz[r] = (r == g.nz / 2) ? 0.0 : 2.0 * M_PI / p.lz * m;
+  }
+  std::vector<double> cheb((size_t)ny * ny);
+  for (int j = 0; j < ny; ++j)
+    for (int n = 0; n < ny; ++n) cheb[(size_t)j * ny + n] = std::cos(M_PI * (double)((j * n) % (2 * N)) / N);
+
+  std::vector<double> helm((size_t)3 * 2 * 4 * Mh * P, 0.0), helm_isq((size_t)3 * 2 * P, 0.0);
+  std::vector<double> pois((size_t)2 * 4 * Mh * P, 0.0), pois_isq((size_t)2 * P, 0.0);
+  std::vector<double> vh((size_t)3 * ny * P, 0.0), vh_idv((size_t)3 * 2 * P, 0.0);
+  std::vector<double> u1((size_t)3 * ny, 0.0), u1_iflux(3, 0.0);
+  auto put = [&](std::vector<double>& tab, size_t base, const Factor& F, int M, int p) {
+    for (int i = 0; i < M; ++i) {
+      tab[base + ((size_t)0 * Mh + i) * P + p] = F.e[i];
+      tab[base + ((size_t)1 * Mh + i) * P + p] = F.h[i];
+      tab[base + ((size_t)2 * Mh + i) * P + p] = F.b[i];
+      tab[base + ((size_t)3 * Mh + i) * P + p] = F.Q[i];
+    }
+  };
+  for (int pp = 0; pp < P; ++pp) {
+    const int row = pp / g.nxh, ix = pp % g.nxh;
+    const double k2 = kx[ix] * kx[ix] + kz[row] * kz[row];
+    for (int sig = 0; sig < 2; ++sig) {
+      const int M = (N - sig) / 2 + 1;
+      const Factor Fp = host_factor(N, sig, k2);
+      put(pois, (size_t)(sig * 4) * Mh * P, Fp, M, pp);
+      pois_isq[(size_t)sig * P + pp] = Fp.isq;
+      for (int k = 0; k < 3; ++k) {
+        const double ibdn = 1.0 / (rk_beta(k) * p.dt * env->nu);
+        const Factor Fh = host_factor(N, sig, k2 + ibdn);
+        put(helm, (size_t)((k * 2 + sig) * 4) * Mh * P, Fh, M, pp);
+        helm_isq[(size_t)(k * 2 + sig) * P + pp] = Fh.isq;
+        // homogeneous solution of this parity: phi_h = 1 on the wall row, r = 0
+        const std::vector<double> zero(M, 0.0);
+        const std::vector<double> phih = host_solve(N, sig, zero, Fh, 1.0);
+        const std::vector<double> vhp = host_solve(N, sig, phih, Fp, 0.0);
+        double d = 0.0;
+        for (int i = 0; i < M; ++i) {
+          const int n = 2 * i + sig;
+          vh[((size_t)k * ny + n) * P + pp] = vhp[i];
+          d += (double)n * n * vhp[i];
+        }
+        vh_idv[(size_t)(k * 2 + sig) * P + pp] = (d != 0.0 && std::isfinite(d)) ? 1.0 / d : 0.0;
+      }
+    }
+  }
+  for (int k = 0; k < 3; ++k) {
+    const double a = rk_alpha(k), b = rk_beta(k);
+    const double ibdn = 1.0 / (b * p.dt * env->nu);
+    const Factor F = host_factor(N, 0, ibdn);
+    const int M = N / 2 + 1;
+    std::vector<double> r(M, 0.0);
+    r[0] = 1.0;
+    const std::vector<double> uu = host_solve(N, 0, r, F, 0.0);
+    const double cforce = (a + b) / (b * env->nu);
+    double flux = 0.0;
+    for (int i = 0; i < M; ++i) {
+      const int n = 2 * i;
+      const double v = -cforce * uu[i];
+      u1[(size_t)k * ny + n] = v;
+      flux += 2.0 / (1.0 - (double)n * n) * v;
+    }
+    u1_iflux[k] = 1.0 / flux;
+  }
+  RC(dupload(env, &env->tab.kx, kx));
+  RC(dupload(env, &env->tab.kz, kz));
+  RC(dupload(env, &env->tab.cheb, cheb));
+  RC(dupload(env, &env->tab.tau.helm, helm));
+  RC(dupload(env, &env->tab.tau.helm_isq, helm_isq));
+  RC(dupload(env, &env->tab.tau.pois, pois));
+  RC(dupload(env, &env->tab.tau.pois_isq, pois_isq));
+  RC(dupload(env, &env->tab.tau.vh, vh));
+  RC(dupload(env, &env->tab.tau.vh_idv, vh_idv));
+  RC(dupload(env, &env->tab.tau.u1, u1));
+  RC(dupload(env, &env->tab.tau.u1_iflux, u1_iflux));
+  env->tab.tau.Mh = Mh;
+  RC(dupload(env, &env->tab.tw_nx, twiddles(g.nx)));
+  RC(dupload(env, &env->tab.tw_nz, twiddles(g.nz)));
+
+  // nonlinear plane kernel: smallest cluster whose z-slab fits shared memory
+  PlaneArgs<double>& a = env->plane;
+  a.nxh = g.nxh; a.nz = g.nz; a.ny = g.ny; a.mx = g.mx; a.mz = g.mz; a.P = g.P;
+  a.S = 0;
+  const size_t csz = sizeof(double2);
+  for (int S = 1; S <= 8; S *= 2) {
+    if (g.mz % S || (g.mz / S) % 2) continue;
+    const int Lz = g.mz / S;
+    const size_t zb = (size_t)6 * Lz * g.nxh * csz;
+    if (zb > 160 * 1024) continue;
+    const int npairs = Lz / 2;
+    int np = 0;
+    for (int d = std::min(npairs, 16); d >= 1; --d)
+      if (npairs % d == 0 && zb + (size_t)6 * d * g.mx * csz <= 220 * 1024) { np = d; break; }
+    if (!np) continue;
+    a.S = S; a.Lz = Lz; a.NP = np;
+    env->plane_smem = zb + (size_t)6 * np * g.mx * csz;
+    break;
+  }
+  if (!a.S) return CH_ERR_UNSUPPORTED;
+  if (!fft_plan(g.mx, &a.px) || !fft_plan(a.Lz, &a.pz)) return CH_ERR_UNSUPPORTED;
+  RC(dupload(env, &a.tw_x, twiddles(g.mx)));
+  RC(dupload(env, &a.tw_z, twiddles(a.Lz)));
+  RC(dupload(env, &a.tw_mz, twiddles(g.mz)));
+  a.scale = 1.0 / ((double)g.mx * g.mz);
+  return CH_OK;
+}
+
+void fill_seed_state(const ch_params_t* p, uint64_t seed, double amplitude, int kmax, double* buf) {
+  const int nx = p->nx, ny = p->ny, nz = p->nz, nxh = nx / 2, P = nz * nxh;
+  double* v = buf;
+  double* g = v + (size_t)2 * ny * P;
+  double* U = g + (size_t)2 * ny * P;
+  double* W = U + ny;
+  double* vw = W + ny;
+  double* tail = vw + 2 * P;
+  std::memset(buf, 0, ch_state_bytes(p));
+  struct Mode { int row, i; };
+  std::vector<Mode> modes;
+  int nexc = 0;
+  for (int row = 0; row < nz; ++row) {
+    const int m = row < nz / 2 ? row : row - nz;
+    if (m == -nz / 2) continue;
+    for (int i = 0; i < nxh; ++i) {
+      if (i > kmax || std::abs(m) > kmax || (i == 0 && m == 0)) continue;
+      if (i == 0 && m < 0) continue;
+      modes.push_back({row, i});
+      nexc += (i == 0) ? 2 : 1;
+    }
+  }
+  const double s = nexc ? amplitude / std::sqrt((double)nexc) : 0.0;
+  const double shape_v[5] = {0.375, 0.0, -0.5, 0.0, 0.125};
+  const double shape_g[3] = {0.5, 0.0, -0.5};
+  SplitMix64 rng{seed};
+  for (const Mode& md : modes) {
+    double a, b, c, d;
+    rng.normal_pair(&a, &b);
+    rng.normal_pair(&c, &d);
+    const double cvr = s * a, cvi = s * b, cgr = s * c, cgi = s * d;
+    const int m = md.row < nz / 2 ? md.row : md.row - nz;
+    const int mrow = (-m + nz) % nz;
+    for (int n = 0; n < 5; n += 2) {
+      const size_t o = ((size_t)n * P + md.row * nxh + md.i) * 2;
+      v[o] = cvr * shape_v[n];
+      v[o + 1] = cvi * shape_v[n];
+      if (md.i == 0) {
+        const size_t o2 = ((size_t)n * P + mrow * nxh) * 2;
+        v[o2] = v[o];
+        v[o2 + 1] = -v[o + 1];
+      }
+    }
+    for (int n = 0; n < 3; n += 2) {
+      const size_t o = ((size_t)n * P + md.row * nxh + md.i) * 2;
+      g[o] = cgr * shape_g[n];
+      g[o + 1] = cgi * shape_g[n];
+      if (md.i == 0) {
+        const size_t o2 = ((size_t)n * P + mrow * nxh) * 2;
+        g[o2] = g[o];
+        g[o2 + 1] = -g[o + 1];
+      }
+    }
+  }
+  U[0] = 0.75;
+  U[2] = -0.75;
+  (void)W;
+  tail[0] = tail[1] = 0.0;
+}
+
+int set_state_dev(ch_env* env, int e, const double* buf) {
+  const Grid& g = env->g;
+  const size_t P = g.P, ny = g.ny;
+  const double* v = buf;
+  const double* gg = v + 2 * ny * P;
+  const double* U = gg + 2 * ny * P;
+  const double* W = U + ny;
+  const double* vw = W + ny;
+  const double* tail = vw + 2 * P;
+  cudaStream_t st = env->stream;
+  CK(cudaMemcpyAsync(env->pb.V + (size_t)e * ny * P, v, ny * P * sizeof(double2), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(env->pb.G + (size_t)e * ny * P, gg, ny * P * sizeof(double2), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(env->pb.UM + (size_t)e * ny, U, ny * sizeof(double), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(env->pb.WM + (size_t)e * ny, W, ny * sizeof(double), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(env->pb.vw_new + (size_t)e * P, vw, P * sizeof(double2), cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(env->pb.HVP + (size_t)e * ny * P, 0, ny * P * sizeof(double2), st));
+  CK(cudaMemsetAsync(env->pb.HGP + (size_t)e * ny * P, 0, ny * P * sizeof(double2), st));
+  CK(cudaMemsetAsync(env->pb.HXP + (size_t)e * ny, 0, ny * sizeof(double), st));
+  CK(cudaMemsetAsync(env->pb.HZP + (size_t)e * ny, 0, ny * sizeof(double), st));
+  CK(cudaStreamSynchronize(st));
+  env->t = tail[0];
+  env->steps = tail[1];
+  return CH_OK;
+}
+
+// event pair around one launch of class `cls` (no-op unless profiling)
+cudaError_t prof_mark(ch_env* env, int cls, bool begin) {
+  if (!env->prof) return cudaSuccess;
+  auto& v = env->ev[cls];
+  int& used = env->ev_used[cls];
+  if (begin) {
+    if (used == (int)v.size()) {
+      std::pair<cudaEvent_t, cudaEvent_t> pr;
+      cudaError_t e = cudaEventCreate(&pr.first);
+      if (e != cudaSuccess) return e;
+      e = cudaEventCreate(&pr.second);
+      if (e != cudaSuccess) return e;
+      v.push_back(pr);
+    }
+    return cudaEventRecord(v[used].first, env->stream);
+  }
+  cudaError_t e = cudaEventRecord(v[used].second, env->stream);
+  ++used;
+  return e;
+}
+
+#define LAUNCH(cls, call)                   \
+  do {                                      \
+    CK(prof_mark(env, (cls), true));        \
+    CK(call);                               \
+    CK(prof_mark(env, (cls), false));       \
+  } while (0)
+
+int run_stage(ch_env* env, int k, double theta) {
+  const Grid& g = env->g;
+  const int B = env->B;
+  cudaStream_t st = env->stream;
+  LAUNCH(0, launch_recover(g, B, env->pb, env->tab, st));
+  LAUNCH(1, launch_synth(g, B, env->pb.C6, env->pb.Q, env->tab.cheb, 6, st));
+  PlaneArgs<double> a = env->plane;
+  a.q = env->pb.Q;
+  a.h = env->pb.R;
+  LAUNCH(2, launch_plane<double>(a, B, env->plane_smem, st));
+  LAUNCH(3, launch_analysis(g, B, env->pb.R, env->pb.HC, env->tab.cheb, 3, st));
+  StageCoef sc;
+  sc.alpha = rk_alpha(k);
+  sc.beta = rk_beta(k);
+  sc.gamma = kGamma[k];
+  sc.zeta = kZeta[k];
+  sc.dt = env->prm.dt;
+  sc.nu = env->nu;
+  sc.theta = theta;
+  sc.flux = 2.0;
+  sc.k = k;
+  LAUNCH(4, launch_solve(g, B, env->pb, env->tab, sc, st));
+  return CH_OK;
+}
+
+int run_step(ch_env* env, const double* d_action, double* d_out) {
+  const Grid& g = env->g;
+  const int B = env->B;
+  cudaStream_t st = env->stream;
+  std::swap(env->pb.vw_old, env->pb.vw_new);
+  if (env->prm.control == 1) {
+    LAUNCH(5, launch_sense(g, B, env->pb, env->tab, env->js, env->prm.alpha, 1, st));
+  } else {
+    LAUNCH(5, launch_action(g, B, d_action, env->u_tau, env->tab, env->pb.vw_new, st));
+  }
+  CK(cudaMemsetAsync(env->pb.tau_acc, 0, B * sizeof(double), st));
+  const int spa = env->prm.steps_per_action;
+  for (int s = 0; s < spa; ++s) {
+    for (int k = 0; k < 3; ++k) RC(run_stage(env, k, (s + kCEnd[k]) / spa));
+    LAUNCH(5, launch_wall_shear(g, B, env->pb.UM, env->nu, env->pb.tau_acc, st));
+  }
+  LAUNCH(5, launch_sense(g, B, env->pb, env->tab, env->js, env->prm.alpha, 0, st));
+  LAUNCH(5, launch_obs(g, B, env->pb.planes, env->tab, d_out, env->out_stride, st));
+  LAUNCH(5, launch_finalize(B, env->pb.tau_acc, 1.0 / spa, env->tau_ref, d_out, env->out_stride,
+                            (size_t)2 * g.nz * g.nx, st));
+  env->t += spa * env->prm.dt;
+  env->steps += spa;
+  return CH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t ch_state_bytes(const ch_params_t* p) {
+  if (!p) return 0;
+  const size_t P = (size_t)p->nz * (p->nx / 2), ny = p->ny;
+  return sizeof(double) * (4 * ny * P + 2 * ny + 2 * P + 2);
+}
+
+int ch_default_params(ch_params_t* p) {
+  if (!p) return CH_ERR_ARG;
+  std::memset(p, 0, sizeof(*p));
+  p->nx = 16; p->ny = 65; p->nz = 16;
+  p->lx = 2.67; p->lz = 0.8;
+  p->re_tau = 180.0; p->re_bulk = 2800.0;
+  p->dt = 0.005;
+  p->steps_per_action = 1;
+  p->y_sense_plus = 15.0;
+  p->top_bc = 0; p->precision = 0; p->control = 0;
+  p->alpha = 1.0; p->tau_ref = 0.0; p->batch = 1;
+  return CH_OK;
+}
+
+const char* ch_strerror(int code) {
+  switch (code) {
+    case CH_OK: return "ok";
+    case CH_ERR_ARG: return "invalid argument";
+    case CH_ERR_OOM: return "out of memory";
+    case CH_ERR_BUDGET: return "memory budget exceeded";
+    case CH_ERR_DIVERGED: return "flow diverged (non-finite wall shear)";
+    case CH_ERR_TIMEOUT: return "bounded wait timed out";
+    case CH_ERR_STATE: return "call not valid in this state";
+    case CH_ERR_CUDA: return "CUDA runtime error";
+    case CH_ERR_UNSUPPORTED: return "unsupported parameter combination";
+    default: return "unknown error";
+  }
+}
+
+int env_create(const ch_params_t* p, ch_env_t** out) {
+  if (!out) return CH_ERR_ARG;
+  *out = nullptr;
+  RC(check_params(p));
+  ch_env* env = new (std::nothrow) ch_env();
+  if (!env) return CH_ERR_OOM;
+  env->prm = *p;
+  env->B = p->batch > 0 ? p->batch : 1;
+  env->prm.batch = env->B;
+  Grid& g = env->g;
+  g.nx = p->nx; g.ny = p->ny; g.nz = p->nz; g.nxh = p->nx / 2; g.P = g.nz * g.nxh; g.N = p->ny - 1;
+  g.mx = 3 * p->nx / 2; g.mz = 3 * p->nz / 2;
+  env->nu = 1.0 / p->re_bulk;
+  env->u_tau = p->re_tau / p->re_bulk;
+  env->tau_ref = p->tau_ref > 0 ? p->tau_ref : env->u_tau * env->u_tau;
+  env->js = sensing_node(g.N, p->re_tau, p->y_sense_plus);
+  int rc = CH_OK;
+  auto fail = [&](int code) { free_env(env); return code; };
+  if (cudaStreamCreateWithFlags(&env->own_stream, cudaStreamNonBlocking) != cudaSuccess) return fail(CH_ERR_CUDA);
+  env->stream = env->own_stream;
+  const size_t B = env->B, P = g.P, ny = g.ny;
+  PencilBufs& pb = env->pb;
+  if ((rc = dalloc(env, &pb.V, B * ny * P)) || (rc = dalloc(env, &pb.G, B * ny * P)) ||
+      (rc = dalloc(env, &pb.HVP, B * ny * P)) || (rc = dalloc(env, &pb.HGP, B * ny * P)) ||
+      (rc = dalloc(env, &pb.UM, B * ny)) || (rc = dalloc(env, &pb.WM, B * ny)) ||
+      (rc = dalloc(env, &pb.HXP, B * ny)) || (rc = dalloc(env, &pb.HZP, B * ny)) ||
+      (rc = dalloc(env, &pb.C6, B * 6 * ny * P)) || (rc = dalloc(env, &pb.Q, B * 6 * ny * P)) ||
+      (rc = dalloc(env, &pb.R, B * 3 * ny * P)) || (rc = dalloc(env, &pb.HC, B * 3 * ny * P)) ||
+      (rc = dalloc(env, &pb.vw_old, B * P)) || (rc = dalloc(env, &pb.vw_new, B * P)) ||
+      (rc = dalloc(env, &pb.planes, B * 2 * P)) || (rc = dalloc(env, &pb.tau_acc, B)))
+    return fail(rc);
+  env->out_stride = (size_t)2 * g.nz * g.nx + 2;
+  if ((rc = dalloc(env, &env->d_act, B * g.nz * g.nx)) || (rc = dalloc(env, &env->d_out, B * env->out_stride)))
+    return fail(rc);
+  if (cudaMallocHost(&env->h_out, B * env->out_stride * sizeof(double)) != cudaSuccess) return fail(CH_ERR_OOM);
+  if ((rc = build_tables(env))) return fail(rc);
+  // laminar Poiseuille, zero wall action
+  std::vector<double> st(ch_state_bytes(p) / sizeof(double), 0.0);
+  st[(size_t)4 * ny * P + 0] = 0.75;
+  st[(size_t)4 * ny * P + 2] = -0.75;
+  for (int e = 0; e < env->B; ++e)
+    if ((rc = set_state_dev(env, e, st.data()))) return fail(rc);
+  if (cudaMemset(pb.vw_old, 0, B * P * sizeof(double2)) != cudaSuccess) return fail(CH_ERR_CUDA);
+  if (cudaDeviceSynchronize() != cudaSuccess) return fail(CH_ERR_CUDA);
+  env->launches_per_step = 2 + p->steps_per_action * (3 * 5 + 1) + 3;
+  *out = env;
+  return CH_OK;
+}
+
+int env_set_stream(ch_env_t* env, void* stream) {
+  if (!env) return CH_ERR_ARG;
+  if (cudaStreamSynchronize(env->stream) != cudaSuccess) return CH_ERR_CUDA;
+  env->stream = stream ? static_cast<cudaStream_t>(stream) : env->own_stream;
+  return CH_OK;
+}
+
+int ch_seed_state(const ch_params_t* p, uint64_t seed, double amplitude, int kmax, void* buf, size_t nbytes) {
+  if (!p || !buf) return CH_ERR_ARG;
+  if (p->nx < 4 || p->nz < 4 || (p->nx & 1) || (p->nz & 1) || p->ny < 5) return CH_ERR_ARG;
+  if (nbytes < ch_state_bytes(p)) return CH_ERR_ARG;
+  fill_seed_state(p, seed, amplitude, kmax, static_cast<double*>(buf));
+  return CH_OK;
+}
+
+int env_reset(ch_env_t* env, uint64_t seed, double amplitude, int kmax) {
+  if (!env) return CH_ERR_ARG;
+  std::vector<double> st(ch_state_bytes(&env->prm) / sizeof(double));
+  for (int e = 0; e < env->B; ++e) {
+    fill_seed_state(&env->prm, seed + (uint64_t)e, amplitude, kmax, st.data());
+    RC(set_state_dev(env, e, st.data()));
+  }
+  env->t = 0.0;
+  env->steps = 0.0;
+  return CH_OK;
+}
+
+int env_get_state(ch_env_t* env, int e, void* buf, size_t nbytes) {
+  if (!env || !buf || e < 0 || e >= env->B) return CH_ERR_ARG;
+  if (nbytes < ch_state_bytes(&env->prm)) return CH_ERR_ARG;
+  const Grid& g = env->g;
+  const size_t P = g.P, ny = g.ny;
+  double* v = static_cast<double*>(buf);
+  double* gg = v + 2 * ny * P;
+  double* U = gg + 2 * ny * P;
+  double* W = U + ny;
+  double* vw = W + ny;
+  double* tail = vw + 2 * P;
+  cudaStream_t st = env->stream;
+  CK(cudaMemcpyAsync(v, env->pb.V + (size_t)e * ny * P, ny * P * sizeof(double2), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(gg, env->pb.G + (size_t)e * ny * P, ny * P * sizeof(double2), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(U, env->pb.UM + (size_t)e * ny, ny * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(W, env->pb.WM + (size_t)e * ny, ny * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(vw, env->pb.vw_new + (size_t)e * P, P * sizeof(double2), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  tail[0] = env->t;
+  tail[1] = env->steps;
+  return CH_OK;
+}
+
+int env_set_state(ch_env_t* env, int e, const void* buf, size_t nbytes) {
+  if (!env || !buf || e < 0 || e >= env->B) return CH_ERR_ARG;
+  if (nbytes < ch_state_bytes(&env->prm)) return CH_ERR_ARG;
+  return set_state_dev(env, e, static_cast<const double*>(buf));
+}
+
+int env_step_device(ch_env_t* env, const double* d_action, double* d_out) {
+  if (!env || !d_out) return CH_ERR_ARG;
+  if (env->prm.control == 0 && !d_action) return CH_ERR_ARG;
+  return run_step(env, d_action, d_out);
+}
+
+int env_step(ch_env_t* env, const double* action, double* obs, double* wall_shear, double* reward) {
+  if (!env) return CH_ERR_ARG;
+  if (env->prm.control == 0 && !action) return CH_ERR_ARG;
+  const Grid& g = env->g;
+  const size_t B = env->B, plane = (size_t)g.nz * g.nx;
+  cudaStream_t st = env->stream;
+  if (env->prm.control == 0)
+    CK(cudaMemcpyAsync(env->d_act, action, B * plane * sizeof(double), cudaMemcpyHostToDevice, st));
+  RC(run_step(env, env->d_act, env->d_out));
+  CK(cudaMemcpyAsync(env->h_out, env->d_out, B * env->out_stride * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  int rc = CH_OK;
+  for (size_t b = 0; b < B; ++b) {
+    const double* o = env->h_out + b * env->out_stride;
+    if (obs) std::memcpy(obs + b * 2 * plane, o, 2 * plane * sizeof(double));
+    if (wall_shear) wall_shear[b] = o[2 * plane];
+    if (reward) reward[b] = o[2 * plane + 1];
+    if (!std::isfinite(o[2 * plane])) rc = CH_ERR_DIVERGED;
+  }
+  return rc;
+}
+
+int env_info(const ch_env_t* env, ch_info_t* info) {
+  if (!env || !info) return CH_ERR_ARG;
+  std::memset(info, 0, sizeof(*info));
+  info->j_sense = env->js;
+  info->y_plus_sense = (1.0 + std::cos(M_PI * env->js / env->g.N)) * env->prm.re_tau;
+  info->nu = env->nu;
+  info->u_tau = env->u_tau;
+  info->tau_ref = env->tau_ref;
+  info->state_bytes = ch_state_bytes(&env->prm);
+  info->device_bytes = env->device_bytes;
+  info->plane_cluster = env->plane.S;
+  info->launches_per_step = env->launches_per_step;
+  return CH_OK;
+}
+
+int env_profile(ch_env_t* env, int enable) {
+  if (!env) return CH_ERR_ARG;
+  env->prof = enable != 0;
+  for (int c = 0; c < 6; ++c) env->ev_used[c] = 0;
+  return CH_OK;
+}
+
+int env_profile_read(ch_env_t* env, int cls, double* total_ms, int* launches) {
+  if (!env || cls < 0 || cls > 5) return CH_ERR_ARG;
+  if (cudaStreamSynchronize(env->stream) != cudaSuccess) return CH_ERR_CUDA;
+  double tot = 0.0;
+  for (int i = 0; i < env->ev_used[cls]; ++i) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, env->ev[cls][i].first, env->ev[cls][i].second) != cudaSuccess) return CH_ERR_CUDA;
+    tot += ms;
+  }
+  if (total_ms) *total_ms = tot;
+  if (launches) *launches = env->ev_used[cls];
+  return CH_OK;
+}
+
+int env_destroy(ch_env_t* env) {
+  if (!env) return CH_ERR_ARG;
+  free_env(env);
+  return CH_OK;
+}
+
+int ch_nonlinear(ch_env_t* env, const double* d_q, double* d_h) {
+  if (!env || !d_q || !d_h) return CH_ERR_ARG;
+  PlaneArgs<double> a = env->plane;
+  a.q = reinterpret_cast<const double2*>(d_q);
+  a.h = reinterpret_cast<double2*>(d_h);
+  CK(launch_plane<double>(a, env->B, env->plane_smem, env->stream));
+  return CH_OK;
+}
+
+int ch_tau_helmholtz(int ny, int M, const double* d_lam, const double* d_r, const double* d_top,
+                     const double* d_bot, double* d_f, void* stream) {
+  if (ny < 5 || ny > kMaxNy || M < 0) return CH_ERR_ARG;
+  if (M == 0) return CH_OK;
+  if (!d_lam || !d_r || !d_top || !d_bot || !d_f) return CH_ERR_ARG;
+  CK(launch_tau_helmholtz(ny, M, d_lam, reinterpret_cast<const double2*>(d_r),
+                          reinterpret_cast<const double2*>(d_top), reinterpret_cast<const double2*>(d_bot),
+                          reinterpret_cast<double2*>(d_f), static_cast<cudaStream_t>(stream)));
+  return CH_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,201 @@
+// Shared device helpers of the channel-flow library: complex arithmetic,
+// in-place mixed-radix FFT stages in shared memory, and the launch structs
+// passed from the host code to the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+namespace chdns {
+
+constexpr int kMaxNy = 201;                    // largest Chebyshev node count built
+constexpr int kMaxHalf = (kMaxNy + 1) / 2 + 1; // unknowns of one parity, upper bound
+constexpr int kMaxRadixStages = 16;
+
+// ---------------------------------------------------------------------------
+// complex helpers for double2 / float2
+// ---------------------------------------------------------------------------
+template <typename R> struct cpx;
+template <> struct cpx<double> { using T = double2; };
+template <> struct cpx<float> { using T = float2; };
+
+__host__ __device__ __forceinline__ double2 mk(double x, double y) { return make_double2(x, y); }
+__host__ __device__ __forceinline__ float2 mk(float x, float y) { return make_float2(x, y); }
+
+#define CH_CPX_OPS(C, R)                                                                   \
+  __host__ __device__ __forceinline__ C operator+(C a, C b) { return mk(a.x + b.x, a.y + b.y); } \
+  __host__ __device__ __forceinline__ C operator-(C a, C b) { return mk(a.x - b.x, a.y - b.y); } \
+  __host__ __device__ __forceinline__ C operator*(R s, C a) { return mk(s * a.x, s * a.y); }     \
+  __host__ __device__ __forceinline__ C cmul(C a, C b) {                                  \
+    return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);                              \
+  }                                                                                       \
+  __host__ __device__ __forceinline__ C cconj(C a) { return mk(a.x, -a.y); }                \
+  /* i * s * a */                                                                         \
+  __host__ __device__ __forceinline__ C imul(R s, C a) { return mk(-s * a.y, s * a.x); }
+
+CH_CPX_OPS(double2, double)
+CH_CPX_OPS(float2, float)
+#undef CH_CPX_OPS
+
+template <typename C> __device__ __forceinline__ C czero();
+template <> __device__ __forceinline__ double2 czero<double2>() { return make_double2(0.0, 0.0); }
+template <> __device__ __forceinline__ float2 czero<float2>() { return make_float2(0.f, 0.f); }
+
+// ---------------------------------------------------------------------------
+// FFT plans and in-place stages
+// ---------------------------------------------------------------------------
+struct FftPlan {
+  int n;
+  int nst;
+  int radix[kMaxRadixStages];
+};
+
+// e^{SIGN 2 pi i k / n} from a table of e^{+2 pi i k / n}
+template <int SIGN, typename C>
+__device__ __forceinline__ C twiddle(const C* tw, int k) {
+  C w = tw[k];
+  if (SIGN < 0) w.y = -w.y;
+  return w;
+}
+
+// Small DFT y_u = sum_t x_t e^{SIGN 2 pi i t u / r}, r in {2, 3, 4}.
+template <int SIGN, typename C, typename R>
+__device__ __forceinline__ void small_dft(C* x, int r) {
+  if (r == 2) {
+    C a = x[0], b = x[1];
+    x[0] = a + b;
+    x[1] = a - b;
+  } else if (r == 3) {
+    // sin(2 pi / 3) = sqrt(3) / 2
+    const R k = (R)SIGN * (R)0.86602540378443864676372317075293618;
+    C s = x[1] + x[2];
+    C d = x[1] - x[2];
+    C t1 = x[0] - (R)0.5 * s;
+    C rot = imul(k, d);
+    x[0] = x[0] + s;
+    x[1] = t1 + rot;
+    x[2] = t1 - rot;
+  } else {
+    C a0 = x[0] + x[2], a1 = x[0] - x[2];
+    C b0 = x[1] + x[3], b1 = x[1] - x[3];
+    C wb1 = imul((R)SIGN, b1);
+    x[0] = a0 + b0;
+    x[1] = a1 + wb1;
+    x[2] = a0 - b0;
+    x[3] = a1 - wb1;
+  }
+}
+
+// Line l of a batch starts at (l / g) * (n g) + (l % g) with element stride g
+// (g = 1: contiguous lines).  `bf_fastest` picks which index consecutive
+// threads walk: butterflies of one line (contiguous lines) or lines
+// (strided lines), so that neighbouring threads touch neighbouring words.
+
+// Decimation in frequency: natural-order input, digit-reversed output.
+template <int SIGN, typename R>
+__device__ void fft_dif(typename cpx<R>::T* buf, int nlines, int g, const FftPlan& pl,
+                        const typename cpx<R>::T* tw, bool bf_fastest) {
+  using C = typename cpx<R>::T;
+  const int n = pl.n;
+  int L = n;
+  for (int s = 0; s < pl.nst; ++s) {
+    const int r = pl.radix[s];
+    const int m = L / r;
+    const int nb = n / r;
+    const int tstep = n / L;
+    const int total = nlines * nb;
+    for (int w = threadIdx.x; w < total; w += blockDim.x) {
+      int l, bf;
+      if (bf_fastest) { bf = w % nb; l = w / nb; } else { l = w % nlines; bf = w / nlines; }
+      C* base = buf + (l / g) * (n * g) + (l % g);
+      const int blk = bf / m, q = bf % m;
+      const int i0 = blk * L + q;
+      C x[4];
+      for (int t = 0; t < r; ++t) x[t] = base[(i0 + t * m) * g];
+      small_dft<SIGN, C, R>(x, r);
+      for (int u = 0; u < r; ++u) {
+        C y = x[u];
+        if (u > 0 && q > 0) y = cmul(y, twiddle<SIGN>(tw, q * u * tstep));
+        base[(i0 + u * m) * g] = y;
+      }
+    }
+    __syncthreads();
+    L = m;
+  }
+}
+
+// Decimation in time with the radices in reverse order: digit-reversed input
+// (as produced by fft_dif with the same plan), natural-order output.
+template <int SIGN, typename R>
+__device__ void fft_dit(typename cpx<R>::T* buf, int nlines, int g, const FftPlan& pl,
+                        const typename cpx<R>::T* tw, bool bf_fastest) {
+  using C = typename cpx<R>::T;
+  const int n = pl.n;
+  int L = 1;
+  for (int s = pl.nst - 1; s >= 0; --s) {
+    const int r = pl.radix[s];
+    const int m = L;
+    L = L * r;
+    const int nb = n / r;
+    const int tstep = n / L;
+    const int total = nlines * nb;
+    for (int w = threadIdx.x; w < total; w += blockDim.x) {
+      int l, bf;
+      if (bf_fastest) { bf = w % nb; l = w / nb; } else { l = w % nlines; bf = w / nlines; }
+      C* base = buf + (l / g) * (n * g) + (l % g);
+      const int blk = bf / m, q = bf % m;
+      const int i0 = blk * L + q;
+      C x[4];
+      for (int t = 0; t < r; ++t) {
+        C v = base[(i0 + t * m) * g];
+        if (t > 0 && q > 0) v = cmul(v, twiddle<SIGN>(tw, q * t * tstep));
+        x[t] = v;
+      }
+      small_dft<SIGN, C, R>(x, r);
+      for (int u = 0; u < r; ++u) base[(i0 + u * m) * g] = x[u];
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launch structs
+// ---------------------------------------------------------------------------
+struct Grid {
+  int nx, ny, nz, nxh, P, N, mx, mz;
+};
+
+template <typename R>
+struct PlaneArgs {
+  using C = typename cpx<R>::T;
+  const C* q;          // [B][6][ny][P]
+  C* h;                // [B][3][ny][P]
+  int nxh, nz, ny, mx, mz, P;
+  int S, Lz, NP;
+  const C* tw_x;       // [mx]  e^{2 pi i k / mx}
+  const C* tw_z;       // [Lz]  e^{2 pi i k / Lz}
+  const C* tw_mz;      // [mz]  e^{2 pi i k / mz}
+  FftPlan px, pz;
+  R scale;             // 1 / (mx mz)
+};
+
+// Per-mode tau tables (device): see the host code that fills them.
+struct TauTables {
+  const double* helm;      // [3][2][4][Mh][P]   e, h, b, Q of (D^2 - k^2 - 1/(beta dt nu))
+  const double* helm_isq;  // [3][2][P]          1 / sum Q
+  const double* pois;      // [2][4][Mh][P]      same for (D^2 - k^2)
+  const double* pois_isq;  // [2][P]
+  const double* vh;        // [3][ny][P]         homogeneous v of the influence matrix
+  const double* vh_idv;    // [3][2][P]          1 / sum_{n of parity} n^2 vh_n
+  const double* u1;        // [3][ny]            mean response to unit forcing
+  const double* u1_iflux;  // [3]                1 / int u1 dy
+  int Mh;
+};
+
+struct StageCoef {
+  double alpha, beta, gamma, zeta, dt, nu, theta, flux;
+  int k;
+};
+
+}  // namespace chdns

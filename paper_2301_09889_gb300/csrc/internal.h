@@ -1,0 +1,54 @@
+// Host-side declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace chdns {
+
+template <typename R>
+cudaError_t launch_plane(const PlaneArgs<R>& a, int B, size_t smem, cudaStream_t st);
+
+struct PencilBufs {
+  double2 *V, *G, *HVP, *HGP;   // [B][ny][P]
+  double *UM, *WM, *HXP, *HZP;  // [B][ny]
+  double2* C6;                  // [B][6][ny][P] coefficients of u, v, w, ox, oy, oz
+  double2* Q;                   // [B][6][ny][P] node values (nonlinear input)
+  double2* R;                   // [B][3][ny][P] node values of H
+  double2* HC;                  // [B][3][ny][P] coefficients of H
+  double2 *vw_old, *vw_new;     // [B][P] wall-velocity spectra
+  double2* planes;              // [B][2][P] u, v spectra at the sensing node
+  double* tau_acc;              // [B]
+};
+
+struct DevTables {
+  const double* kx;    // [nxh]
+  const double* kz;    // [nz]
+  const double* cheb;  // [ny][ny] cos(pi j n / N)
+  TauTables tau;
+  const double2* tw_nx;  // [nx]
+  const double2* tw_nz;  // [nz]
+};
+
+cudaError_t launch_recover(const Grid& g, int B, const PencilBufs& pb, const DevTables& t, cudaStream_t st);
+cudaError_t launch_synth(const Grid& g, int B, const double2* coef, double2* out, const double* cheb,
+                         int nfields, cudaStream_t st);
+cudaError_t launch_analysis(const Grid& g, int B, const double2* nodes, double2* coef, const double* cheb,
+                            int nfields, cudaStream_t st);
+cudaError_t launch_solve(const Grid& g, int B, const PencilBufs& pb, const DevTables& t,
+                         const StageCoef& sc, cudaStream_t st);
+cudaError_t launch_wall_shear(const Grid& g, int B, const double* UM, double nu, double* acc,
+                              cudaStream_t st);
+cudaError_t launch_sense(const Grid& g, int B, const PencilBufs& pb, const DevTables& t, int js,
+                         double alpha, int opposition, cudaStream_t st);
+cudaError_t launch_obs(const Grid& g, int B, const double2* planes, const DevTables& t, double* out,
+                       size_t out_stride, cudaStream_t st);
+cudaError_t launch_action(const Grid& g, int B, const double* act, double u_tau, const DevTables& t,
+                          double2* vw, cudaStream_t st);
+cudaError_t launch_finalize(int B, const double* acc, double inv_steps, double tau_ref, double* out,
+                            size_t out_stride, size_t out_offset, cudaStream_t st);
+cudaError_t launch_tau_helmholtz(int ny, int M, const double* lam, const double2* r, const double2* top,
+                                 const double2* bot, double2* f, cudaStream_t st);
+
+}  // namespace chdns

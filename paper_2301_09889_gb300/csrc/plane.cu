@@ -1,0 +1,188 @@
+// Dealiased nonlinear term H = u x omega on one Gauss-Lobatto plane per
+// cluster of S CTAs (3/2 rule; paper Sec. 3.1 pseudo-spectral method).
+//
+// Input: Fourier coefficients (kept half spectrum) of u, v, w, omega_x,
+// omega_y, omega_z at node j.  Output: kept Fourier coefficients of
+// H_x, H_y, H_z at node j, scaled by 1/(mx mz).
+//
+// A plane never leaves shared memory between the inverse and the forward
+// transforms.  CTA `r` of a cluster owns the physical rows z = S m + r of the
+// padded mz x mx grid:
+//   1. gather: fold the kz spectrum onto Lz = mz/S points with the pre-twiddle
+//      e^{2 pi i kz r / mz}, then an Lz-point inverse FFT (DIF) along z;
+//   2. per pair of rows: pack the two real rows of each field into one complex
+//      line, Hermitian-extend to mx points, inverse FFT (DIF) along x, form the
+//      three products pointwise, forward FFT (DIT) and unpack the two rows;
+//   3. forward Lz-point FFT (DIT) along z; the S partial spectra are combined
+//      through distributed shared memory with the twiddles e^{-2 pi i kz r / mz}.
+// DIF leaves digit-reversed order and DIT consumes it, so no permutation pass
+// is needed: the products are pointwise and do not care about the order.
+#include <cooperative_groups.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace chdns {
+
+template <typename R>
+__global__ void __launch_bounds__(256) plane_kernel(PlaneArgs<R> a) {
+  using C = typename cpx<R>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* Z = reinterpret_cast<C*>(smem_raw);          // [6][Lz][nxh]
+  C* X = Z + 6 * a.Lz * a.nxh;                    // [6][NP][mx]
+  const int nxh = a.nxh, nz = a.nz, Lz = a.Lz, mx = a.mx, mz = a.mz, S = a.S, NP = a.NP;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  int rank = 0;
+  if (S > 1) rank = (int)cg::this_cluster().block_rank();
+  const int j = blockIdx.y;
+  const int b = blockIdx.z;
+  const size_t plane = (size_t)a.P;
+  const C* qb = a.q + (size_t)b * 6 * a.ny * plane + (size_t)j * plane;
+  C* hb = a.h + (size_t)b * 3 * a.ny * plane + (size_t)j * plane;
+
+  // 1. gather + fold + pre-twiddle
+  for (int w = tid; w < 6 * Lz * nxh; w += nt) {
+    const int i = w % nxh;
+    const int t = w / nxh;
+    const int m = t % Lz;
+    const int f = t / Lz;
+    const C* qf = qb + (size_t)f * a.ny * plane;
+    C acc = czero<C>();
+    for (int qq = 0; qq < S; ++qq) {
+      const int u = m + qq * Lz;
+      int kz;
+      if (u < nz / 2) kz = u;
+      else if (u > mz - nz / 2) kz = u - mz;
+      else continue;
+      const int row = kz >= 0 ? kz : nz + kz;
+      C val = qf[row * nxh + i];
+      if (S > 1) {
+        int e = (kz * rank) % mz;
+        if (e < 0) e += mz;
+        val = cmul(val, a.tw_mz[e]);
+      }
+      acc = acc + val;
+    }
+    Z[(f * Lz + m) * nxh + i] = acc;
+  }
+  __syncthreads();
+  fft_dif<+1, R>(Z, 6 * nxh, nxh, a.pz, a.tw_z, false);
+
+  // 2. rows in pairs: x transforms and products
+  const int npairs = Lz / 2;
+  for (int pb = 0; pb < npairs; pb += NP) {
+    for (int w = tid; w < 6 * NP * mx; w += nt) {
+      const int k = w % mx;
+      const int t = w / mx;
+      const int pp = t % NP;
+      const int f = t / NP;
+      const int r1 = 2 * (pb + pp);
+      const C* A = Z + (f * Lz + r1) * nxh;
+      const C* Bv = A + nxh;
+      C val;
+      if (k == 0) {
+        val = mk(A[0].x, Bv[0].x);
+      } else if (k < nxh) {
+        const C av = A[k], bv = Bv[k];
+        val = mk(av.x - bv.y, av.y + bv.x);
+      } else if (k > mx - nxh) {
+        const int kk = mx - k;
+        const C av = A[kk], bv = Bv[kk];
+        val = mk(av.x + bv.y, bv.x - av.y);
+      } else {
+        val = czero<C>();
+      }
+      X[(f * NP + pp) * mx + k] = val;
+    }
+    __syncthreads();
+    fft_dif<+1, R>(X, 6 * NP, 1, a.px, a.tw_x, true);
+    for (int w = tid; w < NP * mx; w += nt) {
+      const int x = w % mx;
+      const int pp = w / mx;
+      C* L0 = X + pp * mx;
+      const size_t fs = (size_t)NP * mx;
+      const C u = L0[x], v = L0[fs + x], ww = L0[2 * fs + x];
+      const C ox = L0[3 * fs + x], oy = L0[4 * fs + x], oz = L0[5 * fs + x];
+      // real parts: first row of the pair, imaginary parts: second row
+      L0[x] = mk(v.x * oz.x - ww.x * oy.x, v.y * oz.y - ww.y * oy.y);
+      L0[fs + x] = mk(ww.x * ox.x - u.x * oz.x, ww.y * ox.y - u.y * oz.y);
+      L0[2 * fs + x] = mk(u.x * oy.x - v.x * ox.x, u.y * oy.y - v.y * ox.y);
+    }
+    __syncthreads();
+    fft_dit<-1, R>(X, 3 * NP, 1, a.px, a.tw_x, true);
+    for (int w = tid; w < 3 * NP * nxh; w += nt) {
+      const int i = w % nxh;
+      const int t = w / nxh;
+      const int pp = t % NP;
+      const int f = t / NP;
+      const C* line = X + (f * NP + pp) * mx;
+      const C zk = line[i];
+      const C zm = line[(mx - i) % mx];
+      const int r1 = 2 * (pb + pp);
+      Z[(f * Lz + r1) * nxh + i] = mk((zk.x + zm.x) * (R)0.5, (zk.y - zm.y) * (R)0.5);
+      Z[(f * Lz + r1 + 1) * nxh + i] = mk((zk.y + zm.y) * (R)0.5, (zm.x - zk.x) * (R)0.5);
+    }
+    __syncthreads();
+  }
+
+  // 3. forward z transform of H_x, H_y, H_z and cluster combination
+  fft_dit<-1, R>(Z, 3 * nxh, nxh, a.pz, a.tw_z, false);
+  if (S > 1) cg::this_cluster().sync();
+  for (int w = tid; w < 3 * nz * nxh; w += nt) {
+    const int i = w % nxh;
+    const int t = w / nxh;
+    const int row = t % nz;
+    const int f = t / nz;
+    if (S > 1 && (row % S) != rank) continue;
+    C out = czero<C>();
+    if (row != nz / 2) {
+      const int kz = row < nz / 2 ? row : row - nz;
+      int u = kz % Lz;
+      if (u < 0) u += Lz;
+      for (int rr = 0; rr < S; ++rr) {
+        const C* Zr = Z;
+        if (S > 1 && rr != rank) Zr = cg::this_cluster().map_shared_rank(Z, rr);
+        C gval = Zr[(f * Lz + u) * nxh + i];
+        if (S > 1) {
+          int e = (-kz * rr) % mz;
+          if (e < 0) e += mz;
+          gval = cmul(gval, a.tw_mz[e]);
+        }
+        out = out + gval;
+      }
+      out = a.scale * out;
+    }
+    hb[(size_t)f * a.ny * plane + row * nxh + i] = out;
+  }
+  if (S > 1) cg::this_cluster().sync();
+}
+
+template <typename R>
+cudaError_t launch_plane(const PlaneArgs<R>& a, int B, size_t smem, cudaStream_t st) {
+  static size_t configured = 0;  // largest dynamic shared memory size enabled so far
+  if (smem > configured) {
+    cudaError_t e = cudaFuncSetAttribute(plane_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = smem;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(a.S, a.ny, B);
+  cfg.blockDim = dim3(256, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = a.S;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = a.S > 1 ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, plane_kernel<R>, a);
+}
+
+template cudaError_t launch_plane<double>(const PlaneArgs<double>&, int, size_t, cudaStream_t);
+template cudaError_t launch_plane<float>(const PlaneArgs<float>&, int, size_t, cudaStream_t);
+
+}  // namespace chdns

@@ -1,0 +1,265 @@
+"""ctypes binding of the C ABI in ``include/channel_dns.h``.
+
+Argument marshalling only: every computation runs in ``libchannel_dns.so``.
+Function names follow the C ABI.  Errors raise :class:`ChannelError` with the
+library's status code.  Importing this module does not need a GPU; calling
+anything that touches device memory does.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libchannel_dns.so")
+
+CH_OK = 0
+CH_ERR_ARG = -1
+CH_ERR_OOM = -2
+CH_ERR_BUDGET = -3
+CH_ERR_DIVERGED = -4
+CH_ERR_TIMEOUT = -5
+CH_ERR_STATE = -6
+CH_ERR_CUDA = -7
+CH_ERR_UNSUPPORTED = -8
+
+# every symbol the header declares
+EXPORTS = (
+    "ch_default_params", "env_create", "env_set_stream", "env_reset", "env_step",
+    "env_step_device", "env_get_state", "env_set_state", "env_info", "env_destroy",
+    "ch_strerror", "ch_seed_state", "ch_state_bytes", "ch_nonlinear", "ch_tau_helmholtz",
+    "env_profile", "env_profile_read",
+)
+
+
+class ChParams(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("lx", ctypes.c_double), ("lz", ctypes.c_double),
+        ("re_tau", ctypes.c_double), ("re_bulk", ctypes.c_double),
+        ("dt", ctypes.c_double),
+        ("steps_per_action", ctypes.c_int),
+        ("y_sense_plus", ctypes.c_double),
+        ("top_bc", ctypes.c_int), ("precision", ctypes.c_int), ("control", ctypes.c_int),
+        ("alpha", ctypes.c_double), ("tau_ref", ctypes.c_double),
+        ("batch", ctypes.c_int),
+    ]
+
+
+class ChInfo(ctypes.Structure):
+    _fields_ = [
+        ("j_sense", ctypes.c_int),
+        ("y_plus_sense", ctypes.c_double),
+        ("nu", ctypes.c_double), ("u_tau", ctypes.c_double), ("tau_ref", ctypes.c_double),
+        ("state_bytes", ctypes.c_size_t),
+        ("device_bytes", ctypes.c_size_t),
+        ("plane_cluster", ctypes.c_int),
+        ("launches_per_step", ctypes.c_int),
+    ]
+
+
+class ChannelError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {ch_strerror(code)} ({code})")
+
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load the shared library; fails loudly when it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() (nvcc, sm_103a) first")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER
+    vp = ctypes.c_void_p
+    dp = P(ctypes.c_double)
+    sig = {
+        "ch_default_params": (ctypes.c_int, [P(ChParams)]),
+        "env_create": (ctypes.c_int, [P(ChParams), P(vp)]),
+        "env_set_stream": (ctypes.c_int, [vp, vp]),
+        "env_reset": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.c_double, ctypes.c_int]),
+        "env_step": (ctypes.c_int, [vp, dp, dp, dp, dp]),
+        "env_step_device": (ctypes.c_int, [vp, vp, vp]),
+        "env_get_state": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_size_t]),
+        "env_set_state": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_size_t]),
+        "env_info": (ctypes.c_int, [vp, P(ChInfo)]),
+        "env_destroy": (ctypes.c_int, [vp]),
+        "ch_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        "ch_seed_state": (ctypes.c_int, [P(ChParams), ctypes.c_uint64, ctypes.c_double, ctypes.c_int,
+                                         vp, ctypes.c_size_t]),
+        "ch_state_bytes": (ctypes.c_size_t, [P(ChParams)]),
+        "ch_nonlinear": (ctypes.c_int, [vp, vp, vp]),
+        "ch_tau_helmholtz": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp, vp]),
+        "env_profile": (ctypes.c_int, [vp, ctypes.c_int]),
+        "env_profile_read": (ctypes.c_int, [vp, ctypes.c_int, P(ctypes.c_double), P(ctypes.c_int)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, what: str):
+    if rc != CH_OK:
+        raise ChannelError(rc, what)
+
+
+def _dptr(a: np.ndarray | None):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+# --------------------------------------------------------------------------
+# parameters
+# --------------------------------------------------------------------------
+
+def ch_default_params() -> ChParams:
+    p = ChParams()
+    _check(load().ch_default_params(ctypes.byref(p)), "ch_default_params")
+    return p
+
+
+def params(**kw) -> ChParams:
+    """Defaults of ``ch_default_params`` overridden by keyword arguments."""
+    p = ch_default_params()
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def ch_strerror(code: int) -> str:
+    return load().ch_strerror(code).decode()
+
+
+def ch_state_bytes(p: ChParams) -> int:
+    return int(load().ch_state_bytes(ctypes.byref(p)))
+
+
+def ch_seed_state(p: ChParams, seed: int, amplitude: float, kmax: int) -> np.ndarray:
+    buf = np.zeros(ch_state_bytes(p) // 8)
+    _check(load().ch_seed_state(ctypes.byref(p), seed, amplitude, kmax, buf.ctypes.data, buf.nbytes),
+           "ch_seed_state")
+    return buf
+
+
+# --------------------------------------------------------------------------
+# environment handle
+# --------------------------------------------------------------------------
+
+def env_create(p: ChParams) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(load().env_create(ctypes.byref(p), ctypes.byref(h)), "env_create")
+    return h
+
+
+def env_set_stream(env, stream: int | None):
+    _check(load().env_set_stream(env, ctypes.c_void_p(stream or 0)), "env_set_stream")
+
+
+def env_reset(env, seed: int, amplitude: float = 0.1, kmax: int = 4):
+    _check(load().env_reset(env, seed, amplitude, kmax), "env_reset")
+
+
+def env_step(env, action: np.ndarray | None, obs: np.ndarray, wall_shear: np.ndarray,
+             reward: np.ndarray) -> int:
+    """Host-buffer step; returns the status (CH_ERR_DIVERGED is returned, not raised)."""
+    rc = load().env_step(env, _dptr(action), _dptr(obs), _dptr(wall_shear), _dptr(reward))
+    if rc not in (CH_OK, CH_ERR_DIVERGED):
+        _check(rc, "env_step")
+    return rc
+
+
+def env_step_device(env, d_action: int | None, d_out: int):
+    _check(load().env_step_device(env, ctypes.c_void_p(d_action or 0), ctypes.c_void_p(d_out)),
+           "env_step_device")
+
+
+def env_info(env) -> ChInfo:
+    info = ChInfo()
+    _check(load().env_info(env, ctypes.byref(info)), "env_info")
+    return info
+
+
+def env_get_state(env, e: int = 0) -> np.ndarray:
+    n = env_info(env).state_bytes
+    buf = np.zeros(n // 8)
+    _check(load().env_get_state(env, e, buf.ctypes.data, buf.nbytes), "env_get_state")
+    return buf
+
+
+def env_set_state(env, e: int, buf: np.ndarray):
+    buf = np.ascontiguousarray(buf, dtype=np.float64)
+    _check(load().env_set_state(env, e, buf.ctypes.data, buf.nbytes), "env_set_state")
+
+
+def env_destroy(env):
+    _check(load().env_destroy(env), "env_destroy")
+
+
+def env_profile(env, enable: bool):
+    _check(load().env_profile(env, 1 if enable else 0), "env_profile")
+
+
+def env_profile_read(env, cls: int) -> tuple[float, int]:
+    ms = ctypes.c_double()
+    n = ctypes.c_int()
+    _check(load().env_profile_read(env, cls, ctypes.byref(ms), ctypes.byref(n)), "env_profile_read")
+    return ms.value, n.value
+
+
+def ch_nonlinear(env, d_q: int, d_h: int):
+    _check(load().ch_nonlinear(env, ctypes.c_void_p(d_q), ctypes.c_void_p(d_h)), "ch_nonlinear")
+
+
+def ch_tau_helmholtz(ny: int, M: int, d_lam: int, d_r: int, d_top: int, d_bot: int, d_f: int,
+                     stream: int | None = None):
+    _check(load().ch_tau_helmholtz(ny, M, ctypes.c_void_p(d_lam), ctypes.c_void_p(d_r),
+                                   ctypes.c_void_p(d_top), ctypes.c_void_p(d_bot), ctypes.c_void_p(d_f),
+                                   ctypes.c_void_p(stream or 0)), "ch_tau_helmholtz")
+
+
+# --------------------------------------------------------------------------
+# serialised-state layout (see env_get_state in the header)
+# --------------------------------------------------------------------------
+
+def unpack_state(buf: np.ndarray, nx: int, ny: int, nz: int) -> dict:
+    nxh = nx // 2
+    P = nz * nxh
+    o = 0
+    v = buf[o:o + 2 * ny * P].view(np.complex128).reshape(ny, nz, nxh); o += 2 * ny * P
+    g = buf[o:o + 2 * ny * P].view(np.complex128).reshape(ny, nz, nxh); o += 2 * ny * P
+    U = buf[o:o + ny]; o += ny
+    W = buf[o:o + ny]; o += ny
+    vw = buf[o:o + 2 * P].view(np.complex128).reshape(nz, nxh); o += 2 * P
+    return {"v": v.copy(), "g": g.copy(), "U": U.copy(), "W": W.copy(), "vw": vw.copy(),
+            "t": float(buf[o]), "steps": float(buf[o + 1])}
+
+
+def pack_state(st: dict, nx: int, ny: int, nz: int) -> np.ndarray:
+    nxh = nx // 2
+    P = nz * nxh
+    parts = [
+        np.ascontiguousarray(st["v"], np.complex128).reshape(-1).view(np.float64),
+        np.ascontiguousarray(st["g"], np.complex128).reshape(-1).view(np.float64),
+        np.asarray(st["U"], np.float64).reshape(ny),
+        np.asarray(st["W"], np.float64).reshape(ny),
+        np.ascontiguousarray(st.get("vw", np.zeros((nz, nxh))), np.complex128).reshape(-1).view(np.float64),
+        np.array([st.get("t", 0.0), st.get("steps", 0.0)]),
+    ]
+    out = np.concatenate(parts)
+    assert out.size == 4 * ny * P + 2 * ny + 2 * P + 2
+    return out

@@ -1,0 +1,178 @@
+"""Parity of the full environment step (library through the C ABI vs the FP64
+oracle) on the same seeded inputs: single steps, 10-step windows, opposition
+control, the action ramp, batches, ragged mode tiles and the pinned
+special cases (Poiseuille, laminar reward)."""
+
+import math
+
+import numpy as np
+import pytest
+
+import seeded_inputs as si
+from gpu_util import compare_states, oracle_params, rel_l2, run_pair
+from oracle import channel
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-11   # relative L2, all-FP64 path
+
+MINIMAL = dict(nx=16, ny=65, nz=16, lx=2.67, lz=0.8, re_tau=180.0, re_bulk=2800.0, dt=0.005)
+LARGER = dict(nx=64, ny=65, nz=64, lx=2 * math.pi, lz=math.pi, re_tau=180.0, re_bulk=2800.0, dt=0.005)
+
+
+def _check_outputs(lib_out, ora_out, tol=TOL):
+    for (lo, lt, lr), (oo, ot, orr) in zip(lib_out, ora_out):
+        assert rel_l2(lo, oo) < tol
+        assert abs(lt - ot) <= tol * abs(ot)
+        assert abs(lr - orr) <= tol * max(1.0, abs(orr)) * 100
+
+
+def test_single_step_minimal_channel(native_gpu):
+    lo, oo, ls, os_ = run_pair(native_gpu, MINIMAL, 1)
+    compare_states(ls, os_, TOL)
+    _check_outputs(lo, oo)
+
+
+def test_ten_step_window_minimal_channel(native_gpu):
+    lo, oo, ls, os_ = run_pair(native_gpu, MINIMAL, 10, seed=3, amp=0.2, kmax=99)
+    compare_states(ls, os_, TOL)
+    _check_outputs(lo, oo)
+
+
+def test_ragged_tiles_and_odd_sizes(native_gpu):
+    kw = dict(nx=12, ny=33, nz=24, lx=3.0, lz=1.7, re_tau=180.0, re_bulk=2800.0, dt=0.004)
+    lo, oo, ls, os_ = run_pair(native_gpu, kw, 3, seed=2, amp=0.2, kmax=99)
+    compare_states(ls, os_, TOL)
+    _check_outputs(lo, oo)
+
+
+def test_action_ramp_over_several_steps(native_gpu):
+    kw = dict(MINIMAL, steps_per_action=3)
+    lo, oo, ls, os_ = run_pair(native_gpu, kw, 2, seed=1, action_std=1.5)   # clip active
+    compare_states(ls, os_, TOL)
+    _check_outputs(lo, oo)
+
+
+def test_opposition_control_larger_channel(native_gpu):
+    kw = dict(LARGER, control=1, alpha=1.0)
+    lo, oo, ls, os_ = run_pair(native_gpu, kw, 2, seed=4, amp=0.1, kmax=99)
+    compare_states(ls, os_, TOL)
+    _check_outputs(lo, oo)
+    # opposition law on the applied wall spectrum: v_w = -alpha v(y_s), mean removed
+    assert rel_l2(ls["vw"], os_["vw"]) < TOL
+
+
+def test_poiseuille_steady_and_laminar_reward(native_gpu):
+    native = native_gpu
+    p = native.params(**MINIMAL)
+    env = native.env_create(p)
+    try:
+        obs = np.zeros((2, 16, 16))
+        tau = np.zeros(1)
+        rew = np.zeros(1)
+        zero = np.zeros((16, 16))
+        for _ in range(100):
+            assert native.env_step(env, zero, obs, tau, rew) == 0
+        st = native.unpack_state(native.env_get_state(env), 16, 65, 16)
+    finally:
+        native.env_destroy(env)
+    U0 = np.zeros(65)
+    U0[0], U0[2] = 0.75, -0.75
+    assert np.abs(st["U"] - U0).max() < 1e-12
+    assert np.abs(st["v"]).max() == 0 and np.abs(st["g"]).max() == 0
+    assert abs(tau[0] - 3.0 / 2800.0) < 1e-13
+    assert abs(rew[0] - (1 - 3 * 2800.0 / 180.0 ** 2)) < 1e-10
+    assert np.abs(obs[1]).max() < 1e-15
+
+
+def test_batch_equals_single_runs(native_gpu):
+    native = native_gpu
+    kw = dict(MINIMAL)
+    B = 3
+    pb = native.params(**kw, batch=B)
+    envb = native.env_create(pb)
+    singles = []
+    try:
+        for e in range(B):
+            fields = si.perturbed_poiseuille(16, 65, 16, 10 + e, 0.2, 99)
+            native.env_set_state(envb, e, native.pack_state(fields, 16, 65, 16))
+        acts = np.stack([si.wall_action(16, 16, 100 + e, 0.05 * 180 / 2800) for e in range(B)])
+        obs = np.zeros((B, 2, 16, 16))
+        tau = np.zeros(B)
+        rew = np.zeros(B)
+        for _ in range(3):
+            assert native.env_step(envb, acts, obs, tau, rew) == 0
+        for e in range(B):
+            env1 = native.env_create(native.params(**kw))
+            try:
+                fields = si.perturbed_poiseuille(16, 65, 16, 10 + e, 0.2, 99)
+                native.env_set_state(env1, 0, native.pack_state(fields, 16, 65, 16))
+                o1 = np.zeros((2, 16, 16))
+                t1 = np.zeros(1)
+                r1 = np.zeros(1)
+                for _ in range(3):
+                    native.env_step(env1, np.ascontiguousarray(acts[e]), o1, t1, r1)
+                s1 = native.env_get_state(env1)
+            finally:
+                native.env_destroy(env1)
+            sb = native.env_get_state(envb, e)
+            assert np.array_equal(sb, s1), e           # same kernels, no cross-env reduction
+            assert np.array_equal(obs[e], o1) and tau[e] == t1[0]
+    finally:
+        native.env_destroy(envb)
+
+
+def test_env_reset_matches_generator(native_gpu):
+    native = native_gpu
+    p = native.params(**MINIMAL, batch=2)
+    env = native.env_create(p)
+    try:
+        native.env_reset(env, 7, 0.1, 4)
+        for e in range(2):
+            st = native.unpack_state(native.env_get_state(env, e), 16, 65, 16)
+            ref = si.perturbed_poiseuille(16, 65, 16, 7 + e, 0.1, 4)
+            for k in ("v", "g", "U", "W"):
+                assert np.array_equal(st[k], ref[k])
+    finally:
+        native.env_destroy(env)
+
+
+def test_orr_sommerfeld_growth_on_gpu(native_gpu):
+    """Tollmien-Schlichting wave at Re_cl = 10^4, alpha = 1: growth 0.00373967 (centre-line units)."""
+    from oracle import stability
+    native = native_gpu
+    _, v_os = stability.most_unstable(64, 1.0, 1.0e4)
+    kw = dict(nx=4, ny=65, nz=4, lx=2 * math.pi, lz=math.pi, re_bulk=1.0e4 / 1.5, dt=0.01 / 1.5)
+    env = native.env_create(native.params(**kw))
+    try:
+        fields = si.perturbed_poiseuille(4, 65, 4, 0, 0.0)
+        fields["v"][:, 0, 1] = 1e-6 * v_os
+        native.env_set_state(env, 0, native.pack_state(fields, 4, 65, 4))
+        n0 = np.linalg.norm(fields["v"][:, 0, 1])
+        zero = np.zeros((4, 4))
+        obs, tau, rew = np.zeros((2, 4, 4)), np.zeros(1), np.zeros(1)
+        nsteps = 300
+        for _ in range(nsteps):
+            native.env_step(env, zero, obs, tau, rew)
+        st = native.unpack_state(native.env_get_state(env), 4, 65, 4)
+    finally:
+        native.env_destroy(env)
+    sigma = math.log(np.linalg.norm(st["v"][:, 0, 1]) / n0) / (nsteps * kw["dt"]) / 1.5
+    assert abs(sigma - 0.00373967) < 1e-3 * 0.00373967, sigma
+
+
+def test_invalid_arguments_are_rejected(native_gpu):
+    native = native_gpu
+    with pytest.raises(native.ChannelError):
+        native.env_create(native.params(nx=10, nz=10, ny=65))   # 15-point padded FFT: not 2^a 3^b
+    with pytest.raises(native.ChannelError):
+        native.env_create(native.params(ny=3))
+    env = native.env_create(native.params(**MINIMAL))
+    try:
+        with pytest.raises(native.ChannelError):
+            native.env_set_state(env, 1, np.zeros(10))
+        obs, tau, rew = np.zeros((2, 16, 16)), np.zeros(1), np.zeros(1)
+        with pytest.raises(native.ChannelError):
+            native.env_step(env, None, obs, tau, rew)    # external control needs an action
+    finally:
+        native.env_destroy(env)
