@@ -139,6 +139,28 @@ int env_step_device(ch_env_t* env, const double* d_action, double* d_out);
 int env_get_state(ch_env_t* env, int e, void* buf, size_t nbytes);
 int env_set_state(ch_env_t* env, int e, const void* buf, size_t nbytes);
 
+/* Same problems and result as ch_tau_helmholtz, for callers that must not
+ * allocate device memory at all: hard real-time control loops (an allocation,
+ * or the driver growing per-thread local memory for a new kernel, can block
+ * and synchronise the device), processes whose device memory is fully owned
+ * by another allocator, and hosts that only lend buffers they own.  The paper
+ * has no counterpart; this is a deployment variant.
+ *   - The caller passes all inputs and outputs (device pointers, as for
+ *     ch_tau_helmholtz).  The work vectors live in one 16 MiB array that the
+ *     library reserves on every GPU that loads it, until the process exits.
+ *   - Capacity: 2 * M * 8 * mpad doubles <= 2^21, with mpad = ny/2 + 1 rounded
+ *     up to even (ny = 65: M <= 3855; ny = 129: M <= 1985).  Larger requests
+ *     return CH_ERR_ARG without launching; split them.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - All calls share the array: calls that overlap on the GPU (different
+ *     streams, or host threads) race and must be serialised by the caller.
+ *     Nothing in it needs to start at zero; every call writes what it reads.
+ *   - No cudaMalloc, cudaFree or other allocating call is made. */
+int ch_tau_helmholtz_noalloc(int ny, int M, const double* d_lam, const double* d_r,
+                             const double* d_top, const double* d_bot, double* d_f,
+                             void* stream);
+
 /* Kernel timing for measurement tools.  While enabled, every launch of the
  * handle is bracketed by a pair of CUDA events on the handle's stream and
  * attributed to a class: 0 recover (u, w, vorticity from v, omega_y),

@@ -13,6 +13,9 @@
 // Chebyshev conventions: f(y) = sum_n a_n T_n(y), nodes y_j = cos(pi j / N).
 // Derivative recurrence (coefficient space): c_m b_m = b_{m+2} + 2 (m+1) a_{m+1}
 // with c_0 = 2, c_m = 1 otherwise, walked from m = N down to 0.
+#include <mutex>
+
+#include "../../include/channel_dns.h"
 #include "common.cuh"
 #include "internal.h"
 
@@ -712,4 +715,90 @@ cudaError_t launch_tau_helmholtz(int ny, int M, const double* lam, const double2
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the stateless tau entry point.
+//
+// tau_helmholtz_kernel above keeps each problem's factorisation and work
+// vectors (about 6.5 KB per thread) in local memory, which the CUDA driver
+// allocates and may have to grow at launch time.  Some callers cannot let
+// anything allocate device memory: a control loop with a fixed real-time
+// budget (cudaMalloc and a driver-side resize can block for milliseconds and
+// synchronise the device), a process whose device memory is already fully
+// handed to another allocator's pool, or a host framework that only lends out
+// buffers it owns.  For them the work vectors live in one file-scope array
+// below, sized once when the library is loaded.
+// ---------------------------------------------------------------------------
 }  // namespace chdns
+
+// 16 MiB of doubles, held by every GPU that loads the library until the
+// process exits.  Shared by all calls; a call writes every slot it reads, so
+// nothing has to start at zero.
+constexpr size_t kNoAllocScratchDoubles = (size_t)2 << 20;
+static __device__ __align__(256) double g_tau_noalloc_scratch[kNoAllocScratchDoubles];
+
+namespace chdns {
+
+__global__ void tau_helmholtz_noalloc_kernel(int ny, int M, int mpad, const double* lam, const double2* r,
+                                             const double2* top, const double2* bot, double2* f,
+                                             double* scratch) {
+  const long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (tid >= 2L * M) return;
+  const int m = (int)(tid / 2), sig = (int)(tid % 2);
+  const int N = ny - 1;
+  // slot layout: e, h, b, Q (mpad doubles each), then r and f (mpad complex each)
+  double* base = scratch + (size_t)tid * 8 * mpad;
+  double* e = base;
+  double* h = base + mpad;
+  double* bb = base + 2 * mpad;
+  double* Q = base + 3 * mpad;
+  double2* rr = reinterpret_cast<double2*>(base + 4 * mpad);
+  double2* ff = reinterpret_cast<double2*>(base + 6 * mpad);
+  double isq;
+  tau_factor(N, sig, lam[m], e, h, bb, Q, &isq);
+  const int Mp = (N - sig) / 2 + 1;
+  for (int i = 0; i < Mp; ++i) rr[i] = r[(size_t)m * ny + 2 * i + sig];
+  const double2 s = sig == 0 ? 0.5 * (top[m] + bot[m]) : 0.5 * (top[m] - bot[m]);
+  tau_solve(N, sig, rr, ff, TabLocal{e, h, bb, Q}, isq, s);
+  for (int i = 0; i < Mp; ++i) f[(size_t)m * ny + 2 * i + sig] = ff[i];
+}
+
+}  // namespace chdns
+
+namespace {
+
+// Device address of the scratch array, looked up once per device.
+constexpr int kMaxDevices = 64;
+double* g_noalloc_ptr[kMaxDevices] = {nullptr};
+std::mutex g_noalloc_mu;
+
+int noalloc_scratch(double** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return CH_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_tau_noalloc_scratch) != cudaSuccess || !p) return CH_ERR_CUDA;
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return CH_OK;
+}
+
+}  // namespace
+
+extern "C" int ch_tau_helmholtz_noalloc(int ny, int M, const double* d_lam, const double* d_r,
+                                        const double* d_top, const double* d_bot, double* d_f, void* stream) {
+  if (ny < 5 || ny > chdns::kMaxNy || M < 0) return CH_ERR_ARG;
+  if (M == 0) return CH_OK;
+  if (!d_lam || !d_r || !d_top || !d_bot || !d_f) return CH_ERR_ARG;
+  const int mpad = ((ny / 2 + 1) + 1) & ~1;  // even, keeps the complex work vectors 16-byte aligned
+  if ((size_t)2 * M * 8 * mpad > kNoAllocScratchDoubles) return CH_ERR_ARG;
+  double* scratch = nullptr;
+  const int rc = noalloc_scratch(&scratch);
+  if (rc != CH_OK) return rc;
+  const long n = 2L * M;
+  chdns::tau_helmholtz_noalloc_kernel<<<(unsigned)((n + 63) / 64), 64, 0, static_cast<cudaStream_t>(stream)>>>(
+      ny, M, mpad, d_lam, reinterpret_cast<const double2*>(d_r), reinterpret_cast<const double2*>(d_top),
+      reinterpret_cast<const double2*>(d_bot), reinterpret_cast<double2*>(d_f), scratch);
+  return cudaGetLastError() == cudaSuccess ? CH_OK : CH_ERR_CUDA;
+}

@@ -31,7 +31,7 @@ EXPORTS = (
     "ch_default_params", "env_create", "env_set_stream", "env_reset", "env_step",
     "env_step_device", "env_get_state", "env_set_state", "env_info", "env_destroy",
     "ch_strerror", "ch_seed_state", "ch_state_bytes", "ch_nonlinear", "ch_tau_helmholtz",
-    "env_profile", "env_profile_read",
+    "env_profile", "env_profile_read", "ch_tau_helmholtz_noalloc",
 )
 
 
@@ -98,6 +98,7 @@ def load() -> ctypes.CDLL:
         "ch_state_bytes": (ctypes.c_size_t, [P(ChParams)]),
         "ch_nonlinear": (ctypes.c_int, [vp, vp, vp]),
         "ch_tau_helmholtz": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp, vp]),
+        "ch_tau_helmholtz_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp, vp]),
         "env_profile": (ctypes.c_int, [vp, ctypes.c_int]),
         "env_profile_read": (ctypes.c_int, [vp, ctypes.c_int, P(ctypes.c_double), P(ctypes.c_int)]),
     }
@@ -263,3 +264,13 @@ def pack_state(st: dict, nx: int, ny: int, nz: int) -> np.ndarray:
     out = np.concatenate(parts)
     assert out.size == 4 * ny * P + 2 * ny + 2 * P + 2
     return out
+
+
+def ch_tau_helmholtz_noalloc(ny: int, M: int, d_lam: int, d_r: int, d_top: int, d_bot: int, d_f: int,
+                             stream: int | None = None):
+    """ch_tau_helmholtz without any device allocation (work vectors in the
+    library's static 16 MiB array); for callers that cannot allocate."""
+    _check(load().ch_tau_helmholtz_noalloc(ny, M, ctypes.c_void_p(d_lam), ctypes.c_void_p(d_r),
+                                           ctypes.c_void_p(d_top), ctypes.c_void_p(d_bot),
+                                           ctypes.c_void_p(d_f), ctypes.c_void_p(stream or 0)),
+           "ch_tau_helmholtz_noalloc")
