@@ -43,7 +43,7 @@ WORKLOAD = dict(nx=64, ny=65, nz=64, lx=2 * math.pi, lz=math.pi, re_tau=180.0, r
 WORKLOAD_NAME = "larger channel Re_tau=180, 64x65x64, all FP64, opposition control, 1 RK3 step per env step"
 METRIC = "env_steps_per_s"
 UNIT = "env-steps/s"
-KERNEL_CLASSES = ("recover", "cheb_synthesis", "nonlinear_plane", "cheb_analysis", "tau_solve", "per_step")
+KERNEL_CLASSES = ("stage_pre", "nonlinear_plane", "stage_post", "per_step")
 L2_FLUSH_BYTES = 256 << 20
 
 

@@ -70,7 +70,10 @@ typedef struct ch_params {
     int steps_per_action;    /* solver steps per env_step (actuation interval, Sec. 3.2) */
     double y_sense_plus;     /* sensing height in wall units; rounded up to a node (Sec. 3.2) */
     int top_bc;              /* 0: no-slip upper wall (only value built)               */
-    int precision;           /* 0: all FP64 (only value built)                         */
+    int precision;           /* 0: all FP64; 1: mixed -- the dealiased nonlinear term
+                                (Chebyshev synthesis/analysis, padded FFTs, products)
+                                in FP32, the tau solves, influence-matrix correction
+                                and flow-rate update in FP64                            */
     int control;             /* 0: external action, 1: opposition control (Sec. 4.1)  */
     double alpha;            /* opposition-control gain                                */
     double tau_ref;          /* reward reference wall shear; <= 0 -> u_tau^2          */
@@ -163,9 +166,10 @@ int ch_tau_helmholtz_noalloc(int ny, int M, const double* d_lam, const double* d
 
 /* Kernel timing for measurement tools.  While enabled, every launch of the
  * handle is bracketed by a pair of CUDA events on the handle's stream and
- * attributed to a class: 0 recover (u, w, vorticity from v, omega_y),
- * 1 Chebyshev synthesis, 2 nonlinear plane kernel, 3 Chebyshev analysis,
- * 4 tau solves, 5 per-step kernels (action, wall shear, observation).
+ * attributed to a class: 0 stage_pre (u, w, vorticity from v, omega_y and
+ * their values at the Chebyshev nodes), 1 nonlinear plane kernel,
+ * 2 stage_post (Chebyshev analysis of H, right-hand sides, tau solves),
+ * 3 per-step kernels (action, wall shear, observation).
  * env_profile(env, 1) clears the totals and starts recording, (env, 0) stops.
  * env_profile_read synchronises the stream and returns the summed device
  * time (ms) and the launch count of one class since the last enable. */

@@ -144,7 +144,7 @@ int check_params(const ch_params_t* p) {
   if (!(p->lx > 0) || !(p->lz > 0) || !(p->re_bulk > 0) || !(p->re_tau > 0) || !(p->dt > 0)) return CH_ERR_ARG;
   if (p->steps_per_action < 1) return CH_ERR_ARG;
   if (p->control != 0 && p->control != 1) return CH_ERR_ARG;
-  if (p->top_bc != 0 || p->precision != 0) return CH_ERR_UNSUPPORTED;
+  if (p->top_bc != 0 || (p->precision != 0 && p->precision != 1)) return CH_ERR_UNSUPPORTED;
   FftPlan a, b;
   if (!fft_plan(3 * p->nx / 2, &a) || !fft_plan(3 * p->nz / 2, &b)) return CH_ERR_UNSUPPORTED;
   if ((3 * p->nx / 2) % 2 || (3 * p->nz / 2) % 2) return CH_ERR_UNSUPPORTED;
@@ -163,6 +163,8 @@ struct ch_env {
   DevTables tab{};
   PlaneArgs<double> plane{};
   size_t plane_smem = 0;
+  PlaneArgs<float> plane_f{};   // FP32 nonlinear term (precision 1)
+  size_t plane_f_smem = 0;
   double* d_act = nullptr;
   double* d_out = nullptr;
   double* h_out = nullptr;
@@ -173,10 +175,11 @@ struct ch_env {
   int js = 0;
   double nu = 0, u_tau = 0, tau_ref = 0;
   int launches_per_step = 0;
+  int ppc_pre = 8, ppc_post = 8;  // modes per CTA of the fused stage kernels
   // kernel timing (env_profile)
   bool prof = false;
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[6];
-  int ev_used[6] = {0, 0, 0, 0, 0, 0};
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[4];
+  int ev_used[4] = {0, 0, 0, 0};
   char err[256] = {0};
 };
 
@@ -229,6 +232,42 @@ void free_env(ch_env* env) {
     if (r_ != CH_OK) return r_;  \
   } while (0)
 
+// nonlinear plane kernel: smallest cluster whose z-slab fits shared memory
+template <typename R>
+int setup_plane(ch_env* env, PlaneArgs<R>* a, size_t* smem) {
+  using C = typename cpx<R>::T;
+  const Grid& g = env->g;
+  a->nxh = g.nxh; a->nz = g.nz; a->ny = g.ny; a->mx = g.mx; a->mz = g.mz; a->P = g.P;
+  a->S = 0;
+  const size_t csz = sizeof(C);
+  for (int S = 1; S <= 8; S *= 2) {
+    if (g.mz % S || (g.mz / S) % 2) continue;
+    const int Lz = g.mz / S;
+    const size_t zb = (size_t)6 * Lz * g.nxh * csz;
+    if (zb > 160 * 1024) continue;
+    const int npairs = Lz / 2;
+    int np = 0;
+    for (int d = std::min(npairs, 16); d >= 1; --d)
+      if (npairs % d == 0 && zb + (size_t)6 * d * g.mx * csz <= 220 * 1024) { np = d; break; }
+    if (!np) continue;
+    a->S = S; a->Lz = Lz; a->NP = np;
+    *smem = zb + (size_t)6 * np * g.mx * csz;
+    break;
+  }
+  if (!a->S) return CH_ERR_UNSUPPORTED;
+  if (!fft_plan(g.mx, &a->px) || !fft_plan(a->Lz, &a->pz)) return CH_ERR_UNSUPPORTED;
+  auto cast = [](const std::vector<double2>& v) {
+    std::vector<C> o(v.size());
+    for (size_t i = 0; i < v.size(); ++i) o[i] = mk((R)v[i].x, (R)v[i].y);
+    return o;
+  };
+  RC(dupload(env, &a->tw_x, cast(twiddles(g.mx))));
+  RC(dupload(env, &a->tw_z, cast(twiddles(a->Lz))));
+  RC(dupload(env, &a->tw_mz, cast(twiddles(g.mz))));
+  a->scale = (R)(1.0 / ((double)g.mx * g.mz));
+  return CH_OK;
+}
+
 int build_tables(ch_env* env) {
   const Grid& g = env->g;
   const int N = g.N, P = g.P, ny = g.ny;
@@ -244,16 +283,17 @@ int build_tables(ch_env* env) {
   for (int j = 0; j < ny; ++j)
     for (int n = 0; n < ny; ++n) cheb[(size_t)j * ny + n] = std::cos(M_PI * (double)((j * n) % (2 * N)) / N);
 
+  // tau tables, mode index fastest: [stage][parity][e, h, b, Q][Mh][P]
   std::vector<double> helm((size_t)3 * 2 * 4 * Mh * P, 0.0), helm_isq((size_t)3 * 2 * P, 0.0);
   std::vector<double> pois((size_t)2 * 4 * Mh * P, 0.0), pois_isq((size_t)2 * P, 0.0);
-  std::vector<double> vh((size_t)3 * ny * P, 0.0), vh_idv((size_t)3 * 2 * P, 0.0);
-  std::vector<double> u1((size_t)3 * ny, 0.0), u1_iflux(3, 0.0);
-  auto put = [&](std::vector<double>& tab, size_t base, const Factor& F, int M, int p) {
+  std::vector<double> vh((size_t)3 * 2 * Mh * P, 0.0), vh_idv((size_t)3 * 2 * P, 0.0);
+  std::vector<double> u1((size_t)3 * Mh, 0.0), u1_iflux(3, 0.0);
+  auto put = [&](std::vector<double>& tab, size_t base, const Factor& F, int M, int pp) {
     for (int i = 0; i < M; ++i) {
-      tab[base + ((size_t)0 * Mh + i) * P + p] = F.e[i];
-      tab[base + ((size_t)1 * Mh + i) * P + p] = F.h[i];
-      tab[base + ((size_t)2 * Mh + i) * P + p] = F.b[i];
-      tab[base + ((size_t)3 * Mh + i) * P + p] = F.Q[i];
+      tab[base + ((size_t)0 * Mh + i) * P + pp] = F.e[i];
+      tab[base + ((size_t)1 * Mh + i) * P + pp] = F.h[i];
+      tab[base + ((size_t)2 * Mh + i) * P + pp] = F.b[i];
+      tab[base + ((size_t)3 * Mh + i) * P + pp] = F.Q[i];
     }
   };
   for (int pp = 0; pp < P; ++pp) {
@@ -262,13 +302,14 @@ int build_tables(ch_env* env) {
     for (int sig = 0; sig < 2; ++sig) {
       const int M = (N - sig) / 2 + 1;
       const Factor Fp = host_factor(N, sig, k2);
-      put(pois, (size_t)(sig * 4) * Mh * P, Fp, M, pp);
+      put(pois, (size_t)sig * 4 * Mh * P, Fp, M, pp);
       pois_isq[(size_t)sig * P + pp] = Fp.isq;
       for (int k = 0; k < 3; ++k) {
         const double ibdn = 1.0 / (rk_beta(k) * p.dt * env->nu);
         const Factor Fh = host_factor(N, sig, k2 + ibdn);
-        put(helm, (size_t)((k * 2 + sig) * 4) * Mh * P, Fh, M, pp);
-        helm_isq[(size_t)(k * 2 + sig) * P + pp] = Fh.isq;
+        const size_t slot = (size_t)(k * 2 + sig);
+        put(helm, slot * 4 * Mh * P, Fh, M, pp);
+        helm_isq[slot * P + pp] = Fh.isq;
         // homogeneous solution of this parity: phi_h = 1 on the wall row, r = 0
         const std::vector<double> zero(M, 0.0);
         const std::vector<double> phih = host_solve(N, sig, zero, Fh, 1.0);
@@ -276,10 +317,10 @@ int build_tables(ch_env* env) {
         double d = 0.0;
         for (int i = 0; i < M; ++i) {
           const int n = 2 * i + sig;
-          vh[((size_t)k * ny + n) * P + pp] = vhp[i];
+          vh[(slot * Mh + i) * P + pp] = vhp[i];
           d += (double)n * n * vhp[i];
         }
-        vh_idv[(size_t)(k * 2 + sig) * P + pp] = (d != 0.0 && std::isfinite(d)) ? 1.0 / d : 0.0;
+        vh_idv[slot * P + pp] = (d != 0.0 && std::isfinite(d)) ? 1.0 / d : 0.0;
       }
     }
   }
@@ -296,14 +337,37 @@ int build_tables(ch_env* env) {
     for (int i = 0; i < M; ++i) {
       const int n = 2 * i;
       const double v = -cforce * uu[i];
-      u1[(size_t)k * ny + n] = v;
+      u1[(size_t)k * Mh + i] = v;
       flux += 2.0 / (1.0 - (double)n * n) * v;
     }
     u1_iflux[k] = 1.0 / flux;
   }
+  // tau row constants per n
+  std::vector<double> rowc((size_t)3 * ny, 0.0);
+  for (int n = 2; n <= N; ++n) {
+    rowc[n] = cA(n);
+    rowc[ny + n] = cB(n, N);
+    rowc[2 * ny + n] = cC(n, N);
+  }
+  RC(dupload(env, &env->tab.tau.rowc, rowc));
+  // T_n'(y_js) = n sin(n theta) / sin(theta), theta = pi js / N (T_n'(+1) = n^2)
+  std::vector<double> dts(ny, 0.0);
+  for (int n = 0; n < ny; ++n) {
+    if (env->js == 0) {
+      dts[n] = (double)n * n;
+    } else {
+      dts[n] = n * std::sin(M_PI * (double)((n * env->js) % (2 * N)) / N) / std::sin(M_PI * (double)env->js / N);
+    }
+  }
+  RC(dupload(env, &env->tab.dts, dts));
   RC(dupload(env, &env->tab.kx, kx));
   RC(dupload(env, &env->tab.kz, kz));
   RC(dupload(env, &env->tab.cheb, cheb));
+  {
+    std::vector<float> chf(cheb.size());
+    for (size_t i = 0; i < cheb.size(); ++i) chf[i] = (float)cheb[i];
+    RC(dupload(env, &env->tab.cheb_f, chf));
+  }
   RC(dupload(env, &env->tab.tau.helm, helm));
   RC(dupload(env, &env->tab.tau.helm_isq, helm_isq));
   RC(dupload(env, &env->tab.tau.pois, pois));
@@ -316,31 +380,8 @@ int build_tables(ch_env* env) {
   RC(dupload(env, &env->tab.tw_nx, twiddles(g.nx)));
   RC(dupload(env, &env->tab.tw_nz, twiddles(g.nz)));
 
-  // nonlinear plane kernel: smallest cluster whose z-slab fits shared memory
-  PlaneArgs<double>& a = env->plane;
-  a.nxh = g.nxh; a.nz = g.nz; a.ny = g.ny; a.mx = g.mx; a.mz = g.mz; a.P = g.P;
-  a.S = 0;
-  const size_t csz = sizeof(double2);
-  for (int S = 1; S <= 8; S *= 2) {
-    if (g.mz % S || (g.mz / S) % 2) continue;
-    const int Lz = g.mz / S;
-    const size_t zb = (size_t)6 * Lz * g.nxh * csz;
-    if (zb > 160 * 1024) continue;
-    const int npairs = Lz / 2;
-    int np = 0;
-    for (int d = std::min(npairs, 16); d >= 1; --d)
-      if (npairs % d == 0 && zb + (size_t)6 * d * g.mx * csz <= 220 * 1024) { np = d; break; }
-    if (!np) continue;
-    a.S = S; a.Lz = Lz; a.NP = np;
-    env->plane_smem = zb + (size_t)6 * np * g.mx * csz;
-    break;
-  }
-  if (!a.S) return CH_ERR_UNSUPPORTED;
-  if (!fft_plan(g.mx, &a.px) || !fft_plan(a.Lz, &a.pz)) return CH_ERR_UNSUPPORTED;
-  RC(dupload(env, &a.tw_x, twiddles(g.mx)));
-  RC(dupload(env, &a.tw_z, twiddles(a.Lz)));
-  RC(dupload(env, &a.tw_mz, twiddles(g.mz)));
-  a.scale = 1.0 / ((double)g.mx * g.mz);
+  RC(setup_plane(env, &env->plane, &env->plane_smem));
+  RC(setup_plane(env, &env->plane_f, &env->plane_f_smem));
   return CH_OK;
 }
 
@@ -461,13 +502,21 @@ int run_stage(ch_env* env, int k, double theta) {
   const Grid& g = env->g;
   const int B = env->B;
   cudaStream_t st = env->stream;
-  LAUNCH(0, launch_recover(g, B, env->pb, env->tab, st));
-  LAUNCH(1, launch_synth(g, B, env->pb.C6, env->pb.Q, env->tab.cheb, 6, st));
-  PlaneArgs<double> a = env->plane;
-  a.q = env->pb.Q;
-  a.h = env->pb.R;
-  LAUNCH(2, launch_plane<double>(a, B, env->plane_smem, st));
-  LAUNCH(3, launch_analysis(g, B, env->pb.R, env->pb.HC, env->tab.cheb, 3, st));
+  const bool mixed = env->prm.precision == 1;
+  if (mixed) {
+    float2* q = reinterpret_cast<float2*>(env->pb.Q);
+    LAUNCH(0, launch_stage_pre<float>(g, B, env->pb, env->tab, q, env->ppc_pre, st));
+    PlaneArgs<float> a = env->plane_f;
+    a.q = q;
+    a.h = reinterpret_cast<float2*>(env->pb.R);
+    LAUNCH(1, launch_plane<float>(a, B, env->plane_f_smem, st));
+  } else {
+    LAUNCH(0, launch_stage_pre<double>(g, B, env->pb, env->tab, env->pb.Q, env->ppc_pre, st));
+    PlaneArgs<double> a = env->plane;
+    a.q = env->pb.Q;
+    a.h = env->pb.R;
+    LAUNCH(1, launch_plane<double>(a, B, env->plane_smem, st));
+  }
   StageCoef sc;
   sc.alpha = rk_alpha(k);
   sc.beta = rk_beta(k);
@@ -478,7 +527,11 @@ int run_stage(ch_env* env, int k, double theta) {
   sc.theta = theta;
   sc.flux = 2.0;
   sc.k = k;
-  LAUNCH(4, launch_solve(g, B, env->pb, env->tab, sc, st));
+  if (mixed)
+    LAUNCH(2, launch_stage_post<float>(g, B, env->pb, env->tab, reinterpret_cast<const float2*>(env->pb.R), sc,
+                                       env->ppc_post, st));
+  else
+    LAUNCH(2, launch_stage_post<double>(g, B, env->pb, env->tab, env->pb.R, sc, env->ppc_post, st));
   return CH_OK;
 }
 
@@ -488,19 +541,19 @@ int run_step(ch_env* env, const double* d_action, double* d_out) {
   cudaStream_t st = env->stream;
   std::swap(env->pb.vw_old, env->pb.vw_new);
   if (env->prm.control == 1) {
-    LAUNCH(5, launch_sense(g, B, env->pb, env->tab, env->js, env->prm.alpha, 1, st));
+    LAUNCH(3, launch_sense(g, B, env->pb, env->tab, env->js, env->prm.alpha, 1, st));
   } else {
-    LAUNCH(5, launch_action(g, B, d_action, env->u_tau, env->tab, env->pb.vw_new, st));
+    LAUNCH(3, launch_action(g, B, d_action, env->u_tau, env->tab, env->pb.vw_new, st));
   }
   CK(cudaMemsetAsync(env->pb.tau_acc, 0, B * sizeof(double), st));
   const int spa = env->prm.steps_per_action;
   for (int s = 0; s < spa; ++s) {
     for (int k = 0; k < 3; ++k) RC(run_stage(env, k, (s + kCEnd[k]) / spa));
-    LAUNCH(5, launch_wall_shear(g, B, env->pb.UM, env->nu, env->pb.tau_acc, st));
+    LAUNCH(3, launch_wall_shear(g, B, env->pb.UM, env->nu, env->pb.tau_acc, st));
   }
-  LAUNCH(5, launch_sense(g, B, env->pb, env->tab, env->js, env->prm.alpha, 0, st));
-  LAUNCH(5, launch_obs(g, B, env->pb.planes, env->tab, d_out, env->out_stride, st));
-  LAUNCH(5, launch_finalize(B, env->pb.tau_acc, 1.0 / spa, env->tau_ref, d_out, env->out_stride,
+  LAUNCH(3, launch_sense(g, B, env->pb, env->tab, env->js, env->prm.alpha, 0, st));
+  LAUNCH(3, launch_obs(g, B, env->pb.planes, env->tab, d_out, env->out_stride, st));
+  LAUNCH(3, launch_finalize(B, env->pb.tau_acc, 1.0 / spa, env->tau_ref, d_out, env->out_stride,
                             (size_t)2 * g.nz * g.nx, st));
   env->t += spa * env->prm.dt;
   env->steps += spa;
@@ -572,8 +625,7 @@ int env_create(const ch_params_t* p, ch_env_t** out) {
       (rc = dalloc(env, &pb.HVP, B * ny * P)) || (rc = dalloc(env, &pb.HGP, B * ny * P)) ||
       (rc = dalloc(env, &pb.UM, B * ny)) || (rc = dalloc(env, &pb.WM, B * ny)) ||
       (rc = dalloc(env, &pb.HXP, B * ny)) || (rc = dalloc(env, &pb.HZP, B * ny)) ||
-      (rc = dalloc(env, &pb.C6, B * 6 * ny * P)) || (rc = dalloc(env, &pb.Q, B * 6 * ny * P)) ||
-      (rc = dalloc(env, &pb.R, B * 3 * ny * P)) || (rc = dalloc(env, &pb.HC, B * 3 * ny * P)) ||
+      (rc = dalloc(env, &pb.Q, B * 6 * ny * P)) || (rc = dalloc(env, &pb.R, B * 3 * ny * P)) ||
       (rc = dalloc(env, &pb.vw_old, B * P)) || (rc = dalloc(env, &pb.vw_new, B * P)) ||
       (rc = dalloc(env, &pb.planes, B * 2 * P)) || (rc = dalloc(env, &pb.tau_acc, B)))
     return fail(rc);
@@ -582,6 +634,17 @@ int env_create(const ch_params_t* p, ch_env_t** out) {
     return fail(rc);
   if (cudaMallocHost(&env->h_out, B * env->out_stride * sizeof(double)) != cudaSuccess) return fail(CH_ERR_OOM);
   if ((rc = build_tables(env))) return fail(rc);
+  {
+    int smem_max = 0;
+    if (cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, 0) != cudaSuccess)
+      return fail(CH_ERR_CUDA);
+    env->ppc_post = 8;
+    while (env->ppc_post > 1 && stage_post_smem(g, env->tab.tau.Mh, env->ppc_post) > (size_t)smem_max)
+      env->ppc_post /= 2;
+    env->ppc_pre = 8;
+    while (env->ppc_pre > 1 && stage_pre_smem(g, env->ppc_pre) > (size_t)smem_max) env->ppc_pre /= 2;
+    if (stage_post_smem(g, env->tab.tau.Mh, env->ppc_post) > (size_t)smem_max) return fail(CH_ERR_UNSUPPORTED);
+  }
   // laminar Poiseuille, zero wall action
   std::vector<double> st(ch_state_bytes(p) / sizeof(double), 0.0);
   st[(size_t)4 * ny * P + 0] = 0.75;
@@ -590,7 +653,7 @@ int env_create(const ch_params_t* p, ch_env_t** out) {
     if ((rc = set_state_dev(env, e, st.data()))) return fail(rc);
   if (cudaMemset(pb.vw_old, 0, B * P * sizeof(double2)) != cudaSuccess) return fail(CH_ERR_CUDA);
   if (cudaDeviceSynchronize() != cudaSuccess) return fail(CH_ERR_CUDA);
-  env->launches_per_step = 2 + p->steps_per_action * (3 * 5 + 1) + 3;
+  env->launches_per_step = 2 + p->steps_per_action * (3 * 3 + 1) + 3;
   *out = env;
   return CH_OK;
 }
@@ -689,7 +752,7 @@ int env_info(const ch_env_t* env, ch_info_t* info) {
   info->tau_ref = env->tau_ref;
   info->state_bytes = ch_state_bytes(&env->prm);
   info->device_bytes = env->device_bytes;
-  info->plane_cluster = env->plane.S;
+  info->plane_cluster = env->prm.precision == 1 ? env->plane_f.S : env->plane.S;
   info->launches_per_step = env->launches_per_step;
   return CH_OK;
 }
@@ -697,12 +760,12 @@ int env_info(const ch_env_t* env, ch_info_t* info) {
 int env_profile(ch_env_t* env, int enable) {
   if (!env) return CH_ERR_ARG;
   env->prof = enable != 0;
-  for (int c = 0; c < 6; ++c) env->ev_used[c] = 0;
+  for (int c = 0; c < 4; ++c) env->ev_used[c] = 0;
   return CH_OK;
 }
 
 int env_profile_read(ch_env_t* env, int cls, double* total_ms, int* launches) {
-  if (!env || cls < 0 || cls > 5) return CH_ERR_ARG;
+  if (!env || cls < 0 || cls > 3) return CH_ERR_ARG;
   if (cudaStreamSynchronize(env->stream) != cudaSuccess) return CH_ERR_CUDA;
   double tot = 0.0;
   for (int i = 0; i < env->ev_used[cls]; ++i) {

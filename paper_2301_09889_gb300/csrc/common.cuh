@@ -180,16 +180,18 @@ struct PlaneArgs {
   R scale;             // 1 / (mx mz)
 };
 
-// Per-mode tau tables (device): see the host code that fills them.
+// Per-mode tau tables (device), mode index fastest so that threads owning
+// consecutive modes read consecutive words.  Mh = N/2 + 1.
 struct TauTables {
-  const double* helm;      // [3][2][4][Mh][P]   e, h, b, Q of (D^2 - k^2 - 1/(beta dt nu))
-  const double* helm_isq;  // [3][2][P]          1 / sum Q
-  const double* pois;      // [2][4][Mh][P]      same for (D^2 - k^2)
+  const double* helm;      // [3][2][4][Mh][P]  e, h, b, Q of (D^2 - k^2 - 1/(beta dt nu)) per stage, parity
+  const double* helm_isq;  // [3][2][P]         1 / sum Q
+  const double* pois;      // [2][4][Mh][P]     same for (D^2 - k^2)
   const double* pois_isq;  // [2][P]
-  const double* vh;        // [3][ny][P]         homogeneous v of the influence matrix
-  const double* vh_idv;    // [3][2][P]          1 / sum_{n of parity} n^2 vh_n
-  const double* u1;        // [3][ny]            mean response to unit forcing
-  const double* u1_iflux;  // [3]                1 / int u1 dy
+  const double* vh;        // [3][2][Mh][P]     homogeneous v of the influence matrix, parity-indexed
+  const double* vh_idv;    // [3][2][P]         1 / sum_{n of parity} n^2 vh_n
+  const double* u1;        // [3][Mh]           mean response to unit forcing (even parity)
+  const double* u1_iflux;  // [3]               1 / int u1 dy
+  const double* rowc;      // [3][ny]           tau row constants cA_n, cB_n, cC_n
   int Mh;
 };
 

@@ -13,10 +13,8 @@ cudaError_t launch_plane(const PlaneArgs<R>& a, int B, size_t smem, cudaStream_t
 struct PencilBufs {
   double2 *V, *G, *HVP, *HGP;   // [B][ny][P]
   double *UM, *WM, *HXP, *HZP;  // [B][ny]
-  double2* C6;                  // [B][6][ny][P] coefficients of u, v, w, ox, oy, oz
-  double2* Q;                   // [B][6][ny][P] node values (nonlinear input)
+  double2* Q;                   // [B][6][ny][P] node values of u, v, w, ox, oy, oz (nonlinear input)
   double2* R;                   // [B][3][ny][P] node values of H
-  double2* HC;                  // [B][3][ny][P] coefficients of H
   double2 *vw_old, *vw_new;     // [B][P] wall-velocity spectra
   double2* planes;              // [B][2][P] u, v spectra at the sensing node
   double* tau_acc;              // [B]
@@ -26,18 +24,22 @@ struct DevTables {
   const double* kx;    // [nxh]
   const double* kz;    // [nz]
   const double* cheb;  // [ny][ny] cos(pi j n / N)
+  const float* cheb_f; // the same table in FP32 (mixed precision)
+  const double* dts;   // [ny] T_n'(y_js) at the sensing node
   TauTables tau;
   const double2* tw_nx;  // [nx]
   const double2* tw_nz;  // [nz]
 };
 
-cudaError_t launch_recover(const Grid& g, int B, const PencilBufs& pb, const DevTables& t, cudaStream_t st);
-cudaError_t launch_synth(const Grid& g, int B, const double2* coef, double2* out, const double* cheb,
-                         int nfields, cudaStream_t st);
-cudaError_t launch_analysis(const Grid& g, int B, const double2* nodes, double2* coef, const double* cheb,
-                            int nfields, cudaStream_t st);
-cudaError_t launch_solve(const Grid& g, int B, const PencilBufs& pb, const DevTables& t,
-                         const StageCoef& sc, cudaStream_t st);
+// fused wall-normal halves of a stage (stage.cu); ppc = modes per CTA
+size_t stage_pre_smem(const Grid& g, int ppc);
+size_t stage_post_smem(const Grid& g, int Mh, int ppc);
+template <typename RN>
+cudaError_t launch_stage_pre(const Grid& g, int B, const PencilBufs& pb, const DevTables& t,
+                             typename cpx<RN>::T* q, int ppc, cudaStream_t st);
+template <typename RN>
+cudaError_t launch_stage_post(const Grid& g, int B, const PencilBufs& pb, const DevTables& t,
+                              const typename cpx<RN>::T* h, const StageCoef& sc, int ppc, cudaStream_t st);
 cudaError_t launch_wall_shear(const Grid& g, int B, const double* UM, double nu, double* acc,
                               cudaStream_t st);
 cudaError_t launch_sense(const Grid& g, int B, const PencilBufs& pb, const DevTables& t, int js,

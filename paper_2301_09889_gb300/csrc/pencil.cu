@@ -1,14 +1,6 @@
-// Wall-normal (Chebyshev) work of one Runge-Kutta stage, one thread per
-// (environment, Fourier mode, symmetry class), plus the small kernels of the
-// environment step (action, observation, wall shear, reward).
-//
-// Symmetry classes.  Every wall-normal operator of the velocity-vorticity
-// system (D, D^2, the tau rows, the wall conditions split into sums and
-// differences) maps even Chebyshev coefficients to even ones or to odd ones
-// in a fixed pattern, so a mode splits into two independent halves:
-//   class 0: even v, odd  omega_y  (u, w odd;  omega_x, omega_z even)
-//   class 1: odd  v, even omega_y  (u, w even; omega_x, omega_z odd)
-// One thread owns one half and never exchanges data with the other.
+// The small kernels of the environment step (action, observation, wall shear,
+// reward) and the stateless Chebyshev-tau entry points.  The Runge-Kutta stage
+// itself lives in stage.cu (wall-normal work) and plane.cu (nonlinear term).
 //
 // Chebyshev conventions: f(y) = sum_n a_n T_n(y), nodes y_j = cos(pi j / N).
 // Derivative recurrence (coefficient space): c_m b_m = b_{m+2} + 2 (m+1) a_{m+1}
@@ -18,6 +10,7 @@
 #include "../../include/channel_dns.h"
 #include "common.cuh"
 #include "internal.h"
+#include "warp.cuh"
 
 namespace chdns {
 
@@ -107,337 +100,6 @@ __device__ void tau_factor(int N, int sig, double lam, double* e, double* h, dou
 }
 
 // ---------------------------------------------------------------------------
-// recover: (v, omega_y, U, W) coefficients -> coefficients of
-// u, v, w, omega_x, omega_y, omega_z.
-//   u = (i kx Dv - i kz g)/k^2, w = (i kz Dv + i kx g)/k^2,
-//   omega_x = Dw - i kz v, omega_z = i kx v - Du;  mean mode: u = U, w = W,
-//   omega_x = DW, omega_z = -DU.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) recover_kernel(Grid g, int B, PencilBufs pb, DevTables t) {
-  const int P = g.P, ny = g.ny, N = g.N;
-  const long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  if (tid >= 2L * P * B) return;
-  const int p = (int)(tid % P);
-  const int c = (int)((tid / P) % 2);
-  const int b = (int)(tid / (2L * P));
-  const int row = p / g.nxh, ix = p % g.nxh;
-  const size_t fo = (size_t)b * ny * P + p;
-  double2* out = pb.C6 + (size_t)b * 6 * ny * P + p;  // field f, coefficient n: out[(f*ny + n)*P]
-  auto W6 = [&](int f, int n, double2 v) { out[((size_t)f * ny + n) * P] = v; };
-  const double2 zero = mk(0.0, 0.0);
-
-  if (row == g.nz / 2) {  // Nyquist row: all zero
-    for (int n = N; n >= 0; --n)
-      if ((n & 1) == c)
-        for (int f = 0; f < 6; ++f) W6(f, n, zero);
-    return;
-  }
-  if (p == 0) {
-    // class c: u = U and w = W on parity 1-c, omega_x = DW, omega_z = -DU on parity c
-    const double* U = pb.UM + (size_t)b * ny;
-    const double* Wm = pb.WM + (size_t)b * ny;
-    double du = 0.0, dw = 0.0, unext = 0.0, wnext = 0.0;
-    for (int n = N; n >= 0; --n) {
-      if ((n & 1) == 1 - c) {
-        const double un = U[n], wn = Wm[n];
-        W6(0, n, mk(un, 0.0));
-        W6(1, n, zero);
-        W6(2, n, mk(wn, 0.0));
-        W6(4, n, zero);
-        unext = un;
-        wnext = wn;
-      } else {
-        double t1 = du + 2.0 * (n + 1) * unext;
-        double t2 = dw + 2.0 * (n + 1) * wnext;
-        du = (n == 0) ? 0.5 * t1 : t1;
-        dw = (n == 0) ? 0.5 * t2 : t2;
-        W6(1, n, zero);
-        W6(3, n, mk(dw, 0.0));
-        W6(5, n, mk(-du, 0.0));
-        // u, w, omega_y on this parity belong to the other class
-      }
-    }
-    return;
-  }
-  const double kx = t.kx[ix], kz = t.kz[row];
-  const double ik2 = 1.0 / (kx * kx + kz * kz);
-  double2 dv = zero, d2v = zero, dg = zero, vnext = zero, gnext = zero;
-  for (int n = N; n >= 0; --n) {
-    if ((n & 1) == 1 - c) {
-      // Dv_n from v_{n+1}; g_n lives on this parity
-      const double2 t1 = dv + (2.0 * (n + 1)) * vnext;
-      dv = (n == 0) ? 0.5 * t1 : t1;
-      const double2 gn = pb.G[fo + (size_t)n * P];
-      const double2 u = ik2 * (imul(kx, dv) - imul(kz, gn));
-      const double2 w = ik2 * (imul(kz, dv) + imul(kx, gn));
-      W6(0, n, u);
-      W6(2, n, w);
-      W6(4, n, gn);
-      gnext = gn;
-    } else {
-      // D^2 v_n from Dv_{n+1}; Dg_n from g_{n+1}; v_n lives on this parity
-      const double2 t1 = d2v + (2.0 * (n + 1)) * dv;
-      const double2 t2 = dg + (2.0 * (n + 1)) * gnext;
-      d2v = (n == 0) ? 0.5 * t1 : t1;
-      dg = (n == 0) ? 0.5 * t2 : t2;
-      const double2 vn = pb.V[fo + (size_t)n * P];
-      const double2 du = ik2 * (imul(kx, d2v) - imul(kz, dg));
-      const double2 dw = ik2 * (imul(kz, d2v) + imul(kx, dg));
-      W6(1, n, vn);
-      W6(3, n, dw - imul(kz, vn));
-      W6(5, n, imul(kx, vn) - du);
-      vnext = vn;
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Chebyshev synthesis: node values f_j = sum_n a_n cos(pi n j / N) of
-// `nfields` fields.  cos(pi n (N-j)/N) = (-1)^n cos(pi n j / N), so the even
-// and odd partial sums E_j, O_j give f_j = E + O and f_{N-j} = E - O.
-// CTA: 32 modes x 8 node groups; grid (ceil(P/32), nfields, B).
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) synth_kernel(int ny, int P, int nfields, const double2* coef,
-                                                    double2* out, const double* cheb) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  double2* sc = reinterpret_cast<double2*>(smem_raw);  // [ny][32]
-  const int pl = threadIdx.x % 32, jg = threadIdx.x / 32;
-  const int p0 = blockIdx.x * 32;
-  const size_t fo = ((size_t)blockIdx.z * nfields + blockIdx.y) * ny * P;
-  const double2* src = coef + fo;
-  for (int idx = threadIdx.x; idx < ny * 32; idx += blockDim.x) {
-    const int n = idx / 32, pp = idx % 32;
-    sc[idx] = (p0 + pp < P) ? src[(size_t)n * P + p0 + pp] : mk(0.0, 0.0);
-  }
-  __syncthreads();
-  const int N = ny - 1;
-  const int p = p0 + pl;
-  if (p >= P) return;
-  double2* dst = out + fo + p;
-  for (int j = jg; 2 * j <= N; j += 8) {
-    const double* crow = cheb + (size_t)j * ny;
-    double2 E = mk(0.0, 0.0), O = mk(0.0, 0.0);
-    for (int n = 0; n <= N; n += 2) E = E + crow[n] * sc[n * 32 + pl];
-    for (int n = 1; n <= N; n += 2) O = O + crow[n] * sc[n * 32 + pl];
-    dst[(size_t)j * P] = E + O;
-    if (N - j != j) dst[(size_t)(N - j) * P] = E - O;
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Chebyshev analysis: a_n = 2/(N cb_n) sum_j f_j cos(pi n j / N) / cb_j with
-// cb_0 = cb_N = 2, else 1.  Node pairs (j, N-j) are folded into
-// e_j = (f_j + f_{N-j})/cb_j for even n and o_j = (f_j - f_{N-j})/cb_j for odd n.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) analysis_kernel(int ny, int P, int nfields, const double2* nodes,
-                                                       double2* coef, const double* cheb) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int N = ny - 1;
-  const int H = N / 2 + 1;
-  double2* se = reinterpret_cast<double2*>(smem_raw);  // [H][32]
-  double2* so = se + H * 32;                            // [H][32]
-  const int pl = threadIdx.x % 32, ng = threadIdx.x / 32;
-  const int p0 = blockIdx.x * 32;
-  const size_t fo = ((size_t)blockIdx.z * nfields + blockIdx.y) * ny * P;
-  const double2* src = nodes + fo;
-  for (int idx = threadIdx.x; idx < H * 32; idx += blockDim.x) {
-    const int j = idx / 32, pp = idx % 32;
-    double2 ev = mk(0.0, 0.0), od = mk(0.0, 0.0);
-    if (p0 + pp < P) {
-      const double2 fj = src[(size_t)j * P + p0 + pp];
-      if (N - j != j) {
-        const double2 fm = src[(size_t)(N - j) * P + p0 + pp];
-        const double w = (j == 0) ? 0.5 : 1.0;
-        ev = w * (fj + fm);
-        od = w * (fj - fm);
-      } else {
-        ev = fj;
-      }
-    }
-    se[idx] = ev;
-    so[idx] = od;
-  }
-  __syncthreads();
-  const int p = p0 + pl;
-  if (p >= P) return;
-  double2* dst = coef + fo + p;
-  const double s0 = 2.0 / N;
-  for (int n = ng; n <= N; n += 8) {
-    const double* crow = cheb + (size_t)n * ny;
-    const double2* sv = (n & 1) ? so : se;
-    double2 acc = mk(0.0, 0.0);
-    for (int j = 0; j < H; ++j) acc = acc + crow[j] * sv[j * 32 + pl];
-    const double cbn = (n == 0 || n == N) ? 2.0 : 1.0;
-    dst[(size_t)n * P] = (s0 / cbn) * acc;
-  }
-}
-
-// ---------------------------------------------------------------------------
-// implicit part of one stage: RHS assembly and the tau solves.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(64) solve_kernel(Grid g, int B, PencilBufs pb, DevTables t, StageCoef sc) {
-  const int P = g.P, ny = g.ny, N = g.N;
-  const long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  if (tid >= 2L * P * B) return;
-  const int p = (int)(tid % P);
-  const int c = (int)((tid / P) % 2);
-  const int b = (int)(tid / (2L * P));
-  const int row = p / g.nxh, ix = p % g.nxh;
-  if (row == g.nz / 2) return;  // Nyquist row stays zero
-  const size_t fo = (size_t)b * ny * P + p;
-  const double2* Hx = pb.HC + (size_t)b * 3 * ny * P + p;
-  const double2* Hy = Hx + (size_t)ny * P;
-  const double2* Hz = Hy + (size_t)ny * P;
-  const double ibdn = 1.0 / (sc.beta * sc.dt * sc.nu);
-  const double adn = sc.alpha * sc.dt * sc.nu;
-  const int Mh = t.tau.Mh;
-  double2 rr[kMaxHalf], ff[kMaxHalf];
-  const double2 zero = mk(0.0, 0.0);
-
-  if (p == 0) {
-    // mean flow: class c owns parity c of U and W
-    const int s = c;
-    double* U = pb.UM + (size_t)b * ny;
-    double* Wm = pb.WM + (size_t)b * ny;
-    double* HXP = pb.HXP + (size_t)b * ny;
-    double* HZP = pb.HZP + (size_t)b * ny;
-    double du = 0.0, d2u = 0.0, unext = 0.0, dw = 0.0, d2w = 0.0, wnext = 0.0;
-    double2 rw[kMaxHalf];
-    for (int n = N; n >= 0; --n) {
-      if ((n & 1) != s) {
-        const double t1 = du + 2.0 * (n + 1) * unext;
-        const double t2 = dw + 2.0 * (n + 1) * wnext;
-        du = (n == 0) ? 0.5 * t1 : t1;
-        dw = (n == 0) ? 0.5 * t2 : t2;
-      } else {
-        const double t1 = d2u + 2.0 * (n + 1) * du;
-        const double t2 = d2w + 2.0 * (n + 1) * dw;
-        d2u = (n == 0) ? 0.5 * t1 : t1;
-        d2w = (n == 0) ? 0.5 * t2 : t2;
-        const double un = U[n], wn = Wm[n];
-        const double hx = Hx[(size_t)n * P].x, hz = Hz[(size_t)n * P].x;
-        const double hxp = HXP[n], hzp = HZP[n];
-        HXP[n] = hx;
-        HZP[n] = hz;
-        const double ru = -ibdn * (un + adn * d2u + sc.dt * (sc.gamma * hx + sc.zeta * hxp));
-        const double rwv = -ibdn * (wn + adn * d2w + sc.dt * (sc.gamma * hz + sc.zeta * hzp));
-        rr[(n - s) / 2] = mk(ru, 0.0);
-        rw[(n - s) / 2] = mk(rwv, 0.0);
-        unext = un;
-        wnext = wn;
-      }
-    }
-    const size_t hb = (size_t)((sc.k * 2 + s) * 4) * Mh * P;
-    const TabGlobal T{t.tau.helm + hb, Mh, P};
-    const double isq = t.tau.helm_isq[(size_t)(sc.k * 2 + s) * P];
-    const int M = (N - s) / 2 + 1;
-    tau_solve(N, s, rr, ff, T, isq, zero);
-    if (s == 0) {
-      double flux = 0.0;
-      for (int i = 0; i < M; ++i) {
-        const int n = 2 * i;
-        flux += 2.0 / (1.0 - (double)n * n) * ff[i].x;
-      }
-      const double fc = (sc.flux - flux) * t.tau.u1_iflux[sc.k];
-      for (int i = 0; i < M; ++i) U[2 * i] = ff[i].x + fc * t.tau.u1[(size_t)sc.k * ny + 2 * i];
-    } else {
-      for (int i = 0; i < M; ++i) U[2 * i + 1] = ff[i].x;
-    }
-    tau_solve(N, s, rw, ff, T, isq, zero);
-    for (int i = 0; i < M; ++i) Wm[2 * i + s] = ff[i].x;
-    return;
-  }
-
-  const double kx = t.kx[ix], kz = t.kz[row], k2 = kx * kx + kz * kz;
-  const int sv = c, sg = 1 - c;
-
-  // ---- wall-normal vorticity (parity sg): (D^2 - lam) g^k = r_g, g = 0 at both walls
-  {
-    double2 dg = zero, d2g = zero, gnext = zero;
-    for (int n = N; n >= 0; --n) {
-      if ((n & 1) == sv) {
-        const double2 t1 = dg + (2.0 * (n + 1)) * gnext;
-        dg = (n == 0) ? 0.5 * t1 : t1;
-      } else {
-        const double2 t1 = d2g + (2.0 * (n + 1)) * dg;
-        d2g = (n == 0) ? 0.5 * t1 : t1;
-        const size_t o = fo + (size_t)n * P;
-        const double2 gn = pb.G[o];
-        const double2 hx = Hx[(size_t)n * P], hz = Hz[(size_t)n * P];
-        const double2 hg = imul(kz, hx) - imul(kx, hz);
-        const double2 hgp = pb.HGP[o];
-        pb.HGP[o] = hg;
-        const double2 lap = d2g - k2 * gn;
-        rr[(n - sg) / 2] = (-ibdn) * (gn + adn * lap + sc.dt * (sc.gamma * hg + sc.zeta * hgp));
-        gnext = gn;
-      }
-    }
-    const size_t hb = (size_t)((sc.k * 2 + sg) * 4) * Mh * P + p;
-    const TabGlobal T{t.tau.helm + hb, Mh, P};
-    const double isq = t.tau.helm_isq[(size_t)(sc.k * 2 + sg) * P + p];
-    tau_solve(N, sg, rr, ff, T, isq, zero);
-    const int M = (N - sg) / 2 + 1;
-    for (int i = 0; i < M; ++i) pb.G[fo + (size_t)(2 * i + sg) * P] = ff[i];
-  }
-
-  // ---- wall-normal velocity (parity sv): phi = lap v
-  {
-    double2 dv = zero, d2v = zero, dphi = zero, d2phi = zero, dtt = zero;
-    double2 vnext = zero, phinext = zero, tnext = zero;
-    for (int n = N; n >= 0; --n) {
-      if ((n & 1) == sg) {
-        const double2 t1 = dv + (2.0 * (n + 1)) * vnext;
-        const double2 t2 = dphi + (2.0 * (n + 1)) * phinext;
-        dv = (n == 0) ? 0.5 * t1 : t1;
-        dphi = (n == 0) ? 0.5 * t2 : t2;
-        const double2 hx = Hx[(size_t)n * P], hz = Hz[(size_t)n * P];
-        tnext = imul(kx, hx) + imul(kz, hz);
-      } else {
-        const double2 t0 = dtt + (2.0 * (n + 1)) * tnext;
-        const double2 t1 = d2v + (2.0 * (n + 1)) * dv;
-        const double2 t2 = d2phi + (2.0 * (n + 1)) * dphi;
-        dtt = (n == 0) ? 0.5 * t0 : t0;
-        d2v = (n == 0) ? 0.5 * t1 : t1;
-        d2phi = (n == 0) ? 0.5 * t2 : t2;
-        const size_t o = fo + (size_t)n * P;
-        const double2 vn = pb.V[o];
-        const double2 phin = d2v - k2 * vn;
-        const double2 hv = (-k2) * Hy[(size_t)n * P] - dtt;
-        const double2 hvp = pb.HVP[o];
-        pb.HVP[o] = hv;
-        rr[(n - sv) / 2] =
-            (-ibdn) * (phin + adn * (d2phi - k2 * phin) + sc.dt * (sc.gamma * hv + sc.zeta * hvp));
-        vnext = vn;
-        phinext = phin;
-      }
-    }
-    // phi_p: (D^2 - lam) phi_p = r_phi, phi_p = 0 at both walls
-    const size_t hb = (size_t)((sc.k * 2 + sv) * 4) * Mh * P + p;
-    const TabGlobal TH{t.tau.helm + hb, Mh, P};
-    tau_solve(N, sv, rr, ff, TH, t.tau.helm_isq[(size_t)(sc.k * 2 + sv) * P + p], zero);
-    // v_p: (D^2 - k^2) v_p = phi_p, v_p(+1) = 0, v_p(-1) = v_w
-    const size_t vo = (size_t)b * P + p;
-    const double2 vw = pb.vw_old[vo] + sc.theta * (pb.vw_new[vo] - pb.vw_old[vo]);
-    const double2 s = (sv == 0) ? 0.5 * vw : (-0.5) * vw;
-    const TabGlobal TP{t.tau.pois + (size_t)(sv * 4) * Mh * P + p, Mh, P};
-    tau_solve(N, sv, ff, rr, TP, t.tau.pois_isq[(size_t)sv * P + p], s);
-    // influence-matrix correction: Dv(+-1) = 0
-    const int M = (N - sv) / 2 + 1;
-    double2 dp = zero;
-    for (int i = 0; i < M; ++i) {
-      const int n = 2 * i + sv;
-      dp = dp + (double)(n * n) * rr[i];
-    }
-    const double2 cI = (-t.tau.vh_idv[(size_t)(sc.k * 2 + sv) * P + p]) * dp;
-    const double* vh = t.tau.vh + (size_t)sc.k * ny * P + p;
-    for (int i = 0; i < M; ++i) {
-      const int n = 2 * i + sv;
-      pb.V[fo + (size_t)n * P] = rr[i] + vh[(size_t)n * P] * cI;
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
 // wall shear of the lower wall: tau_w = nu sum_n U_n T_n'(-1), T_n'(-1) = (-1)^(n+1) n^2
 // one warp per environment, fixed summation order
 // ---------------------------------------------------------------------------
@@ -457,44 +119,44 @@ __global__ void wall_shear_kernel(int ny, int B, const double* UM, double nu, do
 // ---------------------------------------------------------------------------
 // sensing plane: Fourier coefficients of u and v at node js (and, for
 // opposition control, the wall spectrum -alpha v(y_s) with the mean removed,
-// paper Sec. 4.1)
+// paper Sec. 4.1).  One warp per mode: v(y_s) = sum_n v_n T_n(y_s),
+// Dv(y_s) = sum_n v_n T_n'(y_s), omega_y(y_s) likewise.
 // ---------------------------------------------------------------------------
-__global__ void sense_kernel(Grid g, int B, PencilBufs pb, DevTables t, int js, double alpha, int opposition) {
-  const int P = g.P, ny = g.ny, N = g.N;
-  const long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  if (tid >= (long)P * B) return;
-  const int p = (int)(tid % P);
-  const int b = (int)(tid / P);
+__global__ void __launch_bounds__(128) sense_kernel(Grid g, int B, PencilBufs pb, DevTables t, int js, double alpha,
+                                                    int opposition) {
+  const int P = g.P, ny = g.ny;
+  const int lane = threadIdx.x & 31;
+  const long wid = (blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5;
+  if (wid >= (long)P * B) return;
+  const int p = (int)(wid % P);
+  const int b = (int)(wid / P);
   const int row = p / g.nxh, ix = p % g.nxh;
   const double* cj = t.cheb + (size_t)js * ny;
   double2 us = mk(0.0, 0.0), vs = mk(0.0, 0.0);
   if (row != g.nz / 2) {
     if (p == 0) {
       double s = 0.0;
-      for (int n = 0; n <= N; ++n) s += cj[n] * pb.UM[(size_t)b * ny + n];
-      us = mk(s, 0.0);
+      for (int n = lane; n < ny; n += 32) s += cj[n] * pb.UM[(size_t)b * ny + n];
+      us = mk(warp_sum(s), 0.0);
     } else {
       const size_t fo = (size_t)b * ny * P + p;
-      double2 d1 = mk(0.0, 0.0), d2 = mk(0.0, 0.0);  // Dv_{n+1}, Dv_{n+2}
-      double2 vnext = mk(0.0, 0.0);
       double2 dvs = mk(0.0, 0.0), gs = mk(0.0, 0.0);
-      for (int n = N; n >= 0; --n) {
-        const double2 tt = d2 + (2.0 * (n + 1)) * vnext;
-        const double2 dn = (n == 0) ? 0.5 * tt : tt;
+      for (int n = lane; n < ny; n += 32) {
         const double2 vn = pb.V[fo + (size_t)n * P];
         const double2 gn = pb.G[fo + (size_t)n * P];
         vs = vs + cj[n] * vn;
         gs = gs + cj[n] * gn;
-        dvs = dvs + cj[n] * dn;
-        d2 = d1;
-        d1 = dn;
-        vnext = vn;
+        dvs = dvs + t.dts[n] * vn;
       }
+      vs = warp_sum2(vs);
+      gs = warp_sum2(gs);
+      dvs = warp_sum2(dvs);
       const double kx = t.kx[ix], kz = t.kz[row];
       const double ik2 = 1.0 / (kx * kx + kz * kz);
       us = ik2 * (imul(kx, dvs) - imul(kz, gs));
     }
   }
+  if (lane != 0) return;
   if (opposition) {
     pb.vw_new[(size_t)b * P + p] = (p == 0) ? mk(0.0, 0.0) : (-alpha) * vs;
   } else {
@@ -505,18 +167,18 @@ __global__ void sense_kernel(Grid g, int B, PencilBufs pb, DevTables t, int js, 
 
 // ---------------------------------------------------------------------------
 // observation planes: unpadded inverse transform of the two sensing-plane
-// spectra, f(x_a, z_b) = Re sum_kz F[kz,0] e^{i kz z} + 2 Re sum_{kx>0} F e^{i(kx x + kz z)}
-// one CTA per (environment, field)
+// spectra, f(x_a, z_b) = Re sum_kz F[kz,0] e^{i kz z} + 2 Re sum_{kx>0} F e^{i(kx x + kz z)}.
+// One CTA per (output row z_b, field, environment).
 // ---------------------------------------------------------------------------
-__global__ void obs_kernel(int nx, int nz, int nxh, const double2* planes, const double2* tw_nx,
-                           const double2* tw_nz, double* out, size_t out_stride) {
+__global__ void __launch_bounds__(128) obs_kernel(int nx, int nz, int nxh, const double2* planes,
+                                                  const double2* tw_nx, const double2* tw_nz, double* out,
+                                                  size_t out_stride) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double2* tmp = reinterpret_cast<double2*>(smem_raw);  // [nz][nxh]
-  const int b = blockIdx.y, f = blockIdx.x;
+  double2* tmp = reinterpret_cast<double2*>(smem_raw);  // [nxh]
+  const int zb = blockIdx.x, f = blockIdx.y, b = blockIdx.z;
   const int P = nz * nxh;
   const double2* F = planes + ((size_t)b * 2 + f) * P;
-  for (int w = threadIdx.x; w < nz * nxh; w += blockDim.x) {
-    const int i = w % nxh, zb = w / nxh;
+  for (int i = threadIdx.x; i < nxh; i += blockDim.x) {
     double2 acc = mk(0.0, 0.0);
     for (int row = 0; row < nz; ++row) {
       if (row == nz / 2) continue;
@@ -525,19 +187,18 @@ __global__ void obs_kernel(int nx, int nz, int nxh, const double2* planes, const
       if (e < 0) e += nz;
       acc = acc + cmul(F[row * nxh + i], tw_nz[e]);
     }
-    tmp[zb * nxh + i] = acc;
+    tmp[i] = acc;
   }
   __syncthreads();
-  double* o = out + (size_t)b * out_stride + (size_t)f * nz * nx;
-  for (int w = threadIdx.x; w < nz * nx; w += blockDim.x) {
-    const int xa = w % nx, zb = w / nx;
+  double* o = out + (size_t)b * out_stride + (size_t)f * nz * nx + (size_t)zb * nx;
+  for (int xa = threadIdx.x; xa < nx; xa += blockDim.x) {
     double s = 0.0;
     for (int i = 1; i < nxh; ++i) {
       const double2 tw = tw_nx[(i * xa) % nx];
-      const double2 v = tmp[zb * nxh + i];
+      const double2 v = tmp[i];
       s += v.x * tw.x - v.y * tw.y;
     }
-    o[(size_t)zb * nx + xa] = tmp[zb * nxh].x + 2.0 * s;
+    o[xa] = tmp[0].x + 2.0 * s;
   }
 }
 
@@ -622,48 +283,6 @@ __global__ void tau_helmholtz_kernel(int ny, int M, const double* lam, const dou
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-cudaError_t launch_recover(const Grid& g, int B, const PencilBufs& pb, const DevTables& t, cudaStream_t st) {
-  const long n = 2L * g.P * B;
-  recover_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(g, B, pb, t);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_synth(const Grid& g, int B, const double2* coef, double2* out, const double* cheb,
-                         int nfields, cudaStream_t st) {
-  const size_t smem = (size_t)g.ny * 32 * sizeof(double2);
-  static bool cfg = false;
-  if (!cfg) {
-    cudaError_t e = cudaFuncSetAttribute(synth_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e != cudaSuccess) return e;
-    cfg = true;
-  }
-  dim3 grid((g.P + 31) / 32, nfields, B);
-  synth_kernel<<<grid, 256, smem, st>>>(g.ny, g.P, nfields, coef, out, cheb);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_analysis(const Grid& g, int B, const double2* nodes, double2* coef, const double* cheb,
-                            int nfields, cudaStream_t st) {
-  const int H = g.N / 2 + 1;
-  const size_t smem = (size_t)2 * H * 32 * sizeof(double2);
-  static bool cfg = false;
-  if (!cfg) {
-    cudaError_t e = cudaFuncSetAttribute(analysis_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e != cudaSuccess) return e;
-    cfg = true;
-  }
-  dim3 grid((g.P + 31) / 32, nfields, B);
-  analysis_kernel<<<grid, 256, smem, st>>>(g.ny, g.P, nfields, nodes, coef, cheb);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_solve(const Grid& g, int B, const PencilBufs& pb, const DevTables& t, const StageCoef& sc,
-                         cudaStream_t st) {
-  const long n = 2L * g.P * B;
-  solve_kernel<<<(unsigned)((n + 63) / 64), 64, 0, st>>>(g, B, pb, t, sc);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_wall_shear(const Grid& g, int B, const double* UM, double nu, double* acc, cudaStream_t st) {
   wall_shear_kernel<<<B, 32, 0, st>>>(g.ny, B, UM, nu, acc);
   return cudaGetLastError();
@@ -671,21 +290,15 @@ cudaError_t launch_wall_shear(const Grid& g, int B, const double* UM, double nu,
 
 cudaError_t launch_sense(const Grid& g, int B, const PencilBufs& pb, const DevTables& t, int js, double alpha,
                          int opposition, cudaStream_t st) {
-  const long n = (long)g.P * B;
-  sense_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(g, B, pb, t, js, alpha, opposition);
+  const long threads = (long)g.P * B * 32;
+  sense_kernel<<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(g, B, pb, t, js, alpha, opposition);
   return cudaGetLastError();
 }
 
 cudaError_t launch_obs(const Grid& g, int B, const double2* planes, const DevTables& t, double* out,
                        size_t out_stride, cudaStream_t st) {
-  const size_t smem = (size_t)g.nz * g.nxh * sizeof(double2);
-  static bool cfg = false;
-  if (!cfg) {
-    cudaError_t e = cudaFuncSetAttribute(obs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e != cudaSuccess) return e;
-    cfg = true;
-  }
-  obs_kernel<<<dim3(2, B), 256, smem, st>>>(g.nx, g.nz, g.nxh, planes, t.tw_nx, t.tw_nz, out, out_stride);
+  const size_t smem = (size_t)g.nxh * sizeof(double2);
+  obs_kernel<<<dim3(g.nz, 2, B), 128, smem, st>>>(g.nx, g.nz, g.nxh, planes, t.tw_nx, t.tw_nz, out, out_stride);
   return cudaGetLastError();
 }
 
