@@ -38,9 +38,23 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-WORKLOAD = dict(nx=64, ny=65, nz=64, lx=2 * math.pi, lz=math.pi, re_tau=180.0, re_bulk=2800.0,
-                dt=0.005, control=1, alpha=1.0, steps_per_action=1, y_sense_plus=15.0)
-WORKLOAD_NAME = "larger channel Re_tau=180, 64x65x64, all FP64, opposition control, 1 RK3 step per env step"
+LARGER = dict(nx=64, ny=65, nz=64, lx=2 * math.pi, lz=math.pi, re_tau=180.0, re_bulk=2800.0,
+              dt=0.005, control=1, alpha=1.0, steps_per_action=1, y_sense_plus=15.0)
+MINIMAL = dict(nx=16, ny=65, nz=16, lx=2.67, lz=0.8, re_tau=180.0, re_bulk=2800.0,
+               dt=0.005, control=0, alpha=1.0, steps_per_action=1, y_sense_plus=15.0)
+# name -> (parameters, batch, precision, description)
+WORKLOADS = {
+    "larger_fp64": (LARGER, 1, 0,
+                    "larger channel Re_tau=180, 64x65x64, all FP64, opposition control, 1 RK3 step per env step"),
+    "larger_mixed": (LARGER, 1, 1,
+                     "larger channel Re_tau=180, 64x65x64, mixed FP32 nonlinear term / FP64 solves, opposition"),
+    "minimal_batch256_mixed": (MINIMAL, 256, 1,
+                               "256 minimal channels 16x65x16 in one launch per kernel, mixed precision, "
+                               "per-step seeded ZNMF Gaussian actions std 0.05 u_tau"),
+}
+DEFAULT_WORKLOAD = "larger_fp64"
+WORKLOAD = LARGER
+WORKLOAD_NAME = WORKLOADS[DEFAULT_WORKLOAD][3]
 METRIC = "env_steps_per_s"
 UNIT = "env-steps/s"
 KERNEL_CLASSES = ("stage_pre", "nonlinear_plane", "stage_post", "per_step")
@@ -58,6 +72,19 @@ def plane_kernel_flops(nx: int, ny: int, nz: int) -> float:
     z = 9 * nxh * 5.0 * mz * math.log2(mz)
     x = 9 * mz * 2.5 * mx * math.log2(mx)
     return ny * (z + x + 9.0 * mx * mz)
+
+
+def kernel_bytes(nx: int, ny: int, nz: int, batch: int, node_bytes: int) -> dict:
+    """Algorithmic HBM bytes of one launch of each stage kernel.
+
+    Per Fourier mode (complex FP64 = 16 B, nodal complex = node_bytes):
+    stage_pre reads v, omega_y and writes the six nodal fields; the plane kernel
+    reads those six and writes the three nodal H fields; stage_post reads H, v,
+    omega_y and the two previous nonlinear terms and writes the last four back."""
+    M = batch * (nx // 2) * ny * nz
+    return {"stage_pre": M * (2 * 16 + 6 * node_bytes),
+            "nonlinear_plane": M * 9 * node_bytes,
+            "stage_post": M * (3 * node_bytes + 8 * 16)}
 
 
 def measured_peaks() -> dict:
@@ -123,22 +150,29 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def oracle_sample(budget_s: float, max_steps: int):
-    """Time the FP64 oracle on the workload: whole environment steps until the budget is spent."""
-    import numpy as np  # noqa: F401
+def oracle_sample(budget_s: float, max_steps: int, workload: str = DEFAULT_WORKLOAD):
+    """Time the FP64 oracle on one environment of the workload: whole
+    environment steps until the budget is spent."""
+    import numpy as np
 
     import seeded_inputs as si
     from oracle import channel
+    prm = WORKLOADS[workload][0]
     keys = ("nx", "ny", "nz", "lx", "lz", "re_tau", "re_bulk", "dt", "steps_per_action",
             "y_sense_plus", "control", "alpha")
-    op = channel.Params(**{k: WORKLOAD[k] for k in keys})
+    op = channel.Params(**{k: prm[k] for k in keys})
     ops = channel.Operators(op)
     st = channel.new_state(si.perturbed_poiseuille(op.nx, op.ny, op.nz, 0, 0.1, 99), op)
+    rng = np.random.default_rng(0)
     times = []
     t_all = time.perf_counter()
     while len(times) < max_steps and (time.perf_counter() - t_all) < budget_s:
+        act = None
+        if op.control == 0:
+            act = rng.standard_normal((op.nz, op.nx)) * 0.05 * op.u_tau
+            act -= act.mean()
         t0 = time.perf_counter()
-        channel.env_step(st, ops)
+        channel.env_step(st, ops, act)
         times.append(time.perf_counter() - t0)
     return times
 
@@ -146,10 +180,11 @@ def oracle_sample(budget_s: float, max_steps: int):
 def run_reference(args, rank: int, world: int):
     if rank != 0:
         return
+    prm, batch, prec, name = WORKLOADS[args.workload]
     budget = float(os.environ.get("CH_REFERENCE_BUDGET_S", "90"))
     for _ in range(min(args.warmup, 1)):
-        oracle_sample(1e9, 1)
-    times = oracle_sample(budget, args.steps)
+        oracle_sample(1e9, 1, args.workload)
+    times = oracle_sample(budget, args.steps, args.workload)
     total = sum(times)
     value = len(times) / total
     cores = os.cpu_count()
@@ -157,9 +192,10 @@ def run_reference(args, rank: int, world: int):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": len(times), "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD_NAME, "parallelism": "replicas"},
+        "data": "synthetic", "config": {"workload": name, "parallelism": "replicas"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{len(times)} whole environment steps of the workload (budget {budget:.0f} s)"},
+                         "sample": f"{len(times)} whole environment steps of one environment of the workload "
+                                   f"(budget {budget:.0f} s)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -171,6 +207,7 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=tuple(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
 
@@ -186,6 +223,7 @@ def main():
 
     from paper_2301_09889_gb300 import native
 
+    prm, B, prec, wname = WORKLOADS[args.workload]
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -194,19 +232,30 @@ def main():
     native.load()
     W = max(3, args.warmup)
     K = args.steps
-    p = native.params(**WORKLOAD)
+    p = native.params(**prm, batch=B, precision=prec)
     env = native.env_create(p)
     info = native.env_info(env)
-    native.env_reset(env, seed=rank, amplitude=0.1, kmax=99)
+    native.env_reset(env, seed=1000 * rank, amplitude=0.1, kmax=99)
     stream = torch.cuda.current_stream()
     native.env_set_stream(env, stream.cuda_stream)
-    nx, ny, nz = WORKLOAD["nx"], WORKLOAD["ny"], WORKLOAD["nz"]
+    nx, ny, nz = prm["nx"], prm["ny"], prm["nz"]
     out_len = 2 * nz * nx + 2
-    d_out = torch.zeros(out_len, dtype=torch.float64, device="cuda")
+    d_out = torch.zeros(B * out_len, dtype=torch.float64, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    external = prm["control"] == 0
+    u_tau = prm["re_tau"] / prm["re_bulk"]
+    n_cycle = 32
+    if external:
+        # seeded zero-net-mass-flux Gaussian wall actions, std 0.05 u_tau, cycled
+        rng = np.random.default_rng(1234 + rank)
+        acts = rng.standard_normal((n_cycle, B, nz, nx)) * 0.05 * u_tau
+        acts -= acts.mean(axis=(2, 3), keepdims=True)
+        d_acts = torch.from_numpy(acts).to("cuda")
+        h_acts = torch.from_numpy(acts).pin_memory()
+    act_ptr = (lambda i: d_acts[i % n_cycle].data_ptr()) if external else (lambda i: None)
 
-    for _ in range(W):
-        native.env_step_device(env, None, d_out.data_ptr())
+    for i in range(W):
+        native.env_step_device(env, act_ptr(i), d_out.data_ptr())
     torch.cuda.synchronize()
 
     # ---- device-resident timed region
@@ -221,13 +270,13 @@ def main():
     for i in range(K):
         flush.zero_()
         starts[i].record(stream)
-        native.env_step_device(env, None, d_out.data_ptr())
+        native.env_step_device(env, act_ptr(i), d_out.data_ptr())
         ends[i].record(stream)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    step_ms = [s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)]
     kern = {}
     for c, name in enumerate(KERNEL_CLASSES):
         ms, n = native.env_profile_read(env, c)
@@ -238,29 +287,30 @@ def main():
         t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    value = K * world / (total_ms * 1e-3)
+    value = K * B * world / (total_ms * 1e-3)
     finite = bool(torch.isfinite(d_out).all().item())
 
-    # ---- end to end through the host-buffer API
+    # ---- end to end through the host-buffer API (pinned host buffers)
     Ke = min(K, 300)
-    obs = np.zeros((2, nz, nx))
-    tau = np.zeros(1)
-    rew = np.zeros(1)
-    for _ in range(3):
-        native.env_step(env, None, obs, tau, rew)
+    obs = torch.zeros((B, 2, nz, nx), dtype=torch.float64).pin_memory().numpy()
+    tau = torch.zeros(B, dtype=torch.float64).pin_memory().numpy()
+    rew = torch.zeros(B, dtype=torch.float64).pin_memory().numpy()
+    hact = (lambda i: h_acts[i % n_cycle].numpy()) if external else (lambda i: None)
+    for i in range(3):
+        native.env_step(env, hact(i), obs, tau, rew)
     e2e_ms = []
-    for _ in range(Ke):
+    for i in range(Ke):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        native.env_step(env, None, obs, tau, rew)
+        native.env_step(env, hact(i), obs, tau, rew)
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
     e2e_total = sum(e2e_ms)
     if dist:
         t = torch.tensor([e2e_total], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_total = float(t.item())
-    e2e_value = Ke * world / (e2e_total * 1e-3)
+    e2e_value = Ke * B * world / (e2e_total * 1e-3)
     native.env_destroy(env)
 
     if rank != 0:
@@ -270,40 +320,60 @@ def main():
 
     # ---- roofline of the dominant kernel
     dom = max(kern, key=lambda k: kern[k]["ms_total"])
-    plane = kern["nonlinear_plane"]
-    avg_plane_s = plane["ms_total"] * 1e-3 / max(plane["launches"], 1)
-    flops = plane_kernel_flops(nx, ny, nz)
-    achieved = flops / avg_plane_s / 1e12
-    roofline = {
-        "kernel": "nonlinear_plane", "dominant_kernel": dom, "bound": "alu", "unit": "TFLOP/s",
-        "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "frac": achieved / FP64_PEAK_TFLOPS,
-        "peak_source": "FP64 FMA rate measured on GB300 by an FMA-chain probe (MEASURED_PEAKS.json has no FP64 figure)",
-        "flops_per_launch": flops, "avg_launch_ms": avg_plane_s * 1e3, "traffic": None,
-    }
+    peaks = measured_peaks()
+    if prec == 0:
+        kk = "nonlinear_plane"
+        avg_s = kern[kk]["ms_total"] * 1e-3 / max(kern[kk]["launches"], 1)
+        flops = B * plane_kernel_flops(nx, ny, nz)
+        achieved = flops / avg_s / 1e12
+        roofline = {
+            "kernel": kk, "dominant_kernel": dom, "bound": "alu", "unit": "TFLOP/s",
+            "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "frac": achieved / FP64_PEAK_TFLOPS,
+            "peak_source": "FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 FLOP x 2.07 GHz "
+                           "(nominal 1.25 TFLOP/s; FMA probe measured 1.19 at 1.96 GHz)",
+            "flops_per_launch": flops, "avg_launch_ms": avg_s * 1e3, "traffic": None,
+        }
+    else:
+        kk = dom
+        avg_s = kern[kk]["ms_total"] * 1e-3 / max(kern[kk]["launches"], 1)
+        nbytes = kernel_bytes(nx, ny, nz, B, 8).get(kk, 0)
+        achieved = nbytes / avg_s / 1e9
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        roofline = {
+            "kernel": kk, "dominant_kernel": dom, "bound": "hbm", "unit": "GB/s",
+            "achieved": achieved, "peak": hbm, "frac": achieved / hbm,
+            "peak_source": "of measured" if "hbm_gbs" in peaks else "of fallback",
+            "bytes_per_launch": nbytes, "avg_launch_ms": avg_s * 1e3, "traffic": None,
+        }
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        times = oracle_sample(float(os.environ.get("CH_CPU_BASELINE_S", "20")), 1000)
+        times = oracle_sample(float(os.environ.get("CH_CPU_BASELINE_S", "20")), 1000, args.workload)
         cpu = {"value": len(times) / sum(times), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"{len(times)} whole environment steps of the workload (about 20 s of CPU work)"}
+               "sample": f"{len(times)} whole environment steps of one environment of the workload "
+                         "(about 20 s of CPU work)"}
 
     srt = sorted(step_ms)
+    step_bytes = sum(v * 3 for v in kernel_bytes(nx, ny, nz, B, 16 if prec == 0 else 8).values())
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_NAME, "grid": [nx, ny, nz], "re_tau": 180.0, "re_bulk": 2800.0,
-                   "dt": 0.005, "control": "opposition alpha=1, sensing node j=%d (y+=%.2f)" % (
-                       info.j_sense, info.y_plus_sense),
+        "dtype": "f64" if prec == 0 else "f32+f64", "data": "synthetic",
+        "config": {"workload": wname, "grid": [nx, ny, nz], "batch": B, "re_tau": prm["re_tau"],
+                   "re_bulk": prm["re_bulk"], "dt": prm["dt"],
+                   "control": ("opposition alpha=1, sensing node j=%d (y+=%.2f)" % (info.j_sense, info.y_plus_sense))
+                   if not external else "external seeded actions",
                    "l2": "flushed between steps (256 MiB write outside the timed events)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "mpts_rk3_steps_per_s": value * nx * ny * nz / 1e6,
         "p50_ms": srt[len(srt) // 2], "p99_ms": srt[min(len(srt) - 1, int(0.99 * len(srt)))],
         "kernels_ms_per_step": {k: v["ms_total"] / K for k, v in kern.items()},
+        "algorithmic_gbs_per_step": step_bytes / (total_ms / K * 1e-3) / 1e9,
         "roofline": roofline,
         "cpu_baseline": cpu,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 0,
-                "d2h_bytes_per_step": 8 * out_len},
+        "e2e": {"value": e2e_value, "unit": UNIT,
+                "h2d_bytes_per_step": 8 * B * nz * nx if external else 0,
+                "d2h_bytes_per_step": 8 * B * out_len},
         "gpu_launches": int(sum(v["launches"] for v in kern.values())),
         "clocks": clk,
         "finite": finite,

@@ -100,11 +100,19 @@ bool fft_plan(int n, FftPlan* pl) {
   return m == 1;
 }
 
+// e^{2 pi i k / n}; exact at multiples of a quarter turn, so that sums of
+// twiddles that cancel in exact arithmetic also cancel in floating point
 std::vector<double2> twiddles(int n) {
   std::vector<double2> t(n);
+  const double qc[4] = {1.0, 0.0, -1.0, 0.0}, qs[4] = {0.0, 1.0, 0.0, -1.0};
   for (int k = 0; k < n; ++k) {
-    const double a = 2.0 * M_PI * (double)k / (double)n;
-    t[k] = make_double2(std::cos(a), std::sin(a));
+    if ((4L * k) % n == 0) {
+      const int q = (int)((4L * k) / n);
+      t[k] = make_double2(qc[q], qs[q]);
+    } else {
+      const double a = 2.0 * M_PI * (double)k / (double)n;
+      t[k] = make_double2(std::cos(a), std::sin(a));
+    }
   }
   return t;
 }
@@ -240,19 +248,38 @@ int setup_plane(ch_env* env, PlaneArgs<R>* a, size_t* smem) {
   a->nxh = g.nxh; a->nz = g.nz; a->ny = g.ny; a->mx = g.mx; a->mz = g.mz; a->P = g.P;
   a->S = 0;
   const size_t csz = sizeof(C);
+  // cluster size: the smallest feasible S whose ny * S CTAs fill the SMs once;
+  // without one, the largest feasible S.  It depends on the grid only, so an
+  // environment gives bit-identical results alone and inside any batch.
+  int nsm = 152;
+  {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+      nsm = v;
+  }
+  int feasible[4], nf = 0;
   for (int S = 1; S <= 8; S *= 2) {
     if (g.mz % S || (g.mz / S) % 2) continue;
-    const int Lz = g.mz / S;
-    const size_t zb = (size_t)6 * Lz * g.nxh * csz;
-    if (zb > 160 * 1024) continue;
-    const int npairs = Lz / 2;
-    int np = 0;
-    for (int d = std::min(npairs, 16); d >= 1; --d)
-      if (npairs % d == 0 && zb + (size_t)6 * d * g.mx * csz <= 220 * 1024) { np = d; break; }
-    if (!np) continue;
+    if ((size_t)6 * (g.mz / S) * g.nxh * csz > 160 * 1024) continue;
+    feasible[nf++] = S;
+  }
+  if (!nf) return CH_ERR_UNSUPPORTED;
+  int S = feasible[nf - 1];
+  for (int k = 0; k < nf; ++k)
+    if ((long)g.ny * feasible[k] >= nsm) { S = feasible[k]; break; }
+  const int Lz = g.mz / S;
+  const size_t zb = (size_t)6 * Lz * g.nxh * csz;
+  const int npairs = Lz / 2;
+  int np = 0;
+  // row pairs per batch: keep two CTAs per SM (<= 100 KB) when possible
+  for (size_t lim : {(size_t)100 * 1024, (size_t)220 * 1024}) {
+    for (int d = std::min(npairs, 16); d >= 1 && !np; --d)
+      if (npairs % d == 0 && zb + (size_t)6 * d * g.mx * csz <= lim) np = d;
+    if (np) break;
+  }
+  if (np) {
     a->S = S; a->Lz = Lz; a->NP = np;
     *smem = zb + (size_t)6 * np * g.mx * csz;
-    break;
   }
   if (!a->S) return CH_ERR_UNSUPPORTED;
   if (!fft_plan(g.mx, &a->px) || !fft_plan(a->Lz, &a->pz)) return CH_ERR_UNSUPPORTED;

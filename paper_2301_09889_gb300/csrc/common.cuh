@@ -159,6 +159,136 @@ __device__ void fft_dit(typename cpx<R>::T* buf, int nlines, int g, const FftPla
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Compile-time FFT plans and stages: the same in-place DIF/DIT passes with
+// the length, the radix of every pass and the line layout fixed at compile
+// time, so that index arithmetic reduces to constant multiplies and shifts.
+// Plan of n = 4^a 2^b 3^c: radices 4, ..., 4, 2, ..., 2, 3, ..., 3.
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int ct_nst(int n) {
+  int s = 0;
+  while (n % 4 == 0) { n /= 4; ++s; }
+  while (n % 2 == 0) { n /= 2; ++s; }
+  while (n % 3 == 0) { n /= 3; ++s; }
+  return s;
+}
+__host__ __device__ constexpr int ct_radix(int n, int st) {
+  int s = 0;
+  while (n % 4 == 0) { if (s == st) return 4; n /= 4; ++s; }
+  while (n % 2 == 0) { if (s == st) return 2; n /= 2; ++s; }
+  while (n % 3 == 0) { if (s == st) return 3; n /= 3; ++s; }
+  return 1;
+}
+// sub-length L before pass st of the DIF order
+__host__ __device__ constexpr int ct_len_before(int n, int st) {
+  int L = n;
+  for (int s = 0; s < st; ++s) L /= ct_radix(n, s);
+  return L;
+}
+
+template <int SIGN, int RADIX, typename C, typename R>
+__device__ __forceinline__ void small_dft_ct(C* x) {
+  if constexpr (RADIX == 2) {
+    C a = x[0], b = x[1];
+    x[0] = a + b;
+    x[1] = a - b;
+  } else if constexpr (RADIX == 3) {
+    const R k = (R)SIGN * (R)0.86602540378443864676372317075293618;
+    C s = x[1] + x[2];
+    C d = x[1] - x[2];
+    C t1 = x[0] - (R)0.5 * s;
+    C rot = imul(k, d);
+    x[0] = x[0] + s;
+    x[1] = t1 + rot;
+    x[2] = t1 - rot;
+  } else {
+    C a0 = x[0] + x[2], a1 = x[0] - x[2];
+    C b0 = x[1] + x[3], b1 = x[1] - x[3];
+    C wb1 = imul((R)SIGN, b1);
+    x[0] = a0 + b0;
+    x[1] = a1 + wb1;
+    x[2] = a0 - b0;
+    x[3] = a1 - wb1;
+  }
+}
+
+// one DIF pass (natural order in, digit-reversed out after all passes)
+template <int SIGN, typename R, int N, int ST, int NLINES, int G, bool BF_FASTEST, int NT>
+__device__ __forceinline__ void dif_pass(typename cpx<R>::T* buf, const typename cpx<R>::T* tw) {
+  using C = typename cpx<R>::T;
+  constexpr int r = ct_radix(N, ST);
+  constexpr int L = ct_len_before(N, ST);
+  constexpr int m = L / r;
+  constexpr int nb = N / r;
+  constexpr int tstep = N / L;
+  constexpr int total = NLINES * nb;
+  for (int w = threadIdx.x; w < total; w += NT) {
+    int l, bf;
+    if (BF_FASTEST) { bf = w % nb; l = w / nb; } else { l = w % NLINES; bf = w / NLINES; }
+    C* base = buf + (l / G) * (N * G) + (l % G);
+    const int blk = bf / m, q = bf % m;
+    const int i0 = blk * L + q;
+    C x[r];
+#pragma unroll
+    for (int t = 0; t < r; ++t) x[t] = base[(i0 + t * m) * G];
+    small_dft_ct<SIGN, r, C, R>(x);
+#pragma unroll
+    for (int u = 0; u < r; ++u) {
+      C y = x[u];
+      if (u > 0 && q > 0) y = cmul(y, twiddle<SIGN>(tw, q * u * tstep));
+      base[(i0 + u * m) * G] = y;
+    }
+  }
+  __syncthreads();
+}
+
+// one DIT pass, passes applied in reverse plan order (digit-reversed in, natural out)
+template <int SIGN, typename R, int N, int ST, int NLINES, int G, bool BF_FASTEST, int NT>
+__device__ __forceinline__ void dit_pass(typename cpx<R>::T* buf, const typename cpx<R>::T* tw) {
+  using C = typename cpx<R>::T;
+  constexpr int r = ct_radix(N, ST);
+  constexpr int m = ct_len_before(N, ST + 1);  // sub-length before this pass in DIT order
+  constexpr int L = m * r;
+  constexpr int nb = N / r;
+  constexpr int tstep = N / L;
+  constexpr int total = NLINES * nb;
+  for (int w = threadIdx.x; w < total; w += NT) {
+    int l, bf;
+    if (BF_FASTEST) { bf = w % nb; l = w / nb; } else { l = w % NLINES; bf = w / NLINES; }
+    C* base = buf + (l / G) * (N * G) + (l % G);
+    const int blk = bf / m, q = bf % m;
+    const int i0 = blk * L + q;
+    C x[r];
+#pragma unroll
+    for (int t = 0; t < r; ++t) {
+      C v = base[(i0 + t * m) * G];
+      if (t > 0 && q > 0) v = cmul(v, twiddle<SIGN>(tw, q * t * tstep));
+      x[t] = v;
+    }
+    small_dft_ct<SIGN, r, C, R>(x);
+#pragma unroll
+    for (int u = 0; u < r; ++u) base[(i0 + u * m) * G] = x[u];
+  }
+  __syncthreads();
+}
+
+template <int SIGN, typename R, int N, int NLINES, int G, bool BF_FASTEST, int NT, int ST = 0>
+__device__ __forceinline__ void fft_dif_ct(typename cpx<R>::T* buf, const typename cpx<R>::T* tw) {
+  if constexpr (ST < ct_nst(N)) {
+    dif_pass<SIGN, R, N, ST, NLINES, G, BF_FASTEST, NT>(buf, tw);
+    fft_dif_ct<SIGN, R, N, NLINES, G, BF_FASTEST, NT, ST + 1>(buf, tw);
+  }
+}
+
+template <int SIGN, typename R, int N, int NLINES, int G, bool BF_FASTEST, int NT, int ST = ct_nst(N) - 1>
+__device__ __forceinline__ void fft_dit_ct(typename cpx<R>::T* buf, const typename cpx<R>::T* tw) {
+  if constexpr (ST >= 0) {
+    dit_pass<SIGN, R, N, ST, NLINES, G, BF_FASTEST, NT>(buf, tw);
+    fft_dit_ct<SIGN, R, N, NLINES, G, BF_FASTEST, NT, ST - 1>(buf, tw);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // launch structs
 // ---------------------------------------------------------------------------

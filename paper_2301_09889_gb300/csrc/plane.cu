@@ -159,13 +159,150 @@ __global__ void __launch_bounds__(256) plane_kernel(PlaneArgs<R> a) {
   if (S > 1) cg::this_cluster().sync();
 }
 
-template <typename R>
-cudaError_t launch_plane(const PlaneArgs<R>& a, int B, size_t smem, cudaStream_t st) {
-  static size_t configured = 0;  // largest dynamic shared memory size enabled so far
-  if (smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(plane_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+
+// The same kernel with the transform lengths, the kept kx count and the row
+// pairs per batch fixed at compile time (index arithmetic by constants, FFT
+// passes unrolled).  Instantiated for the grids of the configurations in use.
+template <typename R, int MX, int LZ, int NXH, int NP>
+__global__ void __launch_bounds__(256) plane_kernel_ct(PlaneArgs<R> a) {
+  using C = typename cpx<R>::T;
+  constexpr int NT = 256;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* Z = reinterpret_cast<C*>(smem_raw);  // [6][LZ][NXH]
+  C* X = Z + 6 * LZ * NXH;                // [6][NP][MX]
+  const int nz = a.nz, mz = a.mz, S = a.S;
+  const int tid = threadIdx.x;
+  int rank = 0;
+  if (S > 1) rank = (int)cg::this_cluster().block_rank();
+  const int j = blockIdx.y;
+  const int b = blockIdx.z;
+  const size_t plane = (size_t)a.P;
+  const C* qb = a.q + (size_t)b * 6 * a.ny * plane + (size_t)j * plane;
+  C* hb = a.h + (size_t)b * 3 * a.ny * plane + (size_t)j * plane;
+
+  // 1. gather + fold + pre-twiddle
+  for (int w = tid; w < 6 * LZ * NXH; w += NT) {
+    const int i = w % NXH;
+    const int t = w / NXH;
+    const int m = t % LZ;
+    const int f = t / LZ;
+    const C* qf = qb + (size_t)f * a.ny * plane;
+    C acc = czero<C>();
+    for (int qq = 0; qq < S; ++qq) {
+      const int u = m + qq * LZ;
+      int kz;
+      if (u < nz / 2) kz = u;
+      else if (u > mz - nz / 2) kz = u - mz;
+      else continue;
+      const int row = kz >= 0 ? kz : nz + kz;
+      C val = qf[row * NXH + i];
+      if (S > 1 && rank > 0) {
+        int e = (kz * rank) % mz;
+        if (e < 0) e += mz;
+        val = cmul(val, a.tw_mz[e]);
+      }
+      acc = acc + val;
+    }
+    Z[(f * LZ + m) * NXH + i] = acc;
+  }
+  __syncthreads();
+  fft_dif_ct<+1, R, LZ, 6 * NXH, NXH, false, NT>(Z, a.tw_z);
+
+  // 2. rows in pairs: x transforms and products
+  constexpr int NPAIRS = LZ / 2;
+  for (int pb = 0; pb < NPAIRS; pb += NP) {
+    for (int w = tid; w < 6 * NP * MX; w += NT) {
+      const int k = w % MX;
+      const int t = w / MX;
+      const int pp = t % NP;
+      const int f = t / NP;
+      const int r1 = 2 * (pb + pp);
+      const C* A = Z + (f * LZ + r1) * NXH;
+      const C* Bv = A + NXH;
+      C val;
+      if (k == 0) {
+        val = mk(A[0].x, Bv[0].x);
+      } else if (k < NXH) {
+        const C av = A[k], bv = Bv[k];
+        val = mk(av.x - bv.y, av.y + bv.x);
+      } else if (k > MX - NXH) {
+        const int kk = MX - k;
+        const C av = A[kk], bv = Bv[kk];
+        val = mk(av.x + bv.y, bv.x - av.y);
+      } else {
+        val = czero<C>();
+      }
+      X[(f * NP + pp) * MX + k] = val;
+    }
+    __syncthreads();
+    fft_dif_ct<+1, R, MX, 6 * NP, 1, true, NT>(X, a.tw_x);
+    for (int w = tid; w < NP * MX; w += NT) {
+      const int x = w % MX;
+      const int pp = w / MX;
+      C* L0 = X + pp * MX;
+      constexpr int fs = NP * MX;
+      const C u = L0[x], v = L0[fs + x], ww = L0[2 * fs + x];
+      const C ox = L0[3 * fs + x], oy = L0[4 * fs + x], oz = L0[5 * fs + x];
+      L0[x] = mk(v.x * oz.x - ww.x * oy.x, v.y * oz.y - ww.y * oy.y);
+      L0[fs + x] = mk(ww.x * ox.x - u.x * oz.x, ww.y * ox.y - u.y * oz.y);
+      L0[2 * fs + x] = mk(u.x * oy.x - v.x * ox.x, u.y * oy.y - v.y * ox.y);
+    }
+    __syncthreads();
+    fft_dit_ct<-1, R, MX, 3 * NP, 1, true, NT>(X, a.tw_x);
+    for (int w = tid; w < 3 * NP * NXH; w += NT) {
+      const int i = w % NXH;
+      const int t = w / NXH;
+      const int pp = t % NP;
+      const int f = t / NP;
+      const C* line = X + (f * NP + pp) * MX;
+      const C zk = line[i];
+      const C zm = line[(MX - i) % MX];
+      const int r1 = 2 * (pb + pp);
+      Z[(f * LZ + r1) * NXH + i] = mk((zk.x + zm.x) * (R)0.5, (zk.y - zm.y) * (R)0.5);
+      Z[(f * LZ + r1 + 1) * NXH + i] = mk((zk.y + zm.y) * (R)0.5, (zm.x - zk.x) * (R)0.5);
+    }
+    __syncthreads();
+  }
+
+  // 3. forward z transform of H_x, H_y, H_z and cluster combination
+  fft_dit_ct<-1, R, LZ, 3 * NXH, NXH, false, NT>(Z, a.tw_z);
+  if (S > 1) cg::this_cluster().sync();
+  for (int w = tid; w < 3 * nz * NXH; w += NT) {
+    const int i = w % NXH;
+    const int t = w / NXH;
+    const int row = t % nz;
+    const int f = t / nz;
+    if (S > 1 && (row % S) != rank) continue;
+    C out = czero<C>();
+    if (row != nz / 2) {
+      const int kz = row < nz / 2 ? row : row - nz;
+      int u = kz % LZ;
+      if (u < 0) u += LZ;
+      for (int rr = 0; rr < S; ++rr) {
+        const C* Zr = Z;
+        if (S > 1 && rr != rank) Zr = cg::this_cluster().map_shared_rank(Z, rr);
+        C gval = Zr[(f * LZ + u) * NXH + i];
+        if (S > 1 && rr > 0) {
+          int e = (-kz * rr) % mz;
+          if (e < 0) e += mz;
+          gval = cmul(gval, a.tw_mz[e]);
+        }
+        out = out + gval;
+      }
+      out = a.scale * out;
+    }
+    hb[(size_t)f * a.ny * plane + row * NXH + i] = out;
+  }
+  if (S > 1) cg::this_cluster().sync();
+}
+
+template <typename K, typename R>
+static cudaError_t launch_with(K kernel, const PlaneArgs<R>& a, int B, size_t smem, cudaStream_t st,
+                               size_t* configured) {
+  if (smem > *configured) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    configured = smem;
+    *configured = smem;
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(a.S, a.ny, B);
@@ -179,7 +316,33 @@ cudaError_t launch_plane(const PlaneArgs<R>& a, int B, size_t smem, cudaStream_t
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = a.S > 1 ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, plane_kernel<R>, a);
+  return cudaLaunchKernelEx(&cfg, kernel, a);
+}
+
+// compile-time instantiations: (MX, LZ, NXH, NP) of the grids in use
+#define CH_PLANE_CT(MX_, LZ_, NXH_, NP_)                                                              \
+  if (a.mx == MX_ && a.Lz == LZ_ && a.nxh == NXH_ && a.NP == NP_) {                                  \
+    static size_t cfg_ = 0;                                                                           \
+    return launch_with(plane_kernel_ct<R, MX_, LZ_, NXH_, NP_>, a, B, smem, st, &cfg_);               \
+  }
+
+template <typename R>
+cudaError_t launch_plane(const PlaneArgs<R>& a, int B, size_t smem, cudaStream_t st) {
+  if constexpr (sizeof(R) == 8) {
+    CH_PLANE_CT(24, 6, 8, 3)
+    CH_PLANE_CT(24, 24, 8, 12)
+    CH_PLANE_CT(96, 24, 32, 3)
+    CH_PLANE_CT(48, 12, 16, 6)
+    CH_PLANE_CT(192, 24, 64, 4)
+  } else {
+    CH_PLANE_CT(24, 6, 8, 3)
+    CH_PLANE_CT(24, 24, 8, 12)
+    CH_PLANE_CT(96, 24, 32, 12)
+    CH_PLANE_CT(48, 12, 16, 6)
+    CH_PLANE_CT(192, 48, 64, 8)
+  }
+  static size_t cfg_generic = 0;
+  return launch_with(plane_kernel<R>, a, B, smem, st, &cfg_generic);
 }
 
 template cudaError_t launch_plane<double>(const PlaneArgs<double>&, int, size_t, cudaStream_t);
