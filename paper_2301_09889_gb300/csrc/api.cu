@@ -248,9 +248,10 @@ int setup_plane(ch_env* env, PlaneArgs<R>* a, size_t* smem) {
   a->nxh = g.nxh; a->nz = g.nz; a->ny = g.ny; a->mx = g.mx; a->mz = g.mz; a->P = g.P;
   a->S = 0;
   const size_t csz = sizeof(C);
-  // cluster size: the smallest feasible S whose ny * S CTAs fill the SMs once;
-  // without one, the largest feasible S.  It depends on the grid only, so an
-  // environment gives bit-identical results alone and inside any batch.
+  // cluster size: the smallest feasible S whose ny * B * S CTAs fill the SMs
+  // once; without one, the largest feasible S.  Handles of the same grid and
+  // batch capacity give bit-identical results; other capacities may split the
+  // planes differently and agree to rounding.
   int nsm = 152;
   {
     int dev = 0, v = 0;
@@ -266,7 +267,7 @@ int setup_plane(ch_env* env, PlaneArgs<R>* a, size_t* smem) {
   if (!nf) return CH_ERR_UNSUPPORTED;
   int S = feasible[nf - 1];
   for (int k = 0; k < nf; ++k)
-    if ((long)g.ny * feasible[k] >= nsm) { S = feasible[k]; break; }
+    if ((long)g.ny * env->B * feasible[k] >= nsm) { S = feasible[k]; break; }
   const int Lz = g.mz / S;
   const size_t zb = (size_t)6 * Lz * g.nxh * csz;
   const int npairs = Lz / 2;

@@ -208,31 +208,33 @@ __global__ void __launch_bounds__(128) stage_pre_kernel(Grid g, int B, PencilBuf
         }
       }
     } else {
-      const double kx = t.kx[ix], kz = t.kz[row];
-      const double sg = (r == 0) ? -1.0 : 1.0;
-      const double ik2 = sg / (kx * kx + kz * kz);
+      // derivative chains and u, w, omega in the node precision (the nonlinear
+      // term's arithmetic; FP32 in mixed mode)
+      const RN kx = (RN)t.kx[ix], kz = (RN)t.kz[row];
+      const RN sg = (r == 0) ? (RN)-1.0 : (RN)1.0;
+      const RN ik2 = sg / (kx * kx + kz * kz);
       const CompS V{reinterpret_cast<double*>(sV) + 2 * pl + r, 2 * ppc};
       const CompS Va{reinterpret_cast<double*>(sV) + 2 * pl + (1 - r), 2 * ppc};
       const CompS G{reinterpret_cast<double*>(sG) + 2 * pl + r, 2 * ppc};
       const CompS Ga{reinterpret_cast<double*>(sG) + 2 * pl + (1 - r), 2 * ppc};
-      double dv = 0.0, d2v = 0.0, dg = 0.0, vnext = 0.0, gnext = 0.0;
+      RN dv = 0, d2v = 0, dg = 0, vnext = 0, gnext = 0;
       for (int n = N; n >= 0; --n) {
         if ((n & 1) == 1 - c) {
-          const double t1 = dv + 2.0 * (n + 1) * vnext;
-          dv = (n == 0) ? 0.5 * t1 : t1;
-          const double ga = Ga[n];
+          const RN t1 = dv + (RN)(2 * (n + 1)) * vnext;
+          dv = (n == 0) ? (RN)0.5 * t1 : t1;
+          const RN ga = (RN)Ga[n];
           W(0, n, ik2 * (kx * dv - kz * ga));  // u
           W(2, n, ik2 * (kz * dv + kx * ga));  // w
           W(4, n, G[n]);                       // omega_y
           gnext = ga;
         } else {
-          const double t1 = d2v + 2.0 * (n + 1) * dv;
-          const double t2 = dg + 2.0 * (n + 1) * gnext;
-          d2v = (n == 0) ? 0.5 * t1 : t1;
-          dg = (n == 0) ? 0.5 * t2 : t2;
-          const double va = Va[n];
-          const double du = ik2 * (kx * d2v - kz * dg);
-          const double dw = ik2 * (kz * d2v + kx * dg);
+          const RN t1 = d2v + (RN)(2 * (n + 1)) * dv;
+          const RN t2 = dg + (RN)(2 * (n + 1)) * gnext;
+          d2v = (n == 0) ? (RN)0.5 * t1 : t1;
+          dg = (n == 0) ? (RN)0.5 * t2 : t2;
+          const RN va = (RN)Va[n];
+          const RN du = ik2 * (kx * d2v - kz * dg);
+          const RN dw = ik2 * (kz * d2v + kx * dg);
           W(1, n, V[n]);                 // v
           W(3, n, dw - sg * kz * va);    // omega_x = Dw - i kz v
           W(5, n, sg * kx * va - du);    // omega_z = i kx v - Du
@@ -243,23 +245,58 @@ __global__ void __launch_bounds__(128) stage_pre_kernel(Grid g, int B, PencilBuf
   }
   __syncthreads();
 
-  // synthesis of the six fields at the nodes
-  const int J = N / 2 + 1;
-  for (int w = tid; w < 6 * J * ppc; w += nt) {
-    const int pl = w % ppc;
-    const int tt = w / ppc;
-    const int j = tt % J;
-    const int f = tt / J;
-    const int p = p0 + pl;
-    if (p >= P) continue;
-    const RN* crow = cheb_table<RN>(t) + (size_t)j * ny;
-    const CN* col = sC + (size_t)f * ny * ppc + pl;
-    CN E = czero<CN>(), O = czero<CN>();
-    for (int n = 0; n <= N; n += 2) E = E + crow[n] * col[n * ppc];
-    for (int n = 1; n <= N; n += 2) O = O + crow[n] * col[n * ppc];
-    CN* dst = q + ((size_t)(b * 6 + f) * ny) * P + p;
-    dst[(size_t)j * P] = E + O;
-    if (N - j != j) dst[(size_t)(N - j) * P] = E - O;
+  // synthesis of the six fields at the nodes.  Thread (mode pl, group g of
+  // nt / ppc) evaluates the node pairs j = g, g + ng, ... of all six fields of
+  // its mode: each coefficient it loads feeds all of its outputs, which are
+  // independent accumulation chains.
+  {
+    constexpr int KJ = (MH + 15) / 16;  // node pairs per thread (ng = nt / ppc >= 16)
+    const int ng = nt / ppc;
+    const int pl = tid % ppc, gq = tid / ppc;
+    const int J = N / 2 + 1;
+    const RN* cheb = cheb_table<RN>(t);
+    if (gq < ng) {
+      CN E[6][KJ], O[6][KJ];
+#pragma unroll
+      for (int f = 0; f < 6; ++f)
+#pragma unroll
+        for (int k = 0; k < KJ; ++k) {
+          E[f][k] = czero<CN>();
+          O[f][k] = czero<CN>();
+        }
+      const CN* col = sC + pl;
+      for (int n = 0; n <= N; ++n) {
+        CN cf[6];
+#pragma unroll
+        for (int f = 0; f < 6; ++f) cf[f] = col[((size_t)f * ny + n) * ppc];
+#pragma unroll
+        for (int k = 0; k < KJ; ++k) {
+          const int j = gq + ng * k;
+          const RN c = cheb[(size_t)min(j, N) * ny + n];
+          if (n & 1) {
+#pragma unroll
+            for (int f = 0; f < 6; ++f) O[f][k] = O[f][k] + c * cf[f];
+          } else {
+#pragma unroll
+            for (int f = 0; f < 6; ++f) E[f][k] = E[f][k] + c * cf[f];
+          }
+        }
+      }
+      const int p = p0 + pl;
+      if (p < P) {
+#pragma unroll
+        for (int k = 0; k < KJ; ++k) {
+          const int j = gq + ng * k;
+          if (j >= J) continue;
+#pragma unroll
+          for (int f = 0; f < 6; ++f) {
+            CN* dst = q + ((size_t)(b * 6 + f) * ny) * P + p;
+            dst[(size_t)j * P] = E[f][k] + O[f][k];
+            if (N - j != j) dst[(size_t)(N - j) * P] = E[f][k] - O[f][k];
+          }
+        }
+      }
+    }
   }
 }
 
@@ -342,32 +379,57 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
 
   // ---- Chebyshev analysis of H_x, H_y, H_z (in place after a barrier)
   {
-    constexpr int ITEMS = (3 * 2 * MH + 7) / 8;  // items per thread when blockDim = 8 ppc
-    double2 acc[ITEMS];
-    const int H = N / 2;  // pairs (j, N-j) with j < N - j are j = 0..(N-1)/2
+    // Thread (mode pl, group g of 8) computes the coefficients n = g, g+8, ...
+    // of the three fields of its mode: every pair f_j, f_{N-j} it loads feeds
+    // all of its outputs, and the outputs are independent accumulation chains.
+    // n and g share their parity, so the folding sign is fixed per thread.
+    constexpr int KN = (2 * MH + 7) / 8;  // n values per thread
+    const int pl = tid % ppc, gq = tid / ppc;  // blockDim = 8 ppc
+    const RN* cheb = cheb_table<RN>(t);
+    const RN sg = (gq & 1) ? (RN)-1.0 : (RN)1.0;
+    CN a[3][KN];
+    const CN* colf[3];
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+      colf[f] = sN + (size_t)f * ny * ppc + pl;
+      const CN w0 = (RN)0.5 * (colf[f][0] + sg * colf[f][N * ppc]);  // j = 0 and j = N weigh 1/2
+#pragma unroll
+      for (int k = 0; k < KN; ++k) a[f][k] = w0;
+    }
+    for (int j = 1; 2 * j < N; ++j) {
+      CN fold[3];
+#pragma unroll
+      for (int f = 0; f < 3; ++f) fold[f] = colf[f][j * ppc] + sg * colf[f][(N - j) * ppc];
+#pragma unroll
+      for (int k = 0; k < KN; ++k) {
+        const int n = gq + 8 * k;
+        const RN c = cheb[(size_t)min(n, N) * ny + j];
+#pragma unroll
+        for (int f = 0; f < 3; ++f) a[f][k] = a[f][k] + c * fold[f];
+      }
+    }
+    double2 acc[3][KN];
     const RN s0 = (RN)2.0 / (RN)N;
 #pragma unroll
-    for (int it = 0; it < ITEMS; ++it) {
-      const int w = tid + it * nt;
-      acc[it] = mk(0.0, 0.0);
-      if (w < 3 * ny * ppc) {
-        const int pl = w % ppc, fn = w / ppc;
-        const int n = fn % ny, f = fn / ny;
-        const CN* col = sN + (size_t)f * ny * ppc + pl;
-        const RN* crow = cheb_table<RN>(t) + (size_t)n * ny;
-        const RN sgn = (n & 1) ? (RN)-1.0 : (RN)1.0;
-        CN a = (RN)0.5 * (col[0] + sgn * col[N * ppc]);  // j = 0 and j = N carry weight 1/2
-        for (int j = 1; 2 * j < N; ++j) a = a + crow[j] * (col[j * ppc] + sgn * col[(N - j) * ppc]);
-        if ((N & 1) == 0) a = a + crow[H] * col[H * ppc];
-        const RN cbn = (n == 0 || n == N) ? (RN)2.0 : (RN)1.0;
-        acc[it] = to_double((s0 / cbn) * a);
+    for (int k = 0; k < KN; ++k) {
+      const int n = gq + 8 * k;
+      const RN cbn = (n == 0 || n == N) ? (RN)2.0 : (RN)1.0;
+      const RN cH = ((N & 1) == 0) ? cheb[(size_t)min(n, N) * ny + N / 2] : (RN)0.0;
+#pragma unroll
+      for (int f = 0; f < 3; ++f) {
+        CN v = a[f][k];
+        if ((N & 1) == 0) v = v + cH * colf[f][(N / 2) * ppc];
+        acc[f][k] = to_double((s0 / cbn) * v);
       }
     }
     __syncthreads();
 #pragma unroll
-    for (int it = 0; it < ITEMS; ++it) {
-      const int w = tid + it * nt;
-      if (w < 3 * ny * ppc) sH[w] = acc[it];
+    for (int k = 0; k < KN; ++k) {
+      const int n = gq + 8 * k;
+      if (n <= N) {
+#pragma unroll
+        for (int f = 0; f < 3; ++f) sH[((size_t)f * ny + n) * ppc + pl] = acc[f][k];
+      }
     }
     __syncthreads();
   }
