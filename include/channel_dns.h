@@ -58,6 +58,7 @@ extern "C" {
 #define CH_ERR_STATE      -6   /* call not valid in the handle's state       */
 #define CH_ERR_CUDA       -7   /* a CUDA runtime call failed                 */
 #define CH_ERR_UNSUPPORTED -8  /* parameter combination not built            */
+#define CH_PENDING         1   /* srv_poll: request not finished yet (not an error) */
 
 /* ---- parameters ---------------------------------------------------------- */
 typedef struct ch_params {
@@ -121,8 +122,9 @@ int env_reset(ch_env_t* env, uint64_t seed, double amplitude, int kmax);
  *   obs        [B][2][nz][nx] u and v on the sensing plane after the steps;
  *   wall_shear [B] nu dU/dy at the lower wall averaged over the steps;
  *   reward     [B] 1 - wall_shear / tau_ref (Sec. 3.2).
- * Synchronises the stream.  Returns CH_ERR_DIVERGED if any wall shear is not
- * finite (outputs are still written). */
+ * Synchronises the stream.  Returns CH_ERR_ARG without doing any work if the
+ * action holds a non-finite value, and CH_ERR_DIVERGED if any wall shear is
+ * not finite (outputs are still written). */
 int env_step(ch_env_t* env, const double* action, double* obs,
              double* wall_shear, double* reward);
 
@@ -187,6 +189,66 @@ int ch_seed_state(const ch_params_t* p, uint64_t seed, double amplitude, int kma
 
 /* Host only: bytes of one serialised state for these parameters. */
 size_t ch_state_bytes(const ch_params_t* p);
+
+/* ---- serving: continuous batching of env steps from many actors ---------
+ * Environments are grouped into classes by their parameters (everything in
+ * ch_params_t except `batch`).  Each class owns one batched handle with
+ * `slots_per_class` slots and its own CUDA stream.  A worker thread runs
+ * ticks: for each idle class it takes the oldest pending request of every
+ * environment and advances exactly those slots in one masked batched step;
+ * ticks of different classes overlap on the device and requests arriving
+ * during a tick join the next one.  A slot's result does not depend on the
+ * other slots, so an environment steps identically alone and in any mix.
+ * All srv_* functions are thread-safe. */
+typedef struct ch_server ch_server_t;
+
+typedef struct ch_srv_stats {
+    uint64_t completed;      /* requests completed since creation / last reset   */
+    double p50_us, p99_us, mean_us, max_us;  /* submit -> completion latency       */
+    double env_steps_per_s;  /* completed / wall time since creation / last reset */
+    int classes, envs, pending;
+    size_t hbm_used, hbm_budget;  /* device bytes held by the class handles      */
+    int worker_status;       /* last CUDA error seen by the worker (CH_OK if none) */
+} ch_srv_stats_t;
+
+/* Server with a device-memory budget for its class handles.  No GPU work yet. */
+int srv_create(size_t hbm_budget_bytes, int slots_per_class, ch_server_t** out);
+
+/* Admit one environment with the env_reset initial state (seed, amplitude,
+ * kmax).  Uses a free slot of its class; otherwise creates the class, which
+ * fails with CH_ERR_BUDGET if its footprint does not fit the budget (retry
+ * after srv_evict).  Writes the environment id. */
+int srv_admit(ch_server_t* s, const ch_params_t* p, uint64_t seed, double amplitude, int kmax, int* env_id);
+
+/* Remove an environment; its queued requests complete with CH_ERR_STATE.  A
+ * class with no environment left releases its device memory. */
+int srv_evict(ch_server_t* s, int env_id);
+
+/* Queue one env_step (action [nz][nx], copied before return; NULL under
+ * opposition control; a non-finite value is rejected with CH_ERR_ARG).
+ * Requests of one environment run in submission order. */
+int srv_submit(ch_server_t* s, int env_id, const double* action, uint64_t* req_id);
+
+/* Result of a request: CH_PENDING while it runs; otherwise its status, with
+ * obs [2][nz][nx], wall shear, reward and the submit-to-completion latency
+ * written (any output pointer may be NULL) and the request released. */
+int srv_poll(ch_server_t* s, uint64_t req_id, double* obs, double* wall_shear, double* reward,
+             double* latency_us);
+
+/* srv_poll that waits up to timeout_ms; CH_ERR_TIMEOUT if still running. */
+int srv_wait(ch_server_t* s, uint64_t req_id, int timeout_ms, double* obs, double* wall_shear,
+             double* reward, double* latency_us);
+
+/* State of an admitted environment (layout of env_get_state); waits for
+ * its class to be idle.  srv_set_state requires no queued request. */
+int srv_get_state(ch_server_t* s, int env_id, void* buf, size_t nbytes);
+int srv_set_state(ch_server_t* s, int env_id, const void* buf, size_t nbytes);
+
+/* Latency percentiles and throughput; reset != 0 restarts the counters. */
+int srv_stats(ch_server_t* s, ch_srv_stats_t* stats, int reset);
+
+/* Stop the worker, wait for running ticks, release all device memory. */
+int srv_destroy(ch_server_t* s);
 
 /* ---- single stages, exposed for unit checks ---------------------------- */
 

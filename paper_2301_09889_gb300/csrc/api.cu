@@ -179,7 +179,7 @@ struct ch_env {
   size_t out_stride = 0;
   std::vector<void*> allocs;
   size_t device_bytes = 0;
-  double t = 0.0, steps = 0.0;
+  std::vector<double> t, steps;  // per slot
   int js = 0;
   double nu = 0, u_tau = 0, tau_ref = 0;
   int launches_per_step = 0;
@@ -493,8 +493,8 @@ int set_state_dev(ch_env* env, int e, const double* buf) {
   CK(cudaMemsetAsync(env->pb.HXP + (size_t)e * ny, 0, ny * sizeof(double), st));
   CK(cudaMemsetAsync(env->pb.HZP + (size_t)e * ny, 0, ny * sizeof(double), st));
   CK(cudaStreamSynchronize(st));
-  env->t = tail[0];
-  env->steps = tail[1];
+  env->t[e] = tail[0];
+  env->steps[e] = tail[1];
   return CH_OK;
 }
 
@@ -563,32 +563,69 @@ int run_stage(ch_env* env, int k, double theta) {
   return CH_OK;
 }
 
-int run_step(ch_env* env, const double* d_action, double* d_out) {
+// One environment step of every slot flagged in `h_active` (nullptr: all);
+// `d_active` is the same mask on the device.
+int run_step(ch_env* env, const double* d_action, double* d_out, const int* d_active = nullptr,
+             const int* h_active = nullptr) {
   const Grid& g = env->g;
   const int B = env->B;
   cudaStream_t st = env->stream;
-  std::swap(env->pb.vw_old, env->pb.vw_new);
+  env->pb.active = d_active;
+  env->plane.active = d_active;
+  env->plane_f.active = d_active;
+  struct Reset {
+    ch_env* e;
+    ~Reset() { e->pb.active = nullptr; e->plane.active = nullptr; e->plane_f.active = nullptr; }
+  } reset{env};
   if (env->prm.control == 1) {
     LAUNCH(3, launch_sense(g, B, env->pb, env->tab, env->js, env->prm.alpha, 1, st));
   } else {
-    LAUNCH(3, launch_action(g, B, d_action, env->u_tau, env->tab, env->pb.vw_new, st));
+    LAUNCH(3, launch_action(g, B, d_action, env->u_tau, env->tab, env->pb, st));
   }
-  CK(cudaMemsetAsync(env->pb.tau_acc, 0, B * sizeof(double), st));
   const int spa = env->prm.steps_per_action;
   for (int s = 0; s < spa; ++s) {
     for (int k = 0; k < 3; ++k) RC(run_stage(env, k, (s + kCEnd[k]) / spa));
-    LAUNCH(3, launch_wall_shear(g, B, env->pb.UM, env->nu, env->pb.tau_acc, st));
+    LAUNCH(3, launch_wall_shear(g, B, env->pb.UM, env->nu, env->pb.tau_acc, d_active, st));
   }
   LAUNCH(3, launch_sense(g, B, env->pb, env->tab, env->js, env->prm.alpha, 0, st));
-  LAUNCH(3, launch_obs(g, B, env->pb.planes, env->tab, d_out, env->out_stride, st));
+  LAUNCH(3, launch_obs(g, B, env->pb.planes, env->tab, d_out, env->out_stride, d_active, st));
   LAUNCH(3, launch_finalize(B, env->pb.tau_acc, 1.0 / spa, env->tau_ref, d_out, env->out_stride,
-                            (size_t)2 * g.nz * g.nx, st));
-  env->t += spa * env->prm.dt;
-  env->steps += spa;
+                            (size_t)2 * g.nz * g.nx, d_active, st));
+  for (int b = 0; b < B; ++b) {
+    if (h_active && !h_active[b]) continue;
+    env->t[b] += spa * env->prm.dt;
+    env->steps[b] += spa;
+  }
   return CH_OK;
 }
 
 }  // namespace
+
+namespace chdns {
+// internal entry points used by the serving layer (serve.cu)
+int step_masked(ch_env* env, const double* d_action, const int* d_active, const int* h_active) {
+  return run_step(env, d_action, env->d_out, d_active, h_active);
+}
+double* env_dout(ch_env* env) { return env->d_out; }
+double* env_dact(ch_env* env) { return env->d_act; }
+size_t env_out_stride(const ch_env* env) { return env->out_stride; }
+cudaStream_t env_stream(const ch_env* env) { return env->stream; }
+int env_slot_seed(ch_env* env, int e, uint64_t seed, double amplitude, int kmax) {
+  std::vector<double> st(ch_state_bytes(&env->prm) / sizeof(double));
+  fill_seed_state(&env->prm, seed, amplitude, kmax, st.data());
+  return set_state_dev(env, e, st.data());
+}
+// device bytes env_create allocates for these parameters (tables and buffers)
+size_t env_footprint(const ch_params_t* p) {
+  const size_t B = p->batch > 0 ? p->batch : 1;
+  const size_t nxh = p->nx / 2, P = nxh * p->nz, ny = p->ny, Mh = (ny - 1) / 2 + 1;
+  const size_t state = B * (4 * ny * P * 16 + 4 * ny * 8 + 9 * ny * P * 16 + 3 * P * 16 + 8 +
+                            (size_t)p->nz * p->nx * 8 + (2 * (size_t)p->nz * p->nx + 2) * 8);
+  const size_t tables = (3 * 2 * 4 * Mh * P + 3 * 2 * P + 2 * 4 * Mh * P + 2 * P + 3 * 2 * Mh * P + 3 * 2 * P +
+                         3 * Mh + 3 + 3 * ny + ny) * 8 + ny * ny * 12 + (nxh + p->nz) * 8;
+  return state + tables + ((size_t)4 << 20);  // plus twiddles and rounding slack
+}
+}  // namespace chdns
 
 extern "C" {
 
@@ -643,6 +680,8 @@ int env_create(const ch_params_t* p, ch_env_t** out) {
   env->u_tau = p->re_tau / p->re_bulk;
   env->tau_ref = p->tau_ref > 0 ? p->tau_ref : env->u_tau * env->u_tau;
   env->js = sensing_node(g.N, p->re_tau, p->y_sense_plus);
+  env->t.assign(env->B, 0.0);
+  env->steps.assign(env->B, 0.0);
   int rc = CH_OK;
   auto fail = [&](int code) { free_env(env); return code; };
   if (cudaStreamCreateWithFlags(&env->own_stream, cudaStreamNonBlocking) != cudaSuccess) return fail(CH_ERR_CUDA);
@@ -680,6 +719,7 @@ int env_create(const ch_params_t* p, ch_env_t** out) {
   for (int e = 0; e < env->B; ++e)
     if ((rc = set_state_dev(env, e, st.data()))) return fail(rc);
   if (cudaMemset(pb.vw_old, 0, B * P * sizeof(double2)) != cudaSuccess) return fail(CH_ERR_CUDA);
+  if (cudaMemset(pb.tau_acc, 0, B * sizeof(double)) != cudaSuccess) return fail(CH_ERR_CUDA);
   if (cudaDeviceSynchronize() != cudaSuccess) return fail(CH_ERR_CUDA);
   env->launches_per_step = 2 + p->steps_per_action * (3 * 3 + 1) + 3;
   *out = env;
@@ -708,8 +748,6 @@ int env_reset(ch_env_t* env, uint64_t seed, double amplitude, int kmax) {
     fill_seed_state(&env->prm, seed + (uint64_t)e, amplitude, kmax, st.data());
     RC(set_state_dev(env, e, st.data()));
   }
-  env->t = 0.0;
-  env->steps = 0.0;
   return CH_OK;
 }
 
@@ -731,8 +769,8 @@ int env_get_state(ch_env_t* env, int e, void* buf, size_t nbytes) {
   CK(cudaMemcpyAsync(W, env->pb.WM + (size_t)e * ny, ny * sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(vw, env->pb.vw_new + (size_t)e * P, P * sizeof(double2), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  tail[0] = env->t;
-  tail[1] = env->steps;
+  tail[0] = env->t[e];
+  tail[1] = env->steps[e];
   return CH_OK;
 }
 
@@ -754,8 +792,11 @@ int env_step(ch_env_t* env, const double* action, double* obs, double* wall_shea
   const Grid& g = env->g;
   const size_t B = env->B, plane = (size_t)g.nz * g.nx;
   cudaStream_t st = env->stream;
-  if (env->prm.control == 0)
+  if (env->prm.control == 0) {
+    for (size_t i = 0; i < B * plane; ++i)
+      if (!std::isfinite(action[i])) return CH_ERR_ARG;  // poisoned action: reject before any work
     CK(cudaMemcpyAsync(env->d_act, action, B * plane * sizeof(double), cudaMemcpyHostToDevice, st));
+  }
   RC(run_step(env, env->d_act, env->d_out));
   CK(cudaMemcpyAsync(env->h_out, env->d_out, B * env->out_stride * sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));

@@ -308,6 +308,7 @@ struct PlaneArgs {
   const C* tw_mz;      // [mz]  e^{2 pi i k / mz}
   FftPlan px, pz;
   R scale;             // 1 / (mx mz)
+  const int* active;   // [B] slots to process (nullptr: all)
 };
 
 // Per-mode tau tables (device), mode index fastest so that threads owning

@@ -18,6 +18,7 @@ struct PencilBufs {
   double2 *vw_old, *vw_new;     // [B][P] wall-velocity spectra
   double2* planes;              // [B][2][P] u, v spectra at the sensing node
   double* tau_acc;              // [B]
+  const int* active;            // [B] slots advanced by this step (nullptr: all)
 };
 
 struct DevTables {
@@ -41,16 +42,28 @@ template <typename RN>
 cudaError_t launch_stage_post(const Grid& g, int B, const PencilBufs& pb, const DevTables& t,
                               const typename cpx<RN>::T* h, const StageCoef& sc, int ppc, cudaStream_t st);
 cudaError_t launch_wall_shear(const Grid& g, int B, const double* UM, double nu, double* acc,
-                              cudaStream_t st);
+                              const int* active, cudaStream_t st);
 cudaError_t launch_sense(const Grid& g, int B, const PencilBufs& pb, const DevTables& t, int js,
                          double alpha, int opposition, cudaStream_t st);
 cudaError_t launch_obs(const Grid& g, int B, const double2* planes, const DevTables& t, double* out,
-                       size_t out_stride, cudaStream_t st);
+                       size_t out_stride, const int* active, cudaStream_t st);
 cudaError_t launch_action(const Grid& g, int B, const double* act, double u_tau, const DevTables& t,
-                          double2* vw, cudaStream_t st);
+                          const PencilBufs& pb, cudaStream_t st);
 cudaError_t launch_finalize(int B, const double* acc, double inv_steps, double tau_ref, double* out,
-                            size_t out_stride, size_t out_offset, cudaStream_t st);
+                            size_t out_stride, size_t out_offset, const int* active, cudaStream_t st);
 cudaError_t launch_tau_helmholtz(int ny, int M, const double* lam, const double2* r, const double2* top,
                                  const double2* bot, double2* f, cudaStream_t st);
 
+}  // namespace chdns
+
+struct ch_env;
+namespace chdns {
+// internal entry points of api.cu used by the serving layer
+int step_masked(ch_env* env, const double* d_action, const int* d_active, const int* h_active);
+double* env_dout(ch_env* env);
+double* env_dact(ch_env* env);
+size_t env_out_stride(const ch_env* env);
+cudaStream_t env_stream(const ch_env* env);
+int env_slot_seed(ch_env* env, int e, uint64_t seed, double amplitude, int kmax);
+size_t env_footprint(const struct ch_params* p);
 }  // namespace chdns

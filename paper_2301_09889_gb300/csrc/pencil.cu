@@ -103,9 +103,9 @@ __device__ void tau_factor(int N, int sig, double lam, double* e, double* h, dou
 // wall shear of the lower wall: tau_w = nu sum_n U_n T_n'(-1), T_n'(-1) = (-1)^(n+1) n^2
 // one warp per environment, fixed summation order
 // ---------------------------------------------------------------------------
-__global__ void wall_shear_kernel(int ny, int B, const double* UM, double nu, double* acc) {
+__global__ void wall_shear_kernel(int ny, int B, const double* UM, double nu, double* acc, const int* active) {
   const int b = blockIdx.x;
-  if (b >= B) return;
+  if (b >= B || (active && !active[b])) return;
   const int lane = threadIdx.x;
   double s = 0.0;
   for (int n = lane; n < ny; n += 32) {
@@ -130,6 +130,7 @@ __global__ void __launch_bounds__(128) sense_kernel(Grid g, int B, PencilBufs pb
   if (wid >= (long)P * B) return;
   const int p = (int)(wid % P);
   const int b = (int)(wid / P);
+  if (pb.active && !pb.active[b]) return;
   const int row = p / g.nxh, ix = p % g.nxh;
   const double* cj = t.cheb + (size_t)js * ny;
   double2 us = mk(0.0, 0.0), vs = mk(0.0, 0.0);
@@ -158,7 +159,12 @@ __global__ void __launch_bounds__(128) sense_kernel(Grid g, int B, PencilBufs pb
   }
   if (lane != 0) return;
   if (opposition) {
-    pb.vw_new[(size_t)b * P + p] = (p == 0) ? mk(0.0, 0.0) : (-alpha) * vs;
+    // new action: the previous one becomes the start of the ramp, the wall
+    // shear average restarts
+    const size_t o = (size_t)b * P + p;
+    pb.vw_old[o] = pb.vw_new[o];
+    pb.vw_new[o] = (p == 0) ? mk(0.0, 0.0) : (-alpha) * vs;
+    if (p == 0) pb.tau_acc[b] = 0.0;
   } else {
     pb.planes[((size_t)b * 2 + 0) * P + p] = us;
     pb.planes[((size_t)b * 2 + 1) * P + p] = vs;
@@ -172,10 +178,11 @@ __global__ void __launch_bounds__(128) sense_kernel(Grid g, int B, PencilBufs pb
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(128) obs_kernel(int nx, int nz, int nxh, const double2* planes,
                                                   const double2* tw_nx, const double2* tw_nz, double* out,
-                                                  size_t out_stride) {
+                                                  size_t out_stride, const int* active) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2* tmp = reinterpret_cast<double2*>(smem_raw);  // [nxh]
   const int zb = blockIdx.x, f = blockIdx.y, b = blockIdx.z;
+  if (active && !active[b]) return;
   const int P = nz * nxh;
   const double2* F = planes + ((size_t)b * 2 + f) * P;
   for (int i = threadIdx.x; i < nxh; i += blockDim.x) {
@@ -208,12 +215,18 @@ __global__ void __launch_bounds__(128) obs_kernel(int nx, int nz, int nxh, const
 // mode and the Nyquist row are zero.  One CTA per environment.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) action_kernel(int nx, int nz, int nxh, const double* act, double u_tau,
-                                                     const double2* tw_nx, const double2* tw_nz, double2* vw) {
+                                                     const double2* tw_nx, const double2* tw_nz, double2* vw_old,
+                                                     double2* vw, double* acc, const int* active) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* a = reinterpret_cast<double*>(smem_raw);          // [nz][nx]
   double2* tx = reinterpret_cast<double2*>(a + nz * nx);    // [nz][nxh]
   __shared__ double red[256];
   const int b = blockIdx.x;
+  if (active && !active[b]) return;
+  // the previous action becomes the start of the ramp; the wall-shear average restarts
+  for (int w = threadIdx.x; w < nz * nxh; w += blockDim.x)
+    vw_old[(size_t)b * nz * nxh + w] = vw[(size_t)b * nz * nxh + w];
+  if (threadIdx.x == 0) acc[b] = 0.0;
   const double* src = act + (size_t)b * nz * nx;
   double s = 0.0;
   for (int w = threadIdx.x; w < nz * nx; w += blockDim.x) {
@@ -255,9 +268,9 @@ __global__ void __launch_bounds__(256) action_kernel(int nx, int nz, int nxh, co
 }
 
 __global__ void finalize_kernel(int B, const double* acc, double inv_steps, double tau_ref, double* out,
-                                size_t out_stride, size_t out_offset) {
+                                size_t out_stride, size_t out_offset, const int* active) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= B) return;
+  if (b >= B || (active && !active[b])) return;
   const double tau = acc[b] * inv_steps;
   out[(size_t)b * out_stride + out_offset] = tau;
   out[(size_t)b * out_stride + out_offset + 1] = 1.0 - tau / tau_ref;
@@ -283,8 +296,9 @@ __global__ void tau_helmholtz_kernel(int ny, int M, const double* lam, const dou
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-cudaError_t launch_wall_shear(const Grid& g, int B, const double* UM, double nu, double* acc, cudaStream_t st) {
-  wall_shear_kernel<<<B, 32, 0, st>>>(g.ny, B, UM, nu, acc);
+cudaError_t launch_wall_shear(const Grid& g, int B, const double* UM, double nu, double* acc, const int* active,
+                              cudaStream_t st) {
+  wall_shear_kernel<<<B, 32, 0, st>>>(g.ny, B, UM, nu, acc, active);
   return cudaGetLastError();
 }
 
@@ -296,14 +310,15 @@ cudaError_t launch_sense(const Grid& g, int B, const PencilBufs& pb, const DevTa
 }
 
 cudaError_t launch_obs(const Grid& g, int B, const double2* planes, const DevTables& t, double* out,
-                       size_t out_stride, cudaStream_t st) {
+                       size_t out_stride, const int* active, cudaStream_t st) {
   const size_t smem = (size_t)g.nxh * sizeof(double2);
-  obs_kernel<<<dim3(g.nz, 2, B), 128, smem, st>>>(g.nx, g.nz, g.nxh, planes, t.tw_nx, t.tw_nz, out, out_stride);
+  obs_kernel<<<dim3(g.nz, 2, B), 128, smem, st>>>(g.nx, g.nz, g.nxh, planes, t.tw_nx, t.tw_nz, out, out_stride,
+                                                   active);
   return cudaGetLastError();
 }
 
-cudaError_t launch_action(const Grid& g, int B, const double* act, double u_tau, const DevTables& t, double2* vw,
-                          cudaStream_t st) {
+cudaError_t launch_action(const Grid& g, int B, const double* act, double u_tau, const DevTables& t,
+                          const PencilBufs& pb, cudaStream_t st) {
   const size_t smem = (size_t)g.nz * g.nx * sizeof(double) + (size_t)g.nz * g.nxh * sizeof(double2);
   static bool cfg = false;
   if (!cfg) {
@@ -311,13 +326,14 @@ cudaError_t launch_action(const Grid& g, int B, const double* act, double u_tau,
     if (e != cudaSuccess) return e;
     cfg = true;
   }
-  action_kernel<<<B, 256, smem, st>>>(g.nx, g.nz, g.nxh, act, u_tau, t.tw_nx, t.tw_nz, vw);
+  action_kernel<<<B, 256, smem, st>>>(g.nx, g.nz, g.nxh, act, u_tau, t.tw_nx, t.tw_nz, pb.vw_old, pb.vw_new,
+                                      pb.tau_acc, pb.active);
   return cudaGetLastError();
 }
 
 cudaError_t launch_finalize(int B, const double* acc, double inv_steps, double tau_ref, double* out,
-                            size_t out_stride, size_t out_offset, cudaStream_t st) {
-  finalize_kernel<<<(B + 127) / 128, 128, 0, st>>>(B, acc, inv_steps, tau_ref, out, out_stride, out_offset);
+                            size_t out_stride, size_t out_offset, const int* active, cudaStream_t st) {
+  finalize_kernel<<<(B + 127) / 128, 128, 0, st>>>(B, acc, inv_steps, tau_ref, out, out_stride, out_offset, active);
   return cudaGetLastError();
 }
 

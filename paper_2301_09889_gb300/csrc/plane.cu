@@ -38,6 +38,7 @@ __global__ void __launch_bounds__(256) plane_kernel(PlaneArgs<R> a) {
   if (S > 1) rank = (int)cg::this_cluster().block_rank();
   const int j = blockIdx.y;
   const int b = blockIdx.z;
+  if (a.active && !a.active[b]) return;  // whole cluster (same b) returns together
   const size_t plane = (size_t)a.P;
   const C* qb = a.q + (size_t)b * 6 * a.ny * plane + (size_t)j * plane;
   C* hb = a.h + (size_t)b * 3 * a.ny * plane + (size_t)j * plane;
@@ -176,6 +177,7 @@ __global__ void __launch_bounds__(256) plane_kernel_ct(PlaneArgs<R> a) {
   if (S > 1) rank = (int)cg::this_cluster().block_rank();
   const int j = blockIdx.y;
   const int b = blockIdx.z;
+  if (a.active && !a.active[b]) return;  // whole cluster (same b) returns together
   const size_t plane = (size_t)a.P;
   const C* qb = a.q + (size_t)b * 6 * a.ny * plane + (size_t)j * plane;
   C* hb = a.h + (size_t)b * 3 * a.ny * plane + (size_t)j * plane;

@@ -163,6 +163,7 @@ __global__ void __launch_bounds__(128) stage_pre_kernel(Grid g, int B, PencilBuf
   CN* sC = reinterpret_cast<CN*>(sG + ny * ppc);        // [6][ny][ppc] in the node precision
   const int p0 = blockIdx.x * ppc;
   const int b = blockIdx.y;
+  if (pb.active && !pb.active[b]) return;
   const int tid = threadIdx.x, nt = blockDim.x;
 
   for (int w = tid; w < ny * ppc; w += nt) {
@@ -337,6 +338,7 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
   double* ss = svh + 2 * Mh * ppc;                           // helm_isq, pois_isq, vh_idv [3][2][ppc]
   const int p0 = blockIdx.x * ppc;
   const int b = blockIdx.y;
+  if (pb.active && !pb.active[b]) return;
   const int tid = threadIdx.x, nt = blockDim.x;
 
   // ---- load the tile

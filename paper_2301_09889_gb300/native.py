@@ -32,7 +32,10 @@ EXPORTS = (
     "env_step_device", "env_get_state", "env_set_state", "env_info", "env_destroy",
     "ch_strerror", "ch_seed_state", "ch_state_bytes", "ch_nonlinear", "ch_tau_helmholtz",
     "env_profile", "env_profile_read", "ch_tau_helmholtz_noalloc",
+    "srv_create", "srv_admit", "srv_evict", "srv_submit", "srv_poll", "srv_wait", "srv_get_state",
+    "srv_set_state", "srv_stats", "srv_destroy",
 )
+CH_PENDING = 1
 
 
 class ChParams(ctypes.Structure):
@@ -58,6 +61,18 @@ class ChInfo(ctypes.Structure):
         ("device_bytes", ctypes.c_size_t),
         ("plane_cluster", ctypes.c_int),
         ("launches_per_step", ctypes.c_int),
+    ]
+
+
+class ChSrvStats(ctypes.Structure):
+    _fields_ = [
+        ("completed", ctypes.c_uint64),
+        ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double),
+        ("mean_us", ctypes.c_double), ("max_us", ctypes.c_double),
+        ("env_steps_per_s", ctypes.c_double),
+        ("classes", ctypes.c_int), ("envs", ctypes.c_int), ("pending", ctypes.c_int),
+        ("hbm_used", ctypes.c_size_t), ("hbm_budget", ctypes.c_size_t),
+        ("worker_status", ctypes.c_int),
     ]
 
 
@@ -100,6 +115,17 @@ def load() -> ctypes.CDLL:
         "ch_tau_helmholtz": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp, vp]),
         "ch_tau_helmholtz_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp, vp]),
         "env_profile": (ctypes.c_int, [vp, ctypes.c_int]),
+        "srv_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, P(vp)]),
+        "srv_admit": (ctypes.c_int, [vp, P(ChParams), ctypes.c_uint64, ctypes.c_double, ctypes.c_int,
+                                     P(ctypes.c_int)]),
+        "srv_evict": (ctypes.c_int, [vp, ctypes.c_int]),
+        "srv_submit": (ctypes.c_int, [vp, ctypes.c_int, dp, P(ctypes.c_uint64)]),
+        "srv_poll": (ctypes.c_int, [vp, ctypes.c_uint64, dp, dp, dp, dp]),
+        "srv_wait": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.c_int, dp, dp, dp, dp]),
+        "srv_get_state": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_size_t]),
+        "srv_set_state": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_size_t]),
+        "srv_stats": (ctypes.c_int, [vp, P(ChSrvStats), ctypes.c_int]),
+        "srv_destroy": (ctypes.c_int, [vp]),
         "env_profile_read": (ctypes.c_int, [vp, ctypes.c_int, P(ctypes.c_double), P(ctypes.c_int)]),
     }
     for name, (res, args) in sig.items():
@@ -274,3 +300,70 @@ def ch_tau_helmholtz_noalloc(ny: int, M: int, d_lam: int, d_r: int, d_top: int, 
                                            ctypes.c_void_p(d_top), ctypes.c_void_p(d_bot),
                                            ctypes.c_void_p(d_f), ctypes.c_void_p(stream or 0)),
            "ch_tau_helmholtz_noalloc")
+
+
+# --------------------------------------------------------------------------
+# serving
+# --------------------------------------------------------------------------
+
+def srv_create(hbm_budget_bytes: int, slots_per_class: int) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(load().srv_create(hbm_budget_bytes, slots_per_class, ctypes.byref(h)), "srv_create")
+    return h
+
+
+def srv_admit(srv, p: ChParams, seed: int, amplitude: float = 0.1, kmax: int = 4) -> int:
+    eid = ctypes.c_int()
+    _check(load().srv_admit(srv, ctypes.byref(p), seed, amplitude, kmax, ctypes.byref(eid)), "srv_admit")
+    return eid.value
+
+
+def srv_evict(srv, env_id: int):
+    _check(load().srv_evict(srv, env_id), "srv_evict")
+
+
+def srv_submit(srv, env_id: int, action: np.ndarray | None) -> int:
+    rid = ctypes.c_uint64()
+    a = None if action is None else np.ascontiguousarray(action, dtype=np.float64)
+    _check(load().srv_submit(srv, env_id, _dptr(a), ctypes.byref(rid)), "srv_submit")
+    return rid.value
+
+
+def _result_bufs(obs_shape):
+    return (np.zeros(obs_shape), ctypes.c_double(), ctypes.c_double(), ctypes.c_double())
+
+
+def srv_poll(srv, req_id: int, obs: np.ndarray):
+    """(status, wall_shear, reward, latency_us); status CH_PENDING while running."""
+    tau, rew, lat = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    rc = load().srv_poll(srv, req_id, _dptr(obs), ctypes.byref(tau), ctypes.byref(rew), ctypes.byref(lat))
+    return rc, tau.value, rew.value, lat.value
+
+
+def srv_wait(srv, req_id: int, timeout_ms: int, obs: np.ndarray):
+    """(status, wall_shear, reward, latency_us); CH_ERR_TIMEOUT if still running."""
+    tau, rew, lat = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    rc = load().srv_wait(srv, req_id, timeout_ms, _dptr(obs), ctypes.byref(tau), ctypes.byref(rew),
+                         ctypes.byref(lat))
+    return rc, tau.value, rew.value, lat.value
+
+
+def srv_get_state(srv, env_id: int, nbytes: int) -> np.ndarray:
+    buf = np.zeros(nbytes // 8)
+    _check(load().srv_get_state(srv, env_id, buf.ctypes.data, buf.nbytes), "srv_get_state")
+    return buf
+
+
+def srv_set_state(srv, env_id: int, buf: np.ndarray):
+    buf = np.ascontiguousarray(buf, dtype=np.float64)
+    _check(load().srv_set_state(srv, env_id, buf.ctypes.data, buf.nbytes), "srv_set_state")
+
+
+def srv_stats(srv, reset: bool = False) -> ChSrvStats:
+    st = ChSrvStats()
+    _check(load().srv_stats(srv, ctypes.byref(st), 1 if reset else 0), "srv_stats")
+    return st
+
+
+def srv_destroy(srv):
+    _check(load().srv_destroy(srv), "srv_destroy")
