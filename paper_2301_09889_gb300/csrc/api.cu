@@ -721,7 +721,7 @@ int env_create(const ch_params_t* p, ch_env_t** out) {
   if (cudaMemset(pb.vw_old, 0, B * P * sizeof(double2)) != cudaSuccess) return fail(CH_ERR_CUDA);
   if (cudaMemset(pb.tau_acc, 0, B * sizeof(double)) != cudaSuccess) return fail(CH_ERR_CUDA);
   if (cudaDeviceSynchronize() != cudaSuccess) return fail(CH_ERR_CUDA);
-  env->launches_per_step = 2 + p->steps_per_action * (3 * 3 + 1) + 3;
+  env->launches_per_step = (p->control == 0 ? 2 : 1) + p->steps_per_action * (3 * 3 + 1) + 3;
   *out = env;
   return CH_OK;
 }

@@ -210,60 +210,57 @@ __global__ void __launch_bounds__(128) obs_kernel(int nx, int nz, int nxh, const
 }
 
 // ---------------------------------------------------------------------------
-// wall action -> wall spectrum: clip to [-u_tau, u_tau], remove the plane
-// mean (zero net mass flux), forward transform of the kept modes; the mean
-// mode and the Nyquist row are zero.  One CTA per environment.
+// wall action -> wall spectrum: clip to [-u_tau, u_tau] (paper Sec. 3.2),
+// forward transform of the kept modes; the mean mode (zero net mass flux,
+// Sec. 4.1) and the Nyquist row are zero.  Removing the plane mean before the
+// transform changes only the mean mode, which is set to zero, so it is not
+// computed.  Two passes through a scratch plane tx[b][z][kx]:
+//   action_x_kernel: one CTA per (wall row z, environment): x transform of the
+//                    clipped row; also starts the new action (the previous
+//                    spectrum becomes the start of the ramp, the wall-shear
+//                    average restarts);
+//   action_z_kernel: one CTA per (output kz row, environment): z transform.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) action_kernel(int nx, int nz, int nxh, const double* act, double u_tau,
-                                                     const double2* tw_nx, const double2* tw_nz, double2* vw_old,
-                                                     double2* vw, double* acc, const int* active) {
+__global__ void __launch_bounds__(128) action_x_kernel(int nx, int nz, int nxh, const double* act, double u_tau,
+                                                       const double2* tw_nx, double2* tx, double2* vw_old,
+                                                       const double2* vw, double* acc, const int* active) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* a = reinterpret_cast<double*>(smem_raw);          // [nz][nx]
-  double2* tx = reinterpret_cast<double2*>(a + nz * nx);    // [nz][nxh]
-  __shared__ double red[256];
-  const int b = blockIdx.x;
+  double* a = reinterpret_cast<double*>(smem_raw);  // [nx]
+  const int zb = blockIdx.x, b = blockIdx.y;
   if (active && !active[b]) return;
-  // the previous action becomes the start of the ramp; the wall-shear average restarts
-  for (int w = threadIdx.x; w < nz * nxh; w += blockDim.x)
-    vw_old[(size_t)b * nz * nxh + w] = vw[(size_t)b * nz * nxh + w];
-  if (threadIdx.x == 0) acc[b] = 0.0;
-  const double* src = act + (size_t)b * nz * nx;
-  double s = 0.0;
-  for (int w = threadIdx.x; w < nz * nx; w += blockDim.x) {
-    const double v = fmin(fmax(src[w], -u_tau), u_tau);
-    a[w] = v;
-    s += v;
+  const size_t P = (size_t)nz * nxh;
+  if (zb == 0) {
+    for (size_t w = threadIdx.x; w < P; w += blockDim.x) vw_old[b * P + w] = vw[b * P + w];
+    if (threadIdx.x == 0) acc[b] = 0.0;
   }
-  red[threadIdx.x] = s;
+  const double* src = act + ((size_t)b * nz + zb) * nx;
+  for (int xa = threadIdx.x; xa < nx; xa += blockDim.x) a[xa] = fmin(fmax(src[xa], -u_tau), u_tau);
   __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
+  for (int i = threadIdx.x; i < nxh; i += blockDim.x) {
+    double2 s = mk(0.0, 0.0);
+    for (int xa = 0; xa < nx; ++xa) s = s + a[xa] * cconj(tw_nx[(i * xa) % nx]);
+    tx[b * P + (size_t)zb * nxh + i] = s;
   }
-  const double mean = red[0] / (double)(nz * nx);
-  for (int w = threadIdx.x; w < nz * nx; w += blockDim.x) a[w] -= mean;
-  __syncthreads();
-  for (int w = threadIdx.x; w < nz * nxh; w += blockDim.x) {
-    const int i = w % nxh, zb = w / nxh;
-    double2 acc = mk(0.0, 0.0);
-    for (int xa = 0; xa < nx; ++xa) acc = acc + a[zb * nx + xa] * cconj(tw_nx[(i * xa) % nx]);
-    tx[zb * nxh + i] = acc;
-  }
-  __syncthreads();
-  const double sc = 1.0 / (double)(nx * nz);
-  for (int w = threadIdx.x; w < nz * nxh; w += blockDim.x) {
-    const int i = w % nxh, row = w / nxh;
-    double2 acc = mk(0.0, 0.0);
-    if (row != nz / 2 && w != 0) {
-      const int m = row < nz / 2 ? row : row - nz;
+}
+
+__global__ void __launch_bounds__(128) action_z_kernel(int nx, int nz, int nxh, const double2* tx,
+                                                       const double2* tw_nz, double2* vw, const int* active) {
+  const int row = blockIdx.x, b = blockIdx.y;
+  if (active && !active[b]) return;
+  const size_t P = (size_t)nz * nxh;
+  const double sc = 1.0 / ((double)nx * nz);
+  const int m = row < nz / 2 ? row : row - nz;
+  for (int i = threadIdx.x; i < nxh; i += blockDim.x) {
+    double2 s = mk(0.0, 0.0);
+    if (row != nz / 2 && !(row == 0 && i == 0)) {
       for (int zb = 0; zb < nz; ++zb) {
         int e = (m * zb) % nz;
         if (e < 0) e += nz;
-        acc = acc + cmul(tx[zb * nxh + i], cconj(tw_nz[e]));
+        s = s + cmul(tx[b * P + (size_t)zb * nxh + i], cconj(tw_nz[e]));
       }
-      acc = sc * acc;
+      s = sc * s;
     }
-    vw[(size_t)b * nz * nxh + w] = acc;
+    vw[b * P + (size_t)row * nxh + i] = s;
   }
 }
 
@@ -319,15 +316,13 @@ cudaError_t launch_obs(const Grid& g, int B, const double2* planes, const DevTab
 
 cudaError_t launch_action(const Grid& g, int B, const double* act, double u_tau, const DevTables& t,
                           const PencilBufs& pb, cudaStream_t st) {
-  const size_t smem = (size_t)g.nz * g.nx * sizeof(double) + (size_t)g.nz * g.nxh * sizeof(double2);
-  static bool cfg = false;
-  if (!cfg) {
-    cudaError_t e = cudaFuncSetAttribute(action_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e != cudaSuccess) return e;
-    cfg = true;
-  }
-  action_kernel<<<B, 256, smem, st>>>(g.nx, g.nz, g.nxh, act, u_tau, t.tw_nx, t.tw_nz, pb.vw_old, pb.vw_new,
-                                      pb.tau_acc, pb.active);
+  // the sensing-plane buffer is free at this point of the step: it is the scratch plane
+  double2* tx = pb.planes;
+  action_x_kernel<<<dim3(g.nz, B), 128, (size_t)g.nx * sizeof(double), st>>>(
+      g.nx, g.nz, g.nxh, act, u_tau, t.tw_nx, tx, pb.vw_old, pb.vw_new, pb.tau_acc, pb.active);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  action_z_kernel<<<dim3(g.nz, B), 128, 0, st>>>(g.nx, g.nz, g.nxh, tx, t.tw_nz, pb.vw_new, pb.active);
   return cudaGetLastError();
 }
 

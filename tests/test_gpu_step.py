@@ -182,3 +182,59 @@ def test_invalid_arguments_are_rejected(native_gpu):
             native.env_step(env, None, obs, tau, rew)    # external control needs an action
     finally:
         native.env_destroy(env)
+
+
+RE395 = dict(nx=128, ny=129, nz=128, lx=2 * math.pi, lz=math.pi, re_tau=395.0, re_bulk=6875.0, dt=0.0025)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_re395_grid_wall_spectrum_and_boundary_conditions(native_gpu, precision):
+    """128x129x128 channel (too large for the oracle's full step): the applied
+    wall spectrum matches the oracle's clip/zero-mean/transform of the same
+    action, and after the step the state satisfies, at any size, the
+    boundary conditions v(-1) = v_w, v(+1) = 0, v'(+-1) = 0, g(+-1) = 0,
+    U(+-1) = W(+-1) = 0 and the constant flow rate int U dy = 2."""
+    native = native_gpu
+    kw = dict(RE395, precision=precision)
+    op = oracle_params(**RE395)
+    ops = channel.Operators(op)
+    env = native.env_create(native.params(**kw))
+    try:
+        fields = si.perturbed_poiseuille(op.nx, op.ny, op.nz, 5, 0.1, 8)
+        native.env_set_state(env, 0, native.pack_state(fields, op.nx, op.ny, op.nz))
+        act = si.wall_action(op.nx, op.nz, 77, 1.5 * op.u_tau)   # clip active
+        obs = np.zeros((2, op.nz, op.nx))
+        tau = np.zeros(1)
+        rew = np.zeros(1)
+        assert native.env_step(env, np.ascontiguousarray(act), obs, tau, rew) == 0
+        st = native.unpack_state(native.env_get_state(env, 0), op.nx, op.ny, op.nz)
+    finally:
+        native.env_destroy(env)
+    assert np.isfinite(obs).all() and np.isfinite(tau).all() and np.isfinite(rew).all()
+    vw = channel.action_spectrum(act, ops)
+    assert rel_l2(st["vw"], vw) < 1e-13
+    # coefficient arrays are [ny][nz][nx/2]: wall values are signed sums over n
+    n = np.arange(op.ny, dtype=np.float64)
+    bot = (-1.0) ** n                    # T_n(-1)
+    top = np.ones(op.ny)                 # T_n(+1)
+    dbot = -((-1.0) ** n) * n * n        # T_n'(-1)
+    dtop = n * n                         # T_n'(+1)
+    tol = 1e-11 if precision == 0 else 1e-6
+    at = lambda f, w: np.tensordot(w, f, (0, 0))
+    v, g = st["v"], st["g"]
+    sv = float(np.abs(v).max()) * op.ny ** 2
+    sg = float(np.abs(g).max()) * op.ny
+    assert np.abs(at(v, bot) - vw).max() < tol * sv
+    assert np.abs(at(v, top)).max() < tol * sv
+    assert np.abs(at(v, dbot)).max() < tol * sv
+    assert np.abs(at(v, dtop)).max() < tol * sv
+    assert np.abs(at(g, bot)).max() < tol * sg
+    assert np.abs(at(g, top)).max() < tol * sg
+    U, W = st["U"], st["W"]
+    su = float(np.abs(U).max()) * op.ny
+    for w in (bot, top):
+        assert abs(w @ U) < tol * su
+        assert abs(w @ W) < tol * su
+    wint = np.zeros(op.ny)
+    wint[::2] = 2.0 / (1.0 - n[::2] ** 2)             # int_{-1}^{1} T_n dy
+    assert abs(wint @ U - 2.0) < tol * su
