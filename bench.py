@@ -52,6 +52,18 @@ WORKLOADS = {
                                "256 minimal channels 16x65x16 in one launch per kernel, mixed precision, "
                                "per-step seeded ZNMF Gaussian actions std 0.05 u_tau"),
 }
+# served workloads: (list of (parameters, count), slots per class, description)
+MID = dict(LARGER, nx=32, nz=32, control=0)
+BIG395 = dict(LARGER, nx=128, ny=129, nz=128, re_tau=395.0, re_bulk=6890.0, control=0)
+SERVED = {
+    "served_minimal256_mixed": ([(dict(MINIMAL, precision=1), 256)], 256,
+                                "served: 256 minimal channels 16x65x16, mixed precision, actor threads with "
+                                "exponential think time, continuous batching"),
+    "served_mixed_sizes": ([(dict(MINIMAL, precision=1), 24), (dict(MID, precision=1), 12),
+                            (dict(LARGER, control=0, precision=1), 8), (dict(BIG395, precision=1), 4)], 24,
+                           "served: 48 environments 24x16x65x16 + 12x32x65x32 + 8x64x65x64 (Re_tau 180) + "
+                           "4x128x129x128 (Re_tau 395), mixed precision, admitted by HBM budget"),
+}
 DEFAULT_WORKLOAD = "larger_fp64"
 WORKLOAD = LARGER
 WORKLOAD_NAME = WORKLOADS[DEFAULT_WORKLOAD][3]
@@ -201,13 +213,113 @@ def run_reference(args, rank: int, world: int):
     print(json.dumps(line), flush=True)
 
 
+
+def run_served(args):
+    """Continuous-batching server driven by one actor thread per environment.
+
+    Each actor submits an action, waits for the step, thinks for an
+    exponentially distributed time of mean 1/rate (0: none, saturation) and
+    repeats until the time budget is spent."""
+    import random
+    import threading
+
+    import numpy as np
+    import torch
+
+    from paper_2301_09889_gb300 import native
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    native.load()
+    groups, slots, name = SERVED[args.workload]
+    budget = int(float(os.environ.get("CH_SERVE_BUDGET_GB", "64")) * (1 << 30))
+    srv = native.srv_create(budget, slots)
+    envs = []
+    for prm, count in groups:
+        p = native.params(**prm)
+        for k in range(count):
+            envs.append((native.srv_admit(srv, p, seed=len(envs), amplitude=0.1, kmax=99), prm))
+    rate = float(os.environ.get("CH_SERVE_RATE", "0"))
+    duration = float(os.environ.get("CH_SERVE_SECONDS", "10"))
+    warm = 3
+    stop = threading.Event()
+    measuring = threading.Event()
+    errors = []
+    lat = {}   # class label -> submit-to-result latencies (s) seen by the actors while measuring
+
+    def actor(eid, prm, seed):
+        rng = random.Random(seed)
+        nrng = np.random.default_rng(seed)
+        nx, nz = prm["nx"], prm["nz"]
+        u_tau = prm["re_tau"] / prm["re_bulk"]
+        obs = np.zeros((2, nz, nx))
+        acts = nrng.standard_normal((16, nz, nx)) * 0.05 * u_tau
+        acts -= acts.mean(axis=(1, 2), keepdims=True)
+        label = f"{nx}x{prm['ny']}x{nz}"
+        mine = lat.setdefault(label, [])
+        i = 0
+        try:
+            while not stop.is_set():
+                t0 = time.perf_counter()
+                rid = native.srv_submit(srv, eid, acts[i % 16] if prm["control"] == 0 else None)
+                rc, *_ = native.srv_wait(srv, rid, 120000, obs)
+                if rc != native.CH_OK:
+                    errors.append(rc)
+                    return
+                if measuring.is_set():
+                    mine.append(time.perf_counter() - t0)
+                i += 1
+                if rate > 0:
+                    time.sleep(rng.expovariate(rate))
+        except Exception as exc:  # noqa: BLE001
+            errors.append(repr(exc))
+
+    for _, prm in envs:
+        lat.setdefault(f"{prm['nx']}x{prm['ny']}x{prm['nz']}", [])
+    threads = [threading.Thread(target=actor, args=(e, prm, k)) for k, (e, prm) in enumerate(envs)]
+    for t in threads:
+        t.start()
+    time.sleep(warm)
+    native.srv_stats(srv, reset=True)
+    measuring.set()
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    time.sleep(duration)
+    st = native.srv_stats(srv)
+    measuring.clear()
+    clk = clocks.stop()
+    stop.set()
+    for t in threads:
+        t.join()
+    native.srv_destroy(srv)
+    pts = sum(count * prm["nx"] * prm["ny"] * prm["nz"] for prm, count in groups) / len(envs)
+    per_class = {}
+    for label, xs in lat.items():
+        if xs:
+            a = np.sort(np.asarray(xs)) * 1e3
+            per_class[label] = {"steps_per_s": len(a) / duration, "p50_ms": float(np.percentile(a, 50)),
+                                "p99_ms": float(np.percentile(a, 99))}
+    line = {
+        "metric": METRIC, "value": st.env_steps_per_s, "unit": UNIT, "n_gpus": 1,
+        "steps": int(st.completed), "warmup": warm, "ms_per_step": None, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": name, "envs": len(envs), "slots_per_class": slots, "classes": st.classes,
+                   "think_rate_per_s": rate, "seconds": duration, "hbm_used_gb": st.hbm_used / (1 << 30)},
+        "p50_ms": st.p50_us / 1e3, "p99_ms": st.p99_us / 1e3, "mean_ms": st.mean_us / 1e3,
+        "mpts_rk3_steps_per_s": st.env_steps_per_s * pts / 1e6,
+        "per_class_actor_side": per_class,
+        "e2e": {"value": st.env_steps_per_s, "unit": UNIT,
+                "note": "served requests: host actions in, host observations out"},
+        "errors": errors[:5], "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
-    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=tuple(WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=tuple(WORKLOADS) + tuple(SERVED))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
 
@@ -216,6 +328,10 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload in SERVED:
+        if rank == 0:
+            run_served(args)
         return
 
     import numpy as np

@@ -193,7 +193,9 @@ size_t ch_state_bytes(const ch_params_t* p);
 /* ---- serving: continuous batching of env steps from many actors ---------
  * Environments are grouped into classes by their parameters (everything in
  * ch_params_t except `batch`).  Each class owns one batched handle with
- * `slots_per_class` slots and its own CUDA stream.  A worker thread runs
+ * `slots_per_class` slots and its own CUDA stream, prioritised by the cost
+ * of one env-step of the class (cheaper classes first, so that small
+ * environments keep their latency next to large ones).  A worker thread runs
  * ticks: for each idle class it takes the oldest pending request of every
  * environment and advances exactly those slots in one masked batched step;
  * ticks of different classes overlap on the device and requests arriving

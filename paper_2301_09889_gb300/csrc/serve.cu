@@ -10,6 +10,13 @@
 // environment is admitted into a free slot of its class; a new class is
 // created only if its device footprint fits the HBM budget.
 //
+// Ticks of a large class fill every SM; blocks of a small class launched
+// meanwhile would wait for them.  Each class's stream therefore gets a CUDA
+// priority by the cost of one of its env-steps (shortest job first): the
+// block scheduler dispatches pending blocks of a cheaper class before the
+// remaining blocks of a more expensive one, so small environments keep their
+// own latency next to large ones.
+//
 // A slot's result does not depend on which other slots are active (no
 // cross-slot arithmetic, the launch shape depends on the class capacity
 // only), so an environment steps identically alone and in any mix.
@@ -61,6 +68,7 @@ struct Class {
   int* h_active = nullptr;    // pinned [slots]
   int* d_active = nullptr;
   cudaEvent_t ev = nullptr;
+  cudaStream_t stream = nullptr;  // prioritised stream the class's ticks run on
   bool busy = false;
   std::vector<uint64_t> running;  // request per slot in the current tick (0 none)
 };
@@ -72,6 +80,20 @@ struct Env {
 };
 
 bool same_key(const ch_params_t& a, const ch_params_t& b) { return std::memcmp(&a, &b, sizeof(a)) == 0; }
+
+// Stream priority of a class: one level lower for every factor 4 in grid
+// points x solver steps per env-step above the 16x65x16 minimal channel.
+int class_priority(const ch_params_t& p) {
+  int least = 0, greatest = 0;
+  if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) return 0;
+  double cost = (double)p.nx * p.ny * p.nz * std::max(1, p.steps_per_action) / (16.0 * 65.0 * 16.0);
+  int rank = 0;
+  while (cost >= 4.0 && greatest + rank < least) {
+    cost /= 4.0;
+    ++rank;
+  }
+  return greatest + rank;
+}
 
 }  // namespace
 
@@ -125,6 +147,15 @@ int ch_server::make_class(const ch_params_t& key, int* cls) {
   c->nz = p.nz;
   int rc = env_create(&p, &c->env);
   if (rc != CH_OK) return rc;
+  if (cudaStreamCreateWithPriority(&c->stream, cudaStreamNonBlocking, class_priority(p)) != cudaSuccess) {
+    env_destroy(c->env);
+    return CH_ERR_CUDA;
+  }
+  if ((rc = env_set_stream(c->env, c->stream)) != CH_OK) {
+    env_destroy(c->env);
+    cudaStreamDestroy(c->stream);
+    return rc;
+  }
   c->out_stride = chdns::env_out_stride(c->env);
   c->footprint = fp;
   c->slot_env.assign(c->slots, -1);
@@ -140,6 +171,7 @@ int ch_server::make_class(const ch_params_t& key, int* cls) {
     if (c->h_active) cudaFreeHost(c->h_active);
     if (c->d_active) cudaFree(c->d_active);
     env_destroy(c->env);
+    cudaStreamDestroy(c->stream);
     return CH_ERR_OOM;
   }
   std::memset(c->h_act, 0, S * p.nz * p.nx * sizeof(double));
@@ -158,7 +190,8 @@ int ch_server::make_class(const ch_params_t& key, int* cls) {
 void ch_server::free_class(int ci) {
   Class* c = classes[ci].get();
   if (!c) return;
-  env_destroy(c->env);
+  env_destroy(c->env);  // synchronises the class stream first
+  cudaStreamDestroy(c->stream);
   cudaFreeHost(c->h_act);
   cudaFreeHost(c->h_out);
   cudaFreeHost(c->h_active);
