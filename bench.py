@@ -352,7 +352,11 @@ def main():
     env = native.env_create(p)
     info = native.env_info(env)
     native.env_reset(env, seed=1000 * rank, amplitude=0.1, kmax=99)
-    stream = torch.cuda.current_stream()
+    # one dedicated stream for the steps, the L2 flush and the timing events
+    # (the library's own stream is non-blocking and does not order with
+    # torch's legacy default stream)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     native.env_set_stream(env, stream.cuda_stream)
     nx, ny, nz = prm["nx"], prm["ny"], prm["nz"]
     out_len = 2 * nz * nx + 2

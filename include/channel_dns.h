@@ -89,6 +89,8 @@ typedef struct ch_info {
     size_t device_bytes;     /* device memory held by the handle                           */
     int plane_cluster;       /* CTAs cooperating on one y-plane of the nonlinear term       */
     int launches_per_step;   /* kernels launched by one env_step                            */
+    int post_batched;        /* 1: the implicit half of a stage runs one thread per (mode,
+                                class, component) -- chosen when B x modes fills the SMs   */
 } ch_info_t;
 
 typedef struct ch_env ch_env_t;

@@ -184,6 +184,7 @@ struct ch_env {
   double nu = 0, u_tau = 0, tau_ref = 0;
   int launches_per_step = 0;
   int ppc_pre = 8, ppc_post = 8;  // modes per CTA of the fused stage kernels
+  bool post_batched = false;      // batched form of stage_post (one thread per mode, class, component)
   // kernel timing (env_profile)
   bool prof = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[4];
@@ -557,9 +558,10 @@ int run_stage(ch_env* env, int k, double theta) {
   sc.k = k;
   if (mixed)
     LAUNCH(2, launch_stage_post<float>(g, B, env->pb, env->tab, reinterpret_cast<const float2*>(env->pb.R), sc,
-                                       env->ppc_post, st));
+                                       env->ppc_post, env->post_batched, st));
   else
-    LAUNCH(2, launch_stage_post<double>(g, B, env->pb, env->tab, env->pb.R, sc, env->ppc_post, st));
+    LAUNCH(2, launch_stage_post<double>(g, B, env->pb, env->tab, env->pb.R, sc, env->ppc_post, env->post_batched,
+                                        st));
   return CH_OK;
 }
 
@@ -702,8 +704,9 @@ int env_create(const ch_params_t* p, ch_env_t** out) {
   if (cudaMallocHost(&env->h_out, B * env->out_stride * sizeof(double)) != cudaSuccess) return fail(CH_ERR_OOM);
   if ((rc = build_tables(env))) return fail(rc);
   {
-    int smem_max = 0;
-    if (cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, 0) != cudaSuccess)
+    int smem_max = 0, dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
       return fail(CH_ERR_CUDA);
     env->ppc_post = 8;
     while (env->ppc_post > 1 && stage_post_smem(g, env->tab.tau.Mh, env->ppc_post) > (size_t)smem_max)
@@ -711,6 +714,15 @@ int env_create(const ch_params_t* p, ch_env_t** out) {
     env->ppc_pre = 8;
     while (env->ppc_pre > 1 && stage_pre_smem(g, env->ppc_pre) > (size_t)smem_max) env->ppc_pre /= 2;
     if (stage_post_smem(g, env->tab.tau.Mh, env->ppc_post) > (size_t)smem_max) return fail(CH_ERR_UNSUPPORTED);
+    // The batched form of stage_post runs four threads per mode, each with
+    // the same work; it pays once the batch supplies at least two such warps
+    // per SM sub-partition (B P / 8 >= 2 x 4 x SMs).
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return fail(CH_ERR_CUDA);
+    if ((size_t)B * P >= (size_t)64 * sms && stage_post_batched_smem(g, 16) <= (size_t)smem_max) {
+      env->post_batched = true;
+      env->ppc_post = 16;
+    }
   }
   // laminar Poiseuille, zero wall action
   std::vector<double> st(ch_state_bytes(p) / sizeof(double), 0.0);
@@ -823,6 +835,7 @@ int env_info(const ch_env_t* env, ch_info_t* info) {
   info->device_bytes = env->device_bytes;
   info->plane_cluster = env->prm.precision == 1 ? env->plane_f.S : env->plane.S;
   info->launches_per_step = env->launches_per_step;
+  info->post_batched = env->post_batched ? 1 : 0;
   return CH_OK;
 }
 

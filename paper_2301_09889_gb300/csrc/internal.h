@@ -35,12 +35,17 @@ struct DevTables {
 // fused wall-normal halves of a stage (stage.cu); ppc = modes per CTA
 size_t stage_pre_smem(const Grid& g, int ppc);
 size_t stage_post_smem(const Grid& g, int Mh, int ppc);
+size_t stage_post_batched_smem(const Grid& g, int ppc);
 template <typename RN>
 cudaError_t launch_stage_pre(const Grid& g, int B, const PencilBufs& pb, const DevTables& t,
                              typename cpx<RN>::T* q, int ppc, cudaStream_t st);
+// batched: one thread per (mode, class, component) and only H staged in shared
+// memory (for batches that supply many modes); otherwise one thread per
+// (mode, class, component, equation) on a shared-memory tile
 template <typename RN>
 cudaError_t launch_stage_post(const Grid& g, int B, const PencilBufs& pb, const DevTables& t,
-                              const typename cpx<RN>::T* h, const StageCoef& sc, int ppc, cudaStream_t st);
+                              const typename cpx<RN>::T* h, const StageCoef& sc, int ppc, bool batched,
+                              cudaStream_t st);
 cudaError_t launch_wall_shear(const Grid& g, int B, const double* UM, double nu, double* acc,
                               const int* active, cudaStream_t st);
 cudaError_t launch_sense(const Grid& g, int B, const PencilBufs& pb, const DevTables& t, int js,

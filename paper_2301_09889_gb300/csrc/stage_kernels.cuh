@@ -1,0 +1,898 @@
+// The two wall-normal halves of one Runge-Kutta stage, each fused over a tile
+// of `ppc` Fourier modes that lives in shared memory:
+//
+//   stage_pre  : (v, omega_y, U, W) coefficients -> coefficients of
+//                u, v, w, omega_x, omega_y, omega_z -> their values at the
+//                Gauss-Lobatto nodes (input of the nonlinear plane kernel);
+//   stage_post : nodal values of H = u x omega -> Chebyshev coefficients ->
+//                right-hand sides -> Chebyshev-tau solves -> new state.
+//
+// Every global array is read and written once per stage with loads and
+// stores that are contiguous over the modes of the tile; the sequential
+// recurrences then run on shared memory.  RN is the precision of the nodal
+// values exchanged with the plane kernel (double: all-FP64 path).
+//
+// Symmetry classes and components.  All wall-normal operators are real and
+// map even Chebyshev coefficients to even or odd ones in a fixed pattern, so a
+// mode splits into two classes (c = 0: even v, odd omega_y; c = 1: odd v,
+// even omega_y) and two real components (r = 0, 1) that never interact.  The
+// factors i kx, i kz only swap components: component r of (i s X) is
+// sgn_r s X_{1-r} with sgn_0 = -1, sgn_1 = +1.  One thread owns one
+// (mode, class, component[, equation]) and keeps one parity of its arrays in
+// registers (parity index i, n = 2i + sig), bounded at compile time by MH.
+//
+// Chebyshev conventions: f(y) = sum_n a_n T_n(y), nodes y_j = cos(pi j / N);
+// derivative recurrence c_m b_m = b_{m+2} + 2 (m+1) a_{m+1} (c_0 = 2).
+#pragma once
+
+#include "common.cuh"
+#include "internal.h"
+#include "stage_launch.h"
+
+namespace chdns {
+
+// ---------------------------------------------------------------------------
+// shared-memory views
+// ---------------------------------------------------------------------------
+
+// component r of a complex [n][ppc] tile: element n at p[n * stride]
+struct CompS {
+  double* p;
+  int stride;
+  __device__ double& operator[](int n) const { return p[n * stride]; }
+};
+
+// tau factor tables of one (mode, parity): element (f, i) at base[(f * Mh + i) * ppc]
+struct TabSm {
+  const double* base;
+  int Mh, ppc;
+  __device__ double e(int i) const { return base[(0 * Mh + i) * ppc]; }
+  __device__ double h(int i) const { return base[(1 * Mh + i) * ppc]; }
+  __device__ double b(int i) const { return base[(2 * Mh + i) * ppc]; }
+  __device__ double Q(int i) const { return base[(3 * Mh + i) * ppc]; }
+};
+
+// ---------------------------------------------------------------------------
+// Chebyshev-tau Dirichlet solve (D^2 - lam) f = r of one parity of one real
+// component.  For n >= 2 the tau rows are equivalent to the quasi-tridiagonal
+// rows
+//   -lam cA_n f_{n-2} + (1 + lam cB_n) f_n - lam cC_n f_{n+2}
+//       = cA_n r_{n-2} - cB_n r_n + cC_n r_{n+2},
+//   cA_n = c_{n-2}/(4n(n-1)), cB_n = [n <= N-2]/(2(n^2-1)), cC_n = [n+2 <= N-2]/(4n(n+1)),
+// obtained by integrating D^2 f = r + lam f twice; the two highest rows of r
+// are dropped (tau).  With parity index i the rows i >= 1 are tridiagonal and
+// the wall row sum_i f_i = s closes the system.  Bottom-up elimination gives
+// f_i = a_i + b_i f_{i-1}; every f_i is then affine in f_0, which the wall row
+// fixes.  The lam-dependent factors e = 1/den, h = U/den, b = -L/den, Q = prod b
+// and 1/sum Q are precomputed per mode and stage.  rowc = [cA | cB | cC].
+// ---------------------------------------------------------------------------
+template <int MH, class Tab>
+__device__ __forceinline__ void tau_seq(int N, int ny, int sig, const double (&r)[MH], double (&f)[MH],
+                                        const Tab& T, double isq, double s, const double* __restrict__ rowc) {
+  const int M = (N - sig) / 2 + 1;
+  double anext = 0.0;
+#pragma unroll
+  for (int i = MH - 1; i >= 1; --i) {
+    if (i < M) {
+      const int n = 2 * i + sig;
+      double R = rowc[n] * r[i - 1] - rowc[ny + n] * r[i];
+      if (i + 1 < MH && i + 1 < M) R += rowc[2 * ny + n] * r[i + 1 < MH ? i + 1 : i];
+      const double a = T.e(i) * R - T.h(i) * anext;
+      f[i] = a;
+      anext = a;
+    }
+  }
+  double Pp = 0.0, sum = 0.0;
+#pragma unroll
+  for (int i = 1; i < MH; ++i) {
+    if (i < M) {
+      Pp = f[i] + T.b(i) * Pp;
+      f[i] = Pp;
+      sum += Pp;
+    }
+  }
+  const double f0 = isq * (s - sum);
+  f[0] = f0;
+#pragma unroll
+  for (int i = 1; i < MH; ++i)
+    if (i < M) f[i] += T.Q(i) * f0;
+}
+
+// Right-hand side of the v equation of one parity SV and component r, one
+// walk from n = N down to 0 carrying Dv, D^2 v, t = i kx H_x + i kz H_z and
+// Dt; also stores h_v for the next stage.  SV is a template parameter so that
+// every register index is fixed at compile time.
+template <int MH, int SV>
+__device__ __forceinline__ void v_walk(int N, int ny, int ppc, const CompS& Vc, const CompS& HVc,
+                                       const double2* Hx, const double2* Hy, const double2* Hz, int r, double sgn,
+                                       double kx, double kz, double k2, double cc, double ibdn, const StageCoef& sc,
+                                       double (&rhs)[MH]) {
+  const int ra = 1 - r;
+  auto comp = [](const double2 z, int qd) { return qd == 0 ? z.x : z.y; };
+  double dv = 0.0, d2v = 0.0, tt = 0.0, dtt = 0.0;
+#pragma unroll
+  for (int n = 2 * MH - 1; n >= 0; --n) {
+    if (n > N) continue;
+    if ((n & 1) != SV) {
+      const double vn1 = (n + 1 <= N) ? Vc[n + 1] : 0.0;
+      const double t1 = dv + 2.0 * (n + 1) * vn1;
+      dv = (n == 0) ? 0.5 * t1 : t1;
+      tt = sgn * (kx * comp(Hx[n * ppc], ra) + kz * comp(Hz[n * ppc], ra));
+    } else {
+      const double t1 = d2v + 2.0 * (n + 1) * dv;
+      const double t2 = dtt + 2.0 * (n + 1) * ((n + 1 <= N) ? tt : 0.0);
+      d2v = (n == 0) ? 0.5 * t1 : t1;
+      dtt = (n == 0) ? 0.5 * t2 : t2;
+      const double phi = d2v - k2 * Vc[n];
+      const double hv = -k2 * comp(Hy[n * ppc], r) - dtt;
+      const double hp = HVc[n];
+      HVc[n] = hv;
+      const int i = (n - SV) / 2;
+      rhs[i] = -((1.0 + cc) * phi + sc.dt * (sc.gamma * hv + sc.zeta * hp)) * ibdn;
+    }
+  }
+}
+
+// cos(pi j n / N) table in the node precision
+template <typename RN>
+__device__ __forceinline__ const RN* cheb_table(const DevTables& t);
+template <>
+__device__ __forceinline__ const double* cheb_table<double>(const DevTables& t) { return t.cheb; }
+template <>
+__device__ __forceinline__ const float* cheb_table<float>(const DevTables& t) { return t.cheb_f; }
+
+__device__ __forceinline__ double2 to_double(double2 v) { return v; }
+__device__ __forceinline__ double2 to_double(float2 v) { return make_double2((double)v.x, (double)v.y); }
+
+// ---------------------------------------------------------------------------
+// stage_pre
+//   u = (i kx Dv - i kz g)/k^2, w = (i kz Dv + i kx g)/k^2,
+//   omega_x = Dw - i kz v, omega_z = i kx v - Du;  mean mode: u = U, w = W,
+//   omega_x = DW, omega_z = -DU.
+// Thread (mode, class c, component r) writes component r of u, w, omega_y on
+// parity 1-c and of v, omega_x, omega_z on parity c; its derivative chains run
+// on component 1-r from n = N down to 0.  All threads then evaluate the six
+// Chebyshev series at the nodes: f_j = E_j + O_j, f_{N-j} = E_j - O_j with the
+// even/odd partial sums of a_n cos(pi n j / N), for the (N+1)/2 node pairs
+// j < N/2.  For even N the middle node needs no products,
+// f_{N/2} = sum_m (-1)^m a_{2m}; the thread writing the even coefficients of a
+// field sums it on the way, so the node pairs divide evenly over the threads.
+// ---------------------------------------------------------------------------
+template <typename RN, int MH>
+__global__ void __launch_bounds__(128) stage_pre_kernel(Grid g, int B, PencilBufs pb, DevTables t,
+                                                        typename cpx<RN>::T* __restrict__ q, int ppc) {
+  using CN = typename cpx<RN>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int P = g.P, ny = g.ny, N = g.N;
+  double2* sV = reinterpret_cast<double2*>(smem_raw);  // [ny][ppc]
+  double2* sG = sV + ny * ppc;                          // [ny][ppc]
+  CN* sC = reinterpret_cast<CN*>(sG + ny * ppc);        // [6][ny][ppc] in the node precision
+  const int p0 = blockIdx.x * ppc;
+  const int b = blockIdx.y;
+  if (pb.active && !pb.active[b]) return;
+  const int tid = threadIdx.x, nt = blockDim.x;
+
+  for (int w = tid; w < ny * ppc; w += nt) {
+    const int pl = w % ppc, n = w / ppc;
+    const int p = p0 + pl;
+    const size_t o = ((size_t)b * ny + n) * P + p;
+    sV[w] = (p < P) ? pb.V[o] : mk(0.0, 0.0);
+    sG[w] = (p < P) ? pb.G[o] : mk(0.0, 0.0);
+  }
+  __syncthreads();
+
+  if (tid < 4 * ppc) {
+    const int pl = tid % ppc;
+    const int combo = tid / ppc;
+    const int c = combo & 1, r = combo >> 1;
+    const int p = p0 + pl;
+    const int row = p / g.nxh, ix = p % g.nxh;
+    const int fs = 2 * ny * ppc;  // reals per field
+    RN* out = reinterpret_cast<RN*>(sC) + 2 * pl + r;
+    // middle node f_{N/2} = sum over even n of (-1)^(n/2) a_n, per field
+    RN mid[6] = {0, 0, 0, 0, 0, 0};
+    auto W = [&](int f, int n, double v) {
+      const RN x = (RN)v;
+      out[f * fs + n * 2 * ppc] = x;
+      if ((n & 1) == 0) mid[f] = (n & 2) ? mid[f] - x : mid[f] + x;
+    };
+    if (p >= P || row == g.nz / 2 || (p == 0 && r == 1)) {
+      for (int n = 0; n <= N; ++n) {
+        if ((n & 1) == 1 - c) { W(0, n, 0.0); W(2, n, 0.0); W(4, n, 0.0); }
+        else { W(1, n, 0.0); W(3, n, 0.0); W(5, n, 0.0); }
+      }
+    } else if (p == 0) {
+      const double* U = pb.UM + (size_t)b * ny;
+      const double* Wm = pb.WM + (size_t)b * ny;
+      double du = 0.0, dw = 0.0;
+      for (int n = N; n >= 0; --n) {
+        if ((n & 1) == 1 - c) {
+          W(0, n, U[n]);
+          W(2, n, Wm[n]);
+          W(4, n, 0.0);
+        } else {
+          const double un = (n + 1 <= N) ? U[n + 1] : 0.0, wn = (n + 1 <= N) ? Wm[n + 1] : 0.0;
+          const double t1 = du + 2.0 * (n + 1) * un, t2 = dw + 2.0 * (n + 1) * wn;
+          du = (n == 0) ? 0.5 * t1 : t1;
+          dw = (n == 0) ? 0.5 * t2 : t2;
+          W(1, n, 0.0);
+          W(3, n, dw);
+          W(5, n, -du);
+        }
+      }
+    } else {
+      // derivative chains and u, w, omega in the node precision (the nonlinear
+      // term's arithmetic; FP32 in mixed mode)
+      const RN kx = (RN)t.kx[ix], kz = (RN)t.kz[row];
+      const RN sg = (r == 0) ? (RN)-1.0 : (RN)1.0;
+      const RN ik2 = sg / (kx * kx + kz * kz);
+      const CompS V{reinterpret_cast<double*>(sV) + 2 * pl + r, 2 * ppc};
+      const CompS Va{reinterpret_cast<double*>(sV) + 2 * pl + (1 - r), 2 * ppc};
+      const CompS G{reinterpret_cast<double*>(sG) + 2 * pl + r, 2 * ppc};
+      const CompS Ga{reinterpret_cast<double*>(sG) + 2 * pl + (1 - r), 2 * ppc};
+      RN dv = 0, d2v = 0, dg = 0, vnext = 0, gnext = 0;
+      for (int n = N; n >= 0; --n) {
+        if ((n & 1) == 1 - c) {
+          const RN t1 = dv + (RN)(2 * (n + 1)) * vnext;
+          dv = (n == 0) ? (RN)0.5 * t1 : t1;
+          const RN ga = (RN)Ga[n];
+          W(0, n, ik2 * (kx * dv - kz * ga));  // u
+          W(2, n, ik2 * (kz * dv + kx * ga));  // w
+          W(4, n, G[n]);                       // omega_y
+          gnext = ga;
+        } else {
+          const RN t1 = d2v + (RN)(2 * (n + 1)) * dv;
+          const RN t2 = dg + (RN)(2 * (n + 1)) * gnext;
+          d2v = (n == 0) ? (RN)0.5 * t1 : t1;
+          dg = (n == 0) ? (RN)0.5 * t2 : t2;
+          const RN va = (RN)Va[n];
+          const RN du = ik2 * (kx * d2v - kz * dg);
+          const RN dw = ik2 * (kz * d2v + kx * dg);
+          W(1, n, V[n]);                 // v
+          W(3, n, dw - sg * kz * va);    // omega_x = Dw - i kz v
+          W(5, n, sg * kx * va - du);    // omega_z = i kx v - Du
+          vnext = va;
+        }
+      }
+    }
+    // this thread wrote the even coefficients of fields 0, 2, 4 (c = 1) or 1, 3, 5 (c = 0)
+    if ((N & 1) == 0 && p < P) {
+      RN* qr = reinterpret_cast<RN*>(q);
+#pragma unroll
+      for (int f = 0; f < 6; ++f)
+        if ((f & 1) == 1 - c) qr[2 * (((size_t)(b * 6 + f) * ny + N / 2) * P + p) + r] = mid[f];
+    }
+  }
+  __syncthreads();
+
+  // synthesis of the six fields at the nodes.  Thread (mode pl, group g of
+  // nt / ppc) evaluates the node pairs j = g, g + ng, ... of all six fields of
+  // its mode: each coefficient it loads feeds all of its outputs, which are
+  // independent accumulation chains.
+  {
+    constexpr int KJ = (MH - 1 + 15) / 16;  // node pairs per thread (ng = nt / ppc >= 16)
+    const int ng = nt / ppc;
+    const int pl = tid % ppc, gq = tid / ppc;
+    const int J = (N + 1) / 2;  // node pairs (j, N - j), j < N/2
+    const RN* cheb = cheb_table<RN>(t);
+    if (gq < ng) {
+      CN E[6][KJ], O[6][KJ];
+#pragma unroll
+      for (int f = 0; f < 6; ++f)
+#pragma unroll
+        for (int k = 0; k < KJ; ++k) {
+          E[f][k] = czero<CN>();
+          O[f][k] = czero<CN>();
+        }
+      const CN* col = sC + pl;
+      for (int n = 0; n <= N; ++n) {
+        CN cf[6];
+#pragma unroll
+        for (int f = 0; f < 6; ++f) cf[f] = col[((size_t)f * ny + n) * ppc];
+#pragma unroll
+        for (int k = 0; k < KJ; ++k) {
+          const int j = gq + ng * k;
+          const RN c = cheb[(size_t)min(j, N) * ny + n];
+          if (n & 1) {
+#pragma unroll
+            for (int f = 0; f < 6; ++f) O[f][k] = O[f][k] + c * cf[f];
+          } else {
+#pragma unroll
+            for (int f = 0; f < 6; ++f) E[f][k] = E[f][k] + c * cf[f];
+          }
+        }
+      }
+      const int p = p0 + pl;
+      if (p < P) {
+#pragma unroll
+        for (int k = 0; k < KJ; ++k) {
+          const int j = gq + ng * k;
+          if (j >= J) continue;
+#pragma unroll
+          for (int f = 0; f < 6; ++f) {
+            CN* dst = q + ((size_t)(b * 6 + f) * ny) * P + p;
+            dst[(size_t)j * P] = E[f][k] + O[f][k];
+            dst[(size_t)(N - j) * P] = E[f][k] - O[f][k];
+          }
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// stage_post
+// Analysis: a_n = 2/(N cb_n) sum_j f_j cos(pi n j / N) / cb_j (cb_0 = cb_N = 2),
+// node pairs (j, N-j) folded by the parity of n.
+// Implicit part, with c = alpha/beta and the shifted unknowns
+// g' = g^k + c g^{k-1}, phi' = phi^k + c phi^{k-1}, v' = v^k + c v^{k-1}:
+//   (D^2 - lam) g'   = -((1 + c) g + dt (gamma h_g + zeta h_g')) / (beta dt nu)
+//   (D^2 - lam) phi' = -((1 + c) phi + dt (gamma h_v + zeta h_v')) / (beta dt nu),
+//   (D^2 - k^2) v'   = phi',   phi = (D^2 - k^2) v^{k-1},
+// lam = k^2 + 1/(beta dt nu).  (D^2 - k^2) X = (D^2 - lam) X + X/(beta dt nu)
+// holds for every coefficient row, so this is the same tau discretisation as
+// the plain form without derivatives of the old fields.  The wall rows of g'
+// and v' carry c times the old wall values; the influence matrix fixes
+// Dv'(+-1) = c Dv^{k-1}(+-1).  Then g^k = g' - c g^{k-1}, v^k = v' - c v^{k-1}.
+//   h_g = i kz H_x - i kx H_z,  h_v = -k^2 H_y - D(i kx H_x + i kz H_z).
+// Thread (mode, class c, component r, equation e): e = 0 omega_y on parity
+// 1-c, e = 1 v on parity c.  The mean mode solves U at constant flow rate
+// (e = 0) and W (e = 1) on parity c, real component only.
+// ---------------------------------------------------------------------------
+template <typename RN, int MH>
+__global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBufs pb, DevTables t,
+                                                        const typename cpx<RN>::T* __restrict__ hn, StageCoef sc,
+                                                        int ppc) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int P = g.P, ny = g.ny, N = g.N;
+  const int Mh = t.tau.Mh;
+  double2* sH = reinterpret_cast<double2*>(smem_raw);  // [3][ny][ppc] nodes, then coefficients
+  double2* sV = sH + 3 * ny * ppc;                      // [ny][ppc]
+  double2* sG = sV + ny * ppc;
+  double2* sHV = sG + ny * ppc;
+  double2* sHG = sHV + ny * ppc;
+  double* sh = reinterpret_cast<double*>(sHG + ny * ppc);  // helm [2][4][Mh][ppc] of this stage
+  double* sp = sh + 2 * 4 * Mh * ppc;                        // pois [2][4][Mh][ppc]
+  double* svh = sp + 2 * 4 * Mh * ppc;                       // vh [2][Mh][ppc]
+  double* ss = svh + 2 * Mh * ppc;                           // helm_isq, pois_isq, vh_idv [3][2][ppc]
+  const int p0 = blockIdx.x * ppc;
+  const int b = blockIdx.y;
+  if (pb.active && !pb.active[b]) return;
+  const int tid = threadIdx.x, nt = blockDim.x;
+
+  // ---- load the tile
+  for (int w = tid; w < ny * ppc; w += nt) {
+    const int pl = w % ppc, n = w / ppc;
+    const int p = min(p0 + pl, P - 1);
+    const size_t o = ((size_t)b * ny + n) * P + p;
+    sV[w] = pb.V[o];
+    sG[w] = pb.G[o];
+    sHV[w] = pb.HVP[o];
+    sHG[w] = pb.HGP[o];
+  }
+  // nodal values in the node precision, in the first bytes of the sH region
+  using CN = typename cpx<RN>::T;
+  CN* sN = reinterpret_cast<CN*>(sH);
+  for (int w = tid; w < 3 * ny * ppc; w += nt) {
+    const int pl = w % ppc, fn = w / ppc;  // fn = f * ny + n
+    const int p = min(p0 + pl, P - 1);
+    sN[w] = hn[((size_t)b * 3 * ny + fn) * P + p];
+  }
+  for (int w = tid; w < 2 * 4 * Mh * ppc; w += nt) {
+    const int pl = w % ppc, qq = w / ppc;  // qq = (sig * 4 + f) * Mh + i
+    const int p = min(p0 + pl, P - 1);
+    sh[w] = t.tau.helm[((size_t)sc.k * 2 * 4 * Mh + qq) * P + p];
+    sp[w] = t.tau.pois[(size_t)qq * P + p];
+  }
+  for (int w = tid; w < 2 * Mh * ppc; w += nt) {
+    const int pl = w % ppc, qq = w / ppc;
+    const int p = min(p0 + pl, P - 1);
+    svh[w] = t.tau.vh[((size_t)sc.k * 2 * Mh + qq) * P + p];
+  }
+  for (int w = tid; w < 2 * ppc; w += nt) {
+    const int pl = w % ppc, sig = w / ppc;
+    const int p = min(p0 + pl, P - 1);
+    ss[(0 * 2 + sig) * ppc + pl] = t.tau.helm_isq[(size_t)(sc.k * 2 + sig) * P + p];
+    ss[(1 * 2 + sig) * ppc + pl] = t.tau.pois_isq[(size_t)sig * P + p];
+    ss[(2 * 2 + sig) * ppc + pl] = t.tau.vh_idv[(size_t)(sc.k * 2 + sig) * P + p];
+  }
+  __syncthreads();
+
+  // ---- Chebyshev analysis of H_x, H_y, H_z (in place after a barrier)
+  {
+    // Thread (mode pl, group g of 8) computes the coefficients n = g, g+8, ...
+    // of the three fields of its mode: every pair f_j, f_{N-j} it loads feeds
+    // all of its outputs, and the outputs are independent accumulation chains.
+    // n and g share their parity, so the folding sign is fixed per thread.
+    constexpr int KN = (2 * MH + 7) / 8;  // n values per thread
+    const int pl = tid % ppc, gq = tid / ppc;  // blockDim = 8 ppc
+    const RN* cheb = cheb_table<RN>(t);
+    const RN sg = (gq & 1) ? (RN)-1.0 : (RN)1.0;
+    CN a[3][KN];
+    const CN* colf[3];
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+      colf[f] = sN + (size_t)f * ny * ppc + pl;
+      const CN w0 = (RN)0.5 * (colf[f][0] + sg * colf[f][N * ppc]);  // j = 0 and j = N weigh 1/2
+#pragma unroll
+      for (int k = 0; k < KN; ++k) a[f][k] = w0;
+    }
+    for (int j = 1; 2 * j < N; ++j) {
+      CN fold[3];
+#pragma unroll
+      for (int f = 0; f < 3; ++f) fold[f] = colf[f][j * ppc] + sg * colf[f][(N - j) * ppc];
+#pragma unroll
+      for (int k = 0; k < KN; ++k) {
+        const int n = gq + 8 * k;
+        const RN c = cheb[(size_t)min(n, N) * ny + j];
+#pragma unroll
+        for (int f = 0; f < 3; ++f) a[f][k] = a[f][k] + c * fold[f];
+      }
+    }
+    double2 acc[3][KN];
+    const RN s0 = (RN)2.0 / (RN)N;
+#pragma unroll
+    for (int k = 0; k < KN; ++k) {
+      const int n = gq + 8 * k;
+      const RN cbn = (n == 0 || n == N) ? (RN)2.0 : (RN)1.0;
+      const RN cH = ((N & 1) == 0) ? cheb[(size_t)min(n, N) * ny + N / 2] : (RN)0.0;
+#pragma unroll
+      for (int f = 0; f < 3; ++f) {
+        CN v = a[f][k];
+        if ((N & 1) == 0) v = v + cH * colf[f][(N / 2) * ppc];
+        acc[f][k] = to_double((s0 / cbn) * v);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < KN; ++k) {
+      const int n = gq + 8 * k;
+      if (n <= N) {
+#pragma unroll
+        for (int f = 0; f < 3; ++f) sH[((size_t)f * ny + n) * ppc + pl] = acc[f][k];
+      }
+    }
+    __syncthreads();
+  }
+
+  // ---- implicit solves
+  const int pl = tid % ppc;
+  const int combo = tid / ppc;
+  const int p = p0 + pl;
+  if (p < P && combo < 8) {
+    const int c = combo & 1, r = (combo >> 1) & 1, e = combo >> 2;
+    const int row = p / g.nxh, ix = p % g.nxh;
+    const double cc = sc.alpha / sc.beta;
+    const double ibdn = 1.0 / (sc.beta * sc.dt * sc.nu);
+    const double* rowc = t.tau.rowc;
+    const double2* Hx = sH + pl;
+    const double2* Hy = Hx + ny * ppc;
+    const double2* Hz = Hy + ny * ppc;
+    auto helm = [&](int sig) { return TabSm{sh + sig * 4 * Mh * ppc + pl, Mh, ppc}; };
+    auto comp = [&](const double2 z, int qd) { return qd == 0 ? z.x : z.y; };
+    if (row == g.nz / 2) {
+      // Nyquist row stays zero
+    } else if (p == 0) {
+      if (r == 0) {
+        const int s = c;
+        const int M = (N - s) / 2 + 1;
+        double* X = (e == 0 ? pb.UM : pb.WM) + (size_t)b * ny;
+        double* XP = (e == 0 ? pb.HXP : pb.HZP) + (size_t)b * ny;
+        const double2* Hm = (e == 0) ? Hx : Hz;
+        double rhs[MH], f[MH];
+        double sum = 0.0, flux_old = 0.0;
+#pragma unroll
+        for (int i = 0; i < MH; ++i) {
+          rhs[i] = 0.0;
+          if (i < M) {
+            const int n = 2 * i + s;
+            const double xn = X[n];
+            const double hv = Hm[n * ppc].x;
+            const double hp = XP[n];
+            XP[n] = hv;
+            rhs[i] = -((1.0 + cc) * xn + sc.dt * (sc.gamma * hv + sc.zeta * hp)) * ibdn;
+            sum += xn;
+            if (s == 0) flux_old += 2.0 / (1.0 - (double)n * n) * xn;
+          }
+        }
+        tau_seq<MH>(N, ny, s, rhs, f, helm(s), ss[(0 * 2 + s) * ppc + pl], cc * sum, rowc);
+        double fc = 0.0;
+        if (e == 0 && s == 0) {
+          double flux = 0.0;
+#pragma unroll
+          for (int i = 0; i < MH; ++i)
+            if (i < M) flux += 2.0 / (1.0 - 4.0 * (double)i * i) * f[i];
+          fc = (sc.flux + cc * flux_old - flux) * t.tau.u1_iflux[sc.k];
+        }
+#pragma unroll
+        for (int i = 0; i < MH; ++i) {
+          if (i < M) {
+            const int n = 2 * i + s;
+            double v = f[i] - cc * X[n];
+            if (e == 0 && s == 0) v += fc * t.tau.u1[(size_t)sc.k * Mh + i];
+            X[n] = v;
+          }
+        }
+      }
+    } else {
+      const double kx = t.kx[ix], kz = t.kz[row], k2 = kx * kx + kz * kz;
+      const double sgn = (r == 0) ? -1.0 : 1.0;
+      const int ra = 1 - r;
+      if (e == 0) {
+        // wall-normal vorticity, parity 1 - c
+        const int sq = 1 - c;
+        const int M = (N - sq) / 2 + 1;
+        const CompS Gc{reinterpret_cast<double*>(sG) + 2 * pl + r, 2 * ppc};
+        const CompS HGc{reinterpret_cast<double*>(sHG) + 2 * pl + r, 2 * ppc};
+        double rhs[MH], f[MH];
+        double sum = 0.0;
+#pragma unroll
+        for (int i = 0; i < MH; ++i) {
+          rhs[i] = 0.0;
+          if (i < M) {
+            const int n = 2 * i + sq;
+            const double gn = Gc[n];
+            const double hg = sgn * (kz * comp(Hx[n * ppc], ra) - kx * comp(Hz[n * ppc], ra));
+            const double hp = HGc[n];
+            HGc[n] = hg;
+            rhs[i] = -((1.0 + cc) * gn + sc.dt * (sc.gamma * hg + sc.zeta * hp)) * ibdn;
+            sum += gn;
+          }
+        }
+        tau_seq<MH>(N, ny, sq, rhs, f, helm(sq), ss[(0 * 2 + sq) * ppc + pl], cc * sum, rowc);
+#pragma unroll
+        for (int i = 0; i < MH; ++i)
+          if (i < M) {
+            const int n = 2 * i + sq;
+            Gc[n] = f[i] - cc * Gc[n];
+          }
+      } else {
+        // wall-normal velocity, parity c
+        const int sv = c;
+        const int M = (N - sv) / 2 + 1;
+        const CompS Vc{reinterpret_cast<double*>(sV) + 2 * pl + r, 2 * ppc};
+        const CompS HVc{reinterpret_cast<double*>(sHV) + 2 * pl + r, 2 * ppc};
+        double S0 = 0.0, S2 = 0.0;
+        double rhs[MH];
+#pragma unroll
+        for (int i = 0; i < MH; ++i) rhs[i] = 0.0;
+        for (int i = 0; i < M; ++i) {
+          const int n = 2 * i + sv;
+          const double vn = Vc[n];
+          S0 += vn;
+          S2 += (double)n * n * vn;
+        }
+        // one walk from n = N down to 0: Dv, D^2 v, t = i kx H_x + i kz H_z, Dt
+        if (sv == 0)
+          v_walk<MH, 0>(N, ny, ppc, Vc, HVc, Hx, Hy, Hz, r, sgn, kx, kz, k2, cc, ibdn, sc, rhs);
+        else
+          v_walk<MH, 1>(N, ny, ppc, Vc, HVc, Hx, Hy, Hz, r, sgn, kx, kz, k2, cc, ibdn, sc, rhs);
+        double f[MH];
+        tau_seq<MH>(N, ny, sv, rhs, f, helm(sv), ss[(0 * 2 + sv) * ppc + pl], 0.0, rowc);
+        const size_t vo = (size_t)b * P + p;
+        const double vw =
+            comp(pb.vw_old[vo], r) + sc.theta * (comp(pb.vw_new[vo], r) - comp(pb.vw_old[vo], r));
+        const double s = ((sv == 0) ? 0.5 : -0.5) * vw + cc * S0;
+        const TabSm TP{sp + sv * 4 * Mh * ppc + pl, Mh, ppc};
+        tau_seq<MH>(N, ny, sv, f, rhs, TP, ss[(1 * 2 + sv) * ppc + pl], s, rowc);
+        double dp = 0.0;
+#pragma unroll
+        for (int i = 0; i < MH; ++i)
+          if (i < M) {
+            const double n = 2 * i + sv;
+            dp += n * n * rhs[i];
+          }
+        const double cI = (cc * S2 - dp) * ss[(2 * 2 + sv) * ppc + pl];
+        const double* vh = svh + sv * Mh * ppc + pl;
+#pragma unroll
+        for (int i = 0; i < MH; ++i)
+          if (i < M) {
+            const int n = 2 * i + sv;
+            Vc[n] = rhs[i] + cI * vh[i * ppc] - cc * Vc[n];
+          }
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---- store the tile
+  for (int w = tid; w < ny * ppc; w += nt) {
+    const int pl2 = w % ppc, n = w / ppc;
+    const int p2 = p0 + pl2;
+    if (p2 >= P) continue;
+    const size_t o = ((size_t)b * ny + n) * P + p2;
+    pb.V[o] = sV[w];
+    pb.G[o] = sG[w];
+    pb.HVP[o] = sHV[w];
+    pb.HGP[o] = sHG[w];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// stage_post, batched form.  The same arithmetic as stage_post_kernel, mapped
+// for many modes: one thread per (mode, class c, component r) solves both
+// equations of its class (omega_y on parity 1-c, then v on parity c), so every
+// warp carries the same FP64 work, and only the Chebyshev coefficients of H
+// are staged in shared memory (3 ny complex per mode, against 7 ny complex
+// plus the tau tables in the per-tile form), which lets four times as many
+// modes be resident per SM.  The state, the previous right-hand sides and the
+// tau tables are read and written in place in global memory by the thread
+// that owns them; lanes (mode, r) make these accesses contiguous.  The
+// analysis runs field by field with four threads per mode (n = q + 4k); each
+// coefficient is accumulated in the same order as in the per-tile form.
+// ---------------------------------------------------------------------------
+template <typename RN, int MH>
+__global__ void __launch_bounds__(64) stage_post_batched_kernel(Grid g, int B, PencilBufs pb, DevTables t,
+                                                                const typename cpx<RN>::T* __restrict__ hn,
+                                                                StageCoef sc, int ppc) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  using CN = typename cpx<RN>::T;
+  const int P = g.P, ny = g.ny, N = g.N;
+  const int Mh = t.tau.Mh;
+  double2* sH = reinterpret_cast<double2*>(smem_raw);  // [3][ny][ppc] coefficients
+  CN* sN = reinterpret_cast<CN*>(smem_raw);             // [3][ny][ppc] nodal values, same bytes
+  const int p0 = blockIdx.x * ppc;
+  const int b = blockIdx.y;
+  if (pb.active && !pb.active[b]) return;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int w = tid; w < 3 * ny * ppc; w += nt) {
+    const int pl = w % ppc, fn = w / ppc;  // fn = f * ny + n
+    const int p = min(p0 + pl, P - 1);
+    sN[w] = hn[((size_t)b * 3 * ny + fn) * P + p];
+  }
+  __syncthreads();
+  const int r = tid & 1, pl = (tid >> 1) % ppc, c = tid / (2 * ppc);
+
+  // ---- Chebyshev analysis of H_z, H_y, H_x.  In FP32 node precision field f
+  // occupies bytes [8f, 8f + 8) x ny ppc and its coefficients [16f, 16f + 16)
+  // x ny ppc, so going from f = 2 down to 0 with a barrier between reading
+  // and writing a field never overwrites nodal values still to be read.
+  {
+    constexpr int KN = (2 * MH + 3) / 4;  // n values per thread
+    const int qd = r + 2 * c;             // n = qd + 4k, parity of n = r
+    const RN* cheb = cheb_table<RN>(t);
+    const RN sg = r ? (RN)-1.0 : (RN)1.0;
+    const RN s0 = (RN)2.0 / (RN)N;
+    for (int f = 2; f >= 0; --f) {
+      const CN* col = sN + (size_t)f * ny * ppc + pl;
+      CN a[KN];
+      const CN w0 = (RN)0.5 * (col[0] + sg * col[N * ppc]);  // j = 0 and j = N weigh 1/2
+#pragma unroll
+      for (int k = 0; k < KN; ++k) a[k] = w0;
+      for (int j = 1; 2 * j < N; ++j) {
+        const CN fold = col[j * ppc] + sg * col[(N - j) * ppc];
+#pragma unroll
+        for (int k = 0; k < KN; ++k) {
+          const int n = qd + 4 * k;
+          a[k] = a[k] + cheb[(size_t)min(n, N) * ny + j] * fold;
+        }
+      }
+      double2 acc[KN];
+#pragma unroll
+      for (int k = 0; k < KN; ++k) {
+        const int n = qd + 4 * k;
+        const RN cbn = (n == 0 || n == N) ? (RN)2.0 : (RN)1.0;
+        CN v = a[k];
+        if ((N & 1) == 0) v = v + cheb[(size_t)min(n, N) * ny + N / 2] * col[(N / 2) * ppc];
+        acc[k] = to_double((s0 / cbn) * v);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < KN; ++k) {
+        const int n = qd + 4 * k;
+        if (n <= N) sH[((size_t)f * ny + n) * ppc + pl] = acc[k];
+      }
+    }
+    __syncthreads();
+  }
+
+  // ---- implicit solves (no barrier below)
+  const int p = p0 + pl;
+  if (p >= P) return;
+  const int row = p / g.nxh, ix = p % g.nxh;
+  if (row == g.nz / 2) return;  // Nyquist row stays zero
+  const double cc = sc.alpha / sc.beta;
+  const double ibdn = 1.0 / (sc.beta * sc.dt * sc.nu);
+  const double* rowc = t.tau.rowc;
+  const double2* Hx = sH + pl;
+  const double2* Hy = Hx + ny * ppc;
+  const double2* Hz = Hy + ny * ppc;
+  auto comp = [](const double2 z, int qq) { return qq == 0 ? z.x : z.y; };
+  auto helm = [&](int sig) { return TabSm{t.tau.helm + (size_t)(sc.k * 2 + sig) * 4 * Mh * P + p, Mh, P}; };
+  auto helm_isq = [&](int sig) { return t.tau.helm_isq[(size_t)(sc.k * 2 + sig) * P + p]; };
+  if (p == 0) {
+    // mean mode: U (r = 0) at constant flow rate and W (r = 1), parity c
+    const int e = r, s = c;
+    const int M = (N - s) / 2 + 1;
+    double* X = (e == 0 ? pb.UM : pb.WM) + (size_t)b * ny;
+    double* XP = (e == 0 ? pb.HXP : pb.HZP) + (size_t)b * ny;
+    const double2* Hm = (e == 0) ? Hx : Hz;
+    double rhs[MH], f[MH];
+    double sum = 0.0, flux_old = 0.0;
+#pragma unroll
+    for (int i = 0; i < MH; ++i) {
+      rhs[i] = 0.0;
+      if (i < M) {
+        const int n = 2 * i + s;
+        const double xn = X[n];
+        const double hv = Hm[n * ppc].x;
+        const double hp = XP[n];
+        XP[n] = hv;
+        rhs[i] = -((1.0 + cc) * xn + sc.dt * (sc.gamma * hv + sc.zeta * hp)) * ibdn;
+        sum += xn;
+        if (s == 0) flux_old += 2.0 / (1.0 - (double)n * n) * xn;
+      }
+    }
+    tau_seq<MH>(N, ny, s, rhs, f, helm(s), helm_isq(s), cc * sum, rowc);
+    double fc = 0.0;
+    if (e == 0 && s == 0) {
+      double flux = 0.0;
+#pragma unroll
+      for (int i = 0; i < MH; ++i)
+        if (i < M) flux += 2.0 / (1.0 - 4.0 * (double)i * i) * f[i];
+      fc = (sc.flux + cc * flux_old - flux) * t.tau.u1_iflux[sc.k];
+    }
+#pragma unroll
+    for (int i = 0; i < MH; ++i) {
+      if (i < M) {
+        const int n = 2 * i + s;
+        double v = f[i] - cc * X[n];
+        if (e == 0 && s == 0) v += fc * t.tau.u1[(size_t)sc.k * Mh + i];
+        X[n] = v;
+      }
+    }
+    return;
+  }
+  const double kx = t.kx[ix], kz = t.kz[row], k2 = kx * kx + kz * kz;
+  const double sgn = (r == 0) ? -1.0 : 1.0;
+  const int ra = 1 - r;
+  const size_t base = 2 * ((size_t)b * ny * P + p) + r;  // component r of element n at base + 2 P n
+  {
+    // wall-normal vorticity, parity 1 - c
+    const int sq = 1 - c;
+    const int M = (N - sq) / 2 + 1;
+    const CompS Gc{reinterpret_cast<double*>(pb.G) + base, 2 * P};
+    const CompS HGc{reinterpret_cast<double*>(pb.HGP) + base, 2 * P};
+    double rhs[MH], f[MH];
+    double sum = 0.0;
+#pragma unroll
+    for (int i = 0; i < MH; ++i) {
+      rhs[i] = 0.0;
+      if (i < M) {
+        const int n = 2 * i + sq;
+        const double gn = Gc[n];
+        const double hg = sgn * (kz * comp(Hx[n * ppc], ra) - kx * comp(Hz[n * ppc], ra));
+        const double hp = HGc[n];
+        HGc[n] = hg;
+        rhs[i] = -((1.0 + cc) * gn + sc.dt * (sc.gamma * hg + sc.zeta * hp)) * ibdn;
+        sum += gn;
+      }
+    }
+    tau_seq<MH>(N, ny, sq, rhs, f, helm(sq), helm_isq(sq), cc * sum, rowc);
+#pragma unroll
+    for (int i = 0; i < MH; ++i)
+      if (i < M) {
+        const int n = 2 * i + sq;
+        Gc[n] = f[i] - cc * Gc[n];
+      }
+  }
+  {
+    // wall-normal velocity, parity c
+    const int sv = c;
+    const int M = (N - sv) / 2 + 1;
+    const CompS Vc{reinterpret_cast<double*>(pb.V) + base, 2 * P};
+    const CompS HVc{reinterpret_cast<double*>(pb.HVP) + base, 2 * P};
+    double S0 = 0.0, S2 = 0.0;
+    double rhs[MH];
+#pragma unroll
+    for (int i = 0; i < MH; ++i) rhs[i] = 0.0;
+    for (int i = 0; i < M; ++i) {
+      const int n = 2 * i + sv;
+      const double vn = Vc[n];
+      S0 += vn;
+      S2 += (double)n * n * vn;
+    }
+    if (sv == 0)
+      v_walk<MH, 0>(N, ny, ppc, Vc, HVc, Hx, Hy, Hz, r, sgn, kx, kz, k2, cc, ibdn, sc, rhs);
+    else
+      v_walk<MH, 1>(N, ny, ppc, Vc, HVc, Hx, Hy, Hz, r, sgn, kx, kz, k2, cc, ibdn, sc, rhs);
+    double f[MH];
+    tau_seq<MH>(N, ny, sv, rhs, f, helm(sv), helm_isq(sv), 0.0, rowc);
+    const size_t vo = (size_t)b * P + p;
+    const double vw =
+        comp(pb.vw_old[vo], r) + sc.theta * (comp(pb.vw_new[vo], r) - comp(pb.vw_old[vo], r));
+    const double s = ((sv == 0) ? 0.5 : -0.5) * vw + cc * S0;
+    const TabSm TP{t.tau.pois + (size_t)sv * 4 * Mh * P + p, Mh, P};
+    tau_seq<MH>(N, ny, sv, f, rhs, TP, t.tau.pois_isq[(size_t)sv * P + p], s, rowc);
+    double dp = 0.0;
+#pragma unroll
+    for (int i = 0; i < MH; ++i)
+      if (i < M) {
+        const double n = 2 * i + sv;
+        dp += n * n * rhs[i];
+      }
+    const double cI = (cc * S2 - dp) * t.tau.vh_idv[(size_t)(sc.k * 2 + sv) * P + p];
+    const double* vh = t.tau.vh + (size_t)(sc.k * 2 + sv) * Mh * P + p;
+#pragma unroll
+    for (int i = 0; i < MH; ++i)
+      if (i < M) {
+        const int n = 2 * i + sv;
+        Vc[n] = rhs[i] + cI * vh[(size_t)i * P] - cc * Vc[n];
+      }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// per-MH launchers, instantiated in the stage_mh*.cu translation units
+// ---------------------------------------------------------------------------
+template <typename RN, int MH>
+cudaError_t pre_mh(const Grid& g, int B, const PencilBufs& pb, const DevTables& t,
+                          typename cpx<RN>::T* q, int ppc, size_t smem, cudaStream_t st) {
+  static size_t configured = 0;
+  if (smem > configured) {
+    cudaError_t e = cudaFuncSetAttribute(stage_pre_kernel<RN, MH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = smem;
+  }
+  stage_pre_kernel<RN, MH><<<dim3((g.P + ppc - 1) / ppc, B), 128, smem, st>>>(g, B, pb, t, q, ppc);
+  return cudaGetLastError();
+}
+
+template <typename RN, int MH>
+cudaError_t post_mh(const Grid& g, int B, const PencilBufs& pb, const DevTables& t,
+                           const typename cpx<RN>::T* h, const StageCoef& sc, int ppc, size_t smem,
+                           cudaStream_t st) {
+  static size_t configured = 0;
+  if (smem > configured) {
+    cudaError_t e = cudaFuncSetAttribute(stage_post_kernel<RN, MH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = smem;
+  }
+  stage_post_kernel<RN, MH><<<dim3((g.P + ppc - 1) / ppc, B), 8 * ppc, smem, st>>>(g, B, pb, t, h, sc, ppc);
+  return cudaGetLastError();
+}
+
+template <typename RN, int MH>
+cudaError_t post_batched_mh(const Grid& g, int B, const PencilBufs& pb, const DevTables& t,
+                                   const typename cpx<RN>::T* h, const StageCoef& sc, int ppc, size_t smem,
+                                   cudaStream_t st) {
+  static size_t configured = 0;
+  if (smem > configured) {
+    cudaError_t e = cudaFuncSetAttribute(stage_post_batched_kernel<RN, MH>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = smem;
+  }
+  stage_post_batched_kernel<RN, MH><<<dim3((g.P + ppc - 1) / ppc, B), 4 * ppc, smem, st>>>(g, B, pb, t, h, sc,
+                                                                                            ppc);
+  return cudaGetLastError();
+}
+
+}  // namespace chdns
+
+// explicit instantiations of the launchers for one register-array bound MH,
+// both node precisions, by kernel form
+#define CH_STAGE_PRE(MH)                                                                                       \
+  namespace chdns {                                                                                            \
+  template cudaError_t pre_mh<double, MH>(const Grid&, int, const PencilBufs&, const DevTables&, double2*, int,  \
+                                          size_t, cudaStream_t);                                               \
+  template cudaError_t pre_mh<float, MH>(const Grid&, int, const PencilBufs&, const DevTables&, float2*, int,    \
+                                         size_t, cudaStream_t);                                                \
+  }
+#define CH_STAGE_POST(MH)                                                                                      \
+  namespace chdns {                                                                                            \
+  template cudaError_t post_mh<double, MH>(const Grid&, int, const PencilBufs&, const DevTables&, const double2*, \
+                                           const StageCoef&, int, size_t, cudaStream_t);                       \
+  template cudaError_t post_mh<float, MH>(const Grid&, int, const PencilBufs&, const DevTables&, const float2*,   \
+                                          const StageCoef&, int, size_t, cudaStream_t);                        \
+  }
+#define CH_STAGE_POST_BATCHED(MH)                                                                              \
+  namespace chdns {                                                                                            \
+  template cudaError_t post_batched_mh<double, MH>(const Grid&, int, const PencilBufs&, const DevTables&,        \
+                                                   const double2*, const StageCoef&, int, size_t, cudaStream_t); \
+  template cudaError_t post_batched_mh<float, MH>(const Grid&, int, const PencilBufs&, const DevTables&,         \
+                                                  const float2*, const StageCoef&, int, size_t, cudaStream_t);  \
+  }
+#define CH_STAGE_INSTANTIATE(MH) CH_STAGE_PRE(MH) CH_STAGE_POST(MH) CH_STAGE_POST_BATCHED(MH)

@@ -61,6 +61,7 @@ class ChInfo(ctypes.Structure):
         ("device_bytes", ctypes.c_size_t),
         ("plane_cluster", ctypes.c_int),
         ("launches_per_step", ctypes.c_int),
+        ("post_batched", ctypes.c_int),
     ]
 
 

@@ -71,3 +71,41 @@ def compare_states(lst: dict, ost: dict, tol: float):
     bad = {k: e for k, e in errs.items() if not e <= tol}
     assert not bad, f"state mismatch {errs}"
     return errs
+
+
+def run_batch_pair(native, kw: dict, B: int, slots, nsteps: int, seed0: int = 300, amp: float = 0.2,
+                   kmax: int = 99, action_std: float = 0.05, action_seed0: int = 5000):
+    """One batched handle of B environments (seed0 + e) stepped with per-slot
+    seeded actions; the oracle replays the sampled `slots` one by one.
+
+    Returns (info, {slot: (lib_results, oracle_results, lib state, oracle state)})."""
+    op = oracle_params(**kw)
+    ops = channel.Operators(op)
+    nx, ny, nz = op.nx, op.ny, op.nz
+    env = native.env_create(native.params(**kw, batch=B))
+    try:
+        info = native.env_info(env)
+        fields = [si.perturbed_poiseuille(nx, ny, nz, seed0 + e, amp, kmax) for e in range(B)]
+        for e in range(B):
+            native.env_set_state(env, e, native.pack_state(fields[e], nx, ny, nz))
+        acts = []
+        outs = []
+        obs, tau, rew = np.zeros((B, 2, nz, nx)), np.zeros(B), np.zeros(B)
+        for t in range(nsteps):
+            a = None
+            if op.control == 0:
+                a = np.stack([si.wall_action(nx, nz, action_seed0 + 7919 * t + e, action_std * op.u_tau)
+                              for e in range(B)])
+            acts.append(a)
+            assert native.env_step(env, a, obs, tau, rew) == 0
+            outs.append((obs.copy(), tau.copy(), rew.copy()))
+        lib_states = {e: native.unpack_state(native.env_get_state(env, e), nx, ny, nz) for e in slots}
+    finally:
+        native.env_destroy(env)
+    res = {}
+    for e in slots:
+        ost = channel.new_state(fields[e], op)
+        ora = [channel.env_step(ost, ops, None if acts[t] is None else acts[t][e]) for t in range(nsteps)]
+        lib = [(o[e], tt[e], rr[e]) for o, tt, rr in outs]
+        res[e] = (lib, ora, lib_states[e], channel.canonical(ost))
+    return info, res

@@ -17,7 +17,7 @@ import numpy as np
 import pytest
 
 import seeded_inputs as si
-from gpu_util import rel_l2, run_pair, wall_shear_tol
+from gpu_util import rel_l2, run_batch_pair, run_pair, wall_shear_tol
 
 pytestmark = pytest.mark.gpu
 
@@ -100,3 +100,12 @@ def test_mixed_batch_equals_single(native_gpu):
                 native.env_destroy(env1)
     finally:
         native.env_destroy(envb)
+
+
+def test_mixed_batched_implicit_half(native_gpu):
+    """80 minimal channels, mixed precision, batched form of the implicit half:
+    sampled slots against the FP64 oracle."""
+    info, res = run_batch_pair(native_gpu, MINIMAL, 80, (0, 79), 2)
+    assert info.post_batched == 1
+    for e, (lo, oo, ls, os_) in res.items():
+        _report(f"minimal x80 batched, slot {e}, 2 steps", _check(lo, oo, ls, os_, MINIMAL))

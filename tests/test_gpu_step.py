@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 import seeded_inputs as si
-from gpu_util import compare_states, oracle_params, rel_l2, run_pair, wall_shear_tol
+from gpu_util import compare_states, oracle_params, rel_l2, run_batch_pair, run_pair, wall_shear_tol
 from oracle import channel
 
 pytestmark = pytest.mark.gpu
@@ -238,3 +238,24 @@ def test_re395_grid_wall_spectrum_and_boundary_conditions(native_gpu, precision)
     wint = np.zeros(op.ny)
     wint[::2] = 2.0 / (1.0 - n[::2] ** 2)             # int_{-1}^{1} T_n dy
     assert abs(wint @ U - 2.0) < tol * su
+
+
+def test_batched_implicit_half_against_oracle(native_gpu):
+    """80 minimal channels in one handle, enough modes for the batched form of
+    the implicit half of a stage (one thread per mode, class and component):
+    sampled slots, including the first and the last, against the oracle."""
+    info, res = run_batch_pair(native_gpu, MINIMAL, 80, (0, 41, 79), 2)
+    assert info.post_batched == 1
+    for e, (lo, oo, ls, os_) in res.items():
+        compare_states(ls, os_, TOL)
+        _check_outputs(lo, oo, os_, MINIMAL)
+
+
+def test_batched_implicit_half_opposition(native_gpu):
+    """The batched form under opposition control (wall spectrum from the state)."""
+    kw = dict(MINIMAL, control=1, alpha=1.0)
+    info, res = run_batch_pair(native_gpu, kw, 96, (0, 95), 2)
+    assert info.post_batched == 1
+    for e, (lo, oo, ls, os_) in res.items():
+        compare_states(ls, os_, TOL)
+        _check_outputs(lo, oo, os_, kw)
