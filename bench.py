@@ -99,6 +99,19 @@ def kernel_bytes(nx: int, ny: int, nz: int, batch: int, node_bytes: int) -> dict
             "stage_post": M * (3 * node_bytes + 8 * 16)}
 
 
+def implicit_half_fp64_flops(nx: int, ny: int, nz: int, batch: int) -> float:
+    """Algorithmic FP64 FLOPs of one launch of the implicit half of a stage
+    (right-hand sides, tau solves, influence correction), counting a fused
+    multiply-add as 2.  Per Chebyshev coefficient of one class and real
+    component: omega_y right-hand side 12, tau solve 13, update 2; v wall sums
+    4, derivative walk and right-hand side 21, two tau solves 26, influence
+    sum 3, update 4: 85 per coefficient, (N+1) coefficients of both parities
+    over the two classes and 2 components: 170 (N+1) per mode, for every mode
+    but the Nyquist row."""
+    modes = batch * (nx // 2) * (nz - 1)
+    return 170.0 * ny * modes
+
+
 def measured_peaks() -> dict:
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -106,6 +119,14 @@ def measured_peaks() -> dict:
     except OSError:
         return {}
 
+
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# the roofline kernel, from one ncu --set full capture of the same workload
+# (summaries under profiles/); absent where no capture of the current kernel exists
+TRAFFIC_BYTES = {
+    ("larger_fp64", "nonlinear_plane"): 12.644096e6,
+    ("minimal_batch256_mixed", "stage_post"): (181.795072 + 75.341568) * 1e6,
+}
 
 # FP64 FMA rate: 152 SMs x 2 FP64 FMA/clk/SM x 2 FLOP x 2.07 GHz (probe-measured, see the design notes)
 FP64_PEAK_TFLOPS = 1.2586
@@ -451,19 +472,28 @@ def main():
             "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "frac": achieved / FP64_PEAK_TFLOPS,
             "peak_source": "FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 FLOP x 2.07 GHz "
                            "(nominal 1.25 TFLOP/s; FMA probe measured 1.19 at 1.96 GHz)",
-            "flops_per_launch": flops, "avg_launch_ms": avg_s * 1e3, "traffic": None,
+            "flops_per_launch": flops, "avg_launch_ms": avg_s * 1e3,
+            "traffic": TRAFFIC_BYTES.get((args.workload, kk)),
         }
     else:
-        kk = dom
+        # mixed precision: the implicit half (FP64 tau solves) dominates and is
+        # bound by the FP64 pipe; its HBM traffic is a few percent of the peak
+        kk = "stage_post"
         avg_s = kern[kk]["ms_total"] * 1e-3 / max(kern[kk]["launches"], 1)
-        nbytes = kernel_bytes(nx, ny, nz, B, 8).get(kk, 0)
-        achieved = nbytes / avg_s / 1e9
+        flops = implicit_half_fp64_flops(nx, ny, nz, B)
+        achieved = flops / avg_s / 1e12
+        nbytes = kernel_bytes(nx, ny, nz, B, 8)[kk]
         hbm = float(peaks.get("hbm_gbs", 6800.0))
         roofline = {
-            "kernel": kk, "dominant_kernel": dom, "bound": "hbm", "unit": "GB/s",
-            "achieved": achieved, "peak": hbm, "frac": achieved / hbm,
-            "peak_source": "of measured" if "hbm_gbs" in peaks else "of fallback",
-            "bytes_per_launch": nbytes, "avg_launch_ms": avg_s * 1e3, "traffic": None,
+            "kernel": kk, "dominant_kernel": dom, "bound": "alu", "unit": "TFLOP/s",
+            "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "frac": achieved / FP64_PEAK_TFLOPS,
+            "peak_source": "FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 FLOP x 2.07 GHz "
+                           "(nominal 1.25 TFLOP/s; FMA probe measured 1.19 at 1.96 GHz)",
+            "flops_per_launch": flops, "avg_launch_ms": avg_s * 1e3,
+            "traffic": TRAFFIC_BYTES.get((args.workload, kk)),
+            "hbm": {"bytes_per_launch": nbytes, "achieved_gbs": nbytes / avg_s / 1e9, "peak_gbs": hbm,
+                    "frac": nbytes / avg_s / 1e9 / hbm,
+                    "peak_source": "of measured" if "hbm_gbs" in peaks else "of fallback"},
         }
 
     cpu = None

@@ -8,6 +8,7 @@ import math
 import numpy as np
 import pytest
 
+import golden_util
 import seeded_inputs as si
 from gpu_util import compare_states, oracle_params, rel_l2, run_batch_pair, run_pair, wall_shear_tol
 from oracle import channel
@@ -144,10 +145,12 @@ def test_env_reset_matches_generator(native_gpu):
 
 
 def test_orr_sommerfeld_growth_on_gpu(native_gpu):
-    """Tollmien-Schlichting wave at Re_cl = 10^4, alpha = 1: growth 0.00373967 (centre-line units)."""
+    """Tollmien-Schlichting wave at Re_cl = 10^4, alpha = 1 (tests/golden): the
+    amplitude grows at alpha c_i in centre-line units."""
     from oracle import stability
     native = native_gpu
-    _, v_os = stability.most_unstable(64, 1.0, 1.0e4)
+    ref = golden_util.load("orr_sommerfeld_re1e4_alpha1.txt")
+    _, v_os = stability.most_unstable(64, ref["alpha"], ref["reynolds"])
     kw = dict(nx=4, ny=65, nz=4, lx=2 * math.pi, lz=math.pi, re_bulk=1.0e4 / 1.5, dt=0.01 / 1.5)
     env = native.env_create(native.params(**kw))
     try:
@@ -164,7 +167,8 @@ def test_orr_sommerfeld_growth_on_gpu(native_gpu):
     finally:
         native.env_destroy(env)
     sigma = math.log(np.linalg.norm(st["v"][:, 0, 1]) / n0) / (nsteps * kw["dt"]) / 1.5
-    assert abs(sigma - 0.00373967) < 1e-3 * 0.00373967, sigma
+    rate = ref["alpha"] * ref["c_imag"]
+    assert abs(sigma - rate) < 1e-3 * rate, sigma
 
 
 def test_invalid_arguments_are_rejected(native_gpu):

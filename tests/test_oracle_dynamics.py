@@ -21,6 +21,7 @@ import scipy.linalg
 
 import seeded_inputs as si
 from oracle import channel, spectral as sp, stability
+import golden_util
 
 
 def _params(nx=8, ny=33, nz=8, **kw):
@@ -248,8 +249,10 @@ def test_orr_sommerfeld_growth_rate():
     """Tollmien-Schlichting wave, Re_cl = 10^4, alpha = 1: amplitude growth
     rate 0.00373967 in centre-line units.  Bulk units: U = 1.5 (1 - y^2),
     nu = 1.5e-4, so the rate and time step scale by 1.5."""
-    c_os, v_os = stability.most_unstable(64, 1.0, 1.0e4)
-    assert abs(c_os.imag - 0.00373967) < 1e-8
+    ref = golden_util.load("orr_sommerfeld_re1e4_alpha1.txt")
+    c_os, v_os = stability.most_unstable(64, ref["alpha"], ref["reynolds"])
+    assert abs(c_os.real - ref["c_real"]) < 1e-8
+    assert abs(c_os.imag - ref["c_imag"]) < 1e-8
     p = channel.Params(nx=4, ny=65, nz=4, lx=2 * np.pi, lz=np.pi,
                        re_bulk=1.0e4 / 1.5, dt=0.01 / 1.5)
     ops = channel.Operators(p)
@@ -261,7 +264,8 @@ def test_orr_sommerfeld_growth_rate():
         channel.rk3_step(st, ops, st["vw"], st["vw"], 0)
     T = nsteps * p.dt
     sigma = math.log(np.linalg.norm(st["v"][0, 1]) / n0) / T / 1.5
-    assert abs(sigma - 0.00373967) < 1e-3 * 0.00373967, sigma
+    rate = ref["alpha"] * ref["c_imag"]
+    assert abs(sigma - rate) < 1e-3 * rate, sigma
 
 
 # --------------------------------------------------------------------------
@@ -281,7 +285,10 @@ def test_poiseuille_steady_and_laminar_reward():
     assert abs(tau - 3.0 / p.re_bulk) < 1e-13
     # relaminarisation bound (Sec. 3.2): 1 - 3 Re_b / Re_tau^2
     assert abs(reward - (1 - 3 * p.re_bulk / p.re_tau ** 2)) < 1e-10
-    assert abs(reward - 0.7407407407) < 1e-9
+    bound = golden_util.load("laminar_drag_bound.txt")
+    assert abs(reward - bound["closed_form"]) < 1e-9
+    # the paper's printed 73.9 % is this bound at a friction Reynolds number within 0.5 % of 180
+    assert abs(100 * reward - bound["paper_percent"]) < 0.5
     # observation: u = U(y_s) everywhere, v = 0
     ys = math.cos(math.pi * ops.js / ops.N)
     assert np.allclose(obs[0], 1.5 * (1 - ys * ys), atol=1e-13)
