@@ -712,7 +712,7 @@ int env_create(const ch_params_t* p, ch_env_t** out) {
     while (env->ppc_post > 1 && stage_post_smem(g, env->tab.tau.Mh, env->ppc_post) > (size_t)smem_max)
       env->ppc_post /= 2;
     env->ppc_pre = 8;
-    while (env->ppc_pre > 1 && stage_pre_smem(g, env->ppc_pre) > (size_t)smem_max) env->ppc_pre /= 2;
+    while (env->ppc_pre > 1 && stage_pre_smem(g, env->ppc_pre, sizeof(double2)) > (size_t)smem_max) env->ppc_pre /= 2;
     if (stage_post_smem(g, env->tab.tau.Mh, env->ppc_post) > (size_t)smem_max) return fail(CH_ERR_UNSUPPORTED);
     // The batched form of stage_post runs four threads per mode, each with
     // the same work; it pays once the batch supplies at least two such warps

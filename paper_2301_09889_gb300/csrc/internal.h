@@ -33,7 +33,7 @@ struct DevTables {
 };
 
 // fused wall-normal halves of a stage (stage.cu); ppc = modes per CTA
-size_t stage_pre_smem(const Grid& g, int ppc);
+size_t stage_pre_smem(const Grid& g, int ppc, size_t node_bytes);  // node_bytes: one complex node value
 size_t stage_post_smem(const Grid& g, int Mh, int ppc);
 size_t stage_post_batched_smem(const Grid& g, int ppc);
 template <typename RN>

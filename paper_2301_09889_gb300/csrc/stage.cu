@@ -15,7 +15,7 @@ static int mh_bucket(int need) {
   return 0;
 }
 
-size_t stage_pre_smem(const Grid& g, int ppc) { return (size_t)8 * g.ny * ppc * sizeof(double2); }
+size_t stage_pre_smem(const Grid& g, int ppc, size_t node_bytes) { return (size_t)8 * g.ny * ppc * node_bytes; }
 size_t stage_post_batched_smem(const Grid& g, int ppc) { return (size_t)3 * g.ny * ppc * sizeof(double2); }
 // (the coefficient tile is smaller in FP32 node precision; the FP64 size bounds both)
 size_t stage_post_smem(const Grid& g, int Mh, int ppc) {
@@ -25,7 +25,7 @@ size_t stage_post_smem(const Grid& g, int Mh, int ppc) {
 template <typename RN>
 cudaError_t launch_stage_pre(const Grid& g, int B, const PencilBufs& pb, const DevTables& t,
                              typename cpx<RN>::T* q, int ppc, cudaStream_t st) {
-  const size_t smem = stage_pre_smem(g, ppc);
+  const size_t smem = stage_pre_smem(g, ppc, sizeof(typename cpx<RN>::T));
   // 16 (MH - 1) / 16 >= (N + 1) / 2 node pairs per mode
   switch (mh_bucket((g.N + 1) / 2 + 1)) {
     case 5: return pre_mh<RN, 5>(g, B, pb, t, q, ppc, smem, st);

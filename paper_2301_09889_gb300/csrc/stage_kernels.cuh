@@ -36,11 +36,13 @@ namespace chdns {
 // ---------------------------------------------------------------------------
 
 // component r of a complex [n][ppc] tile: element n at p[n * stride]
-struct CompS {
-  double* p;
+template <typename T>
+struct CompT {
+  T* p;
   int stride;
-  __device__ double& operator[](int n) const { return p[n * stride]; }
+  __device__ T& operator[](int n) const { return p[n * stride]; }
 };
+using CompS = CompT<double>;
 
 // tau factor tables of one (mode, parity): element (f, i) at base[(f * Mh + i) * ppc]
 struct TabSm {
@@ -143,6 +145,9 @@ __device__ __forceinline__ const float* cheb_table<float>(const DevTables& t) { 
 
 __device__ __forceinline__ double2 to_double(double2 v) { return v; }
 __device__ __forceinline__ double2 to_double(float2 v) { return make_double2((double)v.x, (double)v.y); }
+template <typename C> __device__ __forceinline__ C to_node(double2 v);
+template <> __device__ __forceinline__ double2 to_node<double2>(double2 v) { return v; }
+template <> __device__ __forceinline__ float2 to_node<float2>(double2 v) { return make_float2((float)v.x, (float)v.y); }
 
 // ---------------------------------------------------------------------------
 // stage_pre
@@ -164,9 +169,11 @@ __global__ void __launch_bounds__(128) stage_pre_kernel(Grid g, int B, PencilBuf
   using CN = typename cpx<RN>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int P = g.P, ny = g.ny, N = g.N;
-  double2* sV = reinterpret_cast<double2*>(smem_raw);  // [ny][ppc]
-  double2* sG = sV + ny * ppc;                          // [ny][ppc]
-  CN* sC = reinterpret_cast<CN*>(sG + ny * ppc);        // [6][ny][ppc] in the node precision
+  // v, omega_y coefficients rounded once to the node precision (every use
+  // below is in that precision), then the six fields
+  CN* sV = reinterpret_cast<CN*>(smem_raw);  // [ny][ppc]
+  CN* sG = sV + ny * ppc;                    // [ny][ppc]
+  CN* sC = sG + ny * ppc;                    // [6][ny][ppc]
   const int p0 = blockIdx.x * ppc;
   const int b = blockIdx.y;
   if (pb.active && !pb.active[b]) return;
@@ -176,8 +183,8 @@ __global__ void __launch_bounds__(128) stage_pre_kernel(Grid g, int B, PencilBuf
     const int pl = w % ppc, n = w / ppc;
     const int p = p0 + pl;
     const size_t o = ((size_t)b * ny + n) * P + p;
-    sV[w] = (p < P) ? pb.V[o] : mk(0.0, 0.0);
-    sG[w] = (p < P) ? pb.G[o] : mk(0.0, 0.0);
+    sV[w] = to_node<CN>((p < P) ? pb.V[o] : mk(0.0, 0.0));
+    sG[w] = to_node<CN>((p < P) ? pb.G[o] : mk(0.0, 0.0));
   }
   __syncthreads();
 
@@ -191,8 +198,7 @@ __global__ void __launch_bounds__(128) stage_pre_kernel(Grid g, int B, PencilBuf
     RN* out = reinterpret_cast<RN*>(sC) + 2 * pl + r;
     // middle node f_{N/2} = sum over even n of (-1)^(n/2) a_n, per field
     RN mid[6] = {0, 0, 0, 0, 0, 0};
-    auto W = [&](int f, int n, double v) {
-      const RN x = (RN)v;
+    auto W = [&](int f, int n, RN x) {
       out[f * fs + n * 2 * ppc] = x;
       if ((n & 1) == 0) mid[f] = (n & 2) ? mid[f] - x : mid[f] + x;
     };
@@ -226,16 +232,16 @@ __global__ void __launch_bounds__(128) stage_pre_kernel(Grid g, int B, PencilBuf
       const RN kx = (RN)t.kx[ix], kz = (RN)t.kz[row];
       const RN sg = (r == 0) ? (RN)-1.0 : (RN)1.0;
       const RN ik2 = sg / (kx * kx + kz * kz);
-      const CompS V{reinterpret_cast<double*>(sV) + 2 * pl + r, 2 * ppc};
-      const CompS Va{reinterpret_cast<double*>(sV) + 2 * pl + (1 - r), 2 * ppc};
-      const CompS G{reinterpret_cast<double*>(sG) + 2 * pl + r, 2 * ppc};
-      const CompS Ga{reinterpret_cast<double*>(sG) + 2 * pl + (1 - r), 2 * ppc};
+      const CompT<RN> V{reinterpret_cast<RN*>(sV) + 2 * pl + r, 2 * ppc};
+      const CompT<RN> Va{reinterpret_cast<RN*>(sV) + 2 * pl + (1 - r), 2 * ppc};
+      const CompT<RN> G{reinterpret_cast<RN*>(sG) + 2 * pl + r, 2 * ppc};
+      const CompT<RN> Ga{reinterpret_cast<RN*>(sG) + 2 * pl + (1 - r), 2 * ppc};
       RN dv = 0, d2v = 0, dg = 0, vnext = 0, gnext = 0;
       for (int n = N; n >= 0; --n) {
         if ((n & 1) == 1 - c) {
           const RN t1 = dv + (RN)(2 * (n + 1)) * vnext;
           dv = (n == 0) ? (RN)0.5 * t1 : t1;
-          const RN ga = (RN)Ga[n];
+          const RN ga = Ga[n];
           W(0, n, ik2 * (kx * dv - kz * ga));  // u
           W(2, n, ik2 * (kz * dv + kx * ga));  // w
           W(4, n, G[n]);                       // omega_y
@@ -245,7 +251,7 @@ __global__ void __launch_bounds__(128) stage_pre_kernel(Grid g, int B, PencilBuf
           const RN t2 = dg + (RN)(2 * (n + 1)) * gnext;
           d2v = (n == 0) ? (RN)0.5 * t1 : t1;
           dg = (n == 0) ? (RN)0.5 * t2 : t2;
-          const RN va = (RN)Va[n];
+          const RN va = Va[n];
           const RN du = ik2 * (kx * d2v - kz * dg);
           const RN dw = ik2 * (kz * d2v + kx * dg);
           W(1, n, V[n]);                 // v
