@@ -189,6 +189,12 @@ struct ch_env {
   bool prof = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[4];
   int ev_used[4] = {0, 0, 0, 0};
+  // The step's launch sequence is fixed for a handle: it is captured once into
+  // a CUDA graph on the internal action/output buffers and replayed (one
+  // launch instead of 14-15).  [0]: every slot; [1]: slots masked by
+  // graph_mask (serving ticks).  Profiling launches the same kernels directly.
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  const int* graph_mask = nullptr;
   char err[256] = {0};
 };
 
@@ -218,6 +224,8 @@ int dupload(ch_env* env, const T** ptr, const std::vector<T>& host) {
 void free_env(ch_env* env) {
   if (!env) return;
   if (env->stream) cudaStreamSynchronize(env->stream);
+  for (cudaGraphExec_t& x : env->graph)
+    if (x) cudaGraphExecDestroy(x);
   for (auto& v : env->ev)
     for (auto& pr : v) {
       cudaEventDestroy(pr.first);
@@ -565,10 +573,8 @@ int run_stage(ch_env* env, int k, double theta) {
   return CH_OK;
 }
 
-// One environment step of every slot flagged in `h_active` (nullptr: all);
-// `d_active` is the same mask on the device.
-int run_step(ch_env* env, const double* d_action, double* d_out, const int* d_active = nullptr,
-             const int* h_active = nullptr) {
+// The kernels of one environment step, in stream order.
+int launch_step(ch_env* env, const double* d_action, double* d_out, const int* d_active) {
   const Grid& g = env->g;
   const int B = env->B;
   cudaStream_t st = env->stream;
@@ -593,6 +599,53 @@ int run_step(ch_env* env, const double* d_action, double* d_out, const int* d_ac
   LAUNCH(3, launch_obs(g, B, env->pb.planes, env->tab, d_out, env->out_stride, d_active, st));
   LAUNCH(3, launch_finalize(B, env->pb.tau_acc, 1.0 / spa, env->tau_ref, d_out, env->out_stride,
                             (size_t)2 * g.nz * g.nx, d_active, st));
+  return CH_OK;
+}
+
+// Capture launch_step on the internal buffers into graph[gi].
+int capture_step(ch_env* env, int gi, const int* d_active) {
+  cudaStream_t st = env->stream;
+  CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+  const int rc = launch_step(env, env->d_act, env->d_out, d_active);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(st, &graph);
+  if (rc != CH_OK || e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc != CH_OK ? rc : CH_ERR_CUDA;
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&env->graph[gi], graph, 0);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) {
+    env->graph[gi] = nullptr;
+    return CH_ERR_CUDA;
+  }
+  return CH_OK;
+}
+
+// One environment step of every slot flagged in `h_active` (nullptr: all);
+// `d_active` is the same mask on the device.
+int run_step(ch_env* env, const double* d_action, double* d_out, const int* d_active = nullptr,
+             const int* h_active = nullptr) {
+  const int B = env->B;
+  if (env->prof) {
+    RC(launch_step(env, d_action, d_out, d_active));
+  } else {
+    cudaStream_t st = env->stream;
+    const int gi = d_active ? 1 : 0;
+    if (d_active && env->graph_mask != d_active) {
+      if (env->graph[1]) CK(cudaGraphExecDestroy(env->graph[1]));
+      env->graph[1] = nullptr;
+      env->graph_mask = d_active;
+    }
+    if (!env->graph[gi]) RC(capture_step(env, gi, d_active));
+    const size_t plane = (size_t)env->g.nz * env->g.nx;
+    if (env->prm.control == 0 && d_action != env->d_act)
+      CK(cudaMemcpyAsync(env->d_act, d_action, B * plane * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CK(cudaGraphLaunch(env->graph[gi], st));
+    if (d_out != env->d_out)
+      CK(cudaMemcpyAsync(d_out, env->d_out, B * env->out_stride * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  }
+  const int spa = env->prm.steps_per_action;
   for (int b = 0; b < B; ++b) {
     if (h_active && !h_active[b]) continue;
     env->t[b] += spa * env->prm.dt;

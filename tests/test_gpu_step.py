@@ -263,3 +263,30 @@ def test_batched_implicit_half_opposition(native_gpu):
     for e, (lo, oo, ls, os_) in res.items():
         compare_states(ls, os_, TOL)
         _check_outputs(lo, oo, os_, kw)
+
+
+@pytest.mark.parametrize("kw", [dict(MINIMAL), dict(MINIMAL, control=1, alpha=1.0), dict(MINIMAL, precision=1)])
+def test_graph_replay_equals_direct_launches(native_gpu, kw):
+    """A step replayed from the captured CUDA graph (profiling off) and the same
+    kernels launched one by one (profiling on) give bit-identical results."""
+    native = native_gpu
+    B = 3
+    acts = np.stack([si.wall_action(16, 16, 400 + e, 0.5 * 180 / 2800) for e in range(B)])
+    res = []
+    for profile in (False, True):
+        env = native.env_create(native.params(**kw, batch=B))
+        try:
+            native.env_profile(env, profile)
+            for e in range(B):
+                native.env_set_state(env, e, native.pack_state(si.perturbed_poiseuille(16, 65, 16, 50 + e, 0.2, 99),
+                                                               16, 65, 16))
+            obs, tau, rew = np.zeros((B, 2, 16, 16)), np.zeros(B), np.zeros(B)
+            for _ in range(3):
+                assert native.env_step(env, acts if kw.get("control", 0) == 0 else None, obs, tau, rew) == 0
+            res.append(([native.env_get_state(env, e) for e in range(B)], obs.copy(), tau.copy()))
+        finally:
+            native.env_destroy(env)
+    (sa, oa, ta), (sb, ob, tb) = res
+    for e in range(B):
+        assert np.array_equal(sa[e], sb[e])
+    assert np.array_equal(oa, ob) and np.array_equal(ta, tb)
