@@ -525,6 +525,10 @@ def main():
                 "h2d_bytes_per_step": 8 * B * nz * nx if external else 0,
                 "d2h_bytes_per_step": 8 * B * out_len},
         "gpu_launches": int(sum(v["launches"] for v in kern.values())),
+        "tiles": {"ppc_pre": info.ppc_pre, "ppc_post": info.ppc_post, "post_batched": info.post_batched,
+                  "autotuned": bool(info.tuned), "tune_ms": info.tune_ms, "plane_cluster": info.plane_cluster},
+        "step_launch": "profiled region: kernels launched one by one (per-class CUDA events); "
+                       "e2e: one captured CUDA graph per step",
         "clocks": clk,
         "finite": finite,
     }

@@ -63,7 +63,7 @@ extern "C" {
 /* ---- parameters ---------------------------------------------------------- */
 typedef struct ch_params {
     int nx, ny, nz;          /* Fourier modes in x, Chebyshev nodes in y, Fourier modes in z
-                                (nx, nz even >= 4; ny odd or even >= 9, <= 257)        */
+                                (nx, nz even >= 4; ny odd or even >= 9, <= 201)        */
     double lx, lz;           /* box length and width in half heights                  */
     double re_tau;           /* friction Reynolds number (sets u_tau and the sensing plane) */
     double re_bulk;          /* bulk Reynolds number U_b h / nu (> 0)                  */
@@ -79,6 +79,11 @@ typedef struct ch_params {
     double alpha;            /* opposition-control gain                                */
     double tau_ref;          /* reward reference wall shear; <= 0 -> u_tau^2          */
     int batch;               /* number of environments B sharing launches; <= 0 -> 1   */
+    int autotune;            /* 1 (default): env_create times the candidate tile shapes of
+                                the stage kernels on this grid and batch and keeps the
+                                fastest; 0: size heuristic.  The candidates perform the
+                                same floating-point operations per output, so the choice
+                                changes speed only, never results                       */
 } ch_params_t;
 
 typedef struct ch_info {
@@ -90,7 +95,10 @@ typedef struct ch_info {
     int plane_cluster;       /* CTAs cooperating on one y-plane of the nonlinear term       */
     int launches_per_step;   /* kernels launched by one env_step                            */
     int post_batched;        /* 1: the implicit half of a stage runs one thread per (mode,
-                                class, component) -- chosen when B x modes fills the SMs   */
+                                class, component); 0: eight threads per mode on a tile  */
+    int ppc_pre, ppc_post;   /* Fourier modes per CTA of the explicit and implicit halves */
+    int tuned;               /* 1 if the tile shapes were chosen by timing (autotune)    */
+    double tune_ms;          /* host time env_create spent timing candidates            */
 } ch_info_t;
 
 typedef struct ch_env ch_env_t;
@@ -181,6 +189,16 @@ int env_profile(ch_env_t* env, int enable);
 int env_profile_read(ch_env_t* env, int cls, double* total_ms, int* launches);
 
 int env_info(const ch_env_t* env, ch_info_t* info);
+
+/* Pin the tile shapes of the two stage kernels (overriding the autotuner):
+ * ppc_pre in {1, 2, 4, 8} modes per 128-thread CTA of the explicit half;
+ * post_batched 0 with ppc_post in {1, 2, 4, 8} (8 threads per mode) or 1
+ * with ppc_post in {1, 2, 4, 8, 16} (4 threads per mode).  Every shape gives
+ * bit-identical results.  Waits for the handle's stream.  No counterpart in
+ * the paper (a tuning control of this implementation).
+ * Errors: CH_ERR_ARG (bad handle or shape, or a shape whose shared memory
+ * exceeds the device limit), CH_ERR_CUDA. */
+int env_set_tiles(ch_env_t* env, int ppc_pre, int ppc_post, int post_batched);
 int env_destroy(ch_env_t* env);
 const char* ch_strerror(int code);
 

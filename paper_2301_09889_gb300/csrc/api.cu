@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <chrono>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -152,6 +153,7 @@ int check_params(const ch_params_t* p) {
   if (!(p->lx > 0) || !(p->lz > 0) || !(p->re_bulk > 0) || !(p->re_tau > 0) || !(p->dt > 0)) return CH_ERR_ARG;
   if (p->steps_per_action < 1) return CH_ERR_ARG;
   if (p->control != 0 && p->control != 1) return CH_ERR_ARG;
+  if (p->autotune != 0 && p->autotune != 1) return CH_ERR_ARG;
   if (p->top_bc != 0 || (p->precision != 0 && p->precision != 1)) return CH_ERR_UNSUPPORTED;
   FftPlan a, b;
   if (!fft_plan(3 * p->nx / 2, &a) || !fft_plan(3 * p->nz / 2, &b)) return CH_ERR_UNSUPPORTED;
@@ -185,6 +187,8 @@ struct ch_env {
   int launches_per_step = 0;
   int ppc_pre = 8, ppc_post = 8;  // modes per CTA of the fused stage kernels
   bool post_batched = false;      // batched form of stage_post (one thread per mode, class, component)
+  bool tuned = false;             // tile shapes chosen by timing at env_create
+  double tune_ms = 0.0;
   // kernel timing (env_profile)
   bool prof = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[4];
@@ -535,6 +539,21 @@ cudaError_t prof_mark(ch_env* env, int cls, bool begin) {
     CK(prof_mark(env, (cls), false));       \
   } while (0)
 
+// Coefficients of RK stage k (C3) with the wall-velocity ramp at theta (C4).
+StageCoef stage_coef(const ch_env* env, int k, double theta) {
+  StageCoef sc;
+  sc.alpha = rk_alpha(k);
+  sc.beta = rk_beta(k);
+  sc.gamma = kGamma[k];
+  sc.zeta = kZeta[k];
+  sc.dt = env->prm.dt;
+  sc.nu = env->nu;
+  sc.theta = theta;
+  sc.flux = 2.0;
+  sc.k = k;
+  return sc;
+}
+
 int run_stage(ch_env* env, int k, double theta) {
   const Grid& g = env->g;
   const int B = env->B;
@@ -554,16 +573,7 @@ int run_stage(ch_env* env, int k, double theta) {
     a.h = env->pb.R;
     LAUNCH(1, launch_plane<double>(a, B, env->plane_smem, st));
   }
-  StageCoef sc;
-  sc.alpha = rk_alpha(k);
-  sc.beta = rk_beta(k);
-  sc.gamma = kGamma[k];
-  sc.zeta = kZeta[k];
-  sc.dt = env->prm.dt;
-  sc.nu = env->nu;
-  sc.theta = theta;
-  sc.flux = 2.0;
-  sc.k = k;
+  const StageCoef sc = stage_coef(env, k, theta);
   if (mixed)
     LAUNCH(2, launch_stage_post<float>(g, B, env->pb, env->tab, reinterpret_cast<const float2*>(env->pb.R), sc,
                                        env->ppc_post, env->post_batched, st));
@@ -619,6 +629,120 @@ int capture_step(ch_env* env, int gi, const int* d_active) {
     env->graph[gi] = nullptr;
     return CH_ERR_CUDA;
   }
+  return CH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Tile shapes of the stage kernels.  Every candidate performs the same
+// floating-point operations per output (each mode's recurrences and sums run
+// in one fixed order whatever the number of modes per CTA or the thread
+// mapping), so the shapes change speed only, never results.
+// ---------------------------------------------------------------------------
+bool tiles_valid(const ch_env* env, int smem_max, int ppc_pre, int ppc_post, int post_batched) {
+  const Grid& g = env->g;
+  const size_t node = env->prm.precision == 1 ? sizeof(float2) : sizeof(double2);
+  auto pow2 = [](int v, int hi) { return v >= 1 && v <= hi && (v & (v - 1)) == 0; };
+  if (!pow2(ppc_pre, 8) || stage_pre_smem(g, ppc_pre, node) > (size_t)smem_max) return false;
+  if (post_batched == 1) return pow2(ppc_post, 16) && stage_post_batched_smem(g, ppc_post) <= (size_t)smem_max;
+  if (post_batched != 0) return false;
+  return pow2(ppc_post, 8) && stage_post_smem(g, env->tab.tau.Mh, ppc_post) <= (size_t)smem_max;
+}
+
+int drop_graphs(ch_env* env) {
+  for (cudaGraphExec_t& x : env->graph) {
+    if (x) CK(cudaGraphExecDestroy(x));
+    x = nullptr;
+  }
+  env->graph_mask = nullptr;
+  return CH_OK;
+}
+
+// Median device time of `reps` launches after one warm-up launch.
+template <class F>
+int time_launches(cudaStream_t st, int reps, F&& launch, float* ms) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+    if (a) cudaEventDestroy(a);
+    return CH_ERR_CUDA;
+  }
+  std::vector<float> t;
+  int rc = launch();
+  for (int i = 0; i < reps && rc == CH_OK; ++i) {
+    float x = 0.f;
+    if (cudaEventRecord(a, st) != cudaSuccess || (rc = launch()) != CH_OK || cudaEventRecord(b, st) != cudaSuccess ||
+        cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&x, a, b) != cudaSuccess) {
+      rc = rc != CH_OK ? rc : CH_ERR_CUDA;
+      break;
+    }
+    t.push_back(x);
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (rc != CH_OK) return rc;
+  std::sort(t.begin(), t.end());
+  *ms = t[t.size() / 2];
+  return CH_OK;
+}
+
+// Time the candidate shapes of both stage kernels on this handle's buffers,
+// before its initial state is written (the kernels run on zeroed fields), and
+// keep the fastest of each.
+int autotune_tiles(ch_env* env, int smem_max) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const Grid& g = env->g;
+  const int B = env->B;
+  const size_t Bs = B, P = g.P, ny = g.ny;
+  cudaStream_t st = env->stream;
+  PencilBufs& pb = env->pb;
+  CK(cudaMemsetAsync(pb.V, 0, Bs * ny * P * sizeof(double2), st));
+  CK(cudaMemsetAsync(pb.G, 0, Bs * ny * P * sizeof(double2), st));
+  CK(cudaMemsetAsync(pb.HVP, 0, Bs * ny * P * sizeof(double2), st));
+  CK(cudaMemsetAsync(pb.HGP, 0, Bs * ny * P * sizeof(double2), st));
+  CK(cudaMemsetAsync(pb.R, 0, Bs * 3 * ny * P * sizeof(double2), st));
+  CK(cudaMemsetAsync(pb.vw_old, 0, Bs * P * sizeof(double2), st));
+  CK(cudaMemsetAsync(pb.vw_new, 0, Bs * P * sizeof(double2), st));
+  for (double* x : {pb.UM, pb.WM, pb.HXP, pb.HZP}) CK(cudaMemsetAsync(x, 0, Bs * ny * sizeof(double), st));
+  const bool mixed = env->prm.precision == 1;
+  const StageCoef sc = stage_coef(env, 0, 1.0);
+  auto pre = [&](int ppc) {
+    const cudaError_t e = mixed ? launch_stage_pre<float>(g, B, pb, env->tab, reinterpret_cast<float2*>(pb.Q), ppc, st)
+                                : launch_stage_pre<double>(g, B, pb, env->tab, pb.Q, ppc, st);
+    return e == cudaSuccess ? CH_OK : CH_ERR_CUDA;
+  };
+  auto post = [&](int ppc, bool batched) {
+    const cudaError_t e =
+        mixed ? launch_stage_post<float>(g, B, pb, env->tab, reinterpret_cast<const float2*>(pb.R), sc, ppc, batched, st)
+              : launch_stage_post<double>(g, B, pb, env->tab, pb.R, sc, ppc, batched, st);
+    return e == cudaSuccess ? CH_OK : CH_ERR_CUDA;
+  };
+  constexpr int kReps = 3;
+  float best = 0.f;
+  bool have = false;
+  for (int ppc : {8, 4, 2}) {
+    if (!tiles_valid(env, smem_max, ppc, env->ppc_post, env->post_batched ? 1 : 0)) continue;
+    float ms = 0.f;
+    RC(time_launches(st, kReps, [&] { return pre(ppc); }, &ms));
+    if (!have || ms < best) {
+      best = ms;
+      env->ppc_pre = ppc;
+      have = true;
+    }
+  }
+  have = false;
+  const std::pair<int, int> cands[] = {{0, 8}, {0, 4}, {0, 2}, {1, 16}, {1, 8}};
+  for (const auto& c : cands) {
+    if (!tiles_valid(env, smem_max, env->ppc_pre, c.second, c.first)) continue;
+    float ms = 0.f;
+    RC(time_launches(st, kReps, [&] { return post(c.second, c.first == 1); }, &ms));
+    if (!have || ms < best) {
+      best = ms;
+      env->post_batched = c.first == 1;
+      env->ppc_post = c.second;
+      have = true;
+    }
+  }
+  env->tuned = true;
+  env->tune_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return CH_OK;
 }
 
@@ -701,6 +825,7 @@ int ch_default_params(ch_params_t* p) {
   p->y_sense_plus = 15.0;
   p->top_bc = 0; p->precision = 0; p->control = 0;
   p->alpha = 1.0; p->tau_ref = 0.0; p->batch = 1;
+  p->autotune = 1;
   return CH_OK;
 }
 
@@ -772,10 +897,12 @@ int env_create(const ch_params_t* p, ch_env_t** out) {
     // per SM sub-partition (B P / 8 >= 2 x 4 x SMs).
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return fail(CH_ERR_CUDA);
-    if ((size_t)B * P >= (size_t)64 * sms && stage_post_batched_smem(g, 16) <= (size_t)smem_max) {
+    if ((size_t)B * P >= (size_t)64 * sms && stage_post_batched_smem(g, 8) <= (size_t)smem_max) {
       env->post_batched = true;
-      env->ppc_post = 16;
+      env->ppc_post = 16;  // 64 threads; 8 when the tile would leave fewer than 3 CTAs per SM
+      if (stage_post_batched_smem(g, 16) > (size_t)76 * 1024) env->ppc_post = 8;
     }
+    if (p->autotune && (rc = autotune_tiles(env, smem_max))) return fail(rc);
   }
   // laminar Poiseuille, zero wall action
   std::vector<double> st(ch_state_bytes(p) / sizeof(double), 0.0);
@@ -889,6 +1016,25 @@ int env_info(const ch_env_t* env, ch_info_t* info) {
   info->plane_cluster = env->prm.precision == 1 ? env->plane_f.S : env->plane.S;
   info->launches_per_step = env->launches_per_step;
   info->post_batched = env->post_batched ? 1 : 0;
+  info->ppc_pre = env->ppc_pre;
+  info->ppc_post = env->ppc_post;
+  info->tuned = env->tuned ? 1 : 0;
+  info->tune_ms = env->tune_ms;
+  return CH_OK;
+}
+
+int env_set_tiles(ch_env_t* env, int ppc_pre, int ppc_post, int post_batched) {
+  if (!env) return CH_ERR_ARG;
+  int smem_max = 0, dev = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if (!tiles_valid(env, smem_max, ppc_pre, ppc_post, post_batched)) return CH_ERR_ARG;
+  CK(cudaStreamSynchronize(env->stream));
+  RC(drop_graphs(env));
+  env->ppc_pre = ppc_pre;
+  env->ppc_post = ppc_post;
+  env->post_batched = post_batched == 1;
+  env->tuned = false;
   return CH_OK;
 }
 

@@ -129,7 +129,7 @@ ch_params_t key_of(const ch_params_t& p) {
   k.nx = p.nx; k.ny = p.ny; k.nz = p.nz; k.lx = p.lx; k.lz = p.lz;
   k.re_tau = p.re_tau; k.re_bulk = p.re_bulk; k.dt = p.dt; k.steps_per_action = p.steps_per_action;
   k.y_sense_plus = p.y_sense_plus; k.top_bc = p.top_bc; k.precision = p.precision; k.control = p.control;
-  k.alpha = p.alpha; k.tau_ref = p.tau_ref; k.batch = 0;
+  k.alpha = p.alpha; k.tau_ref = p.tau_ref; k.batch = 0; k.autotune = p.autotune;
   return k;
 }
 

@@ -31,7 +31,7 @@ EXPORTS = (
     "ch_default_params", "env_create", "env_set_stream", "env_reset", "env_step",
     "env_step_device", "env_get_state", "env_set_state", "env_info", "env_destroy",
     "ch_strerror", "ch_seed_state", "ch_state_bytes", "ch_nonlinear", "ch_tau_helmholtz",
-    "env_profile", "env_profile_read", "ch_tau_helmholtz_noalloc",
+    "env_profile", "env_profile_read", "ch_tau_helmholtz_noalloc", "env_set_tiles",
     "srv_create", "srv_admit", "srv_evict", "srv_submit", "srv_poll", "srv_wait", "srv_get_state",
     "srv_set_state", "srv_stats", "srv_destroy",
 )
@@ -49,6 +49,7 @@ class ChParams(ctypes.Structure):
         ("top_bc", ctypes.c_int), ("precision", ctypes.c_int), ("control", ctypes.c_int),
         ("alpha", ctypes.c_double), ("tau_ref", ctypes.c_double),
         ("batch", ctypes.c_int),
+        ("autotune", ctypes.c_int),
     ]
 
 
@@ -62,6 +63,9 @@ class ChInfo(ctypes.Structure):
         ("plane_cluster", ctypes.c_int),
         ("launches_per_step", ctypes.c_int),
         ("post_batched", ctypes.c_int),
+        ("ppc_pre", ctypes.c_int), ("ppc_post", ctypes.c_int),
+        ("tuned", ctypes.c_int),
+        ("tune_ms", ctypes.c_double),
     ]
 
 
@@ -116,6 +120,7 @@ def load() -> ctypes.CDLL:
         "ch_tau_helmholtz": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp, vp]),
         "ch_tau_helmholtz_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp, vp]),
         "env_profile": (ctypes.c_int, [vp, ctypes.c_int]),
+        "env_set_tiles": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
         "srv_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, P(vp)]),
         "srv_admit": (ctypes.c_int, [vp, P(ChParams), ctypes.c_uint64, ctypes.c_double, ctypes.c_int,
                                      P(ctypes.c_int)]),
@@ -214,6 +219,10 @@ def env_step(env, action: np.ndarray | None, obs: np.ndarray, wall_shear: np.nda
 def env_step_device(env, d_action: int | None, d_out: int):
     _check(load().env_step_device(env, ctypes.c_void_p(d_action or 0), ctypes.c_void_p(d_out)),
            "env_step_device")
+
+
+def env_set_tiles(env, ppc_pre: int, ppc_post: int, post_batched: int):
+    _check(load().env_set_tiles(env, ppc_pre, ppc_post, post_batched), "env_set_tiles")
 
 
 def env_info(env) -> ChInfo:

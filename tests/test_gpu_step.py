@@ -290,3 +290,50 @@ def test_graph_replay_equals_direct_launches(native_gpu, kw):
     for e in range(B):
         assert np.array_equal(sa[e], sb[e])
     assert np.array_equal(oa, ob) and np.array_equal(ta, tb)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_tile_shapes_give_identical_results(native_gpu, precision):
+    """Every tile shape of the stage kernels (modes per CTA; per-tile or batched
+    implicit half) gives bit-identical results, so the autotuner's choice
+    changes speed only."""
+    native = native_gpu
+    B = 3
+    kw = dict(MINIMAL, precision=precision, autotune=0)
+    acts = np.stack([si.wall_action(16, 16, 700 + e, 0.5 * 180 / 2800) for e in range(B)])
+    shapes = [(8, 8, 0), (4, 4, 0), (2, 2, 0), (1, 1, 0), (8, 16, 1), (4, 8, 1), (2, 1, 1)]
+    ref = None
+    for pre, post, bat in shapes:
+        env = native.env_create(native.params(**kw, batch=B))
+        try:
+            native.env_set_tiles(env, pre, post, bat)
+            info = native.env_info(env)
+            assert (info.ppc_pre, info.ppc_post, info.post_batched, info.tuned) == (pre, post, bat, 0)
+            for e in range(B):
+                native.env_set_state(env, e, native.pack_state(si.perturbed_poiseuille(16, 65, 16, 60 + e, 0.2, 99),
+                                                               16, 65, 16))
+            obs, tau, rew = np.zeros((B, 2, 16, 16)), np.zeros(B), np.zeros(B)
+            for _ in range(2):
+                assert native.env_step(env, acts, obs, tau, rew) == 0
+            got = (np.concatenate([native.env_get_state(env, e) for e in range(B)]), obs.copy(), tau.copy())
+        finally:
+            native.env_destroy(env)
+        if ref is None:
+            ref = got
+        else:
+            assert all(np.array_equal(a, b) for a, b in zip(ref, got)), (pre, post, bat)
+
+
+def test_autotune_picks_a_candidate_and_rejects_bad_shapes(native_gpu):
+    native = native_gpu
+    env = native.env_create(native.params(**MINIMAL, batch=80))
+    try:
+        info = native.env_info(env)
+        assert info.tuned == 1 and info.tune_ms > 0
+        assert info.ppc_pre in (2, 4, 8)
+        assert (info.post_batched, info.ppc_post) in {(0, 8), (0, 4), (0, 2), (1, 16), (1, 8)}
+        for bad in ((3, 8, 0), (16, 8, 0), (8, 16, 0), (8, 32, 1), (8, 8, 2)):
+            with pytest.raises(native.ChannelError):
+                native.env_set_tiles(env, *bad)
+    finally:
+        native.env_destroy(env)
