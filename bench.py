@@ -51,6 +51,10 @@ WORKLOADS = {
     "minimal_batch256_mixed": (MINIMAL, 256, 1,
                                "256 minimal channels 16x65x16 in one launch per kernel, mixed precision, "
                                "per-step seeded ZNMF Gaussian actions std 0.05 u_tau"),
+    "large550_mixed": (dict(MINIMAL, nx=256, ny=193, nz=256, lx=2 * math.pi, lz=math.pi, re_tau=550.0,
+                            re_bulk=10030.0, dt=0.002), 1, 1,
+                       "large channel Re_tau=550, 256x193x256, mixed precision, seeded ZNMF Gaussian actions "
+                       "std 0.05 u_tau (the FP64 padded plane does not fit a cluster's shared memory)"),
 }
 # served workloads: (list of (parameters, count), slots per class, description)
 MID = dict(LARGER, nx=32, nz=32, control=0)

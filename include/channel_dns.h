@@ -280,7 +280,9 @@ int srv_destroy(ch_server_t* s);
  *       at each node, of u, v, w, omega_x, omega_y, omega_z;
  *   d_h [B][3][ny][nz][nx/2] complex: Fourier coefficients of the kept modes
  *       of H = u x omega evaluated on the 3nx/2 x 3nz/2 grid.
- * Uses the handle's twiddle tables; allocates nothing. */
+ * Uses the handle's twiddle tables; allocates nothing.  CH_ERR_UNSUPPORTED
+ * where the FP64 padded plane does not fit a cluster's shared memory
+ * (e.g. 256 x 256 Fourier modes; mixed-precision handles of that size run). */
 int ch_nonlinear(ch_env_t* env, const double* d_q, double* d_h);
 
 /* Chebyshev-tau Dirichlet problems (D^2 - lam_m) f = r (coefficient rows

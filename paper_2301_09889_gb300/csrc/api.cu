@@ -271,12 +271,15 @@ int setup_plane(ch_env* env, PlaneArgs<R>* a, size_t* smem) {
     if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
       nsm = v;
   }
-  int feasible[4], nf = 0;
+  int feasible[5], nf = 0;
   for (int S = 1; S <= 8; S *= 2) {
     if (g.mz % S || (g.mz / S) % 2) continue;
     if ((size_t)6 * (g.mz / S) * g.nxh * csz > 160 * 1024) continue;
     feasible[nf++] = S;
   }
+  // a 16-CTA cluster (non-portable opt-in) only where no portable size fits
+  if (!nf && g.mz % 16 == 0 && (g.mz / 16) % 2 == 0 && (size_t)6 * (g.mz / 16) * g.nxh * csz <= 160 * 1024)
+    feasible[nf++] = 16;
   if (!nf) return CH_ERR_UNSUPPORTED;
   int S = feasible[nf - 1];
   for (int k = 0; k < nf; ++k)
@@ -297,6 +300,14 @@ int setup_plane(ch_env* env, PlaneArgs<R>* a, size_t* smem) {
   }
   if (!a->S) return CH_ERR_UNSUPPORTED;
   if (!fft_plan(g.mx, &a->px) || !fft_plan(a->Lz, &a->pz)) return CH_ERR_UNSUPPORTED;
+  if (a->S > 8) {
+    int clusters = 0;
+    if (plane_max_clusters<R>(*a, *smem, &clusters) != cudaSuccess || clusters < 1) {
+      cudaGetLastError();
+      a->S = 0;
+      return CH_ERR_UNSUPPORTED;
+    }
+  }
   auto cast = [](const std::vector<double2>& v) {
     std::vector<C> o(v.size());
     for (size_t i = 0; i < v.size(); ++i) o[i] = mk((R)v[i].x, (R)v[i].y);
@@ -421,8 +432,13 @@ int build_tables(ch_env* env) {
   RC(dupload(env, &env->tab.tw_nx, twiddles(g.nx)));
   RC(dupload(env, &env->tab.tw_nz, twiddles(g.nz)));
 
-  RC(setup_plane(env, &env->plane, &env->plane_smem));
-  RC(setup_plane(env, &env->plane_f, &env->plane_f_smem));
+  // the plane of the handle's precision is required; the other one serves
+  // ch_nonlinear (FP64) and is skipped where its slab does not fit
+  const int r64 = setup_plane(env, &env->plane, &env->plane_smem);
+  const int r32 = setup_plane(env, &env->plane_f, &env->plane_f_smem);
+  if (env->prm.precision == 1 ? r32 != CH_OK : r64 != CH_OK) return env->prm.precision == 1 ? r32 : r64;
+  if (r64 != CH_OK) env->plane.S = 0;
+  if (r32 != CH_OK) env->plane_f.S = 0;
   return CH_OK;
 }
 
@@ -1067,6 +1083,7 @@ int env_destroy(ch_env_t* env) {
 
 int ch_nonlinear(ch_env_t* env, const double* d_q, double* d_h) {
   if (!env || !d_q || !d_h) return CH_ERR_ARG;
+  if (env->plane.S == 0) return CH_ERR_UNSUPPORTED;
   PlaneArgs<double> a = env->plane;
   a.q = reinterpret_cast<const double2*>(d_q);
   a.h = reinterpret_cast<double2*>(d_h);

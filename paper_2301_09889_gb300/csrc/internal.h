@@ -9,6 +9,8 @@ namespace chdns {
 
 template <typename R>
 cudaError_t launch_plane(const PlaneArgs<R>& a, int B, size_t smem, cudaStream_t st);
+template <typename R>
+cudaError_t plane_max_clusters(const PlaneArgs<R>& a, size_t smem, int* clusters);
 
 struct PencilBufs {
   double2 *V, *G, *HVP, *HGP;   // [B][ny][P]

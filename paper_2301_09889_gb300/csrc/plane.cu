@@ -304,6 +304,11 @@ static cudaError_t launch_with(K kernel, const PlaneArgs<R>& a, int B, size_t sm
   if (smem > *configured) {
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    if (a.S > 8) {
+      // clusters above 8 CTAs are a non-portable opt-in
+      e = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      if (e != cudaSuccess) return e;
+    }
     *configured = smem;
   }
   cudaLaunchConfig_t cfg = {};
@@ -347,6 +352,33 @@ cudaError_t launch_plane(const PlaneArgs<R>& a, int B, size_t smem, cudaStream_t
   return launch_with(plane_kernel<R>, a, B, smem, st, &cfg_generic);
 }
 
+// Clusters of a.S CTAs with `smem` bytes each that the device can hold at
+// once for the runtime-size kernel (0: the shape cannot be launched).
+template <typename R>
+cudaError_t plane_max_clusters(const PlaneArgs<R>& a, size_t smem, int* clusters) {
+  *clusters = 0;
+  cudaError_t e = cudaFuncSetAttribute(plane_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (a.S > 8) {
+    e = cudaFuncSetAttribute(plane_kernel<R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(a.S, a.ny, 1);
+  cfg.blockDim = dim3(256, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = a.S;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaOccupancyMaxActiveClusters(clusters, plane_kernel<R>, &cfg);
+}
+
+template cudaError_t plane_max_clusters<double>(const PlaneArgs<double>&, size_t, int*);
+template cudaError_t plane_max_clusters<float>(const PlaneArgs<float>&, size_t, int*);
 template cudaError_t launch_plane<double>(const PlaneArgs<double>&, int, size_t, cudaStream_t);
 template cudaError_t launch_plane<float>(const PlaneArgs<float>&, int, size_t, cudaStream_t);
 

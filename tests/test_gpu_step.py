@@ -189,22 +189,21 @@ def test_invalid_arguments_are_rejected(native_gpu):
 
 
 RE395 = dict(nx=128, ny=129, nz=128, lx=2 * math.pi, lz=math.pi, re_tau=395.0, re_bulk=6875.0, dt=0.0025)
+RE550 = dict(nx=256, ny=193, nz=256, lx=2 * math.pi, lz=math.pi, re_tau=550.0, re_bulk=10030.0, dt=0.002)
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_re395_grid_wall_spectrum_and_boundary_conditions(native_gpu, precision):
-    """128x129x128 channel (too large for the oracle's full step): the applied
+def _large_grid_step_checks(native, grid, precision, seed, kmax):
+    """One step of a grid too large for the oracle's full step: the applied
     wall spectrum matches the oracle's clip/zero-mean/transform of the same
     action, and after the step the state satisfies, at any size, the
     boundary conditions v(-1) = v_w, v(+1) = 0, v'(+-1) = 0, g(+-1) = 0,
     U(+-1) = W(+-1) = 0 and the constant flow rate int U dy = 2."""
-    native = native_gpu
-    kw = dict(RE395, precision=precision)
-    op = oracle_params(**RE395)
+    kw = dict(grid, precision=precision)
+    op = oracle_params(**grid)
     ops = channel.Operators(op)
     env = native.env_create(native.params(**kw))
     try:
-        fields = si.perturbed_poiseuille(op.nx, op.ny, op.nz, 5, 0.1, 8)
+        fields = si.perturbed_poiseuille(op.nx, op.ny, op.nz, seed, 0.1, kmax)
         native.env_set_state(env, 0, native.pack_state(fields, op.nx, op.ny, op.nz))
         act = si.wall_action(op.nx, op.nz, 77, 1.5 * op.u_tau)   # clip active
         obs = np.zeros((2, op.nz, op.nx))
@@ -212,6 +211,7 @@ def test_re395_grid_wall_spectrum_and_boundary_conditions(native_gpu, precision)
         rew = np.zeros(1)
         assert native.env_step(env, np.ascontiguousarray(act), obs, tau, rew) == 0
         st = native.unpack_state(native.env_get_state(env, 0), op.nx, op.ny, op.nz)
+        info = native.env_info(env)
     finally:
         native.env_destroy(env)
     assert np.isfinite(obs).all() and np.isfinite(tau).all() and np.isfinite(rew).all()
@@ -242,6 +242,29 @@ def test_re395_grid_wall_spectrum_and_boundary_conditions(native_gpu, precision)
     wint = np.zeros(op.ny)
     wint[::2] = 2.0 / (1.0 - n[::2] ** 2)             # int_{-1}^{1} T_n dy
     assert abs(wint @ U - 2.0) < tol * su
+    return info
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_re395_grid_wall_spectrum_and_boundary_conditions(native_gpu, precision):
+    """128x129x128 channel at Re_tau 395, FP64 and mixed."""
+    _large_grid_step_checks(native_gpu, RE395, precision, 5, 8)
+
+
+def test_re550_grid_mixed_wall_spectrum_and_boundary_conditions(native_gpu):
+    """256x193x256 channel at Re_tau 550, mixed precision: the padded FP32
+    plane is split over a 16-CTA cluster."""
+    info = _large_grid_step_checks(native_gpu, RE550, 1, 6, 8)
+    assert info.plane_cluster == 16
+
+
+def test_re550_grid_fp64_is_reported_unsupported(native_gpu):
+    """The FP64 padded plane of 256x256 modes exceeds the shared memory of any
+    cluster: env_create refuses it with CH_ERR_UNSUPPORTED."""
+    native = native_gpu
+    with pytest.raises(native.ChannelError) as exc:
+        native.env_create(native.params(**RE550, precision=0))
+    assert exc.value.code == -8
 
 
 def test_batched_implicit_half_against_oracle(native_gpu):
