@@ -161,13 +161,14 @@ __global__ void __launch_bounds__(256) plane_kernel(PlaneArgs<R> a) {
 }
 
 
-// The same kernel with the transform lengths, the kept kx count and the row
-// pairs per batch fixed at compile time (index arithmetic by constants, FFT
-// passes unrolled).  Instantiated for the grids of the configurations in use.
-template <typename R, int MX, int LZ, int NXH, int NP>
-__global__ void __launch_bounds__(256) plane_kernel_ct(PlaneArgs<R> a) {
+// The same kernel with the transform lengths, the kept kx count, the row
+// pairs per batch and the CTA size fixed at compile time (index arithmetic by
+// constants, FFT passes unrolled).  Instantiated for the grids of the
+// configurations in use; planes whose shared memory allows one CTA per SM run
+// more threads per CTA to hide shared-memory latency.
+template <typename R, int MX, int LZ, int NXH, int NP, int NT>
+__global__ void __launch_bounds__(NT) plane_kernel_ct(PlaneArgs<R> a) {
   using C = typename cpx<R>::T;
-  constexpr int NT = 256;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* Z = reinterpret_cast<C*>(smem_raw);  // [6][LZ][NXH]
   C* X = Z + 6 * LZ * NXH;                // [6][NP][MX]
@@ -300,7 +301,7 @@ __global__ void __launch_bounds__(256) plane_kernel_ct(PlaneArgs<R> a) {
 
 template <typename K, typename R>
 static cudaError_t launch_with(K kernel, const PlaneArgs<R>& a, int B, size_t smem, cudaStream_t st,
-                               size_t* configured) {
+                               size_t* configured, int nt = 256) {
   if (smem > *configured) {
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -313,7 +314,7 @@ static cudaError_t launch_with(K kernel, const PlaneArgs<R>& a, int B, size_t sm
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(a.S, a.ny, B);
-  cfg.blockDim = dim3(256, 1, 1);
+  cfg.blockDim = dim3(nt, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
@@ -327,11 +328,12 @@ static cudaError_t launch_with(K kernel, const PlaneArgs<R>& a, int B, size_t sm
 }
 
 // compile-time instantiations: (MX, LZ, NXH, NP) of the grids in use
-#define CH_PLANE_CT(MX_, LZ_, NXH_, NP_)                                                              \
+#define CH_PLANE_CT_NT(MX_, LZ_, NXH_, NP_, NT_)                                                      \
   if (a.mx == MX_ && a.Lz == LZ_ && a.nxh == NXH_ && a.NP == NP_) {                                  \
     static size_t cfg_ = 0;                                                                           \
-    return launch_with(plane_kernel_ct<R, MX_, LZ_, NXH_, NP_>, a, B, smem, st, &cfg_);               \
+    return launch_with(plane_kernel_ct<R, MX_, LZ_, NXH_, NP_, NT_>, a, B, smem, st, &cfg_, NT_);     \
   }
+#define CH_PLANE_CT(MX_, LZ_, NXH_, NP_) CH_PLANE_CT_NT(MX_, LZ_, NXH_, NP_, 256)
 
 template <typename R>
 cudaError_t launch_plane(const PlaneArgs<R>& a, int B, size_t smem, cudaStream_t st) {
@@ -347,6 +349,7 @@ cudaError_t launch_plane(const PlaneArgs<R>& a, int B, size_t smem, cudaStream_t
     CH_PLANE_CT(96, 24, 32, 12)
     CH_PLANE_CT(48, 12, 16, 6)
     CH_PLANE_CT(192, 48, 64, 8)
+    CH_PLANE_CT_NT(384, 24, 128, 4, 1024)
   }
   static size_t cfg_generic = 0;
   return launch_with(plane_kernel<R>, a, B, smem, st, &cfg_generic);
