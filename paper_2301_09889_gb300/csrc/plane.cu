@@ -340,15 +340,15 @@ cudaError_t launch_plane(const PlaneArgs<R>& a, int B, size_t smem, cudaStream_t
   if constexpr (sizeof(R) == 8) {
     CH_PLANE_CT(24, 6, 8, 3)
     CH_PLANE_CT(24, 24, 8, 12)
-    CH_PLANE_CT(96, 24, 32, 3)
+    CH_PLANE_CT_NT(96, 24, 32, 3, 512)
     CH_PLANE_CT(48, 12, 16, 6)
-    CH_PLANE_CT(192, 24, 64, 4)
+    CH_PLANE_CT_NT(192, 24, 64, 4, 1024)
   } else {
     CH_PLANE_CT(24, 6, 8, 3)
     CH_PLANE_CT(24, 24, 8, 12)
     CH_PLANE_CT(96, 24, 32, 12)
     CH_PLANE_CT(48, 12, 16, 6)
-    CH_PLANE_CT(192, 48, 64, 8)
+    CH_PLANE_CT_NT(192, 48, 64, 8, 1024)
     CH_PLANE_CT_NT(384, 24, 128, 4, 1024)
   }
   static size_t cfg_generic = 0;
