@@ -291,7 +291,8 @@ __global__ void __launch_bounds__(128) stage_pre_kernel(Grid g, int B, PencilBuf
           O[f][k] = czero<CN>();
         }
       const CN* col = sC + pl;
-      for (int n = 0; n <= N; ++n) {
+      // even and odd n in one iteration, so that neither update is predicated
+      auto accumulate = [&](int n, CN (&acc)[6][KJ]) {
         CN cf[6];
 #pragma unroll
         for (int f = 0; f < 6; ++f) cf[f] = col[((size_t)f * ny + n) * ppc];
@@ -299,15 +300,15 @@ __global__ void __launch_bounds__(128) stage_pre_kernel(Grid g, int B, PencilBuf
         for (int k = 0; k < KJ; ++k) {
           const int j = gq + ng * k;
           const RN c = cheb[(size_t)min(j, N) * ny + n];
-          if (n & 1) {
 #pragma unroll
-            for (int f = 0; f < 6; ++f) O[f][k] = O[f][k] + c * cf[f];
-          } else {
-#pragma unroll
-            for (int f = 0; f < 6; ++f) E[f][k] = E[f][k] + c * cf[f];
-          }
+          for (int f = 0; f < 6; ++f) acc[f][k] = acc[f][k] + c * cf[f];
         }
+      };
+      for (int n = 0; n + 1 <= N; n += 2) {
+        accumulate(n, E);
+        accumulate(n + 1, O);
       }
+      if ((N & 1) == 0) accumulate(N, E);
       const int p = p0 + pl;
       if (p < P) {
 #pragma unroll
