@@ -431,6 +431,7 @@ int build_tables(ch_env* env) {
   env->tab.tau.Mh = Mh;
   RC(dupload(env, &env->tab.tw_nx, twiddles(g.nx)));
   RC(dupload(env, &env->tab.tw_nz, twiddles(g.nz)));
+  RC(dupload(env, &env->tab.tw_cheb, twiddles(g.N)));
 
   // the plane of the handle's precision is required; the other one serves
   // ch_nonlinear (FP64) and is skipped where its slab does not fit

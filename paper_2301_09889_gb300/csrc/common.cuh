@@ -180,6 +180,14 @@ __host__ __device__ constexpr int ct_radix(int n, int st) {
   while (n % 3 == 0) { if (s == st) return 3; n /= 3; ++s; }
   return 1;
 }
+// true when the radix-4/2/3 plan factors n completely
+__host__ __device__ constexpr bool ct_plan_ok(int n) {
+  if (n < 2) return false;
+  while (n % 4 == 0) n /= 4;
+  while (n % 2 == 0) n /= 2;
+  while (n % 3 == 0) n /= 3;
+  return n == 1;
+}
 // sub-length L before pass st of the DIF order
 __host__ __device__ constexpr int ct_len_before(int n, int st) {
   int L = n;

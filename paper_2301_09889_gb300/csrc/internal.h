@@ -32,6 +32,7 @@ struct DevTables {
   TauTables tau;
   const double2* tw_nx;  // [nx]
   const double2* tw_nz;  // [nz]
+  const double2* tw_cheb;  // [N] e^{2 pi i k / N}: fast Chebyshev synthesis
 };
 
 // fused wall-normal halves of a stage (stage.cu); ppc = modes per CTA

@@ -15,7 +15,10 @@ static int mh_bucket(int need) {
   return 0;
 }
 
-size_t stage_pre_smem(const Grid& g, int ppc, size_t node_bytes) { return (size_t)8 * g.ny * ppc * node_bytes; }
+// (plus two complex values per line for the fast synthesis)
+size_t stage_pre_smem(const Grid& g, int ppc, size_t node_bytes) {
+  return (size_t)8 * g.ny * ppc * node_bytes + (size_t)12 * ppc * sizeof(double2);
+}
 size_t stage_post_batched_smem(const Grid& g, int ppc) { return (size_t)3 * g.ny * ppc * sizeof(double2); }
 // (the coefficient tile is smaller in FP32 node precision; the FP64 size bounds both)
 size_t stage_post_smem(const Grid& g, int Mh, int ppc) {

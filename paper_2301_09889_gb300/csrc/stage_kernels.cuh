@@ -25,6 +25,8 @@
 // derivative recurrence c_m b_m = b_{m+2} + 2 (m+1) a_{m+1} (c_0 = 2).
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "internal.h"
 #include "stage_launch.h"
@@ -150,6 +152,64 @@ template <> __device__ __forceinline__ double2 to_node<double2>(double2 v) { ret
 template <> __device__ __forceinline__ float2 to_node<float2>(double2 v) { return make_float2((float)v.x, (float)v.y); }
 
 // ---------------------------------------------------------------------------
+// Fast Chebyshev synthesis (DCT-I) of complex lines through an N-point FFT,
+// N even:  F_j = sum_{n=0}^{N} x_n cos(pi j n / N), j = 0..N.
+// With y_n = (x_n + x_{N-n})/2 - sin(pi n / N) (x_n - x_{N-n}), n = 0..N-1,
+// and Z_k = sum_n y_n e^{2 pi i k n / N}: the cosine sums pick out the part
+// of y symmetric under n -> N - n, which reproduces the even outputs, and the
+// sine sums the antisymmetric part, which gives differences of odd outputs:
+//   F_{2k} = (Z_k + Z_{N-k}) / 2 + (x_0 + x_N) / 2,          k = 0..N/2,
+//   F_{2k+1} = F_{2k-1} - i (Z_k - Z_{N-k}) / 2,             k = 1..N/2-1,
+//   F_1 = sum_n x_n cos(pi n / N).
+// O(N log N) FP64 operations per line instead of the (N/2)(N+1) of the sums.
+// Lines: line l = f G + pl at buf + f LS + pl, element stride G.
+// ---------------------------------------------------------------------------
+template <int N, int ST>
+__device__ __forceinline__ void lines_dif(double2* buf, const double2* tw, int nlines, int G, int LS) {
+  if constexpr (ST < ct_nst(N)) {
+    constexpr int r = ct_radix(N, ST);
+    constexpr int L = ct_len_before(N, ST);
+    constexpr int m = L / r;
+    constexpr int nb = N / r;
+    constexpr int tstep = N / L;
+    for (int w = threadIdx.x; w < nlines * nb; w += blockDim.x) {
+      const int l = w % nlines, bf = w / nlines;
+      double2* base = buf + (l / G) * LS + (l % G);
+      const int blk = bf / m, q = bf % m;
+      const int i0 = blk * L + q;
+      double2 x[r];
+#pragma unroll
+      for (int t = 0; t < r; ++t) x[t] = base[(i0 + t * m) * G];
+      small_dft_ct<+1, r, double2, double>(x);
+#pragma unroll
+      for (int u = 0; u < r; ++u) {
+        double2 y = x[u];
+        if (u > 0 && q > 0) y = cmul(y, tw[q * u * tstep]);
+        base[(i0 + u * m) * G] = y;
+      }
+    }
+    __syncthreads();
+    lines_dif<N, ST + 1>(buf, tw, nlines, G, LS);
+  }
+}
+
+// position of frequency k in the digit-reversed output of the DIF passes:
+// sum over passes of (digit of k in that pass's radix) x (sub-block length)
+template <int N>
+__device__ __forceinline__ int dif_pos(int k) {
+  int p = 0, L = N;
+#pragma unroll
+  for (int st = 0; st < ct_nst(N); ++st) {
+    const int r = ct_radix(N, st);
+    const int m = L / r;
+    p += (k % r) * m;
+    k /= r;
+    L = m;
+  }
+  return p;
+}
+
+// ---------------------------------------------------------------------------
 // stage_pre
 //   u = (i kx Dv - i kz g)/k^2, w = (i kz Dv + i kx g)/k^2,
 //   omega_x = Dw - i kz v, omega_z = i kx v - Du;  mean mode: u = U, w = W,
@@ -178,6 +238,10 @@ __global__ void __launch_bounds__(128) stage_pre_kernel(Grid g, int B, PencilBuf
   const int b = blockIdx.y;
   if (pb.active && !pb.active[b]) return;
   const int tid = threadIdx.x, nt = blockDim.x;
+  // FP64 nodes on a grid whose N the FFT plan covers: fast synthesis
+  constexpr int NF = 2 * (MH - 1);
+  constexpr bool kFastOk = std::is_same<RN, double>::value && ct_plan_ok(NF);
+  const bool fast = kFastOk && N == NF;
 
   for (int w = tid; w < ny * ppc; w += nt) {
     const int pl = w % ppc, n = w / ppc;
@@ -262,7 +326,7 @@ __global__ void __launch_bounds__(128) stage_pre_kernel(Grid g, int B, PencilBuf
       }
     }
     // this thread wrote the even coefficients of fields 0, 2, 4 (c = 1) or 1, 3, 5 (c = 0)
-    if ((N & 1) == 0 && p < P) {
+    if (!fast && (N & 1) == 0 && p < P) {
       RN* qr = reinterpret_cast<RN*>(q);
 #pragma unroll
       for (int f = 0; f < 6; ++f)
@@ -270,6 +334,71 @@ __global__ void __launch_bounds__(128) stage_pre_kernel(Grid g, int B, PencilBuf
     }
   }
   __syncthreads();
+
+  if constexpr (kFastOk) {
+    if (fast) {
+      const int nl = 6 * ppc;
+      const int LS = ny * ppc;
+      double2* X = sC;                   // [6][ny][ppc] coefficients, then y, then Z
+      double2* sHalf = sC + 6 * ny * ppc;  // [6 ppc] (x_0 + x_N) / 2
+      double2* sF1 = sHalf + nl;           // [6 ppc] F_1
+      const double* cheb = t.cheb;       // cheb[ny + m] = cos(pi m / N)
+      for (int l = tid; l < nl; l += nt) {
+        const double2* x = X + (l / ppc) * LS + (l % ppc);
+        double2 s1 = mk(0.0, 0.0);
+        for (int n = 0; n <= N; ++n) s1 = s1 + cheb[ny + n] * x[n * ppc];
+        sF1[l] = s1;
+        sHalf[l] = 0.5 * (x[0] + x[N * ppc]);
+      }
+      __syncthreads();
+      for (int w = tid; w < nl * (N / 2); w += nt) {
+        const int l = w % nl, n = w / nl;
+        double2* x = X + (l / ppc) * LS + (l % ppc);
+        if (n == 0) {
+          x[0] = sHalf[l];  // y_0; y_{N/2} = x_{N/2} stays
+          continue;
+        }
+        const double2 xa = x[n * ppc], xb = x[(N - n) * ppc];
+        const double sn = cheb[ny + N / 2 - n];  // sin(pi n / N)
+        const double2 sm = 0.5 * (xa + xb), d = xa - xb;
+        x[n * ppc] = sm - sn * d;
+        x[(N - n) * ppc] = sm + sn * d;
+      }
+      __syncthreads();
+      lines_dif<NF, 0>(X, t.tw_cheb, nl, ppc, LS);
+      // even outputs, and the odd-output differences -i (Z_k - Z_{N-k}) / 2
+      // stored in Z_k's own slot (slots of Z_{N-k}, k < N/2, are only read)
+      for (int w = tid; w < nl * (NF / 2 + 1); w += nt) {
+        const int l = w % nl, k = w / nl;
+        const int f = l / ppc, pl = l % ppc, p = p0 + pl;
+        double2* Z = X + f * LS + pl;
+        const int ik = dif_pos<NF>(k) * ppc;
+        const double2 zk = Z[ik];
+        const double2 zn = Z[dif_pos<NF>((NF - k) % NF) * ppc];
+        if (p < P) q[((size_t)(b * 6 + f) * ny + 2 * k) * P + p] = 0.5 * (zk + zn) + sHalf[l];
+        if (k >= 1 && k < NF / 2) {
+          const double2 dd = zk - zn;
+          Z[ik] = mk(0.5 * dd.y, -0.5 * dd.x);
+        }
+      }
+      __syncthreads();
+      // odd outputs: prefix sums from F_1
+      for (int l = tid; l < nl; l += nt) {
+        const int f = l / ppc, pl = l % ppc, p = p0 + pl;
+        if (p >= P) continue;
+        const double2* Z = X + f * LS + pl;
+        double2* dst = q + ((size_t)(b * 6 + f) * ny) * P + p;
+        double2 fo = sF1[l];
+        dst[P] = fo;
+#pragma unroll 4
+        for (int k = 1; k < NF / 2; ++k) {
+          fo = fo + Z[dif_pos<NF>(k) * ppc];
+          dst[(size_t)(2 * k + 1) * P] = fo;
+        }
+      }
+      return;
+    }
+  }
 
   // synthesis of the six fields at the nodes.  Thread (mode pl, group g of
   // nt / ppc) evaluates the node pairs j = g, g + ng, ... of all six fields of
