@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(128) stage_pre_kernel(Grid g, int B, PencilBuf
     RN mid[6] = {0, 0, 0, 0, 0, 0};
     auto W = [&](int f, int n, RN x) {
       out[f * fs + n * 2 * ppc] = x;
-      if ((n & 1) == 0) mid[f] = (n & 2) ? mid[f] - x : mid[f] + x;
+      if (!fast && (n & 1) == 0) mid[f] = (n & 2) ? mid[f] - x : mid[f] + x;
     };
     if (p >= P || row == g.nz / 2 || (p == 0 && r == 1)) {
       for (int n = 0; n <= N; ++n) {
@@ -301,28 +301,49 @@ __global__ void __launch_bounds__(128) stage_pre_kernel(Grid g, int B, PencilBuf
       const CompT<RN> G{reinterpret_cast<RN*>(sG) + 2 * pl + r, 2 * ppc};
       const CompT<RN> Ga{reinterpret_cast<RN*>(sG) + 2 * pl + (1 - r), 2 * ppc};
       RN dv = 0, d2v = 0, dg = 0, vnext = 0, gnext = 0;
-      for (int n = N; n >= 0; --n) {
-        if ((n & 1) == 1 - c) {
-          const RN t1 = dv + (RN)(2 * (n + 1)) * vnext;
-          dv = (n == 0) ? (RN)0.5 * t1 : t1;
-          const RN ga = Ga[n];
-          W(0, n, ik2 * (kx * dv - kz * ga));  // u
-          W(2, n, ik2 * (kz * dv + kx * ga));  // w
-          W(4, n, G[n]);                       // omega_y
-          gnext = ga;
-        } else {
-          const RN t1 = d2v + (RN)(2 * (n + 1)) * dv;
-          const RN t2 = dg + (RN)(2 * (n + 1)) * gnext;
-          d2v = (n == 0) ? (RN)0.5 * t1 : t1;
-          dg = (n == 0) ? (RN)0.5 * t2 : t2;
-          const RN va = Va[n];
-          const RN du = ik2 * (kx * d2v - kz * dg);
-          const RN dw = ik2 * (kz * d2v + kx * dg);
-          W(1, n, V[n]);                 // v
-          W(3, n, dw - sg * kz * va);    // omega_x = Dw - i kz v
-          W(5, n, sg * kx * va - du);    // omega_z = i kx v - Du
-          vnext = va;
-        }
+      const RN skx = sg * kx, skz = sg * kz;
+      // U-step at n (parity 1 - c): Dv_n and u, w, omega_y; V-step at n (parity
+      // c): D^2 v_n, D omega_y_n and v, omega_x, omega_z.  Walking down from N
+      // they alternate; every U-step at n is followed by the V-step at n - 1,
+      // so both classes run the same uniform loop body.  fac = 2 (n + 1).
+      auto ustep = [&](int n, RN fac, bool halve) {
+        const RN t1 = dv + fac * vnext;
+        dv = halve ? (RN)0.5 * t1 : t1;
+        const RN ga = Ga[n];
+        W(0, n, ik2 * (kx * dv - kz * ga));  // u
+        W(2, n, ik2 * (kz * dv + kx * ga));  // w
+        W(4, n, G[n]);                       // omega_y
+        gnext = ga;
+      };
+      auto vstep = [&](int n, RN fac, bool halve) {
+        const RN t1 = d2v + fac * dv;
+        const RN t2 = dg + fac * gnext;
+        d2v = halve ? (RN)0.5 * t1 : t1;
+        dg = halve ? (RN)0.5 * t2 : t2;
+        const RN va = Va[n];
+        const RN du = ik2 * (kx * d2v - kz * dg);
+        const RN dw = ik2 * (kz * d2v + kx * dg);
+        W(1, n, V[n]);            // v
+        W(3, n, dw - skz * va);   // omega_x = Dw - i kz v
+        W(5, n, skx * va - du);   // omega_z = i kx v - Du
+        vnext = va;
+      };
+      int nu = N;                 // first U-step
+      if ((N & 1) != 1 - c) {     // the walk starts with the V-step at N
+        vstep(N, (RN)(2 * (N + 1)), N == 0);
+        nu = N - 1;
+      }
+      RN fu = (RN)(2 * (nu + 1));
+      for (; nu >= 2; nu -= 2) {  // U at nu >= 2, V at nu - 1 >= 1
+        ustep(nu, fu, false);
+        vstep(nu - 1, fu - (RN)2, false);
+        fu = fu - (RN)4;
+      }
+      if (nu == 1) {
+        ustep(1, (RN)4, false);
+        vstep(0, (RN)2, true);
+      } else if (nu == 0) {
+        ustep(0, (RN)2, true);
       }
     }
     // this thread wrote the even coefficients of fields 0, 2, 4 (c = 1) or 1, 3, 5 (c = 0)
