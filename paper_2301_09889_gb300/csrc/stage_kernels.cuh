@@ -102,36 +102,41 @@ __device__ __forceinline__ void tau_seq(int N, int ny, int sig, const double (&r
     if (i < M) f[i] += T.Q(i) * f0;
 }
 
-// Right-hand side of the v equation of one parity SV and component r, one
-// walk from n = N down to 0 carrying Dv, D^2 v, t = i kx H_x + i kz H_z and
-// Dt; also stores h_v for the next stage.  SV is a template parameter so that
-// every register index is fixed at compile time.
-template <int MH, int SV>
-__device__ __forceinline__ void v_walk(int N, int ny, int ppc, const CompS& Vc, const CompS& HVc,
+// Right-hand side of the v equation of parity sv and component r, one walk
+// from n = N down to 0 carrying Dv, D^2 v, t = i kx H_x + i kz H_z and Dt;
+// also stores h_v for the next stage.  Iteration i runs the other-parity step
+// at 2i + sv + 1 (Dv, t) and then the own step at 2i + sv, so the register
+// index i is fixed at compile time and the code is the same for both
+// parities (threads of the two classes share warps).  The other-parity step
+// at n = 0 (sv = 1) has no consumer and is not run.
+template <int MH>
+__device__ __forceinline__ void v_walk(int N, int ny, int ppc, int sv, const CompS& Vc, const CompS& HVc,
                                        const double2* Hx, const double2* Hy, const double2* Hz, int r, double sgn,
                                        double kx, double kz, double k2, double cc, double ibdn, const StageCoef& sc,
                                        double (&rhs)[MH]) {
   const int ra = 1 - r;
   auto comp = [](const double2 z, int qd) { return qd == 0 ? z.x : z.y; };
+  const double dsv = 2.0 * sv;
   double dv = 0.0, d2v = 0.0, tt = 0.0, dtt = 0.0;
 #pragma unroll
-  for (int n = 2 * MH - 1; n >= 0; --n) {
-    if (n > N) continue;
-    if ((n & 1) != SV) {
-      const double vn1 = (n + 1 <= N) ? Vc[n + 1] : 0.0;
-      const double t1 = dv + 2.0 * (n + 1) * vn1;
-      dv = (n == 0) ? 0.5 * t1 : t1;
-      tt = sgn * (kx * comp(Hx[n * ppc], ra) + kz * comp(Hz[n * ppc], ra));
-    } else {
-      const double t1 = d2v + 2.0 * (n + 1) * dv;
-      const double t2 = dtt + 2.0 * (n + 1) * ((n + 1 <= N) ? tt : 0.0);
+  for (int i = MH - 1; i >= 0; --i) {
+    const int no = 2 * i + sv + 1;
+    if (no <= N) {
+      const double vn1 = (no + 1 <= N) ? Vc[no + 1] : 0.0;
+      dv = dv + ((double)(4 * i + 4) + dsv) * vn1;  // 2 (no + 1)
+      tt = sgn * (kx * comp(Hx[no * ppc], ra) + kz * comp(Hz[no * ppc], ra));
+    }
+    const int n = 2 * i + sv;
+    if (n <= N) {
+      const double fac = (double)(4 * i + 2) + dsv;  // 2 (n + 1)
+      const double t1 = d2v + fac * dv;
+      const double t2 = dtt + fac * ((n + 1 <= N) ? tt : 0.0);
       d2v = (n == 0) ? 0.5 * t1 : t1;
       dtt = (n == 0) ? 0.5 * t2 : t2;
       const double phi = d2v - k2 * Vc[n];
       const double hv = -k2 * comp(Hy[n * ppc], r) - dtt;
       const double hp = HVc[n];
       HVc[n] = hv;
-      const int i = (n - SV) / 2;
       rhs[i] = -((1.0 + cc) * phi + sc.dt * (sc.gamma * hv + sc.zeta * hp)) * ibdn;
     }
   }
@@ -720,10 +725,7 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
           S2 += (double)n * n * vn;
         }
         // one walk from n = N down to 0: Dv, D^2 v, t = i kx H_x + i kz H_z, Dt
-        if (sv == 0)
-          v_walk<MH, 0>(N, ny, ppc, Vc, HVc, Hx, Hy, Hz, r, sgn, kx, kz, k2, cc, ibdn, sc, rhs);
-        else
-          v_walk<MH, 1>(N, ny, ppc, Vc, HVc, Hx, Hy, Hz, r, sgn, kx, kz, k2, cc, ibdn, sc, rhs);
+        v_walk<MH>(N, ny, ppc, sv, Vc, HVc, Hx, Hy, Hz, r, sgn, kx, kz, k2, cc, ibdn, sc, rhs);
         double f[MH];
         tau_seq<MH>(N, ny, sv, rhs, f, helm(sv), ss[(0 * 2 + sv) * ppc + pl], 0.0, rowc);
         const size_t vo = (size_t)b * P + p;
@@ -949,10 +951,7 @@ __global__ void __launch_bounds__(64) stage_post_batched_kernel(Grid g, int B, P
       S0 += vn;
       S2 += (double)n * n * vn;
     }
-    if (sv == 0)
-      v_walk<MH, 0>(N, ny, ppc, Vc, HVc, Hx, Hy, Hz, r, sgn, kx, kz, k2, cc, ibdn, sc, rhs);
-    else
-      v_walk<MH, 1>(N, ny, ppc, Vc, HVc, Hx, Hy, Hz, r, sgn, kx, kz, k2, cc, ibdn, sc, rhs);
+    v_walk<MH>(N, ny, ppc, sv, Vc, HVc, Hx, Hy, Hz, r, sgn, kx, kz, k2, cc, ibdn, sc, rhs);
     double f[MH];
     tau_seq<MH>(N, ny, sv, rhs, f, helm(sv), helm_isq(sv), 0.0, rowc);
     const size_t vo = (size_t)b * P + p;

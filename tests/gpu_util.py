@@ -74,9 +74,10 @@ def compare_states(lst: dict, ost: dict, tol: float):
 
 
 def run_batch_pair(native, kw: dict, B: int, slots, nsteps: int, seed0: int = 300, amp: float = 0.2,
-                   kmax: int = 99, action_std: float = 0.05, action_seed0: int = 5000):
+                   kmax: int = 99, action_std: float = 0.05, action_seed0: int = 5000, tiles=None):
     """One batched handle of B environments (seed0 + e) stepped with per-slot
     seeded actions; the oracle replays the sampled `slots` one by one.
+    `tiles` = (ppc_pre, ppc_post, post_batched) pins the stage-kernel shapes.
 
     Returns (info, {slot: (lib_results, oracle_results, lib state, oracle state)})."""
     op = oracle_params(**kw)
@@ -84,6 +85,8 @@ def run_batch_pair(native, kw: dict, B: int, slots, nsteps: int, seed0: int = 30
     nx, ny, nz = op.nx, op.ny, op.nz
     env = native.env_create(native.params(**kw, batch=B))
     try:
+        if tiles is not None:
+            native.env_set_tiles(env, *tiles)
         info = native.env_info(env)
         fields = [si.perturbed_poiseuille(nx, ny, nz, seed0 + e, amp, kmax) for e in range(B)]
         for e in range(B):

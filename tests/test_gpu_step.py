@@ -268,10 +268,10 @@ def test_re550_grid_fp64_is_reported_unsupported(native_gpu):
 
 
 def test_batched_implicit_half_against_oracle(native_gpu):
-    """80 minimal channels in one handle, enough modes for the batched form of
-    the implicit half of a stage (one thread per mode, class and component):
+    """80 minimal channels in one handle, the implicit half of each stage in
+    the batched form (one thread per mode, class and component, pinned):
     sampled slots, including the first and the last, against the oracle."""
-    info, res = run_batch_pair(native_gpu, MINIMAL, 80, (0, 41, 79), 2)
+    info, res = run_batch_pair(native_gpu, MINIMAL, 80, (0, 41, 79), 2, tiles=(8, 16, 1))
     assert info.post_batched == 1
     for e, (lo, oo, ls, os_) in res.items():
         compare_states(ls, os_, TOL)
@@ -281,7 +281,7 @@ def test_batched_implicit_half_against_oracle(native_gpu):
 def test_batched_implicit_half_opposition(native_gpu):
     """The batched form under opposition control (wall spectrum from the state)."""
     kw = dict(MINIMAL, control=1, alpha=1.0)
-    info, res = run_batch_pair(native_gpu, kw, 96, (0, 95), 2)
+    info, res = run_batch_pair(native_gpu, kw, 96, (0, 95), 2, tiles=(8, 16, 1))
     assert info.post_batched == 1
     for e, (lo, oo, ls, os_) in res.items():
         compare_states(ls, os_, TOL)
