@@ -19,10 +19,11 @@ static int mh_bucket(int need) {
 size_t stage_pre_smem(const Grid& g, int ppc, size_t node_bytes) {
   return (size_t)8 * g.ny * ppc * node_bytes + (size_t)12 * ppc * sizeof(double2);
 }
-size_t stage_post_batched_smem(const Grid& g, int ppc) { return (size_t)3 * g.ny * ppc * sizeof(double2); }
-// (the coefficient tile is smaller in FP32 node precision; the FP64 size bounds both)
+// (both with six complex values per mode for the FP64 fast analysis; the
+// coefficient tile is smaller in FP32 node precision, the FP64 size bounds both)
+size_t stage_post_batched_smem(const Grid& g, int ppc) { return ((size_t)3 * g.ny + 6) * ppc * sizeof(double2); }
 size_t stage_post_smem(const Grid& g, int Mh, int ppc) {
-  return (size_t)7 * g.ny * ppc * sizeof(double2) + ((size_t)18 * Mh * ppc + 6 * ppc) * sizeof(double);
+  return ((size_t)7 * g.ny + 6) * ppc * sizeof(double2) + ((size_t)18 * Mh * ppc + 6 * ppc) * sizeof(double);
 }
 
 template <typename RN>

@@ -214,6 +214,86 @@ __device__ __forceinline__ int dif_pos(int k) {
   return p;
 }
 
+// Chebyshev analysis of the three fields of a tile in FP64 through the same
+// FFT form of the DCT-I: a_n = (2 / (N cb_n)) F_n, F the DCT-I of
+// g_j = f_j / cb_j (cb_0 = cb_N = 2).  X: tile [3][ny][ppc], nodal values in,
+// coefficients out.  The FFT leaves Z in digit-reversed order in the tile's
+// own storage: each even output is stored in Z_k's slot and each odd-output
+// difference in Z_{N-k}'s slot (every slot read and written by one item
+// only), and the natural-order coefficients pass through this tile's columns
+// of the global node array Rt (modes of this CTA, read by no other CTA) before
+// they are copied back.  hf: shared scratch of 6 ppc values.
+template <int NF>
+__device__ __forceinline__ void analysis_fft(double2* X, int ppc, int ny, int P, int p0, double2* hf,
+                                             const double* cheb, const double2* tw, double2* Rt) {
+  constexpr int N = NF;
+  const int nl = 3 * ppc, LS = ny * ppc;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  double2* sHalf = hf;       // (g_0 + g_N) / 2
+  double2* sF1 = hf + nl;    // F_1
+  for (int l = tid; l < nl; l += nt) {
+    double2* x = X + (l / ppc) * LS + (l % ppc);
+    x[0] = 0.5 * x[0];
+    x[N * ppc] = 0.5 * x[N * ppc];
+    double2 s1 = mk(0.0, 0.0);
+    for (int n = 0; n <= N; ++n) s1 = s1 + cheb[ny + n] * x[n * ppc];
+    sF1[l] = s1;
+    sHalf[l] = 0.5 * (x[0] + x[N * ppc]);
+  }
+  __syncthreads();
+  for (int w = tid; w < nl * (N / 2); w += nt) {
+    const int l = w % nl, n = w / nl;
+    double2* x = X + (l / ppc) * LS + (l % ppc);
+    if (n == 0) {
+      x[0] = sHalf[l];
+      continue;
+    }
+    const double2 xa = x[n * ppc], xb = x[(N - n) * ppc];
+    const double sn = cheb[ny + N / 2 - n];  // sin(pi n / N)
+    const double2 sm = 0.5 * (xa + xb), d = xa - xb;
+    x[n * ppc] = sm - sn * d;
+    x[(N - n) * ppc] = sm + sn * d;
+  }
+  __syncthreads();
+  lines_dif<NF, 0>(X, tw, nl, ppc, LS);
+  for (int w = tid; w < nl * (N / 2 + 1); w += nt) {
+    const int l = w % nl, k = w / nl;
+    double2* Z = X + (l / ppc) * LS + (l % ppc);
+    const int ik = dif_pos<NF>(k) * ppc, in = dif_pos<NF>((N - k) % N) * ppc;
+    const double2 zk = Z[ik], zn = Z[in];
+    Z[ik] = 0.5 * (zk + zn) + sHalf[l];
+    if (k >= 1 && k < N / 2) {
+      const double2 dd = zk - zn;
+      Z[in] = mk(0.5 * dd.y, -0.5 * dd.x);
+    }
+  }
+  __syncthreads();
+  const double s0 = 2.0 / N;
+  for (int l = tid; l < nl; l += nt) {
+    const int f = l / ppc, pl = l % ppc;
+    if (p0 + pl >= P) continue;
+    const double2* Z = X + f * LS + pl;
+    double2* dst = Rt + (size_t)f * ny * P + pl;
+    double2 fo = sF1[l];
+    dst[0] = (0.5 * s0) * Z[0];
+    dst[P] = s0 * fo;
+#pragma unroll 4
+    for (int k = 1; k <= N / 2; ++k) {
+      dst[(size_t)(2 * k) * P] = (2 * k == N ? 0.5 * s0 : s0) * Z[dif_pos<NF>(k) * ppc];
+      if (k < N / 2) {
+        fo = fo + Z[dif_pos<NF>(N - k) * ppc];
+        dst[(size_t)(2 * k + 1) * P] = s0 * fo;
+      }
+    }
+  }
+  __syncthreads();
+  for (int w = tid; w < 3 * ny * ppc; w += nt) {
+    const int pl = w % ppc, fn = w / ppc;
+    if (p0 + pl < P) X[w] = Rt[(size_t)fn * P + pl];
+  }
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------------------
 // stage_pre
 //   u = (i kx Dv - i kz g)/k^2, w = (i kz Dv + i kx g)/k^2,
@@ -561,7 +641,16 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
   __syncthreads();
 
   // ---- Chebyshev analysis of H_x, H_y, H_z (in place after a barrier)
-  {
+  constexpr int NF = 2 * (MH - 1);
+  bool analysed = false;
+  if constexpr (std::is_same<RN, double>::value && ct_plan_ok(NF)) {
+    if (N == NF) {
+      analysis_fft<NF>(sH, ppc, ny, P, p0, reinterpret_cast<double2*>(ss + 6 * ppc), t.cheb, t.tw_cheb,
+                       pb.R + (size_t)b * 3 * ny * P + p0);
+      analysed = true;
+    }
+  }
+  if (!analysed) {
     // Thread (mode pl, group g of 8) computes the coefficients n = g, g+8, ...
     // of the three fields of its mode: every pair f_j, f_{N-j} it loads feeds
     // all of its outputs, and the outputs are independent accumulation chains.
@@ -806,7 +895,16 @@ __global__ void __launch_bounds__(64) stage_post_batched_kernel(Grid g, int B, P
   // occupies bytes [8f, 8f + 8) x ny ppc and its coefficients [16f, 16f + 16)
   // x ny ppc, so going from f = 2 down to 0 with a barrier between reading
   // and writing a field never overwrites nodal values still to be read.
-  {
+  constexpr int NF = 2 * (MH - 1);
+  bool analysed = false;
+  if constexpr (std::is_same<RN, double>::value && ct_plan_ok(NF)) {
+    if (N == NF) {
+      analysis_fft<NF>(sH, ppc, ny, P, p0, sH + 3 * ny * ppc, t.cheb, t.tw_cheb,
+                       pb.R + (size_t)b * 3 * ny * P + p0);
+      analysed = true;
+    }
+  }
+  if (!analysed) {
     constexpr int KN = (2 * MH + 3) / 4;  // n values per thread
     const int qd = r + 2 * c;             // n = qd + 4k, parity of n = r
     const RN* cheb = cheb_table<RN>(t);
