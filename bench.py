@@ -56,15 +56,16 @@ WORKLOADS = {
                        "large channel Re_tau=550, 256x193x256, mixed precision, seeded ZNMF Gaussian actions "
                        "std 0.05 u_tau (the FP64 padded plane does not fit a cluster's shared memory)"),
 }
-# served workloads: (list of (parameters, count), slots per class, description)
+# served workloads: (list of (parameters, count), slots per class, environments per actor thread,
+# description)
 MID = dict(LARGER, nx=32, nz=32, control=0)
 BIG395 = dict(LARGER, nx=128, ny=129, nz=128, re_tau=395.0, re_bulk=6890.0, control=0)
 SERVED = {
-    "served_minimal256_mixed": ([(dict(MINIMAL, precision=1), 256)], 256,
+    "served_minimal256_mixed": ([(dict(MINIMAL, precision=1), 256)], 256, 32,
                                 "served: 256 minimal channels 16x65x16, mixed precision, actor threads with "
                                 "exponential think time, continuous batching"),
     "served_mixed_sizes": ([(dict(MINIMAL, precision=1), 24), (dict(MID, precision=1), 12),
-                            (dict(LARGER, control=0, precision=1), 8), (dict(BIG395, precision=1), 4)], 24,
+                            (dict(LARGER, control=0, precision=1), 8), (dict(BIG395, precision=1), 4)], 24, 4,
                            "served: 48 environments 24x16x65x16 + 12x32x65x32 + 8x64x65x64 (Re_tau 180) + "
                            "4x128x129x128 (Re_tau 395), mixed precision, admitted by HBM budget"),
 }
@@ -240,11 +241,14 @@ def run_reference(args, rank: int, world: int):
 
 
 def run_served(args):
-    """Continuous-batching server driven by one actor thread per environment.
+    """Continuous-batching server driven by actor threads.
 
-    Each actor submits an action, waits for the step, thinks for an
-    exponentially distributed time of mean 1/rate (0: none, saturation) and
-    repeats until the time budget is spent."""
+    Each actor thread drives a group of CH_SERVE_GROUP environments of one
+    class (default per workload): it submits one action for every environment of its
+    group, waits for each result, thinks for an exponentially distributed
+    time of mean 1/rate (0: none, saturation) and repeats until the time
+    budget is spent.  Groups larger than one keep the Python threads few, so
+    that the host side does not limit the measured server."""
     import random
     import threading
 
@@ -255,7 +259,7 @@ def run_served(args):
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     native.load()
-    groups, slots, name = SERVED[args.workload]
+    groups, slots, group_default, name = SERVED[args.workload]
     budget = int(float(os.environ.get("CH_SERVE_BUDGET_GB", "64")) * (1 << 30))
     srv = native.srv_create(budget, slots)
     envs = []
@@ -271,7 +275,9 @@ def run_served(args):
     errors = []
     lat = {}   # class label -> submit-to-result latencies (s) seen by the actors while measuring
 
-    def actor(eid, prm, seed):
+    group = max(1, int(os.environ.get("CH_SERVE_GROUP", str(group_default))))
+
+    def actor(eids, prm, seed):
         rng = random.Random(seed)
         nrng = np.random.default_rng(seed)
         nx, nz = prm["nx"], prm["nz"]
@@ -285,13 +291,15 @@ def run_served(args):
         try:
             while not stop.is_set():
                 t0 = time.perf_counter()
-                rid = native.srv_submit(srv, eid, acts[i % 16] if prm["control"] == 0 else None)
-                rc, *_ = native.srv_wait(srv, rid, 120000, obs)
-                if rc != native.CH_OK:
-                    errors.append(rc)
-                    return
-                if measuring.is_set():
-                    mine.append(time.perf_counter() - t0)
+                rids = [native.srv_submit(srv, eid, acts[(i + k) % 16] if prm["control"] == 0 else None)
+                        for k, eid in enumerate(eids)]
+                for rid in rids:
+                    rc, *_ = native.srv_wait(srv, rid, 120000, obs)
+                    if rc != native.CH_OK:
+                        errors.append(rc)
+                        return
+                    if measuring.is_set():
+                        mine.append(time.perf_counter() - t0)
                 i += 1
                 if rate > 0:
                     time.sleep(rng.expovariate(rate))
@@ -300,7 +308,17 @@ def run_served(args):
 
     for _, prm in envs:
         lat.setdefault(f"{prm['nx']}x{prm['ny']}x{prm['nz']}", [])
-    threads = [threading.Thread(target=actor, args=(e, prm, k)) for k, (e, prm) in enumerate(envs)]
+    # actors: consecutive environments of one class, `group` at a time
+    work = []
+    k = 0
+    while k < len(envs):
+        prm = envs[k][1]
+        j = k
+        while j < len(envs) and j - k < group and envs[j][1] is prm:
+            j += 1
+        work.append(([e for e, _ in envs[k:j]], prm))
+        k = j
+    threads = [threading.Thread(target=actor, args=(eids, prm, n)) for n, (eids, prm) in enumerate(work)]
     for t in threads:
         t.start()
     time.sleep(warm)
@@ -328,7 +346,8 @@ def run_served(args):
         "steps": int(st.completed), "warmup": warm, "ms_per_step": None, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": name, "envs": len(envs), "slots_per_class": slots, "classes": st.classes,
-                   "think_rate_per_s": rate, "seconds": duration, "hbm_used_gb": st.hbm_used / (1 << 30)},
+                   "think_rate_per_s": rate, "envs_per_actor_thread": group, "actor_threads": len(work),
+                   "seconds": duration, "hbm_used_gb": st.hbm_used / (1 << 30)},
         "p50_ms": st.p50_us / 1e3, "p99_ms": st.p99_us / 1e3, "mean_ms": st.mean_us / 1e3,
         "mpts_rk3_steps_per_s": st.env_steps_per_s * pts / 1e6,
         "per_class_actor_side": per_class,
