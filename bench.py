@@ -130,7 +130,7 @@ def measured_peaks() -> dict:
 # (summaries under profiles/); absent where no capture of the current kernel exists
 TRAFFIC_BYTES = {
     ("larger_fp64", "nonlinear_plane"): 12.637696e6,
-    ("minimal_batch256_mixed", "stage_post"): (181.795072 + 75.341568) * 1e6,
+    ("minimal_batch256_mixed", "stage_post"): (181.530112 + 71.413760) * 1e6,
 }
 
 # FP64 FMA rate: 152 SMs x 2 FP64 FMA/clk/SM x 2 FLOP x 2.07 GHz (probe-measured, see the design notes)
@@ -365,6 +365,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=tuple(WORKLOADS) + tuple(SERVED))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="tile shapes from the size rule instead of timing at env_create "
+                         "(for profiler runs, whose timings would mislead the autotuner)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -392,7 +395,7 @@ def main():
     native.load()
     W = max(3, args.warmup)
     K = args.steps
-    p = native.params(**prm, batch=B, precision=prec)
+    p = native.params(**prm, batch=B, precision=prec, autotune=0 if args.no_autotune else 1)
     env = native.env_create(p)
     info = native.env_info(env)
     native.env_reset(env, seed=1000 * rank, amplitude=0.1, kmax=99)
