@@ -117,6 +117,23 @@ def implicit_half_fp64_flops(nx: int, ny: int, nz: int, batch: int) -> float:
     return 170.0 * ny * modes
 
 
+def slowest_rank_ms(total_ms: float, dist, device: str = "cuda") -> float:
+    """Job time of a replica run: the maximum over ranks of the per-rank timed
+    totals (the slowest rank sets it); a single process keeps its own."""
+    if dist is None:
+        return total_ms
+    import torch
+    t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(steps: int, batch: int, world: int, job_ms: float) -> float:
+    """Environment steps of all ranks per second of job time (weak scaling:
+    every rank advances its own `batch` environments `steps` times)."""
+    return steps * batch * world / (job_ms * 1e-3)
+
+
 def measured_peaks() -> dict:
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -449,12 +466,8 @@ def main():
         ms, n = native.env_profile_read(env, c)
         kern[name] = {"ms_total": ms, "launches": n}
     native.env_profile(env, False)
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = K * B * world / (total_ms * 1e-3)
+    total_ms = slowest_rank_ms(sum(step_ms), dist)
+    value = job_throughput(K, B, world, total_ms)
     finite = bool(torch.isfinite(d_out).all().item())
 
     # ---- end to end through the host-buffer API (pinned host buffers)
@@ -472,12 +485,8 @@ def main():
         t0 = time.perf_counter()
         native.env_step(env, hact(i), obs, tau, rew)
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
-    e2e_total = sum(e2e_ms)
-    if dist:
-        t = torch.tensor([e2e_total], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = Ke * B * world / (e2e_total * 1e-3)
+    e2e_total = slowest_rank_ms(sum(e2e_ms), dist)
+    e2e_value = job_throughput(Ke, B, world, e2e_total)
     native.env_destroy(env)
 
     if rank != 0:
