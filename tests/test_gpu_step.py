@@ -360,3 +360,14 @@ def test_autotune_picks_a_candidate_and_rejects_bad_shapes(native_gpu):
                 native.env_set_tiles(env, *bad)
     finally:
         native.env_destroy(env)
+
+
+@pytest.mark.parametrize("ny", [97, 41])
+def test_transform_paths_against_oracle(native_gpu, ny):
+    """FP64 Chebyshev transforms on the two remaining paths: N = 96, an FFT
+    plan with a radix-3 pass, and N = 40, which the FFT plan does not cover
+    (direct sums).  Two steps with seeded actions, all modes excited."""
+    kw = dict(nx=12 if ny == 41 else 8, ny=ny, nz=8, lx=2.67, lz=0.8, re_tau=180.0, re_bulk=2800.0, dt=0.004)
+    lo, oo, ls, os_ = run_pair(native_gpu, kw, 2, seed=6, amp=0.2, kmax=99)
+    compare_states(ls, os_, TOL)
+    _check_outputs(lo, oo, os_, kw)
