@@ -1,10 +1,11 @@
 // The small kernels of the environment step (action, observation, wall shear,
 // reward) and the stateless Chebyshev-tau entry points.  The Runge-Kutta stage
-// itself lives in stage.cu (wall-normal work) and plane.cu (nonlinear term).
+// itself lives in stage_kernels.cuh (wall-normal work) and plane.cu (nonlinear term).
 //
 // Chebyshev conventions: f(y) = sum_n a_n T_n(y), nodes y_j = cos(pi j / N).
 // Derivative recurrence (coefficient space): c_m b_m = b_{m+2} + 2 (m+1) a_{m+1}
 // with c_0 = 2, c_m = 1 otherwise, walked from m = N down to 0.
+#include <algorithm>
 #include <mutex>
 
 #include "../../include/channel_dns.h"
@@ -179,32 +180,62 @@ __global__ void __launch_bounds__(128) sense_kernel(Grid g, int B, PencilBufs pb
 __global__ void __launch_bounds__(128) obs_kernel(int nx, int nz, int nxh, const double2* planes,
                                                   const double2* tw_nx, const double2* tw_nz, double* out,
                                                   size_t out_stride, const int* active) {
+  // one CTA per (physical row z, field, environment); the sums over kz and
+  // over kx are split across all threads and combined in shared memory
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double2* tmp = reinterpret_cast<double2*>(smem_raw);  // [nxh]
+  double2* part = reinterpret_cast<double2*>(smem_raw);  // [max(nt, nxh)] partial sums
+  double2* tmp = part + max((int)blockDim.x, nxh);        // [nxh]
   const int zb = blockIdx.x, f = blockIdx.y, b = blockIdx.z;
   if (active && !active[b]) return;
+  const int tid = threadIdx.x, nt = blockDim.x;
   const int P = nz * nxh;
   const double2* F = planes + ((size_t)b * 2 + f) * P;
-  for (int i = threadIdx.x; i < nxh; i += blockDim.x) {
+  // z sums: thread (kx i, part q) takes the rows q, q + nq, ...
+  const int nq = max(1, nt / nxh);
+  for (int w = tid; w < nxh * nq; w += nt) {
+    const int i = w % nxh, q = w / nxh;
     double2 acc = mk(0.0, 0.0);
-    for (int row = 0; row < nz; ++row) {
-      if (row == nz / 2) continue;
-      const int m = row < nz / 2 ? row : row - nz;
-      int e = (m * zb) % nz;
-      if (e < 0) e += nz;
-      acc = acc + cmul(F[row * nxh + i], tw_nz[e]);
+    int e = (q * zb) % nz;             // twiddle index of row q (m = row for row < nz/2)
+    const int step = (nq * zb) % nz;
+    for (int row = q; row < nz; row += nq) {
+      if (row != nz / 2) {
+        // m = row - nz for row > nz/2 gives the same index modulo nz
+        acc = acc + cmul(F[row * nxh + i], tw_nz[e]);
+      }
+      e += step;
+      if (e >= nz) e -= nz;
     }
+    part[w] = acc;
+  }
+  __syncthreads();
+  for (int i = tid; i < nxh; i += nt) {
+    double2 acc = part[i];
+    for (int q = 1; q < nq; ++q) acc = acc + part[q * nxh + i];
     tmp[i] = acc;
   }
   __syncthreads();
-  double* o = out + (size_t)b * out_stride + (size_t)f * nz * nx + (size_t)zb * nx;
-  for (int xa = threadIdx.x; xa < nx; xa += blockDim.x) {
+  // x sums: thread (x, part q) takes kx = 1 + q, 1 + q + nr, ...
+  double* pr = reinterpret_cast<double*>(part);
+  const int nr = max(1, nt / nx);
+  for (int w = tid; w < nx * nr; w += nt) {
+    const int xa = w % nx, q = w / nx;
     double s = 0.0;
-    for (int i = 1; i < nxh; ++i) {
-      const double2 tw = tw_nx[(i * xa) % nx];
+    int e = ((1 + q) * xa) % nx;
+    const int step = (nr * xa) % nx;
+    for (int i = 1 + q; i < nxh; i += nr) {
+      const double2 tw = tw_nx[e];
       const double2 v = tmp[i];
       s += v.x * tw.x - v.y * tw.y;
+      e += step;
+      if (e >= nx) e -= nx;
     }
+    pr[w] = s;
+  }
+  __syncthreads();
+  double* o = out + (size_t)b * out_stride + (size_t)f * nz * nx + (size_t)zb * nx;
+  for (int xa = tid; xa < nx; xa += nt) {
+    double s = 0.0;
+    for (int q = 0; q < nr; ++q) s += pr[q * nx + xa];
     o[xa] = tmp[0].x + 2.0 * s;
   }
 }
@@ -308,7 +339,7 @@ cudaError_t launch_sense(const Grid& g, int B, const PencilBufs& pb, const DevTa
 
 cudaError_t launch_obs(const Grid& g, int B, const double2* planes, const DevTables& t, double* out,
                        size_t out_stride, const int* active, cudaStream_t st) {
-  const size_t smem = (size_t)g.nxh * sizeof(double2);
+  const size_t smem = (size_t)(std::max(128, g.nxh) + g.nxh) * sizeof(double2);
   obs_kernel<<<dim3(g.nz, 2, B), 128, smem, st>>>(g.nx, g.nz, g.nxh, planes, t.tw_nx, t.tw_nz, out, out_stride,
                                                    active);
   return cudaGetLastError();
