@@ -164,10 +164,13 @@ __device__ void fft_dit(typename cpx<R>::T* buf, int nlines, int g, const FftPla
 // Compile-time FFT plans and stages: the same in-place DIF/DIT passes with
 // the length, the radix of every pass and the line layout fixed at compile
 // time, so that index arithmetic reduces to constant multiplies and shifts.
-// Plan of n = 4^a 2^b 3^c: radices 4, ..., 4, 2, ..., 2, 3, ..., 3.
+// Plan of n = 8^a 4^b 2^c 3^d: radices 8, ..., 8, 4, ..., 4, 2, ..., 2, 3, ..., 3
+// (radix 8 first: fewest passes, hence fewest barriers and shared-memory
+// round trips per transform).
 // ---------------------------------------------------------------------------
 __host__ __device__ constexpr int ct_nst(int n) {
   int s = 0;
+  while (n % 8 == 0) { n /= 8; ++s; }
   while (n % 4 == 0) { n /= 4; ++s; }
   while (n % 2 == 0) { n /= 2; ++s; }
   while (n % 3 == 0) { n /= 3; ++s; }
@@ -175,14 +178,16 @@ __host__ __device__ constexpr int ct_nst(int n) {
 }
 __host__ __device__ constexpr int ct_radix(int n, int st) {
   int s = 0;
+  while (n % 8 == 0) { if (s == st) return 8; n /= 8; ++s; }
   while (n % 4 == 0) { if (s == st) return 4; n /= 4; ++s; }
   while (n % 2 == 0) { if (s == st) return 2; n /= 2; ++s; }
   while (n % 3 == 0) { if (s == st) return 3; n /= 3; ++s; }
   return 1;
 }
-// true when the radix-4/2/3 plan factors n completely
+// true when the radix-8/4/2/3 plan factors n completely
 __host__ __device__ constexpr bool ct_plan_ok(int n) {
   if (n < 2) return false;
+  while (n % 8 == 0) n /= 8;
   while (n % 4 == 0) n /= 4;
   while (n % 2 == 0) n /= 2;
   while (n % 3 == 0) n /= 3;
@@ -210,7 +215,7 @@ __device__ __forceinline__ void small_dft_ct(C* x) {
     x[0] = x[0] + s;
     x[1] = t1 + rot;
     x[2] = t1 - rot;
-  } else {
+  } else if constexpr (RADIX == 4) {
     C a0 = x[0] + x[2], a1 = x[0] - x[2];
     C b0 = x[1] + x[3], b1 = x[1] - x[3];
     C wb1 = imul((R)SIGN, b1);
@@ -218,6 +223,28 @@ __device__ __forceinline__ void small_dft_ct(C* x) {
     x[1] = a1 + wb1;
     x[2] = a0 - b0;
     x[3] = a1 - wb1;
+  } else {
+    // radix 8: length-4 DFTs of the even and the odd samples, combined with
+    // w^u, w = e^{SIGN 2 pi i / 8} = (1 + SIGN i) / sqrt 2
+    const C a0 = x[0] + x[4], a1 = x[0] - x[4], a2 = x[2] + x[6], a3 = x[2] - x[6];
+    const C e0 = a0 + a2, e2 = a0 - a2;
+    const C e1 = a1 + imul((R)SIGN, a3), e3 = a1 - imul((R)SIGN, a3);
+    const C b0 = x[1] + x[5], b1 = x[1] - x[5], b2 = x[3] + x[7], b3 = x[3] - x[7];
+    const C o0 = b0 + b2;
+    const C p2 = b0 - b2;
+    const C p1 = b1 + imul((R)SIGN, b3), p3 = b1 - imul((R)SIGN, b3);
+    const R h = (R)0.70710678118654752440084436210484904;
+    const C o1 = mk(h * (p1.x - (R)SIGN * p1.y), h * (p1.y + (R)SIGN * p1.x));    // p1 w
+    const C o2 = imul((R)SIGN, p2);                                               // p2 w^2
+    const C o3 = mk(h * (-p3.x - (R)SIGN * p3.y), h * (-p3.y + (R)SIGN * p3.x));  // p3 w^3
+    x[0] = e0 + o0;
+    x[4] = e0 - o0;
+    x[1] = e1 + o1;
+    x[5] = e1 - o1;
+    x[2] = e2 + o2;
+    x[6] = e2 - o2;
+    x[3] = e3 + o3;
+    x[7] = e3 - o3;
   }
 }
 
