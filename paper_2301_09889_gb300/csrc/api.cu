@@ -518,8 +518,10 @@ int set_state_dev(ch_env* env, int e, const double* buf) {
   CK(cudaMemcpyAsync(env->pb.UM + (size_t)e * ny, U, ny * sizeof(double), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(env->pb.WM + (size_t)e * ny, W, ny * sizeof(double), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(env->pb.vw_new + (size_t)e * P, vw, P * sizeof(double2), cudaMemcpyHostToDevice, st));
-  CK(cudaMemsetAsync(env->pb.HVP + (size_t)e * ny * P, 0, ny * P * sizeof(double2), st));
-  CK(cudaMemsetAsync(env->pb.HGP + (size_t)e * ny * P, 0, ny * P * sizeof(double2), st));
+  // previous right-hand sides: complex values in the node precision, [B][ny][P]
+  const size_t hsz = env->prm.precision == 1 ? sizeof(float2) : sizeof(double2);
+  CK(cudaMemsetAsync(reinterpret_cast<char*>(env->pb.HVP) + (size_t)e * ny * P * hsz, 0, ny * P * hsz, st));
+  CK(cudaMemsetAsync(reinterpret_cast<char*>(env->pb.HGP) + (size_t)e * ny * P * hsz, 0, ny * P * hsz, st));
   CK(cudaMemsetAsync(env->pb.HXP + (size_t)e * ny, 0, ny * sizeof(double), st));
   CK(cudaMemsetAsync(env->pb.HZP + (size_t)e * ny, 0, ny * sizeof(double), st));
   CK(cudaStreamSynchronize(st));

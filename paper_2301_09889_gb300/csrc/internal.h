@@ -13,7 +13,8 @@ template <typename R>
 cudaError_t plane_max_clusters(const PlaneArgs<R>& a, size_t smem, int* clusters);
 
 struct PencilBufs {
-  double2 *V, *G, *HVP, *HGP;   // [B][ny][P]
+  double2 *V, *G;               // [B][ny][P]
+  double2 *HVP, *HGP;           // [B][ny][P] complex in the node precision (FP32 pairs in mixed mode)
   double *UM, *WM, *HXP, *HZP;  // [B][ny]
   double2* Q;                   // [B][6][ny][P] node values of u, v, w, ox, oy, oz (nonlinear input)
   double2* R;                   // [B][3][ny][P] node values of H

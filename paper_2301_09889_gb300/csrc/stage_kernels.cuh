@@ -108,36 +108,48 @@ __device__ __forceinline__ void tau_seq(int N, int ny, int sig, const double (&r
 // at 2i + sv + 1 (Dv, t) and then the own step at 2i + sv, so the register
 // index i is fixed at compile time and the code is the same for both
 // parities (threads of the two classes share warps).  The other-parity step
-// at n = 0 (sv = 1) has no consumer and is not run.
-template <int MH>
-__device__ __forceinline__ void v_walk(int N, int ny, int ppc, int sv, const CompS& Vc, const CompS& HVc,
-                                       const double2* Hx, const double2* Hy, const double2* Hz, int r, double sgn,
-                                       double kx, double kz, double k2, double cc, double ibdn, const StageCoef& sc,
-                                       double (&rhs)[MH]) {
+// at n = 0 (sv = 1) has no consumer and is not run.  The terms of v (Dv, D^2 v,
+// phi) are FP64; the nonlinear-term part (t, Dt, h_v and dt (gamma h_v +
+// zeta h_v')) runs in the node precision RN, FP32 in the mixed path, where
+// H itself is FP32-accurate.  h_v' is read through HVr and the new h_v
+// written through HVw (the same column, or a shared-memory copy and global).
+template <int MH, typename RN>
+__device__ __forceinline__ void v_walk(int N, int ny, int ppc, int sv, const CompS& Vc, const CompT<RN>& HVr,
+                                       const CompT<RN>& HVw,
+                                       const typename cpx<RN>::T* Hx, const typename cpx<RN>::T* Hy,
+                                       const typename cpx<RN>::T* Hz, int r, double sgn, double kx, double kz,
+                                       double k2, double cc, double ibdn, const StageCoef& sc, double (&rhs)[MH]) {
+  using CN = typename cpx<RN>::T;
   const int ra = 1 - r;
-  auto comp = [](const double2 z, int qd) { return qd == 0 ? z.x : z.y; };
+  auto comp = [](const CN z, int qd) { return qd == 0 ? z.x : z.y; };
   const double dsv = 2.0 * sv;
-  double dv = 0.0, d2v = 0.0, tt = 0.0, dtt = 0.0;
+  const RN dsvn = (RN)(2 * sv);
+  const RN sgnn = (RN)sgn, kxn = (RN)kx, kzn = (RN)kz, k2n = (RN)k2;
+  const RN dtn = (RN)sc.dt, gan = (RN)sc.gamma, zen = (RN)sc.zeta;
+  double dv = 0.0, d2v = 0.0;
+  RN tt = 0, dtt = 0;
 #pragma unroll
   for (int i = MH - 1; i >= 0; --i) {
     const int no = 2 * i + sv + 1;
     if (no <= N) {
       const double vn1 = (no + 1 <= N) ? Vc[no + 1] : 0.0;
       dv = dv + ((double)(4 * i + 4) + dsv) * vn1;  // 2 (no + 1)
-      tt = sgn * (kx * comp(Hx[no * ppc], ra) + kz * comp(Hz[no * ppc], ra));
+      tt = sgnn * (kxn * comp(Hx[no * ppc], ra) + kzn * comp(Hz[no * ppc], ra));
     }
     const int n = 2 * i + sv;
     if (n <= N) {
       const double fac = (double)(4 * i + 2) + dsv;  // 2 (n + 1)
+      const RN facn = (RN)(4 * i + 2) + dsvn;
       const double t1 = d2v + fac * dv;
-      const double t2 = dtt + fac * ((n + 1 <= N) ? tt : 0.0);
+      const RN t2 = dtt + facn * ((n + 1 <= N) ? tt : (RN)0);
       d2v = (n == 0) ? 0.5 * t1 : t1;
-      dtt = (n == 0) ? 0.5 * t2 : t2;
+      dtt = (n == 0) ? (RN)0.5 * t2 : t2;
       const double phi = d2v - k2 * Vc[n];
-      const double hv = -k2 * comp(Hy[n * ppc], r) - dtt;
-      const double hp = HVc[n];
-      HVc[n] = hv;
-      rhs[i] = -((1.0 + cc) * phi + sc.dt * (sc.gamma * hv + sc.zeta * hp)) * ibdn;
+      const RN hv = -k2n * comp(Hy[n * ppc], r) - dtt;
+      const RN hp = HVr[n];
+      HVw[n] = hv;
+      const RN q = dtn * (gan * hv + zen * hp);
+      rhs[i] = -((1.0 + cc) * phi + (double)q) * ibdn;
     }
   }
 }
@@ -588,12 +600,14 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int P = g.P, ny = g.ny, N = g.N;
   const int Mh = t.tau.Mh;
-  double2* sH = reinterpret_cast<double2*>(smem_raw);  // [3][ny][ppc] nodes, then coefficients
+  using CN = typename cpx<RN>::T;
+  double2* sH = reinterpret_cast<double2*>(smem_raw);  // [3][ny][ppc] nodes, then coefficients (RN)
   double2* sV = sH + 3 * ny * ppc;                      // [ny][ppc]
   double2* sG = sV + ny * ppc;
-  double2* sHV = sG + ny * ppc;
-  double2* sHG = sHV + ny * ppc;
-  double* sh = reinterpret_cast<double*>(sHG + ny * ppc);  // helm [2][4][Mh][ppc] of this stage
+  // previous right-hand sides h_v', h_g' in the node precision (FP64-sized slots)
+  CN* sHV = reinterpret_cast<CN*>(sG + ny * ppc);
+  CN* sHG = reinterpret_cast<CN*>(sG + 2 * ny * ppc);
+  double* sh = reinterpret_cast<double*>(sG + 3 * ny * ppc);  // helm [2][4][Mh][ppc] of this stage
   double* sp = sh + 2 * 4 * Mh * ppc;                        // pois [2][4][Mh][ppc]
   double* svh = sp + 2 * 4 * Mh * ppc;                       // vh [2][Mh][ppc]
   double* ss = svh + 2 * Mh * ppc;                           // helm_isq, pois_isq, vh_idv [3][2][ppc]
@@ -609,11 +623,10 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
     const size_t o = ((size_t)b * ny + n) * P + p;
     sV[w] = pb.V[o];
     sG[w] = pb.G[o];
-    sHV[w] = pb.HVP[o];
-    sHG[w] = pb.HGP[o];
+    sHV[w] = reinterpret_cast<const CN*>(pb.HVP)[o];
+    sHG[w] = reinterpret_cast<const CN*>(pb.HGP)[o];
   }
   // nodal values in the node precision, in the first bytes of the sH region
-  using CN = typename cpx<RN>::T;
   CN* sN = reinterpret_cast<CN*>(sH);
   for (int w = tid; w < 3 * ny * ppc; w += nt) {
     const int pl = w % ppc, fn = w / ppc;  // fn = f * ny + n
@@ -680,7 +693,7 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
         for (int f = 0; f < 3; ++f) a[f][k] = a[f][k] + c * fold[f];
       }
     }
-    double2 acc[3][KN];
+    CN acc[3][KN];
     const RN s0 = (RN)2.0 / (RN)N;
 #pragma unroll
     for (int k = 0; k < KN; ++k) {
@@ -691,7 +704,7 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
       for (int f = 0; f < 3; ++f) {
         CN v = a[f][k];
         if ((N & 1) == 0) v = v + cH * colf[f][(N / 2) * ppc];
-        acc[f][k] = to_double((s0 / cbn) * v);
+        acc[f][k] = (s0 / cbn) * v;
       }
     }
     __syncthreads();
@@ -700,7 +713,7 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
       const int n = gq + 8 * k;
       if (n <= N) {
 #pragma unroll
-        for (int f = 0; f < 3; ++f) sH[((size_t)f * ny + n) * ppc + pl] = acc[f][k];
+        for (int f = 0; f < 3; ++f) sN[((size_t)f * ny + n) * ppc + pl] = acc[f][k];
       }
     }
     __syncthreads();
@@ -716,11 +729,12 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
     const double cc = sc.alpha / sc.beta;
     const double ibdn = 1.0 / (sc.beta * sc.dt * sc.nu);
     const double* rowc = t.tau.rowc;
-    const double2* Hx = sH + pl;
-    const double2* Hy = Hx + ny * ppc;
-    const double2* Hz = Hy + ny * ppc;
+    const CN* Hx = reinterpret_cast<const CN*>(sH) + pl;
+    const CN* Hy = Hx + ny * ppc;
+    const CN* Hz = Hy + ny * ppc;
     auto helm = [&](int sig) { return TabSm{sh + sig * 4 * Mh * ppc + pl, Mh, ppc}; };
-    auto comp = [&](const double2 z, int qd) { return qd == 0 ? z.x : z.y; };
+    auto comp = [](auto z, int qd) { return qd == 0 ? z.x : z.y; };
+    const RN dtn = (RN)sc.dt, gan = (RN)sc.gamma, zen = (RN)sc.zeta;
     if (row == g.nz / 2) {
       // Nyquist row stays zero
     } else if (p == 0) {
@@ -729,7 +743,7 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
         const int M = (N - s) / 2 + 1;
         double* X = (e == 0 ? pb.UM : pb.WM) + (size_t)b * ny;
         double* XP = (e == 0 ? pb.HXP : pb.HZP) + (size_t)b * ny;
-        const double2* Hm = (e == 0) ? Hx : Hz;
+        const CN* Hm = (e == 0) ? Hx : Hz;
         double rhs[MH], f[MH];
         double sum = 0.0, flux_old = 0.0;
 #pragma unroll
@@ -738,7 +752,7 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
           if (i < M) {
             const int n = 2 * i + s;
             const double xn = X[n];
-            const double hv = Hm[n * ppc].x;
+            const double hv = (double)Hm[n * ppc].x;
             const double hp = XP[n];
             XP[n] = hv;
             rhs[i] = -((1.0 + cc) * xn + sc.dt * (sc.gamma * hv + sc.zeta * hp)) * ibdn;
@@ -774,7 +788,8 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
         const int sq = 1 - c;
         const int M = (N - sq) / 2 + 1;
         const CompS Gc{reinterpret_cast<double*>(sG) + 2 * pl + r, 2 * ppc};
-        const CompS HGc{reinterpret_cast<double*>(sHG) + 2 * pl + r, 2 * ppc};
+        const CompT<RN> HGc{reinterpret_cast<RN*>(sHG) + 2 * pl + r, 2 * ppc};
+        const RN sgnn = (RN)sgn, kxn = (RN)kx, kzn = (RN)kz;
         double rhs[MH], f[MH];
         double sum = 0.0;
 #pragma unroll
@@ -783,10 +798,12 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
           if (i < M) {
             const int n = 2 * i + sq;
             const double gn = Gc[n];
-            const double hg = sgn * (kz * comp(Hx[n * ppc], ra) - kx * comp(Hz[n * ppc], ra));
-            const double hp = HGc[n];
+            // nonlinear part in the node precision
+            const RN hg = sgnn * (kzn * comp(Hx[n * ppc], ra) - kxn * comp(Hz[n * ppc], ra));
+            const RN hp = HGc[n];
             HGc[n] = hg;
-            rhs[i] = -((1.0 + cc) * gn + sc.dt * (sc.gamma * hg + sc.zeta * hp)) * ibdn;
+            const RN q = dtn * (gan * hg + zen * hp);
+            rhs[i] = -((1.0 + cc) * gn + (double)q) * ibdn;
             sum += gn;
           }
         }
@@ -802,7 +819,7 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
         const int sv = c;
         const int M = (N - sv) / 2 + 1;
         const CompS Vc{reinterpret_cast<double*>(sV) + 2 * pl + r, 2 * ppc};
-        const CompS HVc{reinterpret_cast<double*>(sHV) + 2 * pl + r, 2 * ppc};
+        const CompT<RN> HVc{reinterpret_cast<RN*>(sHV) + 2 * pl + r, 2 * ppc};
         double S0 = 0.0, S2 = 0.0;
         double rhs[MH];
 #pragma unroll
@@ -814,7 +831,7 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
           S2 += (double)n * n * vn;
         }
         // one walk from n = N down to 0: Dv, D^2 v, t = i kx H_x + i kz H_z, Dt
-        v_walk<MH>(N, ny, ppc, sv, Vc, HVc, Hx, Hy, Hz, r, sgn, kx, kz, k2, cc, ibdn, sc, rhs);
+        v_walk<MH, RN>(N, ny, ppc, sv, Vc, HVc, HVc, Hx, Hy, Hz, r, sgn, kx, kz, k2, cc, ibdn, sc, rhs);
         double f[MH];
         tau_seq<MH>(N, ny, sv, rhs, f, helm(sv), ss[(0 * 2 + sv) * ppc + pl], 0.0, rowc);
         const size_t vo = (size_t)b * P + p;
@@ -851,8 +868,8 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
     const size_t o = ((size_t)b * ny + n) * P + p2;
     pb.V[o] = sV[w];
     pb.G[o] = sG[w];
-    pb.HVP[o] = sHV[w];
-    pb.HGP[o] = sHG[w];
+    reinterpret_cast<CN*>(pb.HVP)[o] = sHV[w];
+    reinterpret_cast<CN*>(pb.HGP)[o] = sHG[w];
   }
 }
 
@@ -888,13 +905,26 @@ __global__ void __launch_bounds__(64) stage_post_batched_kernel(Grid g, int B, P
     const int p = min(p0 + pl, P - 1);
     sN[w] = hn[((size_t)b * 3 * ny + fn) * P + p];
   }
+  // FP32 nodes: the previous right-hand sides (FP32 pairs) are staged in shared
+  // memory by one coalesced load, behind the node tile within the space the
+  // FP64 coefficient tile takes; the new ones go straight to global memory
+  constexpr bool kStageH = sizeof(RN) == 4;
+  CN* sHVt = sN + 3 * ny * ppc;
+  CN* sHGt = sHVt + ny * ppc;
+  if (kStageH) {
+    for (int w = tid; w < ny * ppc; w += nt) {
+      const int pl = w % ppc, n = w / ppc;
+      const size_t o = ((size_t)b * ny + n) * P + min(p0 + pl, P - 1);
+      sHVt[w] = reinterpret_cast<const CN*>(pb.HVP)[o];
+      sHGt[w] = reinterpret_cast<const CN*>(pb.HGP)[o];
+    }
+  }
   __syncthreads();
   const int r = tid & 1, pl = (tid >> 1) % ppc, c = tid / (2 * ppc);
 
-  // ---- Chebyshev analysis of H_z, H_y, H_x.  In FP32 node precision field f
-  // occupies bytes [8f, 8f + 8) x ny ppc and its coefficients [16f, 16f + 16)
-  // x ny ppc, so going from f = 2 down to 0 with a barrier between reading
-  // and writing a field never overwrites nodal values still to be read.
+  // ---- Chebyshev analysis of H_z, H_y, H_x, coefficients in the node
+  // precision over the nodal values of the same field (a barrier between
+  // reading and writing each field).
   constexpr int NF = 2 * (MH - 1);
   bool analysed = false;
   if constexpr (std::is_same<RN, double>::value && ct_plan_ok(NF)) {
@@ -924,20 +954,20 @@ __global__ void __launch_bounds__(64) stage_post_batched_kernel(Grid g, int B, P
           a[k] = a[k] + cheb[(size_t)min(n, N) * ny + j] * fold;
         }
       }
-      double2 acc[KN];
+      CN acc[KN];
 #pragma unroll
       for (int k = 0; k < KN; ++k) {
         const int n = qd + 4 * k;
         const RN cbn = (n == 0 || n == N) ? (RN)2.0 : (RN)1.0;
         CN v = a[k];
         if ((N & 1) == 0) v = v + cheb[(size_t)min(n, N) * ny + N / 2] * col[(N / 2) * ppc];
-        acc[k] = to_double((s0 / cbn) * v);
+        acc[k] = (s0 / cbn) * v;
       }
       __syncthreads();
 #pragma unroll
       for (int k = 0; k < KN; ++k) {
         const int n = qd + 4 * k;
-        if (n <= N) sH[((size_t)f * ny + n) * ppc + pl] = acc[k];
+        if (n <= N) sN[((size_t)f * ny + n) * ppc + pl] = acc[k];
       }
     }
     __syncthreads();
@@ -951,10 +981,11 @@ __global__ void __launch_bounds__(64) stage_post_batched_kernel(Grid g, int B, P
   const double cc = sc.alpha / sc.beta;
   const double ibdn = 1.0 / (sc.beta * sc.dt * sc.nu);
   const double* rowc = t.tau.rowc;
-  const double2* Hx = sH + pl;
-  const double2* Hy = Hx + ny * ppc;
-  const double2* Hz = Hy + ny * ppc;
-  auto comp = [](const double2 z, int qq) { return qq == 0 ? z.x : z.y; };
+  const CN* Hx = sN + pl;
+  const CN* Hy = Hx + ny * ppc;
+  const CN* Hz = Hy + ny * ppc;
+  auto comp = [](auto z, int qq) { return qq == 0 ? z.x : z.y; };
+  const RN dtn = (RN)sc.dt, gan = (RN)sc.gamma, zen = (RN)sc.zeta;
   auto helm = [&](int sig) { return TabSm{t.tau.helm + (size_t)(sc.k * 2 + sig) * 4 * Mh * P + p, Mh, P}; };
   auto helm_isq = [&](int sig) { return t.tau.helm_isq[(size_t)(sc.k * 2 + sig) * P + p]; };
   if (p == 0) {
@@ -963,7 +994,7 @@ __global__ void __launch_bounds__(64) stage_post_batched_kernel(Grid g, int B, P
     const int M = (N - s) / 2 + 1;
     double* X = (e == 0 ? pb.UM : pb.WM) + (size_t)b * ny;
     double* XP = (e == 0 ? pb.HXP : pb.HZP) + (size_t)b * ny;
-    const double2* Hm = (e == 0) ? Hx : Hz;
+    const CN* Hm = (e == 0) ? Hx : Hz;
     double rhs[MH], f[MH];
     double sum = 0.0, flux_old = 0.0;
 #pragma unroll
@@ -972,7 +1003,7 @@ __global__ void __launch_bounds__(64) stage_post_batched_kernel(Grid g, int B, P
       if (i < M) {
         const int n = 2 * i + s;
         const double xn = X[n];
-        const double hv = Hm[n * ppc].x;
+        const double hv = (double)Hm[n * ppc].x;
         const double hp = XP[n];
         XP[n] = hv;
         rhs[i] = -((1.0 + cc) * xn + sc.dt * (sc.gamma * hv + sc.zeta * hp)) * ibdn;
@@ -1009,7 +1040,10 @@ __global__ void __launch_bounds__(64) stage_post_batched_kernel(Grid g, int B, P
     const int sq = 1 - c;
     const int M = (N - sq) / 2 + 1;
     const CompS Gc{reinterpret_cast<double*>(pb.G) + base, 2 * P};
-    const CompS HGc{reinterpret_cast<double*>(pb.HGP) + base, 2 * P};
+    // previous right-hand sides are stored in the node precision
+    const CompT<RN> HGc{reinterpret_cast<RN*>(pb.HGP) + base, 2 * P};
+    const CompT<RN> HGr = kStageH ? CompT<RN>{reinterpret_cast<RN*>(sHGt) + 2 * pl + r, 2 * ppc} : HGc;
+    const RN sgnn = (RN)sgn, kxn = (RN)kx, kzn = (RN)kz;
     double rhs[MH], f[MH];
     double sum = 0.0;
 #pragma unroll
@@ -1018,10 +1052,11 @@ __global__ void __launch_bounds__(64) stage_post_batched_kernel(Grid g, int B, P
       if (i < M) {
         const int n = 2 * i + sq;
         const double gn = Gc[n];
-        const double hg = sgn * (kz * comp(Hx[n * ppc], ra) - kx * comp(Hz[n * ppc], ra));
-        const double hp = HGc[n];
+        const RN hg = sgnn * (kzn * comp(Hx[n * ppc], ra) - kxn * comp(Hz[n * ppc], ra));
+        const RN hp = HGr[n];
         HGc[n] = hg;
-        rhs[i] = -((1.0 + cc) * gn + sc.dt * (sc.gamma * hg + sc.zeta * hp)) * ibdn;
+        const RN q = dtn * (gan * hg + zen * hp);
+        rhs[i] = -((1.0 + cc) * gn + (double)q) * ibdn;
         sum += gn;
       }
     }
@@ -1038,7 +1073,8 @@ __global__ void __launch_bounds__(64) stage_post_batched_kernel(Grid g, int B, P
     const int sv = c;
     const int M = (N - sv) / 2 + 1;
     const CompS Vc{reinterpret_cast<double*>(pb.V) + base, 2 * P};
-    const CompS HVc{reinterpret_cast<double*>(pb.HVP) + base, 2 * P};
+    const CompT<RN> HVc{reinterpret_cast<RN*>(pb.HVP) + base, 2 * P};
+    const CompT<RN> HVr = kStageH ? CompT<RN>{reinterpret_cast<RN*>(sHVt) + 2 * pl + r, 2 * ppc} : HVc;
     double S0 = 0.0, S2 = 0.0;
     double rhs[MH];
 #pragma unroll
@@ -1049,7 +1085,7 @@ __global__ void __launch_bounds__(64) stage_post_batched_kernel(Grid g, int B, P
       S0 += vn;
       S2 += (double)n * n * vn;
     }
-    v_walk<MH>(N, ny, ppc, sv, Vc, HVc, Hx, Hy, Hz, r, sgn, kx, kz, k2, cc, ibdn, sc, rhs);
+    v_walk<MH, RN>(N, ny, ppc, sv, Vc, HVr, HVc, Hx, Hy, Hz, r, sgn, kx, kz, k2, cc, ibdn, sc, rhs);
     double f[MH];
     tau_seq<MH>(N, ny, sv, rhs, f, helm(sv), helm_isq(sv), 0.0, rowc);
     const size_t vo = (size_t)b * P + p;
