@@ -125,39 +125,55 @@ __global__ void wall_shear_kernel(int ny, int B, const double* UM, double nu, do
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(128) sense_kernel(Grid g, int B, PencilBufs pb, DevTables t, int js, double alpha,
                                                     int opposition) {
+  // 8 lanes per mode (4 modes per warp): the sums over the ny coefficients are
+  // split over the lanes and combined by shuffles within the 8-lane group
+  constexpr int L = 8;
   const int P = g.P, ny = g.ny;
-  const int lane = threadIdx.x & 31;
-  const long wid = (blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5;
-  if (wid >= (long)P * B) return;
-  const int p = (int)(wid % P);
-  const int b = (int)(wid / P);
-  if (pb.active && !pb.active[b]) return;
+  const int lane = threadIdx.x & (L - 1);
+  const long wid = (blockIdx.x * (long)blockDim.x + threadIdx.x) / L;
+  const bool live = wid < (long)P * B;
+  const int p = live ? (int)(wid % P) : 0;
+  const int b = live ? (int)(wid / P) : 0;
+  const bool act = live && !(pb.active && !pb.active[b]);
+  auto gsum = [](double v) {
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, L);
+    return v;
+  };
+  auto gsum2 = [&](double2 v) { return mk(gsum(v.x), gsum(v.y)); };
   const int row = p / g.nxh, ix = p % g.nxh;
   const double* cj = t.cheb + (size_t)js * ny;
-  double2 us = mk(0.0, 0.0), vs = mk(0.0, 0.0);
-  if (row != g.nz / 2) {
+  // partial sums (only the loads are conditional; every lane of the warp then
+  // takes part in the same shuffles)
+  double su = 0.0;
+  double2 vs = mk(0.0, 0.0), gs = mk(0.0, 0.0), dvs = mk(0.0, 0.0);
+  if (act && row != g.nz / 2) {
     if (p == 0) {
-      double s = 0.0;
-      for (int n = lane; n < ny; n += 32) s += cj[n] * pb.UM[(size_t)b * ny + n];
-      us = mk(warp_sum(s), 0.0);
+      for (int n = lane; n < ny; n += L) su += cj[n] * pb.UM[(size_t)b * ny + n];
     } else {
       const size_t fo = (size_t)b * ny * P + p;
-      double2 dvs = mk(0.0, 0.0), gs = mk(0.0, 0.0);
-      for (int n = lane; n < ny; n += 32) {
+      for (int n = lane; n < ny; n += L) {
         const double2 vn = pb.V[fo + (size_t)n * P];
         const double2 gn = pb.G[fo + (size_t)n * P];
         vs = vs + cj[n] * vn;
         gs = gs + cj[n] * gn;
         dvs = dvs + t.dts[n] * vn;
       }
-      vs = warp_sum2(vs);
-      gs = warp_sum2(gs);
-      dvs = warp_sum2(dvs);
-      const double kx = t.kx[ix], kz = t.kz[row];
-      const double ik2 = 1.0 / (kx * kx + kz * kz);
-      us = ik2 * (imul(kx, dvs) - imul(kz, gs));
     }
   }
+  su = gsum(su);
+  vs = gsum2(vs);
+  gs = gsum2(gs);
+  dvs = gsum2(dvs);
+  double2 us = mk(0.0, 0.0);
+  if (p == 0) {
+    us = mk(su, 0.0);
+  } else if (row != g.nz / 2) {
+    const double kx = t.kx[ix], kz = t.kz[row];
+    const double ik2 = 1.0 / (kx * kx + kz * kz);
+    us = ik2 * (imul(kx, dvs) - imul(kz, gs));
+  }
+  if (!act) return;
   if (lane != 0) return;
   if (opposition) {
     // new action: the previous one becomes the start of the ramp, the wall
@@ -332,7 +348,7 @@ cudaError_t launch_wall_shear(const Grid& g, int B, const double* UM, double nu,
 
 cudaError_t launch_sense(const Grid& g, int B, const PencilBufs& pb, const DevTables& t, int js, double alpha,
                          int opposition, cudaStream_t st) {
-  const long threads = (long)g.P * B * 32;
+  const long threads = (long)g.P * B * 8;  // 8 lanes per mode
   sense_kernel<<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(g, B, pb, t, js, alpha, opposition);
   return cudaGetLastError();
 }
