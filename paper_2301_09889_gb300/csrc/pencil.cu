@@ -11,7 +11,6 @@
 #include "../../include/channel_dns.h"
 #include "common.cuh"
 #include "internal.h"
-#include "warp.cuh"
 
 namespace chdns {
 

@@ -162,8 +162,6 @@ __device__ __forceinline__ const double* cheb_table<double>(const DevTables& t) 
 template <>
 __device__ __forceinline__ const float* cheb_table<float>(const DevTables& t) { return t.cheb_f; }
 
-__device__ __forceinline__ double2 to_double(double2 v) { return v; }
-__device__ __forceinline__ double2 to_double(float2 v) { return make_double2((double)v.x, (double)v.y); }
 template <typename C> __device__ __forceinline__ C to_node(double2 v);
 template <> __device__ __forceinline__ double2 to_node<double2>(double2 v) { return v; }
 template <> __device__ __forceinline__ float2 to_node<float2>(double2 v) { return make_float2((float)v.x, (float)v.y); }
