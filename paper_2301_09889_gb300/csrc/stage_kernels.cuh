@@ -347,9 +347,21 @@ __global__ void __launch_bounds__(128) stage_pre_kernel(Grid g, int B, PencilBuf
   }
   __syncthreads();
 
-  if (tid < 4 * ppc) {
-    const int pl = tid % ppc;
-    const int combo = tid / ppc;
+  // Recover: the chain of every (mode, class c, component r) is walked by
+  // LC = 4 lanes (fixed, so every tile shape sums in the same order).  Lane lc
+  // takes a contiguous block of the step pairs (U-step at n_u = nu0 - 2k,
+  // V-step at n_u - 1), counted from the top; Dv, D omega_y and then D^2 v are
+  // inclusive prefix sums of their terms over k, formed per block and
+  // completed by the block totals of the lanes above (shuffles within the
+  // 4-lane group); the halvings at n = 0 come last.
+  {
+    constexpr int LC = 4;
+    constexpr int KB = (MH + 1 + LC - 1) / LC;  // step pairs per lane, bound
+    const int lc = tid % LC;
+    const int chain = tid / LC;  // (mode, combo) as tid did before: pl fastest
+    const bool on = chain < 4 * ppc;
+    const int pl = chain % ppc;
+    const int combo = chain / ppc;
     const int c = combo & 1, r = combo >> 1;
     const int p = p0 + pl;
     const int row = p / g.nxh, ix = p % g.nxh;
@@ -361,12 +373,25 @@ __global__ void __launch_bounds__(128) stage_pre_kernel(Grid g, int B, PencilBuf
       out[f * fs + n * 2 * ppc] = x;
       if (!fast && (n & 1) == 0) mid[f] = (n & 2) ? mid[f] - x : mid[f] + x;
     };
-    if (p >= P || row == g.nz / 2 || (p == 0 && r == 1)) {
-      for (int n = 0; n <= N; ++n) {
+    // inclusive prefix over the 4-lane group of this lane's block total;
+    // returns the exclusive offset
+    auto lane_offset = [&](RN tot) {
+      RN inc = tot;
+#pragma unroll
+      for (int o = 1; o < LC; o <<= 1) {
+        const RN v = __shfl_up_sync(0xffffffffu, inc, o, LC);
+        if (lc >= o) inc = inc + v;
+      }
+      return inc - tot;
+    };
+    const bool zero = !on || p >= P || row == g.nz / 2 || (p == 0 && r == 1);
+    const bool mean = on && !zero && p == 0;
+    if (on && zero) {
+      for (int n = lc; n <= N; n += LC) {
         if ((n & 1) == 1 - c) { W(0, n, 0.0); W(2, n, 0.0); W(4, n, 0.0); }
         else { W(1, n, 0.0); W(3, n, 0.0); W(5, n, 0.0); }
       }
-    } else if (p == 0) {
+    } else if (mean && lc == 0) {
       const double* U = pb.UM + (size_t)b * ny;
       const double* Wm = pb.WM + (size_t)b * ny;
       double du = 0.0, dw = 0.0;
@@ -385,64 +410,84 @@ __global__ void __launch_bounds__(128) stage_pre_kernel(Grid g, int B, PencilBuf
           W(5, n, -du);
         }
       }
-    } else {
-      // derivative chains and u, w, omega in the node precision (the nonlinear
-      // term's arithmetic; FP32 in mixed mode)
-      const RN kx = (RN)t.kx[ix], kz = (RN)t.kz[row];
-      const RN sg = (r == 0) ? (RN)-1.0 : (RN)1.0;
-      const RN ik2 = sg / (kx * kx + kz * kz);
-      const CompT<RN> V{reinterpret_cast<RN*>(sV) + 2 * pl + r, 2 * ppc};
-      const CompT<RN> Va{reinterpret_cast<RN*>(sV) + 2 * pl + (1 - r), 2 * ppc};
-      const CompT<RN> G{reinterpret_cast<RN*>(sG) + 2 * pl + r, 2 * ppc};
-      const CompT<RN> Ga{reinterpret_cast<RN*>(sG) + 2 * pl + (1 - r), 2 * ppc};
-      RN dv = 0, d2v = 0, dg = 0, vnext = 0, gnext = 0;
-      const RN skx = sg * kx, skz = sg * kz;
-      // U-step at n (parity 1 - c): Dv_n and u, w, omega_y; V-step at n (parity
-      // c): D^2 v_n, D omega_y_n and v, omega_x, omega_z.  Walking down from N
-      // they alternate; every U-step at n is followed by the V-step at n - 1,
-      // so both classes run the same uniform loop body.  fac = 2 (n + 1).
-      auto ustep = [&](int n, RN fac, bool halve) {
-        const RN t1 = dv + fac * vnext;
-        dv = halve ? (RN)0.5 * t1 : t1;
-        const RN ga = Ga[n];
-        W(0, n, ik2 * (kx * dv - kz * ga));  // u
-        W(2, n, ik2 * (kz * dv + kx * ga));  // w
-        W(4, n, G[n]);                       // omega_y
-        gnext = ga;
-      };
-      auto vstep = [&](int n, RN fac, bool halve) {
-        const RN t1 = d2v + fac * dv;
-        const RN t2 = dg + fac * gnext;
-        d2v = halve ? (RN)0.5 * t1 : t1;
-        dg = halve ? (RN)0.5 * t2 : t2;
-        const RN va = Va[n];
-        const RN du = ik2 * (kx * d2v - kz * dg);
-        const RN dw = ik2 * (kz * d2v + kx * dg);
-        W(1, n, V[n]);            // v
-        W(3, n, dw - skz * va);   // omega_x = Dw - i kz v
-        W(5, n, skx * va - du);   // omega_z = i kx v - Du
-        vnext = va;
-      };
-      int nu = N;                 // first U-step
-      if ((N & 1) != 1 - c) {     // the walk starts with the V-step at N
-        vstep(N, (RN)(2 * (N + 1)), N == 0);
-        nu = N - 1;
+    }
+    // the scans run on every lane (shuffles); only general modes use them
+    const bool gen = on && !zero && !mean;
+    const RN kx = gen ? (RN)t.kx[ix] : (RN)0, kz = gen ? (RN)t.kz[row] : (RN)0;
+    const RN sg = (r == 0) ? (RN)-1.0 : (RN)1.0;
+    const RN ik2 = gen ? sg / (kx * kx + kz * kz) : (RN)0;
+    const RN skx = sg * kx, skz = sg * kz;
+    const CompT<RN> V{reinterpret_cast<RN*>(sV) + 2 * pl + r, 2 * ppc};
+    const CompT<RN> Va{reinterpret_cast<RN*>(sV) + 2 * pl + (1 - r), 2 * ppc};
+    const CompT<RN> G{reinterpret_cast<RN*>(sG) + 2 * pl + r, 2 * ppc};
+    const CompT<RN> Ga{reinterpret_cast<RN*>(sG) + 2 * pl + (1 - r), 2 * ppc};
+    const int nu0 = ((N & 1) == 1 - c) ? N : N + 1;  // first U-step (N + 1: none)
+    const int K = nu0 / 2 + 1;                       // step pairs
+    const int Bk = (K + LC - 1) / LC;
+    const int k0 = lc * Bk;
+    RN dvk[KB], dgk[KB], d2k[KB];
+    RN sdv = 0, sdg = 0;
+#pragma unroll
+    for (int j = 0; j < KB; ++j) {
+      const int k = k0 + j;
+      const int nu = nu0 - 2 * k;
+      RN tdv = 0, tdg = 0;
+      if (gen && j < Bk && k < K) {
+        if (nu + 1 <= N) tdv = (RN)(2 * (nu + 1)) * Va[nu + 1];  // U-step at nu
+        if (nu <= N && nu >= 1) tdg = (RN)(2 * nu) * Ga[nu];      // V-step at nu - 1
       }
-      RN fu = (RN)(2 * (nu + 1));
-      for (; nu >= 2; nu -= 2) {  // U at nu >= 2, V at nu - 1 >= 1
-        ustep(nu, fu, false);
-        vstep(nu - 1, fu - (RN)2, false);
-        fu = fu - (RN)4;
-      }
-      if (nu == 1) {
-        ustep(1, (RN)4, false);
-        vstep(0, (RN)2, true);
-      } else if (nu == 0) {
-        ustep(0, (RN)2, true);
+      sdv = sdv + tdv;
+      sdg = sdg + tdg;
+      dvk[j] = sdv;
+      dgk[j] = sdg;
+    }
+    const RN odv = lane_offset(sdv), odg = lane_offset(sdg);
+    RN sd2 = 0;
+#pragma unroll
+    for (int j = 0; j < KB; ++j) {
+      const int k = k0 + j;
+      const int nu = nu0 - 2 * k;
+      dvk[j] = dvk[j] + odv;
+      dgk[j] = dgk[j] + odg;
+      RN td2 = 0;
+      if (gen && j < Bk && k < K && nu >= 1) td2 = (RN)(2 * nu) * dvk[j];  // V-step at nu - 1
+      sd2 = sd2 + td2;
+      d2k[j] = sd2;
+    }
+    const RN od2 = lane_offset(sd2);
+    if (gen) {
+#pragma unroll
+      for (int j = 0; j < KB; ++j) {
+        const int k = k0 + j;
+        if (j >= Bk || k >= K) continue;
+        const int nu = nu0 - 2 * k, nv = nu - 1;
+        if (nu <= N) {
+          const RN dv = (nu == 0) ? (RN)0.5 * dvk[j] : dvk[j];
+          const RN ga = Ga[nu];
+          W(0, nu, ik2 * (kx * dv - kz * ga));  // u
+          W(2, nu, ik2 * (kz * dv + kx * ga));  // w
+          W(4, nu, G[nu]);                      // omega_y
+        }
+        if (nv >= 0) {
+          const RN h = (nv == 0) ? (RN)0.5 : (RN)1.0;
+          const RN d2v = h * (d2k[j] + od2), dg = h * dgk[j];
+          const RN va = Va[nv];
+          const RN du = ik2 * (kx * d2v - kz * dg);
+          const RN dw = ik2 * (kz * d2v + kx * dg);
+          W(1, nv, V[nv]);            // v
+          W(3, nv, dw - skz * va);    // omega_x = Dw - i kz v
+          W(5, nv, skx * va - du);    // omega_z = i kx v - Du
+        }
       }
     }
-    // this thread wrote the even coefficients of fields 0, 2, 4 (c = 1) or 1, 3, 5 (c = 0)
-    if (!fast && (N & 1) == 0 && p < P) {
+    // middle node: the even coefficients of this chain's fields are spread over
+    // its 4 lanes
+#pragma unroll
+    for (int f = 0; f < 6; ++f)
+#pragma unroll
+      for (int o = 1; o < LC; o <<= 1) mid[f] = mid[f] + __shfl_xor_sync(0xffffffffu, mid[f], o, LC);
+    // this chain wrote the even coefficients of fields 0, 2, 4 (c = 1) or 1, 3, 5 (c = 0)
+    if (on && lc == 0 && !fast && (N & 1) == 0 && p < P) {
       RN* qr = reinterpret_cast<RN*>(q);
 #pragma unroll
       for (int f = 0; f < 6; ++f)
