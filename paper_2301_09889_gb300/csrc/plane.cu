@@ -26,6 +26,31 @@ namespace cg = cooperative_groups;
 
 namespace chdns {
 
+// v e^{2 pi i e / S} for 0 <= e < S (w = e^{2 pi i / mz}, mz = S Lz, table
+// tw_mz[k] = w^k).  Multiples of a quarter turn are exact component swaps;
+// other angles multiply by w^{e Lz}.
+template <typename C>
+__device__ __forceinline__ C turn(C v, int e, int S, int Lz, const C* tw_mz) {
+  if (e == 0) return v;
+  if ((4 * e) % S == 0) {
+    const int k = 4 * e / S;
+    if (k == 1) return mk(-v.y, v.x);
+    if (k == 2) return mk(-v.x, -v.y);
+    return mk(v.y, -v.x);
+  }
+  return cmul(v, tw_mz[e * Lz]);
+}
+
+// The cluster split of the z transforms.  CTA r owns the rows z = S m + r; the
+// inverse transform at those rows is an Lz-point transform of the folded
+// spectrum  sum_q X[u] w^{u r}  over u = m + q Lz (kz = u mod mz), and
+// w^{u r} = w^{m r} e^{2 pi i q r / S}: the terms take turns by S-th roots of
+// unity (exact quarter turns for S = 4) and the sum takes one table twiddle.
+// The forward direction mirrors it: output kz = u + q Lz of the forward
+// transform is  sum_r Z_r[u] w^{-u r} e^{-2 pi i q r / S},  and the factor
+// w^{-u r} depends on u alone, so CTA r applies it to its own Z_r before the
+// exchange.
+
 template <typename R>
 __global__ void __launch_bounds__(256) plane_kernel(PlaneArgs<R> a) {
   using C = typename cpx<R>::T;
@@ -59,13 +84,10 @@ __global__ void __launch_bounds__(256) plane_kernel(PlaneArgs<R> a) {
       else continue;
       const int row = kz >= 0 ? kz : nz + kz;
       C val = qf[row * nxh + i];
-      if (S > 1) {
-        int e = (kz * rank) % mz;
-        if (e < 0) e += mz;
-        val = cmul(val, a.tw_mz[e]);
-      }
+      if (S > 1) val = turn(val, (qq * rank) % S, S, Lz, a.tw_mz);
       acc = acc + val;
     }
+    if (rank > 0) acc = cmul(acc, a.tw_mz[m * rank]);
     Z[(f * Lz + m) * nxh + i] = acc;
   }
   __syncthreads();
@@ -130,6 +152,9 @@ __global__ void __launch_bounds__(256) plane_kernel(PlaneArgs<R> a) {
 
   // 3. forward z transform of H_x, H_y, H_z and cluster combination
   fft_dit<-1, R>(Z, 3 * nxh, nxh, a.pz, a.tw_z, false);
+  if (rank > 0) {
+    for (int w = tid; w < 3 * Lz * nxh; w += nt) Z[w] = cmul(Z[w], cconj(a.tw_mz[((w / nxh) % Lz) * rank]));
+  }
   if (S > 1) cg::this_cluster().sync();
   for (int w = tid; w < 3 * nz * nxh; w += nt) {
     const int i = w % nxh;
@@ -142,15 +167,13 @@ __global__ void __launch_bounds__(256) plane_kernel(PlaneArgs<R> a) {
       const int kz = row < nz / 2 ? row : row - nz;
       int u = kz % Lz;
       if (u < 0) u += Lz;
+      int q = ((kz - u) / Lz) % S;
+      if (q < 0) q += S;
       for (int rr = 0; rr < S; ++rr) {
         const C* Zr = Z;
         if (S > 1 && rr != rank) Zr = cg::this_cluster().map_shared_rank(Z, rr);
         C gval = Zr[(f * Lz + u) * nxh + i];
-        if (S > 1) {
-          int e = (-kz * rr) % mz;
-          if (e < 0) e += mz;
-          gval = cmul(gval, a.tw_mz[e]);
-        }
+        if (S > 1) gval = turn(gval, (S - (q * rr) % S) % S, S, Lz, a.tw_mz);
         out = out + gval;
       }
       out = a.scale * out;
@@ -167,15 +190,17 @@ __global__ void __launch_bounds__(256) plane_kernel(PlaneArgs<R> a) {
 // configurations in use; planes whose shared memory allows one CTA per SM run
 // more threads per CTA to hide shared-memory latency.
 template <typename R, int MX, int LZ, int NXH, int NP, int NT>
-__global__ void __launch_bounds__(NT) plane_kernel_ct(PlaneArgs<R> a) {
+__global__ void __launch_bounds__(NT, (sizeof(R) == 4 && NT == 256 && MX == LZ) ? 8 : 0) plane_kernel_ct(PlaneArgs<R> a) {
   using C = typename cpx<R>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* Z = reinterpret_cast<C*>(smem_raw);  // [6][LZ][NXH]
   C* X = Z + 6 * LZ * NXH;                // [6][NP][MX]
-  const int nz = a.nz, mz = a.mz, S = a.S;
+  // launched only when the cluster size a.S equals MX / LZ (mz = mx)
+  constexpr int S = MX / LZ;
+  const int nz = a.nz, mz = a.mz;
   const int tid = threadIdx.x;
   int rank = 0;
-  if (S > 1) rank = (int)cg::this_cluster().block_rank();
+  if constexpr (S > 1) rank = (int)cg::this_cluster().block_rank();
   const int j = blockIdx.y;
   const int b = blockIdx.z;
   if (a.active && !a.active[b]) return;  // whole cluster (same b) returns together
@@ -199,13 +224,10 @@ __global__ void __launch_bounds__(NT) plane_kernel_ct(PlaneArgs<R> a) {
       else continue;
       const int row = kz >= 0 ? kz : nz + kz;
       C val = qf[row * NXH + i];
-      if (S > 1 && rank > 0) {
-        int e = (kz * rank) % mz;
-        if (e < 0) e += mz;
-        val = cmul(val, a.tw_mz[e]);
-      }
+      if (rank > 0) val = turn(val, (qq * rank) % S, S, LZ, a.tw_mz);
       acc = acc + val;
     }
+    if (rank > 0) acc = cmul(acc, a.tw_mz[m * rank]);
     Z[(f * LZ + m) * NXH + i] = acc;
   }
   __syncthreads();
@@ -269,6 +291,9 @@ __global__ void __launch_bounds__(NT) plane_kernel_ct(PlaneArgs<R> a) {
 
   // 3. forward z transform of H_x, H_y, H_z and cluster combination
   fft_dit_ct<-1, R, LZ, 3 * NXH, NXH, false, NT>(Z, a.tw_z);
+  if (rank > 0) {
+    for (int w = tid; w < 3 * LZ * NXH; w += NT) Z[w] = cmul(Z[w], cconj(a.tw_mz[((w / NXH) % LZ) * rank]));
+  }
   if (S > 1) cg::this_cluster().sync();
   for (int w = tid; w < 3 * nz * NXH; w += NT) {
     const int i = w % NXH;
@@ -281,15 +306,13 @@ __global__ void __launch_bounds__(NT) plane_kernel_ct(PlaneArgs<R> a) {
       const int kz = row < nz / 2 ? row : row - nz;
       int u = kz % LZ;
       if (u < 0) u += LZ;
+      int q = ((kz - u) / LZ) % S;
+      if (q < 0) q += S;
       for (int rr = 0; rr < S; ++rr) {
         const C* Zr = Z;
         if (S > 1 && rr != rank) Zr = cg::this_cluster().map_shared_rank(Z, rr);
         C gval = Zr[(f * LZ + u) * NXH + i];
-        if (S > 1 && rr > 0) {
-          int e = (-kz * rr) % mz;
-          if (e < 0) e += mz;
-          gval = cmul(gval, a.tw_mz[e]);
-        }
+        if (rr > 0) gval = turn(gval, (S - (q * rr) % S) % S, S, LZ, a.tw_mz);
         out = out + gval;
       }
       out = a.scale * out;
@@ -329,7 +352,7 @@ static cudaError_t launch_with(K kernel, const PlaneArgs<R>& a, int B, size_t sm
 
 // compile-time instantiations: (MX, LZ, NXH, NP) of the grids in use
 #define CH_PLANE_CT_NT(MX_, LZ_, NXH_, NP_, NT_)                                                      \
-  if (a.mx == MX_ && a.Lz == LZ_ && a.nxh == NXH_ && a.NP == NP_) {                                  \
+  if (a.mx == MX_ && a.Lz == LZ_ && a.nxh == NXH_ && a.NP == NP_ && a.S == MX_ / LZ_) {             \
     static size_t cfg_ = 0;                                                                           \
     return launch_with(plane_kernel_ct<R, MX_, LZ_, NXH_, NP_, NT_>, a, B, smem, st, &cfg_, NT_);     \
   }
