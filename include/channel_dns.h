@@ -192,8 +192,8 @@ int env_info(const ch_env_t* env, ch_info_t* info);
 
 /* Pin the tile shapes of the two stage kernels (overriding the autotuner):
  * ppc_pre in {1, 2, 4, 8} modes per 128-thread CTA of the explicit half;
- * post_batched 0 with ppc_post in {1, 2, 4, 8} (8 threads per mode) or 1
- * with ppc_post in {1, 2, 4, 8, 16} (4 threads per mode).  Every shape gives
+ * post_batched 0 with ppc_post in 1..8 (8 threads per mode) or 1 with
+ * ppc_post in {1, 2, 4, 8, 16} (4 threads per mode).  Every shape gives
  * bit-identical results.  Waits for the handle's stream.  No counterpart in
  * the paper (a tuning control of this implementation).
  * Errors: CH_ERR_ARG (bad handle or shape, or a shape whose shared memory

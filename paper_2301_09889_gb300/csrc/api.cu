@@ -664,7 +664,9 @@ bool tiles_valid(const ch_env* env, int smem_max, int ppc_pre, int ppc_post, int
   if (!pow2(ppc_pre, 8) || stage_pre_smem(g, ppc_pre, node) > (size_t)smem_max) return false;
   if (post_batched == 1) return pow2(ppc_post, 16) && stage_post_batched_smem(g, ppc_post) <= (size_t)smem_max;
   if (post_batched != 0) return false;
-  return pow2(ppc_post, 8) && stage_post_smem(g, env->tab.tau.Mh, ppc_post) <= (size_t)smem_max;
+  // the per-tile form runs 8 ppc threads and any tile width up to 8 (widths
+  // that are not powers of two fill the resident CTA slots more evenly)
+  return ppc_post >= 1 && ppc_post <= 8 && stage_post_smem(g, env->tab.tau.Mh, ppc_post) <= (size_t)smem_max;
 }
 
 int drop_graphs(ch_env* env) {
@@ -748,7 +750,7 @@ int autotune_tiles(ch_env* env, int smem_max) {
     }
   }
   have = false;
-  const std::pair<int, int> cands[] = {{0, 8}, {0, 4}, {0, 2}, {1, 16}, {1, 8}};
+  const std::pair<int, int> cands[] = {{0, 8}, {0, 7}, {0, 6}, {0, 5}, {0, 4}, {0, 3}, {0, 2}, {1, 16}, {1, 8}};
   for (const auto& c : cands) {
     if (!tiles_valid(env, smem_max, env->ppc_pre, c.second, c.first)) continue;
     float ms = 0.f;

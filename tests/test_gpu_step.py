@@ -324,7 +324,9 @@ def test_tile_shapes_give_identical_results(native_gpu, precision):
     B = 3
     kw = dict(MINIMAL, precision=precision, autotune=0)
     acts = np.stack([si.wall_action(16, 16, 700 + e, 0.5 * 180 / 2800) for e in range(B)])
-    shapes = [(8, 8, 0), (4, 4, 0), (2, 2, 0), (1, 1, 0), (8, 16, 1), (4, 8, 1), (2, 1, 1)]
+    # post widths 7, 5 and 3 leave a ragged last tile of the 128 modes
+    shapes = [(8, 8, 0), (4, 4, 0), (2, 2, 0), (1, 1, 0), (8, 7, 0), (2, 5, 0), (4, 3, 0), (8, 16, 1), (4, 8, 1),
+              (2, 1, 1)]
     ref = None
     for pre, post, bat in shapes:
         env = native.env_create(native.params(**kw, batch=B))
@@ -354,8 +356,8 @@ def test_autotune_picks_a_candidate_and_rejects_bad_shapes(native_gpu):
         info = native.env_info(env)
         assert info.tuned == 1 and info.tune_ms > 0
         assert info.ppc_pre in (2, 4, 8)
-        assert (info.post_batched, info.ppc_post) in {(0, 8), (0, 4), (0, 2), (1, 16), (1, 8)}
-        for bad in ((3, 8, 0), (16, 8, 0), (8, 16, 0), (8, 32, 1), (8, 8, 2)):
+        assert (info.post_batched, info.ppc_post) in {(0, w) for w in range(2, 9)} | {(1, 16), (1, 8)}
+        for bad in ((3, 8, 0), (16, 8, 0), (8, 16, 0), (8, 9, 0), (8, 0, 0), (8, 12, 1), (8, 32, 1), (8, 8, 2)):
             with pytest.raises(native.ChannelError):
                 native.env_set_tiles(env, *bad)
     finally:
