@@ -149,8 +149,8 @@ def measured_peaks() -> dict:
 # the roofline kernel, from one ncu --set full capture of the same workload
 # (summaries under profiles/); absent where no capture of the current kernel exists
 TRAFFIC_BYTES = {
-    ("larger_fp64", "nonlinear_plane"): 12.649984e6,
-    ("minimal_batch256_mixed", "stage_post"): (151.632128 + 41.984768) * 1e6,
+    ("larger_fp64", "nonlinear_plane"): 12.639232e6,
+    ("minimal_batch256_mixed", "stage_post"): (151.807488 + 41.975552) * 1e6,
 }
 
 # FP64 FMA rate: 152 SMs x 2 FP64 FMA/clk/SM x 2 FLOP x 2.07 GHz (probe-measured, see the design notes)

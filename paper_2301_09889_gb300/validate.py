@@ -1,0 +1,171 @@
+"""Opposition-control validation run (Sec. 4.1; the baselines of Sec. 4.2-4.3).
+
+Spins up B seeded channels without control, then branches every channel into
+an uncontrolled copy and an opposition-controlled copy (v_w = -alpha (v_s -
+<v_s>), sensing plane at y+ = 15 rounded up to a node) and runs both at
+constant flow rate.  Reported, over the window after the transient:
+
+* the drag reduction DR = 1 - <tau_w>_controlled / <tau_w>_uncontrolled of
+  the channels still turbulent when the copies branch (wall shear above twice
+  the laminar 3 nu U_b / h), with the spread of the per-channel values;
+* the laminar upper bound 1 - tau_lam / <tau_w>_uncontrolled (Sec. 3.2 quotes
+  73.9 % at its Reynolds number);
+* on the sensing plane, the rms of u' and v' in wall units of the uncontrolled
+  flow and the fractions of the four quadrants of (u', v') (Q2 ejections,
+  Q4 sweeps; Sec. 4.2-4.3 discuss how control changes them).
+
+The paper reports DR of 26 % (minimal channel) and 20 % (larger channel) for
+opposition control at y+ = 15, after an initial transient of t+ = 500.
+Every step runs through the C ABI; this module only averages its outputs.
+
+    python -m paper_2301_09889_gb300.validate --grid minimal --batch 16
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import time
+
+import numpy as np
+
+from . import native
+
+GRIDS = {
+    "minimal": dict(nx=16, ny=65, nz=16, lx=2.67, lz=0.8),
+    "larger": dict(nx=64, ny=65, nz=64, lx=2 * math.pi, lz=math.pi),
+}
+
+
+class PlaneStats:
+    """Running sums of the wall shear and of the sensing-plane fluctuations."""
+
+    def __init__(self, batch: int):
+        self.n = 0
+        self.tau = np.zeros(batch)
+        self.uu = self.vv = self.uv = 0.0
+        self.quad = np.zeros(4)
+        self.points = 0
+
+    def add(self, tau: np.ndarray, obs: np.ndarray, keep: np.ndarray):
+        self.n += 1
+        self.tau += tau
+        u, v = obs[keep, 0], obs[keep, 1]
+        up = u - u.mean(axis=(1, 2), keepdims=True)
+        vp = v - v.mean(axis=(1, 2), keepdims=True)
+        self.uu += float((up * up).sum())
+        self.vv += float((vp * vp).sum())
+        self.uv += float((up * vp).sum())
+        self.quad += [np.count_nonzero((up > 0) & (vp > 0)), np.count_nonzero((up < 0) & (vp > 0)),
+                      np.count_nonzero((up < 0) & (vp < 0)), np.count_nonzero((up > 0) & (vp < 0))]
+        self.points += up.size
+
+    def summary(self, u_tau0: float) -> dict:
+        m = max(self.points, 1)
+        return {
+            "u_rms_plus": math.sqrt(self.uu / m) / u_tau0,
+            "v_rms_plus": math.sqrt(self.vv / m) / u_tau0,
+            "uv_plus": self.uv / m / u_tau0 ** 2,
+            "quadrants_Q1_Q2_Q3_Q4": (self.quad / m).round(4).tolist(),
+        }
+
+
+def _step(env, act, obs, tau, rew):
+    rc = native.env_step(env, act, obs, tau, rew)
+    if rc != native.CH_OK:
+        raise RuntimeError(f"env_step: {native.ch_strerror(rc)}")
+
+
+def run(grid: str = "minimal", batch: int = 16, precision: int = 0, seed: int = 0, amplitude: float = 1.0,
+        kmax: int = 4, t_spin: float = 300.0, t_trans: float = 43.2, t_avg: float = 300.0, spa: int = 20,
+        alpha: float = 1.0, y_plus: float = 15.0, dt: float = 0.005, re_tau: float = 180.0,
+        re_bulk: float = 2800.0) -> dict:
+    """Times in bulk units (h / U_b); t_trans = 43.2 is t+ = 500 at Re_tau 180,
+    Re_b 2800.  spa: solver steps per env_step call (wall shear averaged over
+    them)."""
+    t0 = time.perf_counter()
+    base = dict(GRIDS[grid], re_tau=re_tau, re_bulk=re_bulk, dt=dt, precision=precision, batch=batch,
+                steps_per_action=spa, y_sense_plus=y_plus, alpha=alpha)
+    nz, nx = base["nz"], base["nx"]
+    t_call = spa * dt
+    zero = np.zeros((batch, nz, nx))
+    obs = np.zeros((batch, 2, nz, nx))
+    tau, rew = np.zeros(batch), np.zeros(batch)
+    unc = native.env_create(native.params(**base, control=0))
+    ctl = None
+    try:
+        native.env_reset(unc, seed, amplitude, kmax)
+        n_spin = max(1, round(t_spin / t_call))
+        spin_tau = np.zeros(batch)
+        for i in range(n_spin):
+            _step(unc, zero, obs, tau, rew)
+            if i >= n_spin - max(1, n_spin // 10):
+                spin_tau += tau
+        spin_tau /= max(1, n_spin // 10)
+        tau_lam = 3.0 / re_bulk
+        keep = spin_tau > 2.0 * tau_lam
+        ctl = native.env_create(native.params(**base, control=1))
+        info = native.env_info(ctl)
+        for b in range(batch):
+            native.env_set_state(ctl, b, native.env_get_state(unc, b))
+        n_trans, n_avg = round(t_trans / t_call), max(1, round(t_avg / t_call))
+        stats = {}
+        for name, env, act in (("uncontrolled", unc, zero), ("opposition", ctl, None)):
+            st = PlaneStats(batch)
+            for i in range(n_trans + n_avg):
+                _step(env, act, obs, tau, rew)
+                if i >= n_trans and keep.any():
+                    st.add(tau, obs, keep)
+            stats[name] = st
+    finally:
+        native.env_destroy(unc)
+        if ctl is not None:
+            native.env_destroy(ctl)
+    out = {
+        "grid": grid, "nx_ny_nz": [nx, base["ny"], nz], "precision": "f64" if precision == 0 else "mixed",
+        "batch": batch, "seed": seed, "amplitude": amplitude, "kmax": kmax, "dt": dt, "steps_per_call": spa,
+        "t_spin": t_spin, "t_transient": t_trans, "t_average": t_avg, "alpha": alpha,
+        "sensing_node": int(info.j_sense), "sensing_y_plus": float(info.y_plus_sense),
+        "turbulent_at_branch": int(keep.sum()),
+    }
+    if keep.any():
+        tu = stats["uncontrolled"].tau[keep] / stats["uncontrolled"].n
+        tc = stats["opposition"].tau[keep] / stats["opposition"].n
+        u_tau0 = math.sqrt(float(tu.mean()))
+        dr_each = 1.0 - tc / tu
+        out.update({
+            "tau_w_uncontrolled": float(tu.mean()), "tau_w_opposition": float(tc.mean()),
+            "re_tau_uncontrolled": u_tau0 * re_bulk,
+            "drag_reduction": 1.0 - float(tc.mean()) / float(tu.mean()),
+            "drag_reduction_spread": float(dr_each.std()),
+            "laminar_bound": 1.0 - tau_lam / float(tu.mean()),
+            "plane_uncontrolled": stats["uncontrolled"].summary(u_tau0),
+            "plane_opposition": stats["opposition"].summary(u_tau0),
+        })
+    out["wall_s"] = time.perf_counter() - t0
+    return out
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--grid", choices=tuple(GRIDS), default="minimal")
+    ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--precision", type=int, choices=(0, 1), default=0)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--amplitude", type=float, default=1.0)
+    ap.add_argument("--kmax", type=int, default=4)
+    ap.add_argument("--t-spin", type=float, default=300.0)
+    ap.add_argument("--t-transient", type=float, default=43.2)
+    ap.add_argument("--t-average", type=float, default=300.0)
+    ap.add_argument("--steps-per-call", type=int, default=20)
+    ap.add_argument("--alpha", type=float, default=1.0)
+    ap.add_argument("--y-plus", type=float, default=15.0)
+    a = ap.parse_args(argv)
+    res = run(a.grid, a.batch, a.precision, a.seed, a.amplitude, a.kmax, a.t_spin, a.t_transient, a.t_average,
+              a.steps_per_call, a.alpha, a.y_plus)
+    print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()
