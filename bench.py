@@ -34,6 +34,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -51,11 +53,31 @@ WORKLOADS = {
     "minimal_batch256_mixed": (MINIMAL, 256, 1,
                                "256 minimal channels 16x65x16 in one launch per kernel, mixed precision, "
                                "per-step seeded ZNMF Gaussian actions std 0.05 u_tau"),
+    "minimal_batch256_policy_mixed": (dict(MINIMAL, control=2), 256, 1,
+                                      "256 minimal channels 16x65x16, mixed precision, on-device policy closing "
+                                      "the loop: 3x3 window of u, v per agent, two ReLU layers of 64, u_tau tanh "
+                                      "output, seeded random weights"),
     "large550_mixed": (dict(MINIMAL, nx=256, ny=193, nz=256, lx=2 * math.pi, lz=math.pi, re_tau=550.0,
                             re_bulk=10030.0, dt=0.002), 1, 1,
                        "large channel Re_tau=550, 256x193x256, mixed precision, seeded ZNMF Gaussian actions "
                        "std 0.05 u_tau (the FP64 padded plane does not fit a cluster's shared memory)"),
 }
+# on-device policy of the control-2 workloads: (wz, wx, hidden widths, u_tau tanh output, weight seed)
+POLICIES = {"minimal_batch256_policy_mixed": (3, 3, (64, 64), True, 77)}
+
+
+def policy_weights(wz: int, wx: int, hidden: tuple, seed: int) -> np.ndarray:
+    """Seeded random weights (no trained policy exists): N(0, 1/fan_in) per
+    layer, biases N(0, 0.01); layer layout W [out][in] then b [out]."""
+    rng = np.random.default_rng(seed)
+    sizes = [2 * wz * wx] + list(hidden) + [1]
+    parts = []
+    for i in range(len(sizes) - 1):
+        parts.append(rng.standard_normal(sizes[i + 1] * sizes[i]) / math.sqrt(sizes[i]))
+        parts.append(rng.standard_normal(sizes[i + 1]) * 0.1)
+    return np.concatenate(parts)
+
+
 # served workloads: (list of (parameters, count), slots per class, environments per actor thread,
 # description)
 MID = dict(LARGER, nx=32, nz=32, control=0)
@@ -211,26 +233,35 @@ class ClockSampler:
 def oracle_sample(budget_s: float, max_steps: int, workload: str = DEFAULT_WORKLOAD):
     """Time the FP64 oracle on one environment of the workload: whole
     environment steps until the budget is spent."""
-    import numpy as np
-
     import seeded_inputs as si
     from oracle import channel
+    from oracle import policy as opol
     prm = WORKLOADS[workload][0]
     keys = ("nx", "ny", "nz", "lx", "lz", "re_tau", "re_bulk", "dt", "steps_per_action",
             "y_sense_plus", "control", "alpha")
-    op = channel.Params(**{k: prm[k] for k in keys})
+    kw = {k: prm[k] for k in keys}
+    pol = POLICIES.get(workload) if prm["control"] == 2 else None
+    if pol:
+        kw["control"] = 0  # the oracle's policy supplies the external action
+    op = channel.Params(**kw)
     ops = channel.Operators(op)
     st = channel.new_state(si.perturbed_poiseuille(op.nx, op.ny, op.nz, 0, 0.1, 99), op)
     rng = np.random.default_rng(0)
+    if pol:
+        wz, wx, hidden, tanh_out, wseed = pol
+        w = policy_weights(wz, wx, hidden, wseed)
+        obs = channel.observation(st, ops)
     times = []
     t_all = time.perf_counter()
     while len(times) < max_steps and (time.perf_counter() - t_all) < budget_s:
         act = None
-        if op.control == 0:
+        if op.control == 0 and not pol:
             act = rng.standard_normal((op.nz, op.nx)) * 0.05 * op.u_tau
             act -= act.mean()
         t0 = time.perf_counter()
-        channel.env_step(st, ops, act)
+        if pol:
+            act = opol.actions(obs[None], w, wz, wx, hidden, tanh_out, op.u_tau)[0]
+        obs, _, _ = channel.env_step(st, ops, act)
         times.append(time.perf_counter() - t0)
     return times
 
@@ -418,6 +449,9 @@ def main():
     p = native.params(**prm, batch=B, precision=prec, autotune=0 if args.no_autotune else 1)
     env = native.env_create(p)
     info = native.env_info(env)
+    if prm["control"] == 2:
+        wz, wx, hidden, tanh_out, wseed = POLICIES[args.workload]
+        native.env_set_policy(env, native.policy(wz, wx, hidden, tanh_out), policy_weights(wz, wx, hidden, wseed))
     native.env_reset(env, seed=1000 * rank, amplitude=0.1, kmax=99)
     # one dedicated stream for the steps, the L2 flush and the timing events
     # (the library's own stream is non-blocking and does not order with

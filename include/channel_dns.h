@@ -75,7 +75,8 @@ typedef struct ch_params {
                                 (Chebyshev synthesis/analysis, padded FFTs, products)
                                 in FP32, the tau solves, influence-matrix correction
                                 and flow-rate update in FP64                            */
-    int control;             /* 0: external action, 1: opposition control (Sec. 4.1)  */
+    int control;             /* 0: external action, 1: opposition control (Sec. 4.1),
+                                2: on-device policy (env_set_policy)                    */
     double alpha;            /* opposition-control gain                                */
     double tau_ref;          /* reward reference wall shear; <= 0 -> u_tau^2          */
     int batch;               /* number of environments B sharing launches; <= 0 -> 1   */
@@ -199,6 +200,40 @@ int env_info(const ch_env_t* env, ch_info_t* info);
  * Errors: CH_ERR_ARG (bad handle or shape, or a shape whose shared memory
  * exceeds the device limit), CH_ERR_CUDA. */
 int env_set_tiles(ch_env_t* env, int ppc_pre, int ppc_post, int post_batched);
+
+/* On-device policy (control = 2).  Sec. 3.2: one agent per wall grid point,
+ * all sharing one policy that maps the observed part of the sensing plane
+ * above the agent's actuator to its wall-normal velocity (learnt by DDPG,
+ * whose actor is a multilayer perceptron; the paper gives no architecture).
+ * At the start of every step the library evaluates, for every agent, a
+ * perceptron with n_hidden ReLU layers on the u and v values of a periodic
+ * wz x wx window of the current sensing plane centred on the agent, in FP32,
+ * and applies the result as the wall action of the step (clipped to
+ * [-u_tau, u_tau], plane mean removed, ramped from the previous action, as an
+ * external action is).  The policy's input is the observation the previous
+ * step returned. */
+typedef struct ch_policy {
+    int wz, wx;              /* odd window sides, 1..7, at most nz and nx         */
+    int n_hidden;            /* 0 (linear), 1 or 2 hidden layers                   */
+    int width[2];            /* hidden widths, 1..64 (width[1] used if n_hidden 2) */
+    int out_tanh;            /* 1: action = u_tau tanh(y); 0: action = y           */
+} ch_policy_t;
+
+/* Set the policy.  weights (host, FP64, rounded to FP32 on upload): per layer,
+ * W [out][in] row-major then the bias [out]; layer 0 has K = 2 wz wx inputs
+ * x[(c wz + dz) wx + dx] = plane c (0: u, 1: v) at row (iz + dz - wz/2) mod nz
+ * and column (ix + dx - wx/2) mod nx of agent (iz, ix); the last layer has one
+ * output.  n_weights must be the count these sizes give.  Waits for the
+ * handle's stream.  Errors: CH_ERR_ARG (sizes, count or a non-finite weight),
+ * CH_ERR_STATE (handle not created with control = 2), CH_ERR_CUDA.  env_step on
+ * a control-2 handle without a policy returns CH_ERR_STATE. */
+int env_set_policy(ch_env_t* env, const ch_policy_t* pol, const double* weights, size_t n_weights);
+
+/* The wall action [B][nz][nx] of the last step before clipping and mean
+ * removal: the caller's (control 0) or the policy's (control 2), host buffer.
+ * Synchronises the stream.  Errors: CH_ERR_ARG, CH_ERR_STATE (control 1),
+ * CH_ERR_CUDA. */
+int env_get_action(ch_env_t* env, double* action);
 int env_destroy(ch_env_t* env);
 const char* ch_strerror(int code);
 
@@ -239,7 +274,8 @@ int srv_create(size_t hbm_budget_bytes, int slots_per_class, ch_server_t** out);
 /* Admit one environment with the env_reset initial state (seed, amplitude,
  * kmax).  Uses a free slot of its class; otherwise creates the class, which
  * fails with CH_ERR_BUDGET if its footprint does not fit the budget (retry
- * after srv_evict).  Writes the environment id. */
+ * after srv_evict).  Writes the environment id.  CH_ERR_UNSUPPORTED for
+ * control = 2 (the server takes actions from its requests). */
 int srv_admit(ch_server_t* s, const ch_params_t* p, uint64_t seed, double amplitude, int kmax, int* env_id);
 
 /* Remove an environment; its queued requests complete with CH_ERR_STATE.  A

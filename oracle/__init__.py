@@ -13,6 +13,9 @@ dense operators and library primitives (numpy matrix products, dense LU via
   formulation, the wall action, observation, wall shear and reward.
 * ``stability`` the Orr-Sommerfeld eigenvalue problem used to pin the linear
   dynamics (Tollmien-Schlichting growth rate at Re = 10^4, alpha = 1).
+* ``policy``    the shared agent policy (a multilayer perceptron on the
+  sensing-plane window above each actuator, Sec. 3.2) of the on-device
+  control mode.
 
 Every function cites the part of the paper it follows.  The paper fixes the
 Fourier x Chebyshev basis (Sec. 3.1), the RK3 + Crank-Nicolson time scheme
@@ -24,4 +27,4 @@ design notes (closed channel, SMR low-storage RK3 with alpha = beta, 3/2 rule,
 velocity-vorticity form with an influence-matrix equivalent coupled solve).
 """
 
-from . import spectral, channel, stability  # noqa: F401
+from . import spectral, channel, stability, policy  # noqa: F401

@@ -152,7 +152,7 @@ int check_params(const ch_params_t* p) {
   if (p->ny < 9 || p->ny > kMaxNy) return CH_ERR_ARG;
   if (!(p->lx > 0) || !(p->lz > 0) || !(p->re_bulk > 0) || !(p->re_tau > 0) || !(p->dt > 0)) return CH_ERR_ARG;
   if (p->steps_per_action < 1) return CH_ERR_ARG;
-  if (p->control != 0 && p->control != 1) return CH_ERR_ARG;
+  if (p->control < 0 || p->control > 2) return CH_ERR_ARG;
   if (p->autotune != 0 && p->autotune != 1) return CH_ERR_ARG;
   if (p->top_bc != 0 || (p->precision != 0 && p->precision != 1)) return CH_ERR_UNSUPPORTED;
   FftPlan a, b;
@@ -199,6 +199,11 @@ struct ch_env {
   // graph_mask (serving ticks).  Profiling launches the same kernels directly.
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   const int* graph_mask = nullptr;
+  // on-device policy (control 2): FP32 weights, its input planes [B][2][nz][nx]
+  float* d_pol_w = nullptr;
+  double* d_pol_in = nullptr;
+  PolicyDesc pol{};
+  bool pol_set = false;
   char err[256] = {0};
 };
 
@@ -616,6 +621,15 @@ int launch_step(ch_env* env, const double* d_action, double* d_out, const int* d
   } reset{env};
   if (env->prm.control == 1) {
     LAUNCH(3, launch_sense(g, B, env->pb, env->tab, env->js, env->prm.alpha, 1, st));
+  } else if (env->prm.control == 2) {
+    // the policy sees the sensing plane of the current flow, the same values
+    // the previous step returned as its observation
+    const size_t pstride = (size_t)2 * g.nz * g.nx;
+    LAUNCH(3, launch_sense(g, B, env->pb, env->tab, env->js, env->prm.alpha, 0, st));
+    LAUNCH(3, launch_obs(g, B, env->pb.planes, env->tab, env->d_pol_in, pstride, d_active, st));
+    LAUNCH(3, launch_policy(g.nx, g.nz, B, env->pol, env->d_pol_w, env->d_pol_in, env->d_act, env->u_tau, d_active,
+                            st));
+    LAUNCH(3, launch_action(g, B, env->d_act, env->u_tau, env->tab, env->pb, st));
   } else {
     LAUNCH(3, launch_action(g, B, d_action, env->u_tau, env->tab, env->pb, st));
   }
@@ -772,6 +786,7 @@ int autotune_tiles(ch_env* env, int smem_max) {
 int run_step(ch_env* env, const double* d_action, double* d_out, const int* d_active = nullptr,
              const int* h_active = nullptr) {
   const int B = env->B;
+  if (env->prm.control == 2 && !env->pol_set) return CH_ERR_STATE;
   if (env->prof) {
     RC(launch_step(env, d_action, d_out, d_active));
   } else {
@@ -900,6 +915,9 @@ int env_create(const ch_params_t* p, ch_env_t** out) {
   env->out_stride = (size_t)2 * g.nz * g.nx + 2;
   if ((rc = dalloc(env, &env->d_act, B * g.nz * g.nx)) || (rc = dalloc(env, &env->d_out, B * env->out_stride)))
     return fail(rc);
+  if (p->control == 2 && ((rc = dalloc(env, &env->d_pol_w, (size_t)kPolicyMaxWeights)) ||
+                          (rc = dalloc(env, &env->d_pol_in, B * 2 * g.nz * g.nx))))
+    return fail(rc);
   if (cudaMallocHost(&env->h_out, B * env->out_stride * sizeof(double)) != cudaSuccess) return fail(CH_ERR_OOM);
   if ((rc = build_tables(env))) return fail(rc);
   {
@@ -934,7 +952,7 @@ int env_create(const ch_params_t* p, ch_env_t** out) {
   if (cudaMemset(pb.vw_old, 0, B * P * sizeof(double2)) != cudaSuccess) return fail(CH_ERR_CUDA);
   if (cudaMemset(pb.tau_acc, 0, B * sizeof(double)) != cudaSuccess) return fail(CH_ERR_CUDA);
   if (cudaDeviceSynchronize() != cudaSuccess) return fail(CH_ERR_CUDA);
-  env->launches_per_step = (p->control == 0 ? 2 : 1) + p->steps_per_action * (3 * 3 + 1) + 3;
+  env->launches_per_step = (p->control == 0 ? 2 : p->control == 1 ? 1 : 5) + p->steps_per_action * (3 * 3 + 1) + 3;
   *out = env;
   return CH_OK;
 }
@@ -1056,6 +1074,47 @@ int env_set_tiles(ch_env_t* env, int ppc_pre, int ppc_post, int post_batched) {
   env->ppc_post = ppc_post;
   env->post_batched = post_batched == 1;
   env->tuned = false;
+  return CH_OK;
+}
+
+int env_set_policy(ch_env_t* env, const ch_policy_t* pol, const double* weights, size_t n_weights) {
+  if (!env || !pol || !weights) return CH_ERR_ARG;
+  if (env->prm.control != 2) return CH_ERR_STATE;
+  const Grid& g = env->g;
+  auto odd_side = [](int w, int n) { return w >= 1 && w <= kPolicyMaxWindow && (w & 1) && w <= n; };
+  auto width = [](int h) { return h >= 1 && h <= kPolicyMaxWidth; };
+  if (!odd_side(pol->wz, g.nz) || !odd_side(pol->wx, g.nx)) return CH_ERR_ARG;
+  if (pol->n_hidden < 0 || pol->n_hidden > 2 || (pol->out_tanh != 0 && pol->out_tanh != 1)) return CH_ERR_ARG;
+  if (pol->n_hidden >= 1 && !width(pol->width[0])) return CH_ERR_ARG;
+  if (pol->n_hidden == 2 && !width(pol->width[1])) return CH_ERR_ARG;
+  PolicyDesc d{};
+  d.wz = pol->wz;
+  d.wx = pol->wx;
+  d.n_hidden = pol->n_hidden;
+  d.h1 = pol->n_hidden >= 1 ? pol->width[0] : 0;
+  d.h2 = pol->n_hidden == 2 ? pol->width[1] : 0;
+  d.out_tanh = pol->out_tanh;
+  d.n_weights = policy_weight_count(d);
+  if (n_weights != (size_t)d.n_weights || d.n_weights > kPolicyMaxWeights) return CH_ERR_ARG;
+  std::vector<float> w(n_weights);
+  for (size_t i = 0; i < n_weights; ++i) {
+    if (!std::isfinite(weights[i])) return CH_ERR_ARG;
+    w[i] = (float)weights[i];
+  }
+  CK(cudaStreamSynchronize(env->stream));
+  CK(cudaMemcpy(env->d_pol_w, w.data(), n_weights * sizeof(float), cudaMemcpyHostToDevice));
+  RC(drop_graphs(env));  // the captured launches hold the previous descriptor
+  env->pol = d;
+  env->pol_set = true;
+  return CH_OK;
+}
+
+int env_get_action(ch_env_t* env, double* action) {
+  if (!env || !action) return CH_ERR_ARG;
+  if (env->prm.control == 1) return CH_ERR_STATE;
+  const size_t n = (size_t)env->B * env->g.nz * env->g.nx;
+  CK(cudaMemcpyAsync(action, env->d_act, n * sizeof(double), cudaMemcpyDeviceToHost, env->stream));
+  CK(cudaStreamSynchronize(env->stream));
   return CH_OK;
 }
 

@@ -63,6 +63,25 @@ cudaError_t launch_finalize(int B, const double* acc, double inv_steps, double t
 cudaError_t launch_tau_helmholtz(int ny, int M, const double* lam, const double2* r, const double2* top,
                                  const double2* bot, double2* f, cudaStream_t st);
 
+// on-device policy (policy.cu): a multilayer perceptron shared by every agent
+constexpr int kPolicyMaxWidth = 64;
+constexpr int kPolicyMaxWindow = 7;
+// weights of the largest network: 2 (7 x 7) inputs, two hidden layers of 64
+constexpr int kPolicyMaxWeights =
+    kPolicyMaxWidth * 2 * kPolicyMaxWindow * kPolicyMaxWindow + kPolicyMaxWidth +
+    kPolicyMaxWidth * kPolicyMaxWidth + kPolicyMaxWidth + kPolicyMaxWidth + 1;
+struct PolicyDesc {
+  int wz, wx;      // observation window (odd)
+  int n_hidden;    // 0, 1 or 2 ReLU layers
+  int h1, h2;      // hidden widths
+  int out_tanh;    // 1: action = u_tau tanh(y)
+  int n_weights;   // FP32 values at w
+};
+int policy_weight_count(const PolicyDesc& d);
+// plane [B][2][nz][nx] (u, v on the sensing plane) -> act [B][nz][nx]
+cudaError_t launch_policy(int nx, int nz, int B, const PolicyDesc& d, const float* w, const double* plane,
+                          double* act, double u_tau, const int* active, cudaStream_t st);
+
 }  // namespace chdns
 
 struct ch_env;

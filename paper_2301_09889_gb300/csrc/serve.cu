@@ -326,6 +326,7 @@ int srv_create(size_t hbm_budget_bytes, int slots_per_class, ch_server_t** out) 
 
 int srv_admit(ch_server_t* s, const ch_params_t* p, uint64_t seed, double amplitude, int kmax, int* env_id) {
   if (!s || !p || !env_id) return CH_ERR_ARG;
+  if (p->control == 2) return CH_ERR_UNSUPPORTED;  // no policy can be set through the server
   std::unique_lock<std::mutex> lk(s->mu);
   const ch_params_t key = key_of(*p);
   int ci = -1, slot = -1;

@@ -33,7 +33,7 @@ EXPORTS = (
     "ch_strerror", "ch_seed_state", "ch_state_bytes", "ch_nonlinear", "ch_tau_helmholtz",
     "env_profile", "env_profile_read", "ch_tau_helmholtz_noalloc", "env_set_tiles",
     "srv_create", "srv_admit", "srv_evict", "srv_submit", "srv_poll", "srv_wait", "srv_get_state",
-    "srv_set_state", "srv_stats", "srv_destroy",
+    "srv_set_state", "srv_stats", "srv_destroy", "env_set_policy", "env_get_action",
 )
 CH_PENDING = 1
 
@@ -66,6 +66,15 @@ class ChInfo(ctypes.Structure):
         ("ppc_pre", ctypes.c_int), ("ppc_post", ctypes.c_int),
         ("tuned", ctypes.c_int),
         ("tune_ms", ctypes.c_double),
+    ]
+
+
+class ChPolicy(ctypes.Structure):
+    _fields_ = [
+        ("wz", ctypes.c_int), ("wx", ctypes.c_int),
+        ("n_hidden", ctypes.c_int),
+        ("width", ctypes.c_int * 2),
+        ("out_tanh", ctypes.c_int),
     ]
 
 
@@ -133,6 +142,8 @@ def load() -> ctypes.CDLL:
         "srv_stats": (ctypes.c_int, [vp, P(ChSrvStats), ctypes.c_int]),
         "srv_destroy": (ctypes.c_int, [vp]),
         "env_profile_read": (ctypes.c_int, [vp, ctypes.c_int, P(ctypes.c_double), P(ctypes.c_int)]),
+        "env_set_policy": (ctypes.c_int, [vp, P(ChPolicy), vp, ctypes.c_size_t]),
+        "env_get_action": (ctypes.c_int, [vp, dp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -223,6 +234,37 @@ def env_step_device(env, d_action: int | None, d_out: int):
 
 def env_set_tiles(env, ppc_pre: int, ppc_post: int, post_batched: int):
     _check(load().env_set_tiles(env, ppc_pre, ppc_post, post_batched), "env_set_tiles")
+
+
+def policy(wz: int = 1, wx: int = 1, hidden: tuple = (), out_tanh: bool = True) -> ChPolicy:
+    """Policy descriptor: odd window (wz, wx), up to two hidden widths."""
+    pol = ChPolicy()
+    pol.wz, pol.wx, pol.n_hidden = wz, wx, len(hidden)
+    for i, h in enumerate(hidden[:2]):
+        pol.width[i] = h
+    pol.out_tanh = 1 if out_tanh else 0
+    return pol
+
+
+def policy_weight_count(pol: ChPolicy) -> int:
+    k = 2 * pol.wz * pol.wx
+    if pol.n_hidden == 0:
+        return k + 1
+    h1 = pol.width[0]
+    if pol.n_hidden == 1:
+        return h1 * k + h1 + h1 + 1
+    h2 = pol.width[1]
+    return h1 * k + h1 + h2 * h1 + h2 + h2 + 1
+
+
+def env_set_policy(env, pol: ChPolicy, weights: np.ndarray):
+    w = np.ascontiguousarray(weights, dtype=np.float64).ravel()
+    _check(load().env_set_policy(env, ctypes.byref(pol), w.ctypes.data, w.size), "env_set_policy")
+
+
+def env_get_action(env, action: np.ndarray):
+    """Copy the last step's wall action [B][nz][nx] into `action` (float64)."""
+    _check(load().env_get_action(env, _dptr(action)), "env_get_action")
 
 
 def env_info(env) -> ChInfo:
