@@ -583,8 +583,9 @@ def main():
         "dtype": "f64" if prec == 0 else "f32+f64", "data": "synthetic",
         "config": {"workload": wname, "grid": [nx, ny, nz], "batch": B, "re_tau": prm["re_tau"],
                    "re_bulk": prm["re_bulk"], "dt": prm["dt"],
-                   "control": ("opposition alpha=1, sensing node j=%d (y+=%.2f)" % (info.j_sense, info.y_plus_sense))
-                   if not external else "external seeded actions",
+                   "control": ("external seeded actions" if external else
+                               ("on-device policy, sensing node j=%d (y+=%.2f)" if prm["control"] == 2 else
+                                "opposition alpha=1, sensing node j=%d (y+=%.2f)") % (info.j_sense, info.y_plus_sense)),
                    "l2": "flushed between steps (256 MiB write outside the timed events)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "mpts_rk3_steps_per_s": value * nx * ny * nz / 1e6,
