@@ -64,6 +64,7 @@ __global__ void __launch_bounds__(256) plane_kernel(PlaneArgs<R> a) {
   const int j = blockIdx.y;
   const int b = blockIdx.z;
   if (a.active && !a.active[b]) return;  // whole cluster (same b) returns together
+  pdl_wait_then_release();               // the node values come from stage_pre
   const size_t plane = (size_t)a.P;
   const C* qb = a.q + (size_t)b * 6 * a.ny * plane + (size_t)j * plane;
   C* hb = a.h + (size_t)b * 3 * a.ny * plane + (size_t)j * plane;
@@ -204,6 +205,7 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 && NT == 256 && MX == LZ) 
   const int j = blockIdx.y;
   const int b = blockIdx.z;
   if (a.active && !a.active[b]) return;  // whole cluster (same b) returns together
+  pdl_wait_then_release();               // the node values come from stage_pre
   const size_t plane = (size_t)a.P;
   const C* qb = a.q + (size_t)b * 6 * a.ny * plane + (size_t)j * plane;
   C* hb = a.h + (size_t)b * 3 * a.ny * plane + (size_t)j * plane;
@@ -340,13 +342,22 @@ static cudaError_t launch_with(K kernel, const PlaneArgs<R>& a, int B, size_t sm
   cfg.blockDim = dim3(nt, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = a.S;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
+  cudaLaunchAttribute attr[2];
+  int na = 0;
+  if (sizeof(R) == 4) {  // programmatic launch for the FP32 plane only (see launch_pdl_if)
+    attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[na].val.programmaticStreamSerializationAllowed = 1;
+    ++na;
+  }
+  if (a.S > 1) {
+    attr[na].id = cudaLaunchAttributeClusterDimension;
+    attr[na].val.clusterDim.x = a.S;
+    attr[na].val.clusterDim.y = 1;
+    attr[na].val.clusterDim.z = 1;
+    ++na;
+  }
   cfg.attrs = attr;
-  cfg.numAttrs = a.S > 1 ? 1 : 0;
+  cfg.numAttrs = na;
   return cudaLaunchKernelEx(&cfg, kernel, a);
 }
 

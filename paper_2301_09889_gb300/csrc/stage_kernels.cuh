@@ -333,6 +333,7 @@ __global__ void __launch_bounds__(128) stage_pre_kernel(Grid g, int B, PencilBuf
   const int b = blockIdx.y;
   if (pb.active && !pb.active[b]) return;
   const int tid = threadIdx.x, nt = blockDim.x;
+  pdl_wait_then_release();  // v, omega_y come from the previous stage
   // FP64 nodes on a grid whose N the FFT plan covers: fast synthesis
   constexpr int NF = 2 * (MH - 1);
   constexpr bool kFastOk = std::is_same<RN, double>::value && ct_plan_ok(NF);
@@ -669,13 +670,6 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
     sHV[w] = reinterpret_cast<const CN*>(pb.HVP)[o];
     sHG[w] = reinterpret_cast<const CN*>(pb.HGP)[o];
   }
-  // nodal values in the node precision, in the first bytes of the sH region
-  CN* sN = reinterpret_cast<CN*>(sH);
-  for (int w = tid; w < 3 * ny * ppc; w += nt) {
-    const int pl = w % ppc, fn = w / ppc;  // fn = f * ny + n
-    const int p = min(p0 + pl, P - 1);
-    sN[w] = hn[((size_t)b * 3 * ny + fn) * P + p];
-  }
   for (int w = tid; w < 2 * 4 * Mh * ppc; w += nt) {
     const int pl = w % ppc, qq = w / ppc;  // qq = (sig * 4 + f) * Mh + i
     const int p = min(p0 + pl, P - 1);
@@ -693,6 +687,16 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
     ss[(0 * 2 + sig) * ppc + pl] = t.tau.helm_isq[(size_t)(sc.k * 2 + sig) * P + p];
     ss[(1 * 2 + sig) * ppc + pl] = t.tau.pois_isq[(size_t)sig * P + p];
     ss[(2 * 2 + sig) * ppc + pl] = t.tau.vh_idv[(size_t)(sc.k * 2 + sig) * P + p];
+  }
+  // everything above is independent of the nonlinear term; H comes from the
+  // preceding kernel
+  pdl_wait_then_release();
+  // nodal values in the node precision, in the first bytes of the sH region
+  CN* sN = reinterpret_cast<CN*>(sH);
+  for (int w = tid; w < 3 * ny * ppc; w += nt) {
+    const int pl = w % ppc, fn = w / ppc;  // fn = f * ny + n
+    const int p = min(p0 + pl, P - 1);
+    sN[w] = hn[((size_t)b * 3 * ny + fn) * P + p];
   }
   __syncthreads();
 
@@ -943,11 +947,6 @@ __global__ void __launch_bounds__(64) stage_post_batched_kernel(Grid g, int B, P
   const int b = blockIdx.y;
   if (pb.active && !pb.active[b]) return;
   const int tid = threadIdx.x, nt = blockDim.x;
-  for (int w = tid; w < 3 * ny * ppc; w += nt) {
-    const int pl = w % ppc, fn = w / ppc;  // fn = f * ny + n
-    const int p = min(p0 + pl, P - 1);
-    sN[w] = hn[((size_t)b * 3 * ny + fn) * P + p];
-  }
   // FP32 nodes: the previous right-hand sides (FP32 pairs) are staged in shared
   // memory by one coalesced load, behind the node tile within the space the
   // FP64 coefficient tile takes; the new ones go straight to global memory
@@ -961,6 +960,12 @@ __global__ void __launch_bounds__(64) stage_post_batched_kernel(Grid g, int B, P
       sHVt[w] = reinterpret_cast<const CN*>(pb.HVP)[o];
       sHGt[w] = reinterpret_cast<const CN*>(pb.HGP)[o];
     }
+  }
+  pdl_wait_then_release();  // H comes from the preceding kernel
+  for (int w = tid; w < 3 * ny * ppc; w += nt) {
+    const int pl = w % ppc, fn = w / ppc;  // fn = f * ny + n
+    const int p = min(p0 + pl, P - 1);
+    sN[w] = hn[((size_t)b * 3 * ny + fn) * P + p];
   }
   __syncthreads();
   const int r = tid & 1, pl = (tid >> 1) % ppc, c = tid / (2 * ppc);
@@ -1168,8 +1173,8 @@ cudaError_t pre_mh(const Grid& g, int B, const PencilBufs& pb, const DevTables& 
     if (e != cudaSuccess) return e;
     configured = smem;
   }
-  stage_pre_kernel<RN, MH><<<dim3((g.P + ppc - 1) / ppc, B), 128, smem, st>>>(g, B, pb, t, q, ppc);
-  return cudaGetLastError();
+  return launch_pdl_if<sizeof(RN) == 4>(stage_pre_kernel<RN, MH>, dim3((g.P + ppc - 1) / ppc, B), dim3(128), smem, st, g, B, pb, t, q,
+                    ppc);
 }
 
 template <typename RN, int MH>
@@ -1183,8 +1188,8 @@ cudaError_t post_mh(const Grid& g, int B, const PencilBufs& pb, const DevTables&
     if (e != cudaSuccess) return e;
     configured = smem;
   }
-  stage_post_kernel<RN, MH><<<dim3((g.P + ppc - 1) / ppc, B), 8 * ppc, smem, st>>>(g, B, pb, t, h, sc, ppc);
-  return cudaGetLastError();
+  return launch_pdl_if<sizeof(RN) == 4>(stage_post_kernel<RN, MH>, dim3((g.P + ppc - 1) / ppc, B), dim3(8 * ppc), smem, st, g, B, pb,
+                    t, h, sc, ppc);
 }
 
 template <typename RN, int MH>
@@ -1198,9 +1203,8 @@ cudaError_t post_batched_mh(const Grid& g, int B, const PencilBufs& pb, const De
     if (e != cudaSuccess) return e;
     configured = smem;
   }
-  stage_post_batched_kernel<RN, MH><<<dim3((g.P + ppc - 1) / ppc, B), 4 * ppc, smem, st>>>(g, B, pb, t, h, sc,
-                                                                                            ppc);
-  return cudaGetLastError();
+  return launch_pdl_if<sizeof(RN) == 4>(stage_post_batched_kernel<RN, MH>, dim3((g.P + ppc - 1) / ppc, B), dim3(4 * ppc), smem, st, g,
+                    B, pb, t, h, sc, ppc);
 }
 
 }  // namespace chdns
