@@ -39,6 +39,12 @@ path reaches the same solution through an influence-matrix superposition.)
 The mean profile is one dense system with the unknown forcing ``f_x`` and the
 flow-rate row appended.
 
+Open channel (``top_bc = 1``; Sec. 3.1: an open channel of height h with a
+free-slip top): ``y in [-1, 1]`` is the whole channel, so Re_b and Re_tau
+are based on the height 2 (``nu = 2 / Re_b``, ``y+ = (1 + y) Re_tau / 2``),
+and the top rows become ``Dg(+1) = 0``, ``D^2 v(+1) = 0`` (with ``v(+1) = 0``),
+``DU(+1) = DW(+1) = 0``.  The library does not implement it yet.
+
 Wall action (Sec. 3.2): clipped to ``[-u_tau, u_tau]``, plane mean removed
 (zero net mass flux, Sec. 4.1), ramped linearly from the previous action over
 the actuation interval; stage k of step s sees the ramp at its end time.
@@ -82,10 +88,18 @@ class Params:
     control: int = 0          # 0 external action, 1 opposition control
     alpha: float = 1.0        # opposition gain
     tau_ref: float = 0.0      # 0 -> (Re_tau / Re_b)^2
+    top_bc: int = 0           # 0 no-slip wall at y = +1, 1 free slip (open channel)
+
+    @property
+    def height(self) -> float:
+        """Length on which Re_b and Re_tau are based, in units of y: the
+        half-height 1 of the closed channel; the whole height 2 of the open
+        channel (Sec. 3.1: an open channel of height h)."""
+        return 2.0 if self.top_bc == 1 else 1.0
 
     @property
     def nu(self) -> float:
-        return 1.0 / self.re_bulk
+        return self.height / self.re_bulk
 
     @property
     def u_tau(self) -> float:
@@ -96,15 +110,16 @@ class Params:
         return self.tau_ref if self.tau_ref > 0 else self.u_tau ** 2
 
 
-def sensing_node(N: int, re_tau: float, y_plus: float) -> int:
+def sensing_node(N: int, re_tau: float, y_plus: float, height: float = 1.0) -> int:
     """First Gauss-Lobatto node, walking up from the lower wall, with y+ >= y_plus.
 
     Sec. 3.2: the sampling height is rounded up to a Chebyshev node;
-    y+ = (1 + y) Re_tau measured from the lower wall.
+    y+ = (1 + y) u_tau / nu = (1 + y) Re_tau / height measured from the lower
+    wall (height: the length Re_tau is based on, in units of y).
     """
     for j in range(N, -1, -1):
         yj = math.cos(math.pi * j / N)
-        if (1.0 + yj) * re_tau >= y_plus:
+        if (1.0 + yj) * re_tau / height >= y_plus:
             return j
     return 0
 
@@ -124,6 +139,8 @@ class Operators:
         self.Tm = sp.cheb_at_minus1(N)
         self.dTp = self.Tp @ self.D      # T_n'(+1)
         self.dTm = self.Tm @ self.D      # T_n'(-1)
+        self.d2Tp = self.Tp @ self.D2    # T_n''(+1)
+        self.free_slip = p.top_bc == 1
         self.wint = sp.cheb_integral(N)
         kx, kz, kept = sp.wavenumbers(p.nx, p.nz, p.lx, p.lz)
         self.kx = kx[None, :, None]          # [1, nxh, 1]
@@ -132,7 +149,7 @@ class Operators:
         self.k2 = self.kx ** 2 + self.kz ** 2
         self.mx = 3 * p.nx // 2
         self.mz = 3 * p.nz // 2
-        self.js = sensing_node(N, p.re_tau, p.y_sense_plus)
+        self.js = sensing_node(N, p.re_tau, p.y_sense_plus, p.height)
 
     # coefficient-space derivative along the last axis
     def d(self, a):
@@ -276,10 +293,11 @@ def _solve_real(M, rhs):
 
 
 def tau_dirichlet(ops: Operators, lam: np.ndarray, r: np.ndarray,
-                  top: np.ndarray, bottom: np.ndarray) -> np.ndarray:
+                  top: np.ndarray, bottom: np.ndarray, top_neumann: bool = False) -> np.ndarray:
     """Solve ``(D^2 - lam) f = r`` (tau rows 0..N-2), ``f(+1) = top``, ``f(-1) = bottom``.
 
     ``lam[P]``, ``r[P, N+1]`` (complex), ``top/bottom[P]`` -> ``f[P, N+1]``.
+    With ``top_neumann`` the top row is ``Df(+1) = top`` (free slip).
     """
     N = ops.N
     P = lam.shape[0]
@@ -287,7 +305,7 @@ def tau_dirichlet(ops: Operators, lam: np.ndarray, r: np.ndarray,
     M[:, : N - 1, :] = ops.D2[None, : N - 1, :]
     idx = np.arange(N - 1)
     M[:, idx, idx] -= lam[:, None]
-    M[:, N - 1, :] = ops.Tp
+    M[:, N - 1, :] = ops.dTp if top_neumann else ops.Tp
     M[:, N, :] = ops.Tm
     b = np.zeros((P, N + 1), np.complex128)
     b[:, : N - 1] = r[:, : N - 1]
@@ -303,6 +321,9 @@ def coupled_v(ops: Operators, lam: np.ndarray, k2: np.ndarray, r: np.ndarray,
     Rows: tau rows of ``(D^2 - lam) phi = r``; tau rows of
     ``(D^2 - k^2) v - phi = 0``; ``v(+1) = 0``, ``v(-1) = vw``,
     ``Dv(+1) = 0``, ``Dv(-1) = 0``.  Returns v coefficients ``[P, N+1]``.
+    Free-slip top (``ops.free_slip``): ``D^2 v(+1) = 0`` replaces
+    ``Dv(+1) = 0`` (u, w free of shear there, and by continuity
+    ``D^2 v = -(i kx Du + i kz Dw) = 0``).
     """
     N = ops.N
     n1 = N + 1
@@ -319,7 +340,7 @@ def coupled_v(ops: Operators, lam: np.ndarray, k2: np.ndarray, r: np.ndarray,
     # wall rows
     M[:, 2 * N - 2, n1:] = ops.Tp
     M[:, 2 * N - 1, n1:] = ops.Tm
-    M[:, 2 * N, n1:] = ops.dTp
+    M[:, 2 * N, n1:] = ops.d2Tp if ops.free_slip else ops.dTp
     M[:, 2 * N + 1, n1:] = ops.dTm
     b = np.zeros((P, 2 * n1), np.complex128)
     b[:, : N - 1] = r[:, : N - 1]
@@ -333,7 +354,8 @@ def mean_cfr(ops: Operators, lam0: float, cforce: float, r: np.ndarray,
     """Mean streamwise profile at constant flow rate.
 
     Unknowns ``(U, f)``: tau rows of ``(D^2 - lam0) U + cforce f T_0 = r``,
-    ``U(+1) = U(-1) = 0`` and ``int_{-1}^{1} U dy = flux``.
+    ``U(+1) = U(-1) = 0`` and ``int_{-1}^{1} U dy = flux``.  Free-slip top:
+    ``DU(+1) = 0`` replaces ``U(+1) = 0``.
     Returns ``(U, f)``.
     """
     N = ops.N
@@ -342,7 +364,7 @@ def mean_cfr(ops: Operators, lam0: float, cforce: float, r: np.ndarray,
     M[: N - 1, :n1] = ops.D2[: N - 1, :]
     M[np.arange(N - 1), np.arange(N - 1)] -= lam0
     M[0, n1] = cforce
-    M[N - 1, :n1] = ops.Tp
+    M[N - 1, :n1] = ops.dTp if ops.free_slip else ops.Tp
     M[N, :n1] = ops.Tm
     M[N + 1, :n1] = ops.wint
     b = np.zeros(n1 + 1)
@@ -353,12 +375,13 @@ def mean_cfr(ops: Operators, lam0: float, cforce: float, r: np.ndarray,
 
 
 def mean_dirichlet(ops: Operators, lam0: float, r: np.ndarray) -> np.ndarray:
-    """Mean spanwise profile: tau rows of ``(D^2 - lam0) W = r``, ``W(+-1) = 0``."""
+    """Mean spanwise profile: tau rows of ``(D^2 - lam0) W = r``, ``W(+-1) = 0``
+    (``DW(+1) = 0`` under a free-slip top)."""
     N = ops.N
     M = np.zeros((N + 1, N + 1))
     M[: N - 1] = ops.D2[: N - 1]
     M[np.arange(N - 1), np.arange(N - 1)] -= lam0
-    M[N - 1] = ops.Tp
+    M[N - 1] = ops.dTp if ops.free_slip else ops.Tp
     M[N] = ops.Tm
     b = np.zeros(N + 1)
     b[: N - 1] = r[: N - 1]
@@ -398,7 +421,7 @@ def stage(st: dict, ops: Operators, k: int, vw: np.ndarray, prev: dict | None) -
     zero = np.zeros(lam.shape[0])
     g_new = np.zeros_like(g)
     v_new = np.zeros_like(v)
-    g_new[act] = tau_dirichlet(ops, lam, rg[act], zero, zero)
+    g_new[act] = tau_dirichlet(ops, lam, rg[act], zero, zero, top_neumann=ops.free_slip)
     v_new[act] = coupled_v(ops, lam, k2[..., 0][act], rphi[act], vw[act])
 
     # mean flow
