@@ -230,6 +230,26 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def cpu_model() -> str:
+    """Host CPU model for the oracle timing (lscpu, else /proc/cpuinfo, else the machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
 def oracle_sample(budget_s: float, max_steps: int, workload: str = DEFAULT_WORKLOAD):
     """Time the FP64 oracle on one environment of the workload: whole
     environment steps until the budget is spent."""
@@ -282,7 +302,7 @@ def run_reference(args, rank: int, world: int):
         "steps": len(times), "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": name, "parallelism": "replicas"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "cpu": cpu_model(), "kind": "oracle",
                          "sample": f"{len(times)} whole environment steps of one environment of the workload "
                                    f"(budget {budget:.0f} s)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -571,7 +591,8 @@ def main():
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         times = oracle_sample(float(os.environ.get("CH_CPU_BASELINE_S", "20")), 1000, args.workload)
-        cpu = {"value": len(times) / sum(times), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+        cpu = {"value": len(times) / sum(times), "unit": UNIT, "cores": os.cpu_count(), "cpu": cpu_model(),
+               "kind": "oracle",
                "sample": f"{len(times)} whole environment steps of one environment of the workload "
                          "(about 20 s of CPU work)"}
 

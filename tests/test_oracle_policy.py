@@ -69,3 +69,12 @@ def test_weight_counts_agree_with_the_binding():
         assert native.policy_weight_count(native.policy(wz, wx, hidden)) == policy.weight_count(wz, wx, hidden)
     with pytest.raises(ValueError):
         policy.unpack(np.zeros(5), 1, 1, ())
+
+
+def test_bench_policy_weights_fit_the_layout():
+    import bench
+    for name, (wz, wx, hidden, tanh_out, seed) in bench.POLICIES.items():
+        w = bench.policy_weights(wz, wx, hidden, seed)
+        assert w.size == policy.weight_count(wz, wx, hidden)
+        assert np.array_equal(w, bench.policy_weights(wz, wx, hidden, seed))  # seeded
+        assert bench.WORKLOADS[name][0]["control"] == 2
