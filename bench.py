@@ -250,6 +250,21 @@ def cpu_model() -> str:
     return platform.machine()
 
 
+def oracle_single_thread(budget_s: float, workload: str) -> dict | None:
+    """The oracle sample in a fresh process with one BLAS/OpenMP thread."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import json, bench; t = bench.oracle_sample(%r, 1000, %r); "
+            "print(json.dumps({'steps': len(t), 'seconds': sum(t)}))" % (budget_s, workload))
+    try:
+        out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                             timeout=budget_s * 4 + 120)
+        r = json.loads(out.stdout.strip().splitlines()[-1])
+    except (OSError, subprocess.SubprocessError, ValueError, IndexError):
+        return None
+    return {"value": r["steps"] / r["seconds"], "cores": 1,
+            "sample": f"{r['steps']} whole environment steps, one BLAS/OpenMP thread"}
+
+
 def oracle_sample(budget_s: float, max_steps: int, workload: str = DEFAULT_WORKLOAD):
     """Time the FP64 oracle on one environment of the workload: whole
     environment steps until the budget is spent."""
@@ -594,7 +609,9 @@ def main():
         cpu = {"value": len(times) / sum(times), "unit": UNIT, "cores": os.cpu_count(), "cpu": cpu_model(),
                "kind": "oracle",
                "sample": f"{len(times)} whole environment steps of one environment of the workload "
-                         "(about 20 s of CPU work)"}
+                         "(about 20 s of CPU work)",
+               "single_thread": oracle_single_thread(float(os.environ.get("CH_CPU_BASELINE_1T_S", "10")),
+                                                     args.workload)}
 
     srt = sorted(step_ms)
     step_bytes = sum(v * 3 for v in kernel_bytes(nx, ny, nz, B, 16 if prec == 0 else 8).values())
