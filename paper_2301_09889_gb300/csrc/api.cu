@@ -788,7 +788,12 @@ int run_step(ch_env* env, const double* d_action, double* d_out, const int* d_ac
   const int B = env->B;
   if (env->prm.control == 2 && !env->pol_set) return CH_ERR_STATE;
   if (env->prof) {
-    RC(launch_step(env, d_action, d_out, d_active));
+    // the action goes through the internal buffer as in the captured graph,
+    // so env_get_action reports it in both modes
+    const size_t plane = (size_t)env->g.nz * env->g.nx;
+    if (env->prm.control == 0 && d_action != env->d_act)
+      CK(cudaMemcpyAsync(env->d_act, d_action, B * plane * sizeof(double), cudaMemcpyDeviceToDevice, env->stream));
+    RC(launch_step(env, env->d_act, d_out, d_active));
   } else {
     cudaStream_t st = env->stream;
     const int gi = d_active ? 1 : 0;

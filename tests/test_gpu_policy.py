@@ -129,3 +129,28 @@ def test_policy_errors(native_gpu):
     finally:
         native.env_destroy(ext)
         native.env_destroy(pol)
+
+
+def test_get_action_reports_a_device_action_in_both_launch_modes(native_gpu):
+    """env_get_action returns the caller's action after env_step_device, whether
+    the step is replayed from the captured graph or launched kernel by kernel."""
+    import torch
+
+    import seeded_inputs as si
+    native = native_gpu
+    B = 2
+    acts = np.stack([si.wall_action(16, 16, 500 + e, 0.5 * 180 / 2800) for e in range(B)])
+    d_act = torch.from_numpy(acts).to("cuda")
+    d_out = torch.zeros(B * (2 * 16 * 16 + 2), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    for profile in (False, True):
+        env = native.env_create(native.params(**MINIMAL, batch=B))
+        try:
+            native.env_profile(env, profile)
+            native.env_reset(env, 3, 0.1, 4)
+            native.env_step_device(env, d_act.data_ptr(), d_out.data_ptr())
+            got = np.zeros((B, 16, 16))
+            native.env_get_action(env, got)
+            assert np.array_equal(got, acts), profile
+        finally:
+            native.env_destroy(env)
