@@ -229,6 +229,11 @@ typedef struct ch_policy {
  * a control-2 handle without a policy returns CH_ERR_STATE. */
 int env_set_policy(ch_env_t* env, const ch_policy_t* pol, const double* weights, size_t n_weights);
 
+/* STATE without a step (Sec. 3.3): u and v on the sensing plane of the
+ * current flow, obs [B][2][nz][nx] (host), the same values env_step returns
+ * after a step.  Synchronises the stream.  Errors: CH_ERR_ARG, CH_ERR_CUDA. */
+int env_observe(ch_env_t* env, double* obs);
+
 /* The wall action [B][nz][nx] of the last step before clipping and mean
  * removal: the caller's (control 0) or the policy's (control 2), host buffer.
  * Synchronises the stream.  Errors: CH_ERR_ARG, CH_ERR_STATE (control 1),

@@ -1114,6 +1114,22 @@ int env_set_policy(ch_env_t* env, const ch_policy_t* pol, const double* weights,
   return CH_OK;
 }
 
+int env_observe(ch_env_t* env, double* obs) {
+  if (!env || !obs) return CH_ERR_ARG;
+  const Grid& g = env->g;
+  const size_t plane = (size_t)g.nz * g.nx;
+  cudaStream_t st = env->stream;
+  // the same kernels and buffers as the end of a step: the sensing-plane
+  // spectra, then the observation planes into the output rows
+  CK(launch_sense(g, env->B, env->pb, env->tab, env->js, env->prm.alpha, 0, st));
+  CK(launch_obs(g, env->B, env->pb.planes, env->tab, env->d_out, env->out_stride, nullptr, st));
+  CK(cudaMemcpyAsync(env->h_out, env->d_out, env->B * env->out_stride * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (int b = 0; b < env->B; ++b)
+    std::memcpy(obs + (size_t)b * 2 * plane, env->h_out + (size_t)b * env->out_stride, 2 * plane * sizeof(double));
+  return CH_OK;
+}
+
 int env_get_action(ch_env_t* env, double* action) {
   if (!env || !action) return CH_ERR_ARG;
   if (env->prm.control == 1) return CH_ERR_STATE;

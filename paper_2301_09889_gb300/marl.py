@@ -153,8 +153,10 @@ class ChannelMARL:
         return np.ascontiguousarray(w.transpose(0, 2, 3, 1, 4, 5))
 
     def reset_arrays(self, seed: int | None = None, amplitude: float = 0.1, kmax: int = 4) -> np.ndarray:
-        """Restore the initial condition (or seed a new one) and return the
-        windows of the sensing plane after one interval without actuation."""
+        """Restore the initial condition (or seed a new one, which then becomes
+        the stored one) and return the windows of its sensing plane (STATE:
+        no step is taken).  The restored state carries its wall action, zero
+        for a seeded one, from which the first interval ramps."""
         self._require_open()
         if seed is None:
             for b in range(self.B):
@@ -163,8 +165,9 @@ class ChannelMARL:
             self._nat.env_reset(self._env, seed, amplitude, kmax)
             self._init = [self._nat.env_get_state(self._env, b) for b in range(self.B)]
         self._action[...] = 0.0
-        self.evolve()
+        self._nat.env_observe(self._env, self._plane)
         self._cycles = 0
+        self._diverged = False
         return self.observe_arrays()
 
     def step_arrays(self, action) -> tuple[np.ndarray, np.ndarray, np.ndarray, bool, bool]:

@@ -33,7 +33,7 @@ EXPORTS = (
     "ch_strerror", "ch_seed_state", "ch_state_bytes", "ch_nonlinear", "ch_tau_helmholtz",
     "env_profile", "env_profile_read", "ch_tau_helmholtz_noalloc", "env_set_tiles",
     "srv_create", "srv_admit", "srv_evict", "srv_submit", "srv_poll", "srv_wait", "srv_get_state",
-    "srv_set_state", "srv_stats", "srv_destroy", "env_set_policy", "env_get_action",
+    "srv_set_state", "srv_stats", "srv_destroy", "env_set_policy", "env_get_action", "env_observe",
 )
 CH_PENDING = 1
 
@@ -144,6 +144,7 @@ def load() -> ctypes.CDLL:
         "env_profile_read": (ctypes.c_int, [vp, ctypes.c_int, P(ctypes.c_double), P(ctypes.c_int)]),
         "env_set_policy": (ctypes.c_int, [vp, P(ChPolicy), vp, ctypes.c_size_t]),
         "env_get_action": (ctypes.c_int, [vp, dp]),
+        "env_observe": (ctypes.c_int, [vp, dp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -260,6 +261,11 @@ def policy_weight_count(pol: ChPolicy) -> int:
 def env_set_policy(env, pol: ChPolicy, weights: np.ndarray):
     w = np.ascontiguousarray(weights, dtype=np.float64).ravel()
     _check(load().env_set_policy(env, ctypes.byref(pol), w.ctypes.data, w.size), "env_set_policy")
+
+
+def env_observe(env, obs: np.ndarray):
+    """Sensing plane [B][2][nz][nx] of the current flow into `obs` (float64)."""
+    _check(load().env_observe(env, _dptr(obs)), "env_observe")
 
 
 def env_get_action(env, action: np.ndarray):

@@ -1,7 +1,8 @@
 """The multi-agent interface (Sec. 3.2-3.3) on the GPU: it adds nothing to the
 physics, so its observations and rewards are bit-identical to the C ABI
 driven by the same requests, every episode starts from the same flow, and the
-per-agent dictionary and the array forms agree."""
+per-agent dictionary and the array forms agree.  env_observe (STATE without a
+step) returns the plane a step returns."""
 
 import numpy as np
 import pytest
@@ -26,7 +27,7 @@ def test_wrapper_matches_the_c_abi(native_gpu):
         obs = np.zeros((B, 2, 16, 16))
         tau, rew = np.zeros(B), np.zeros(B)
         w = env.reset_arrays()
-        assert native.env_step(raw, np.zeros((B, 16, 16)), obs, tau, rew) == 0
+        native.env_observe(raw, obs)
         assert np.array_equal(env.state(), obs)
         assert np.array_equal(w[:, :, :, :, 1, 1], obs.transpose(0, 2, 3, 1))
         for _ in range(3):
@@ -34,6 +35,10 @@ def test_wrapper_matches_the_c_abi(native_gpu):
             w, r, ws, term, trunc = env.step_arrays(act)
             assert native.env_step(raw, act, obs, tau, rew) == 0
             assert np.array_equal(env.state(), obs) and np.array_equal(r, rew) and np.array_equal(ws, tau)
+            # STATE without a step returns the same plane the step returned
+            again = np.zeros_like(obs)
+            native.env_observe(raw, again)
+            assert np.array_equal(again, obs)
             assert not term and not trunc
             assert np.all(np.isfinite(w))
     finally:

@@ -46,13 +46,18 @@ class FakeBinding:
         self.calls.append(("set_state", b, float(buf[0])))
         self.state[b] = np.array(buf, dtype=float)
 
-    def env_step(self, env, action, obs, wall_shear, reward):
-        self.step += 1
-        self.actions.append(np.array(action))
+    def env_observe(self, env, obs):
+        self.calls.append("observe")
         B, _, nz, nx = obs.shape
         b, c, iz, ix = np.meshgrid(np.arange(B), np.arange(2), np.arange(nz), np.arange(nx), indexing="ij")
         obs[...] = 1e4 * self.step + 1000 * b + 100 * c + 10 * iz + ix
-        reward[...] = 0.5 - 0.01 * self.step - 0.1 * np.arange(B)
+
+    def env_step(self, env, action, obs, wall_shear, reward):
+        self.step += 1
+        self.actions.append(np.array(action))
+        self.env_observe(env, obs)
+        self.calls.pop()
+        reward[...] = 0.5 - 0.01 * self.step - 0.1 * np.arange(obs.shape[0])
         wall_shear[...] = 1.0 - reward
         if self.diverge_at == self.step:
             wall_shear[0] = np.nan
@@ -103,7 +108,8 @@ def test_dict_actions_land_on_their_grid_points_and_reward_is_shared():
     want[0, 3, 4], want[1, 15, 0], want[1, 0, 15] = 0.01, -0.02, 0.005
     assert np.array_equal(a, want)
     assert len(set(r[n] for n in r if n.startswith("env0"))) == 1
-    assert r["env0_agent_0_0"] == pytest.approx(0.5 - 0.02) and r["env1_agent_9_9"] == pytest.approx(0.5 - 0.02 - 0.1)
+    # reset takes no step, so this is step 1
+    assert r["env0_agent_0_0"] == pytest.approx(0.5 - 0.01) and r["env1_agent_9_9"] == pytest.approx(0.5 - 0.01 - 0.1)
     assert info["env1_agent_2_2"]["wall_shear"] == pytest.approx(1 - r["env1_agent_2_2"])
     assert not any(term.values()) and not any(trunc.values())
     assert np.array_equal(o["env1_agent_5_6"], env.observe_arrays()[1, 5, 6])
@@ -122,7 +128,7 @@ def test_single_environment_names_and_truncation():
 
 
 def test_divergence_terminates_every_agent():
-    env, _ = make(diverge_at=3)
+    env, _ = make(diverge_at=2)
     env.reset()
     _, _, term, _, _ = env.step({})
     assert not any(term.values())
@@ -141,8 +147,11 @@ def test_reset_restores_the_same_initial_condition_unless_reseeded():
     fake.calls.clear()
     env.reset()
     assert [c for c in fake.calls if c[0] == "set_state"] == [("set_state", 0, 11.0), ("set_state", 1, 12.0)]
-    # every reset starts with one unactuated interval
-    assert np.array_equal(fake.actions[-1], np.zeros((2, 16, 16)))
+    # a reset observes the restored flow (STATE) without stepping it
+    n_steps = len(fake.actions)
+    obs = env.reset_arrays()
+    assert len(fake.actions) == n_steps and fake.calls[-1] == "observe"
+    assert obs[0, 0, 0, 0, 0, 0] == 1e4 * fake.step
 
 
 def test_requests_map_and_termn_releases():
