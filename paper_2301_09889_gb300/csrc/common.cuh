@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <cstddef>
 #include <cstdint>
+#include <mutex>
 #include <utility>
 
 namespace chdns {
@@ -55,6 +56,34 @@ template <> __device__ __forceinline__ float2 czero<float2>() { return make_floa
 __device__ __forceinline__ void pdl_wait_then_release() {
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// A kernel's dynamic shared-memory limit (and the non-portable cluster-size
+// opt-in) as configured so far.  raise_smem_limit only ever raises it, under
+// one lock for every kernel, so handles of different sizes driven from
+// several host threads never leave a kernel below a size another one needs.
+struct SmemLimit {
+  size_t bytes = 0;
+  bool nonportable = false;
+};
+inline std::mutex& kernel_attr_mutex() {
+  static std::mutex m;
+  return m;
+}
+template <typename K>
+inline cudaError_t raise_smem_limit(K kernel, SmemLimit* lim, size_t smem, bool nonportable_cluster = false) {
+  std::lock_guard<std::mutex> lock(kernel_attr_mutex());
+  if (smem > lim->bytes) {
+    const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    lim->bytes = smem;
+  }
+  if (nonportable_cluster && !lim->nonportable) {
+    const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    lim->nonportable = true;
+  }
+  return cudaSuccess;
 }
 
 // launch with the programmatic-serialisation attribute (see above)

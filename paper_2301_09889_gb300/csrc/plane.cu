@@ -326,17 +326,10 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 && NT == 256 && MX == LZ) 
 
 template <typename K, typename R>
 static cudaError_t launch_with(K kernel, const PlaneArgs<R>& a, int B, size_t smem, cudaStream_t st,
-                               size_t* configured, int nt = 256) {
-  if (smem > *configured) {
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    if (a.S > 8) {
-      // clusters above 8 CTAs are a non-portable opt-in
-      e = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-      if (e != cudaSuccess) return e;
-    }
-    *configured = smem;
-  }
+                               SmemLimit* lim, int nt = 256) {
+  // clusters above 8 CTAs are a non-portable opt-in
+  const cudaError_t e = raise_smem_limit(kernel, lim, smem, a.S > 8);
+  if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(a.S, a.ny, B);
   cfg.blockDim = dim3(nt, 1, 1);
@@ -361,11 +354,18 @@ static cudaError_t launch_with(K kernel, const PlaneArgs<R>& a, int B, size_t sm
   return cudaLaunchKernelEx(&cfg, kernel, a);
 }
 
+// limit of the runtime-size kernel, shared by its launches and the occupancy query
+template <typename R>
+static SmemLimit& generic_limit() {
+  static SmemLimit lim;
+  return lim;
+}
+
 // compile-time instantiations: (MX, LZ, NXH, NP) of the grids in use
 #define CH_PLANE_CT_NT(MX_, LZ_, NXH_, NP_, NT_)                                                      \
   if (a.mx == MX_ && a.Lz == LZ_ && a.nxh == NXH_ && a.NP == NP_ && a.S == MX_ / LZ_) {             \
-    static size_t cfg_ = 0;                                                                           \
-    return launch_with(plane_kernel_ct<R, MX_, LZ_, NXH_, NP_, NT_>, a, B, smem, st, &cfg_, NT_);     \
+    static SmemLimit lim_;                                                                            \
+    return launch_with(plane_kernel_ct<R, MX_, LZ_, NXH_, NP_, NT_>, a, B, smem, st, &lim_, NT_);     \
   }
 #define CH_PLANE_CT(MX_, LZ_, NXH_, NP_) CH_PLANE_CT_NT(MX_, LZ_, NXH_, NP_, 256)
 
@@ -385,8 +385,7 @@ cudaError_t launch_plane(const PlaneArgs<R>& a, int B, size_t smem, cudaStream_t
     CH_PLANE_CT_NT(192, 48, 64, 8, 1024)
     CH_PLANE_CT_NT(384, 24, 128, 4, 1024)
   }
-  static size_t cfg_generic = 0;
-  return launch_with(plane_kernel<R>, a, B, smem, st, &cfg_generic);
+  return launch_with(plane_kernel<R>, a, B, smem, st, &generic_limit<R>());
 }
 
 // Clusters of a.S CTAs with `smem` bytes each that the device can hold at
@@ -394,12 +393,8 @@ cudaError_t launch_plane(const PlaneArgs<R>& a, int B, size_t smem, cudaStream_t
 template <typename R>
 cudaError_t plane_max_clusters(const PlaneArgs<R>& a, size_t smem, int* clusters) {
   *clusters = 0;
-  cudaError_t e = cudaFuncSetAttribute(plane_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const cudaError_t e = raise_smem_limit(plane_kernel<R>, &generic_limit<R>(), smem, a.S > 8);
   if (e != cudaSuccess) return e;
-  if (a.S > 8) {
-    e = cudaFuncSetAttribute(plane_kernel<R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e != cudaSuccess) return e;
-  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(a.S, a.ny, 1);
   cfg.blockDim = dim3(256, 1, 1);

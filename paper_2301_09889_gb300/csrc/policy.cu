@@ -165,16 +165,11 @@ cudaError_t launch_policy(int nx, int nz, int B, const PolicyDesc& d, const floa
   const long agents = (long)B * nz * nx;
   constexpr int kThreads = 256;
   const size_t smem = (size_t)d.n_weights * sizeof(float);
-  static bool configured = false;
-  if (!configured) {
-    const int bytes = (int)(kPolicyMaxWeights * sizeof(float));
-    cudaError_t e = cudaFuncSetAttribute(policy_kernel<kPolicyMaxWidth>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(policy_kernel_64x64, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  static SmemLimit lim_generic, lim_64x64;
+  const size_t bytes = kPolicyMaxWeights * sizeof(float);
+  cudaError_t e = raise_smem_limit(policy_kernel<kPolicyMaxWidth>, &lim_generic, bytes);
+  if (e == cudaSuccess) e = raise_smem_limit(policy_kernel_64x64, &lim_64x64, bytes);
+  if (e != cudaSuccess) return e;
   const unsigned blocks = (unsigned)((agents + kThreads - 1) / kThreads);
   if (d.n_hidden == 2 && d.h1 == 64 && d.h2 == 64) {
     policy_kernel_64x64<<<blocks, kThreads, smem, st>>>(nx, nz, B, d, w, plane, act, u_tau, active);

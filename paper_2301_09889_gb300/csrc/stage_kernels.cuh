@@ -1166,45 +1166,33 @@ __global__ void __launch_bounds__(64) stage_post_batched_kernel(Grid g, int B, P
 template <typename RN, int MH>
 cudaError_t pre_mh(const Grid& g, int B, const PencilBufs& pb, const DevTables& t,
                           typename cpx<RN>::T* q, int ppc, size_t smem, cudaStream_t st) {
-  static size_t configured = 0;
-  if (smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(stage_pre_kernel<RN, MH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    configured = smem;
-  }
-  return launch_pdl_if<sizeof(RN) == 4>(stage_pre_kernel<RN, MH>, dim3((g.P + ppc - 1) / ppc, B), dim3(128), smem, st, g, B, pb, t, q,
-                    ppc);
+  static SmemLimit lim;
+  const cudaError_t e = raise_smem_limit(stage_pre_kernel<RN, MH>, &lim, smem);
+  if (e != cudaSuccess) return e;
+  return launch_pdl_if<sizeof(RN) == 4>(stage_pre_kernel<RN, MH>, dim3((g.P + ppc - 1) / ppc, B), dim3(128), smem,
+                                        st, g, B, pb, t, q, ppc);
 }
 
 template <typename RN, int MH>
 cudaError_t post_mh(const Grid& g, int B, const PencilBufs& pb, const DevTables& t,
                            const typename cpx<RN>::T* h, const StageCoef& sc, int ppc, size_t smem,
                            cudaStream_t st) {
-  static size_t configured = 0;
-  if (smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(stage_post_kernel<RN, MH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    configured = smem;
-  }
-  return launch_pdl_if<sizeof(RN) == 4>(stage_post_kernel<RN, MH>, dim3((g.P + ppc - 1) / ppc, B), dim3(8 * ppc), smem, st, g, B, pb,
-                    t, h, sc, ppc);
+  static SmemLimit lim;
+  const cudaError_t e = raise_smem_limit(stage_post_kernel<RN, MH>, &lim, smem);
+  if (e != cudaSuccess) return e;
+  return launch_pdl_if<sizeof(RN) == 4>(stage_post_kernel<RN, MH>, dim3((g.P + ppc - 1) / ppc, B), dim3(8 * ppc),
+                                        smem, st, g, B, pb, t, h, sc, ppc);
 }
 
 template <typename RN, int MH>
 cudaError_t post_batched_mh(const Grid& g, int B, const PencilBufs& pb, const DevTables& t,
                                    const typename cpx<RN>::T* h, const StageCoef& sc, int ppc, size_t smem,
                                    cudaStream_t st) {
-  static size_t configured = 0;
-  if (smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(stage_post_batched_kernel<RN, MH>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured = smem;
-  }
-  return launch_pdl_if<sizeof(RN) == 4>(stage_post_batched_kernel<RN, MH>, dim3((g.P + ppc - 1) / ppc, B), dim3(4 * ppc), smem, st, g,
-                    B, pb, t, h, sc, ppc);
+  static SmemLimit lim;
+  const cudaError_t e = raise_smem_limit(stage_post_batched_kernel<RN, MH>, &lim, smem);
+  if (e != cudaSuccess) return e;
+  return launch_pdl_if<sizeof(RN) == 4>(stage_post_batched_kernel<RN, MH>, dim3((g.P + ppc - 1) / ppc, B),
+                                        dim3(4 * ppc), smem, st, g, B, pb, t, h, sc, ppc);
 }
 
 }  // namespace chdns
