@@ -721,7 +721,10 @@ int time_launches(cudaStream_t st, int reps, F&& launch, float* ms) {
 
 // Time the candidate shapes of both stage kernels on this handle's buffers,
 // before its initial state is written (the kernels run on zeroed fields), and
-// keep the fastest of each.
+// keep the fastest of each.  Repeated launches of one kernel may overlap (an
+// FP32-node stage kernel starts its prologue while the previous launch
+// drains); the fields they touch are scratch here and are all rewritten when
+// the initial state is set.
 int autotune_tiles(ch_env* env, int smem_max) {
   const auto t0 = std::chrono::steady_clock::now();
   const Grid& g = env->g;
