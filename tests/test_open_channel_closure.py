@@ -6,7 +6,7 @@ n >= 2 the tau rows, integrated twice, are quasi-tridiagonal in the
 coefficients of one parity, so elimination leaves each parity affine in its
 lowest coefficient, f = P + x Q.  Under two no-slip walls each parity is
 closed by its own wall sum.  Under a free-slip top the wall rows couple the
-parities, and these tests pin the two closures that replace the per-parity
+parities, and these tests pin the closures that replace the per-parity
 ones (Sec. 3.1, the open channel):
 
 * omega_y: f(-1) = sum_e f - sum_o f and Df(+1) = sum_e n^2 f + sum_o n^2 f
@@ -14,7 +14,9 @@ ones (Sec. 3.1, the open channel):
 * v: phi = D^2 v - k^2 v has both wall values unknown; with phi_1, phi_2 the
   responses to unit values at y = +1 and y = -1 (and v_1, v_2 their v), two
   influence coefficients fixed by D^2 v(+1) = 0 and Dv(-1) = 0 reproduce the
-  dense system's rows exactly.
+  dense system's rows exactly;
+* mean U at constant flow rate: U(-1) = 0, DU(+1) = 0 and the flux row give a
+  3 x 3 system in (x_even, x_odd, forcing).
 """
 
 import numpy as np
@@ -131,3 +133,34 @@ def test_two_influence_coefficients_close_the_free_slip_v_problem(ny):
         v = v_p + c1 * v_1 + c2 * v_2
         want = channel.coupled_v(ops, L, K, r[None], np.array([vw]))[0]
         assert np.max(np.abs(v - want)) <= 1e-10 * np.max(np.abs(want)), (k2, lam)
+
+
+@pytest.mark.parametrize("ny", [17, 65])
+def test_three_unknown_closure_for_the_mean_flow_at_constant_flow_rate(ny):
+    """Mean U under a free-slip top: the parity-split parts, the response to the
+    forcing (it enters the n = 0 tau row, so only the even parity), and the
+    3 x 3 closure U(-1) = 0, DU(+1) = 0, int U dy = flux in (x_even, x_odd, f)."""
+    ops = _ops(ny)
+    N = ops.N
+    rng = np.random.default_rng(ny + 3)
+    w = ops.wint                                    # int_{-1}^{1} T_n dy
+    for lam0, cforce in ((5.0, 3.0), (4.8e5, 2.2e6)):
+        r = rng.standard_normal(N + 1)
+        rF = np.zeros(N + 1)
+        rF[0] = -cforce                             # the forcing term moved to the right-hand side
+        (Pe, Qe, ne), (Po, Qo, no) = _split_solve(N, lam0, r, 0), _split_solve(N, lam0, r, 1)
+        PF = _split_solve(N, lam0, rF, 0)[0]
+        S = lambda v: v.sum()
+        T = lambda v, n: (n * n * v).sum()
+        I = lambda v, n: (w[n] * v).sum()
+        A = np.array([[S(Qe), -S(Qo), S(PF)],
+                      [T(Qe, ne), T(Qo, no), T(PF, ne)],
+                      [I(Qe, ne), 0.0, I(PF, ne)]]).real
+        b = np.array([-S(Pe) + S(Po), -T(Pe, ne) - T(Po, no), 2.0 - I(Pe, ne)]).real
+        xe, xo, f = np.linalg.solve(A, b)
+        U = np.zeros(N + 1)
+        U[ne] = (Pe + f * PF + xe * Qe).real
+        U[no] = (Po + xo * Qo).real
+        want_U, want_f = channel.mean_cfr(ops, lam0, cforce, r)
+        assert np.max(np.abs(U - want_U)) <= 1e-11 * np.max(np.abs(want_U))
+        assert abs(f - want_f) <= 1e-10 * abs(want_f)
