@@ -243,7 +243,11 @@ int env_destroy(ch_env_t* env);
 const char* ch_strerror(int code);
 
 /* Host only (no GPU): write the env_reset initial state of one environment
- * into `buf` (same layout as env_get_state). */
+ * into `buf` (same layout as env_get_state).  With p->top_bc = 1 (free-slip
+ * top, not yet stepped by the library) the perturbation shapes are
+ * v ~ (1+y)^2 (1-y) (2-y) / 2 and omega_y ~ (1+y) (3-y) / 4 and the mean flow is
+ * the half-Poiseuille 1.5 (2s - s^2), s = (1+y)/2, which meet the free-slip
+ * conditions exactly. */
 int ch_seed_state(const ch_params_t* p, uint64_t seed, double amplitude, int kmax,
                   void* buf, size_t nbytes);
 

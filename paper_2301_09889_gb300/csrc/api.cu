@@ -471,8 +471,16 @@ void fill_seed_state(const ch_params_t* p, uint64_t seed, double amplitude, int 
     }
   }
   const double s = nexc ? amplitude / std::sqrt((double)nexc) : 0.0;
-  const double shape_v[5] = {0.375, 0.0, -0.5, 0.0, 0.125};
-  const double shape_g[3] = {0.5, 0.0, -0.5};
+  // wall-normal shapes (Chebyshev coefficients): closed channel (1 - y^2)^2 and
+  // 1 - y^2; open channel (free-slip top) (1+y)^2 (1-y) (2-y) / 2 and
+  // (1+y) (3-y) / 4
+  const bool open = p->top_bc == 1;
+  const double shape_v_closed[5] = {0.375, 0.0, -0.5, 0.0, 0.125};
+  const double shape_g_closed[3] = {0.5, 0.0, -0.5};
+  const double shape_v_open[5] = {0.4375, 0.125, -0.5, -0.125, 0.0625};
+  const double shape_g_open[3] = {0.625, 0.5, -0.125};
+  const double* shape_v = open ? shape_v_open : shape_v_closed;
+  const double* shape_g = open ? shape_g_open : shape_g_closed;
   SplitMix64 rng{seed};
   for (const Mode& md : modes) {
     double a, b, c, d;
@@ -481,7 +489,8 @@ void fill_seed_state(const ch_params_t* p, uint64_t seed, double amplitude, int 
     const double cvr = s * a, cvi = s * b, cgr = s * c, cgi = s * d;
     const int m = md.row < nz / 2 ? md.row : md.row - nz;
     const int mrow = (-m + nz) % nz;
-    for (int n = 0; n < 5; n += 2) {
+    for (int n = 0; n < 5; ++n) {
+      if (shape_v[n] == 0.0) continue;
       const size_t o = ((size_t)n * P + md.row * nxh + md.i) * 2;
       v[o] = cvr * shape_v[n];
       v[o + 1] = cvi * shape_v[n];
@@ -491,7 +500,8 @@ void fill_seed_state(const ch_params_t* p, uint64_t seed, double amplitude, int 
         v[o2 + 1] = -v[o + 1];
       }
     }
-    for (int n = 0; n < 3; n += 2) {
+    for (int n = 0; n < 3; ++n) {
+      if (shape_g[n] == 0.0) continue;
       const size_t o = ((size_t)n * P + md.row * nxh + md.i) * 2;
       g[o] = cgr * shape_g[n];
       g[o + 1] = cgi * shape_g[n];
@@ -502,8 +512,14 @@ void fill_seed_state(const ch_params_t* p, uint64_t seed, double amplitude, int 
       }
     }
   }
-  U[0] = 0.75;
-  U[2] = -0.75;
+  if (open) {  // half-Poiseuille 1.5 (2 s - s^2), s = (1 + y) / 2
+    U[0] = 0.9375;
+    U[1] = 0.75;
+    U[2] = -0.1875;
+  } else {
+    U[0] = 0.75;
+    U[2] = -0.75;
+  }
   (void)W;
   tail[0] = tail[1] = 0.0;
 }

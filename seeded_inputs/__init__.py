@@ -34,6 +34,12 @@ with its y-derivative at both walls and ``g`` vanishes at both walls.  On the
 ``kx = 0`` column only ``m > 0`` is drawn; ``m < 0`` takes the complex
 conjugate so that the physical field is real.  The mean flow is laminar
 Poiseuille ``U = 1.5 (1 - y^2)`` (bulk velocity 1), ``W = 0``.
+
+Open channel (``top_bc = 1``: free slip at ``y = +1``): the same draws with
+the shapes ``v: (1 + y)^2 (1 - y) (2 - y) / 2`` (v = Dv = 0 at ``y = -1``,
+v = D^2 v = 0 at ``y = +1``) and ``g: (1 + y) (3 - y) / 4`` (g = 0 at
+``y = -1``, Dg = 0 at ``y = +1``), and the half-Poiseuille mean flow
+``U = 1.5 (2 s - s^2)``, ``s = (1 + y) / 2`` (bulk velocity 1 over the height).
 """
 
 from __future__ import annotations
@@ -50,6 +56,14 @@ _MASK64 = (1 << 64) - 1
 SHAPE_G = {0: 0.5, 2: -0.5}
 SHAPE_V = {0: 0.375, 2: -0.5, 4: 0.125}
 POISEUILLE_U = {0: 0.75, 2: -0.75}
+# open channel:
+#   (1 + y)^2 (1 - y) (2 - y) / 2 = (2 + y - 3 y^2 - y^3 + y^4) / 2
+#                                 = 7/16 T0 + 1/8 T1 - 1/2 T2 - 1/8 T3 + 1/16 T4
+#   (1 + y) (3 - y) / 4           = 5/8 T0 + 1/2 T1 - 1/8 T2
+#   1.5 (2 s - s^2), s = (1+y)/2  = 15/16 T0 + 3/4 T1 - 3/16 T2
+SHAPE_V_OPEN = {0: 0.4375, 1: 0.125, 2: -0.5, 3: -0.125, 4: 0.0625}
+SHAPE_G_OPEN = {0: 0.625, 1: 0.5, 2: -0.125}
+HALF_POISEUILLE_U = {0: 0.9375, 1: 0.75, 2: -0.1875}
 
 
 class SplitMix64:
@@ -107,8 +121,9 @@ def excited_modes(nx: int, nz: int, kmax: int) -> list[tuple[int, int]]:
 
 
 def perturbed_poiseuille(nx: int, ny: int, nz: int, seed: int,
-                         amplitude: float = 0.1, kmax: int = 4) -> dict:
-    """Laminar Poiseuille flow plus the seeded perturbation described above."""
+                         amplitude: float = 0.1, kmax: int = 4, top_bc: int = 0) -> dict:
+    """Laminar Poiseuille flow plus the seeded perturbation described above
+    (``top_bc = 1``: the open-channel shapes and the half-Poiseuille profile)."""
     if nx % 2 or nz % 2 or ny < 5:
         raise ValueError("nx, nz must be even and ny >= 5")
     nxh = nx // 2
@@ -119,20 +134,22 @@ def perturbed_poiseuille(nx: int, ny: int, nz: int, seed: int,
     n_exc = len(modes) + sum(1 for (r, i) in modes if i == 0)
     s = amplitude / math.sqrt(n_exc) if n_exc else 0.0
     kzi = kz_index(nz)
+    shape_v, shape_g, mean_u = ((SHAPE_V_OPEN, SHAPE_G_OPEN, HALF_POISEUILLE_U) if top_bc == 1 else
+                                (SHAPE_V, SHAPE_G, POISEUILLE_U))
     for (row, i) in modes:
         a, b, c, d = rng.normals(4)
         cv = s * complex(a, b)
         cg = s * complex(c, d)
-        for n, coef in SHAPE_V.items():
+        for n, coef in shape_v.items():
             v[n, row, i] = cv * coef
-        for n, coef in SHAPE_G.items():
+        for n, coef in shape_g.items():
             g[n, row, i] = cg * coef
         if i == 0:
             mrow = int(np.nonzero(kzi == -kzi[row])[0][0])
             v[:, mrow, 0] = np.conj(v[:, row, 0])
             g[:, mrow, 0] = np.conj(g[:, row, 0])
     U = np.zeros(ny)
-    for n, coef in POISEUILLE_U.items():
+    for n, coef in mean_u.items():
         U[n] = coef
     W = np.zeros(ny)
     return {"v": v, "g": g, "U": U, "W": W}

@@ -60,6 +60,15 @@ def test_seed_state_matches_python_generator(native, nx, ny, nz, seed, kmax):
     assert np.all(st["vw"] == 0) and st["t"] == 0 and st["steps"] == 0
 
 
+@pytest.mark.parametrize("nx,ny,nz,seed,kmax", [(16, 65, 16, 2, 4), (12, 33, 24, 9, 99)])
+def test_open_channel_seed_state_matches_python_generator(native, nx, ny, nz, seed, kmax):
+    p = native.params(nx=nx, ny=ny, nz=nz, top_bc=1)
+    st = native.unpack_state(native.ch_seed_state(p, seed, 0.2, kmax), nx, ny, nz)
+    ref = si.perturbed_poiseuille(nx, ny, nz, seed, 0.2, kmax, top_bc=1)
+    for k in ("v", "g", "U", "W"):
+        assert np.array_equal(st[k], ref[k]), k
+
+
 def test_host_argument_checks(native):
     p = native.params(nx=15)
     with pytest.raises(native.ChannelError):
