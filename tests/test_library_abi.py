@@ -73,3 +73,17 @@ def test_host_argument_checks(native):
     p = native.params(nx=15)
     with pytest.raises(native.ChannelError):
         native.ch_seed_state(p, 0, 0.1, 4)
+
+
+def test_env_create_rejects_unsupported_parameters_before_any_device_work(native):
+    """Parameter checks run before env_create touches the device, so they hold
+    on a machine without a GPU: the free-slip top (top_bc = 1) is refused until
+    the library steps it, and malformed grids or modes are argument errors."""
+    cases = [(dict(top_bc=1), native.CH_ERR_UNSUPPORTED), (dict(precision=2), native.CH_ERR_UNSUPPORTED),
+             (dict(control=3), native.CH_ERR_ARG), (dict(nx=15), native.CH_ERR_ARG),
+             (dict(ny=5), native.CH_ERR_ARG), (dict(steps_per_action=0), native.CH_ERR_ARG),
+             (dict(dt=0.0), native.CH_ERR_ARG)]
+    for kw, code in cases:
+        with pytest.raises(native.ChannelError) as e:
+            native.env_create(native.params(**kw))
+        assert e.value.code == code, kw
