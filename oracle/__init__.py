@@ -22,9 +22,11 @@ Fourier x Chebyshev basis (Sec. 3.1), the RK3 + Crank-Nicolson time scheme
 (Sec. 3.1), the wall blowing/suction action with its linear ramp and clip
 (Sec. 3.2), the sensing plane snapped up to a Chebyshev node (Sec. 3.2), the
 wall-shear reward (Sec. 3.2) and the opposition-control law (Sec. 4.1,
-equation for v_w).  Where it is silent the readings are those listed in the
-design notes (closed channel, SMR low-storage RK3 with alpha = beta, 3/2 rule,
-velocity-vorticity form with an influence-matrix equivalent coupled solve).
+equation for v_w).  Where it is silent this oracle takes these readings: a
+closed channel y in [-1, 1] with the action on the lower wall (an open channel
+with a free-slip top as the option top_bc = 1), the SMR low-storage RK3 with
+alpha = beta, the 3/2 rule, and the velocity-vorticity form with the v problem
+solved as one coupled dense system.
 """
 
 from . import spectral, channel, stability, policy  # noqa: F401

@@ -2,8 +2,8 @@
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 
-What is computed (paper Sec. 3.1 and Sec. 3.2, readings of the design notes)
----------------------------------------------------------------------------
+What is computed (paper Sec. 3.1 and Sec. 3.2, and the readings stated below)
+----------------------------------------------------------------------------
 Incompressible Navier-Stokes in a plane channel ``y in [-1, 1]`` (half height
 1, bulk velocity 1, ``nu = 1 / Re_b``) in rotational form,
 ``du/dt = H - grad p + nu lap u + f_x e_x`` with ``H = u x omega``.  The state
@@ -292,6 +292,39 @@ def _solve_real(M, rhs):
     return x[..., 0] + 1j * x[..., 1]
 
 
+# The dense systems of independent pencils are assembled and solved in chunks
+# of at most PENCIL_CHUNK pencils, so that the stacked (P, n, n) matrices of a
+# large grid (32768 pencils of 386 x 386 at 256 x 193 x 256) never exist at
+# once.  Each pencil's system and its LU solve are the same as in one batch.
+# The chunks are independent; `_pencil_starmap(func, tasks)` runs them
+# (serially by default; a caller may install a process pool's starmap with
+# set_pencil_starmap).
+PENCIL_CHUNK = 256
+
+
+def _serial_starmap(func, tasks):
+    return [func(*t) for t in tasks]
+
+
+_pencil_starmap = _serial_starmap
+
+
+def set_pencil_starmap(fn=None):
+    """Run the pencil chunks with ``fn(func, list_of_argument_tuples)``
+    (serially in this process if None)."""
+    global _pencil_starmap
+    _pencil_starmap = _serial_starmap if fn is None else fn
+
+
+def _chunked(func, fixed: tuple, *per_pencil):
+    """``func(*fixed, *chunk)`` over chunks of the per-pencil arrays, concatenated."""
+    P = per_pencil[0].shape[0]
+    if P == 0:
+        return func(*fixed, *per_pencil)
+    tasks = [fixed + tuple(a[i:i + PENCIL_CHUNK] for a in per_pencil) for i in range(0, P, PENCIL_CHUNK)]
+    return np.concatenate(_pencil_starmap(func, tasks), axis=0)
+
+
 def tau_dirichlet(ops: Operators, lam: np.ndarray, r: np.ndarray,
                   top: np.ndarray, bottom: np.ndarray, top_neumann: bool = False) -> np.ndarray:
     """Solve ``(D^2 - lam) f = r`` (tau rows 0..N-2), ``f(+1) = top``, ``f(-1) = bottom``.
@@ -299,14 +332,20 @@ def tau_dirichlet(ops: Operators, lam: np.ndarray, r: np.ndarray,
     ``lam[P]``, ``r[P, N+1]`` (complex), ``top/bottom[P]`` -> ``f[P, N+1]``.
     With ``top_neumann`` the top row is ``Df(+1) = top`` (free slip).
     """
-    N = ops.N
+    top_row = ops.dTp if top_neumann else ops.Tp
+    return _chunked(_tau_dirichlet_pencils, (ops.D2, top_row, ops.Tm), lam, r, top, bottom)
+
+
+def _tau_dirichlet_pencils(D2, top_row, bot_row, lam, r, top, bottom):
+    """Dense tau systems of ``tau_dirichlet`` for one set of pencils."""
+    N = D2.shape[0] - 1
     P = lam.shape[0]
     M = np.zeros((P, N + 1, N + 1))
-    M[:, : N - 1, :] = ops.D2[None, : N - 1, :]
+    M[:, : N - 1, :] = D2[None, : N - 1, :]
     idx = np.arange(N - 1)
     M[:, idx, idx] -= lam[:, None]
-    M[:, N - 1, :] = ops.dTp if top_neumann else ops.Tp
-    M[:, N, :] = ops.Tm
+    M[:, N - 1, :] = top_row
+    M[:, N, :] = bot_row
     b = np.zeros((P, N + 1), np.complex128)
     b[:, : N - 1] = r[:, : N - 1]
     b[:, N - 1] = top
@@ -325,23 +364,29 @@ def coupled_v(ops: Operators, lam: np.ndarray, k2: np.ndarray, r: np.ndarray,
     ``Dv(+1) = 0`` (u, w free of shear there, and by continuity
     ``D^2 v = -(i kx Du + i kz Dw) = 0``).
     """
-    N = ops.N
+    third = ops.d2Tp if ops.free_slip else ops.dTp
+    return _chunked(_coupled_v_pencils, (ops.D2, ops.Tp, ops.Tm, third, ops.dTm), lam, k2, r, vw)
+
+
+def _coupled_v_pencils(D2, Tp, Tm, third, dTm, lam, k2, r, vw):
+    """Dense coupled (phi, v) systems of ``coupled_v`` for one set of pencils."""
+    N = D2.shape[0] - 1
     n1 = N + 1
     P = lam.shape[0]
     M = np.zeros((P, 2 * n1, 2 * n1))
     idx = np.arange(N - 1)
     # (D^2 - lam) phi = r
-    M[:, : N - 1, :n1] = ops.D2[None, : N - 1, :]
+    M[:, : N - 1, :n1] = D2[None, : N - 1, :]
     M[:, idx, idx] -= lam[:, None]
     # (D^2 - k^2) v - phi = 0
     M[:, N - 1 + idx, idx] = -1.0
-    M[:, N - 1: 2 * N - 2, n1:] = ops.D2[None, : N - 1, :]
+    M[:, N - 1: 2 * N - 2, n1:] = D2[None, : N - 1, :]
     M[:, N - 1 + idx, n1 + idx] -= k2[:, None]
     # wall rows
-    M[:, 2 * N - 2, n1:] = ops.Tp
-    M[:, 2 * N - 1, n1:] = ops.Tm
-    M[:, 2 * N, n1:] = ops.d2Tp if ops.free_slip else ops.dTp
-    M[:, 2 * N + 1, n1:] = ops.dTm
+    M[:, 2 * N - 2, n1:] = Tp
+    M[:, 2 * N - 1, n1:] = Tm
+    M[:, 2 * N, n1:] = third
+    M[:, 2 * N + 1, n1:] = dTm
     b = np.zeros((P, 2 * n1), np.complex128)
     b[:, : N - 1] = r[:, : N - 1]
     b[:, 2 * N - 1] = vw

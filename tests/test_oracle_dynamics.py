@@ -341,3 +341,100 @@ def test_sensing_node_rounded_up(ny, re_tau, yplus):
     assert yp >= 15.0 and abs(yp - yplus) < 0.01
     yp_next = (1 + math.cos(math.pi * (j + 1) / N)) * re_tau
     assert yp_next < 15.0
+
+
+# --------------------------------------------------------------------------
+# actuation ramp and the wall shear averaged over an action (Sec. 3.2)
+# --------------------------------------------------------------------------
+
+def _stage_end_times():
+    """Fraction of the step reached at the end of each stage, from the scheme
+    itself: with a constant right-hand side (dq/dt = 1) the explicit part of
+    stage k advances q by dt (gamma_k + zeta_k), so the stage ends at the
+    running sum of gamma + zeta (and the Crank-Nicolson part spans
+    (alpha_k + beta_k) dt, the same interval)."""
+    out, c = [], 0.0
+    for k in range(3):
+        assert abs((channel.ALPHA[k] + channel.BETA[k]) - (channel.GAMMA[k] + channel.ZETA[k])) < 1e-15
+        c += channel.GAMMA[k] + channel.ZETA[k]
+        out.append(c)
+    return out
+
+
+def test_stage_end_times_of_the_scheme():
+    c = _stage_end_times()
+    assert abs(c[0] - 8.0 / 15.0) < 1e-15 and abs(c[1] - 2.0 / 3.0) < 1e-15 and abs(c[2] - 1.0) < 1e-15
+
+
+def test_actuation_ramp_reaches_the_action_linearly(monkeypatch):
+    """Sec. 3.2: the wall velocity goes linearly from the previous action to
+    the new one over the actuation interval (here 3 solver steps).  The
+    Dirichlet wall row imposes v(-1) exactly, so after stage k of step s the
+    lower-wall value sum_n (-1)^n v_n of the actuated mode is the ramp at that
+    stage's end time, (s + c_k) / 3 of the action's coefficient; after the
+    last step it is the action itself.  A ramp evaluated at the stage start, or
+    one that reaches the action after the first step, fails this."""
+    p = _params(nx=8, ny=33, nz=8, steps_per_action=3, re_bulk=2800.0, dt=0.005)
+    ops = channel.Operators(p)
+    st = channel.new_state(si.perturbed_poiseuille(p.nx, p.ny, p.nz, 0, 0.0), p)
+    # one oblique wall mode well inside the clip: a cos(2 pi x / Lx + 2 pi 2 z / Lz)
+    x = np.arange(p.nx) / p.nx
+    z = np.arange(p.nz) / p.nz
+    amp = 0.2 * p.u_tau
+    act = amp * np.cos(2 * np.pi * (x[None, :] + 2 * z[:, None]))
+    vw_hat = channel.action_spectrum(act, ops)
+    row, col = 2, 1                                   # kz index +2, kx index 1
+    assert abs(vw_hat[row, col] - amp / 2) < 1e-15   # the complex amplitude of the mode
+    walls = []
+    real_stage = channel.stage
+
+    def stage_recording(s_, ops_, k, vw, prev):
+        out = real_stage(s_, ops_, k, vw, prev)
+        walls.append(complex(ops.Tm @ s_["v"][row, col]))
+        return out
+
+    monkeypatch.setattr(channel, "stage", stage_recording)
+    channel.env_step(st, ops, act)
+    assert len(walls) == 9
+    c = _stage_end_times()
+    for s in range(3):
+        for k in range(3):
+            theta = (s + c[k]) / 3.0
+            assert abs(walls[3 * s + k] - theta * vw_hat[row, col]) < 1e-14 * amp, (s, k, walls[3 * s + k])
+    assert abs(walls[-1] - vw_hat[row, col]) < 1e-14 * amp
+    # the next action ramps from this one: a zero action brings the wall back
+    walls.clear()
+    channel.env_step(st, ops, np.zeros_like(act))
+    for s in range(3):
+        theta = (s + 1.0) / 3.0
+        assert abs(walls[3 * s + 2] - (1.0 - theta) * vw_hat[row, col]) < 1e-14 * amp
+
+
+def test_wall_shear_reward_is_the_mean_over_the_action():
+    """Sec. 3.2: the reward is the drag reduction averaged between actions.
+    Laminar flow plus a small antisymmetric mean-flow mode u_1 of the discrete
+    tau operator (eigenvalue mu ~ -pi^2): the flux of u_1 is zero, so the
+    constant-flow-rate forcing stays 3 nu, the nonlinear term of a mean flow
+    alone is zero, and after solver step s the profile is
+    U_P + eps A^(s+1) u_1 with A the pinned amplification of the scheme.  The
+    wall shear of one 3-step action is therefore
+    3 nu + eps nu u_1'(-1) (A + A^2 + A^3) / 3; the shear after the last step
+    alone differs from it by far more than the tolerance."""
+    p = _params(nx=4, ny=33, nz=4, steps_per_action=3, re_bulk=100.0, re_tau=10.0, dt=0.05)
+    ops = channel.Operators(p)
+    mu, V = _tau_eigs(ops)
+    which = 1
+    u1 = V[:, which] / np.abs(V[:, which]).max()
+    assert abs(mu[which] + np.pi ** 2) < 1e-6        # slowest odd mode, close to sin(pi y)
+    assert abs(ops.wint @ u1) < 1e-14                 # zero flux
+    st = channel.new_state(si.perturbed_poiseuille(p.nx, p.ny, p.nz, 0, 0.0), p)
+    eps = 0.01
+    st["U"] = st["U"] + eps * u1
+    A = _factor(p.nu * mu[which], p.dt)
+    du1 = float(ops.dTm @ u1)
+    mean = 3.0 * p.nu + eps * p.nu * du1 * (A + A ** 2 + A ** 3) / 3.0
+    last = 3.0 * p.nu + eps * p.nu * du1 * A ** 3
+    assert abs(mean - last) > 1e-5 * 3.0 * p.nu
+    _, tau, reward = channel.env_step(st, ops, np.zeros((p.nz, p.nx)))
+    assert abs(tau - mean) < 1e-12 * 3.0 * p.nu, (tau, mean, last)
+    assert abs(reward - (1.0 - mean / p.tau_reference)) < 1e-12 * mean / p.tau_reference
