@@ -59,13 +59,6 @@ def run_pair(native, kw: dict, nsteps: int, seed: int = 0, amp: float = 0.1, kma
     return lib_out, ora_out, lst, channel.canonical(ost)
 
 
-def wall_shear_tol(U: np.ndarray, nu: float, tol: float) -> float:
-    """Error bound of tau_w = nu sum_n (-1)^(n+1) n^2 U_n implied by a relative
-    L2 error `tol` on the coefficients U (Cauchy-Schwarz): nu ||n^2||_2 tol ||U||_2."""
-    n = np.arange(U.size, dtype=np.float64)
-    return nu * float(np.linalg.norm(n * n)) * tol * float(np.linalg.norm(U))
-
-
 def compare_states(lst: dict, ost: dict, tol: float):
     errs = {k: rel_l2(lst[k], ost[k]) for k in ("v", "g", "U", "W")}
     bad = {k: e for k, e in errs.items() if not e <= tol}

@@ -1,0 +1,127 @@
+"""Full-size parity on the two large grids: one environment step of the
+library through the C ABI against one step of the FP64 oracle, element by
+element, from the same seeded state and action.
+
+* 128 x 129 x 128 at Re_tau 395 (2 pi x 2 x pi): all-FP64 (relative L2
+  <= 1e-11) and mixed precision (<= 1e-4).  This runs the 1024-thread plane
+  kernel, the MH = 65 stage kernels and their per-tile implicit half.
+* 256 x 193 x 256 at Re_tau 550 (dt 0.002): mixed precision (<= 1e-4), the
+  FP32 plane split over a 16-CTA cluster, the MH = 101 stage kernels; and
+  all-FP64 where the handle accepts it (the FP64 padded plane needs the
+  two-pass nonlinear term).
+
+Every Fourier mode of the initial perturbation is excited (amplitude 0.1) and
+the action's standard deviation is 1.5 u_tau, so the clip is active.  The
+oracle's dense pencil solves run in a process pool (spawned, one BLAS thread
+per worker); the pool changes where the independent pencils are solved, not
+how.  One oracle step takes about 10 s at 128 x 129 x 128 and 1-2 minutes at
+256 x 193 x 256 on 8-16 host cores; each is computed once and shared by the
+precisions.
+"""
+
+import math
+import multiprocessing as mp
+import os
+
+import numpy as np
+import pytest
+
+import seeded_inputs as si
+from gpu_util import compare_states, oracle_params, rel_l2
+from oracle import channel
+
+pytestmark = pytest.mark.gpu
+
+RE395 = dict(nx=128, ny=129, nz=128, lx=2 * math.pi, lz=math.pi, re_tau=395.0, re_bulk=6875.0, dt=0.0025)
+RE550 = dict(nx=256, ny=193, nz=256, lx=2 * math.pi, lz=math.pi, re_tau=550.0, re_bulk=10030.0, dt=0.002)
+TOL = {0: 1e-11, 1: 1e-4}
+SEED, AMP, ACTION_SEED, ACTION_STD = 5, 0.1, 77, 1.5
+
+
+@pytest.fixture(scope="module")
+def oracle_pool():
+    """Spawned workers for the oracle's pencil chunks (never forked: the
+    parent holds a CUDA context)."""
+    saved = {k: os.environ.get(k) for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    try:
+        pool = mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1)))
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    channel.set_pencil_starmap(pool.starmap)
+    try:
+        yield pool
+    finally:
+        channel.set_pencil_starmap(None)
+        pool.close()
+        pool.join()
+
+
+_ORACLE = {}
+
+
+def _inputs(grid):
+    op = oracle_params(**grid)
+    fields = si.perturbed_poiseuille(op.nx, op.ny, op.nz, SEED, AMP, 99)
+    act = si.wall_action(op.nx, op.nz, ACTION_SEED, ACTION_STD * op.u_tau)
+    return op, fields, act
+
+
+def _oracle_step(grid):
+    key = tuple(sorted(grid.items()))
+    if key not in _ORACLE:
+        op, fields, act = _inputs(grid)
+        ops = channel.Operators(op)
+        st = channel.new_state(fields, op)
+        obs, tau, rew = channel.env_step(st, ops, act)
+        _ORACLE[key] = (obs, tau, rew, channel.canonical(st))
+    return _ORACLE[key]
+
+
+def _library_step(native, grid, precision):
+    op, fields, act = _inputs(grid)
+    env = native.env_create(native.params(**grid, precision=precision))
+    try:
+        native.env_set_state(env, 0, native.pack_state(fields, op.nx, op.ny, op.nz))
+        obs = np.zeros((2, op.nz, op.nx))
+        tau, rew = np.zeros(1), np.zeros(1)
+        assert native.env_step(env, np.ascontiguousarray(act), obs, tau, rew) == native.CH_OK
+        st = native.unpack_state(native.env_get_state(env, 0), op.nx, op.ny, op.nz)
+        info = native.env_info(env)
+    finally:
+        native.env_destroy(env)
+    return obs, tau[0], rew[0], st, info
+
+
+def _compare(native, grid, precision):
+    tol = TOL[precision]
+    obs, tau, rew, st, info = _library_step(native, grid, precision)
+    o_obs, o_tau, o_rew, o_st = _oracle_step(grid)
+    errs = compare_states(st, o_st, tol)
+    errs["obs"] = rel_l2(obs, o_obs)
+    errs["vw"] = rel_l2(st["vw"], o_st["vw"])
+    errs["wall_shear"] = abs(tau - o_tau) / abs(o_tau)
+    u_tau = grid["re_tau"] / grid["re_bulk"]
+    # the reward 1 - tau / tau_ref is measured against the size of its tau term
+    errs["reward"] = abs(rew - o_rew) / max(abs(o_rew), o_tau / u_tau ** 2)
+    print(f"\n{grid['nx']}x{grid['ny']}x{grid['nz']} precision {precision}: "
+          + ", ".join(f"{k} {v:.2e}" for k, v in errs.items()))
+    for k in ("obs", "vw", "wall_shear", "reward"):
+        assert errs[k] <= tol, (k, errs)
+    return info
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_re395_grid_one_step_against_oracle(native_gpu, oracle_pool, precision):
+    info = _compare(native_gpu, RE395, precision)
+    assert info.plane_cluster >= 1
+
+
+def test_re550_grid_mixed_one_step_against_oracle(native_gpu, oracle_pool):
+    info = _compare(native_gpu, RE550, 1)
+    assert info.plane_cluster == 16

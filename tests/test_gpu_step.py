@@ -10,7 +10,7 @@ import pytest
 
 import golden_util
 import seeded_inputs as si
-from gpu_util import compare_states, oracle_params, rel_l2, run_batch_pair, run_pair, wall_shear_tol
+from gpu_util import compare_states, oracle_params, rel_l2, run_batch_pair, run_pair
 from oracle import channel
 
 pytestmark = pytest.mark.gpu
@@ -22,16 +22,18 @@ LARGER = dict(nx=64, ny=65, nz=64, lx=2 * math.pi, lz=math.pi, re_tau=180.0, re_
 
 
 def _check_outputs(lib_out, ora_out, ost, kw, tol=TOL):
-    """Observation planes to `tol` in relative L2; the wall shear (a weighted
-    sum of the U coefficients, weights n^2) and the reward to the bound that
-    the state tolerance implies."""
-    nu = 1.0 / kw["re_bulk"]
+    """Observation planes, wall shear and reward to `tol`, relative.  The
+    reward 1 - tau_w / tau_ref is measured against the size of its tau_w term
+    (the reward itself may be near zero).  (A looser bound follows from the
+    state tolerance alone: tau_w = nu sum_n (-1)^(n+1) n^2 U_n, so by
+    Cauchy-Schwarz |d tau_w| <= nu ||n^2||_2 tol ||U||_2; the measured errors
+    are far below it.)"""
     u_tau = kw["re_tau"] / kw["re_bulk"]
-    ttol = wall_shear_tol(ost["U"], nu, tol)
+    tau_ref = kw.get("tau_ref", 0.0) or u_tau ** 2
     for (lo, lt, lr), (oo, ot, orr) in zip(lib_out, ora_out):
         assert rel_l2(lo, oo) < tol
-        assert abs(lt - ot) <= ttol, (lt, ot, ttol)
-        assert abs(lr - orr) <= ttol / u_tau ** 2
+        assert abs(lt - ot) <= tol * abs(ot), (lt, ot)
+        assert abs(lr - orr) <= tol * max(abs(orr), abs(ot) / tau_ref), (lr, orr)
 
 
 def test_single_step_minimal_channel(native_gpu):
@@ -169,6 +171,30 @@ def test_orr_sommerfeld_growth_on_gpu(native_gpu):
     sigma = math.log(np.linalg.norm(st["v"][:, 0, 1]) / n0) / (nsteps * kw["dt"]) / 1.5
     rate = ref["alpha"] * ref["c_imag"]
     assert abs(sigma - rate) < 1e-3 * rate, sigma
+
+
+def test_non_finite_state_reports_divergence(native_gpu):
+    """A state that holds a non-finite coefficient (set from the host, as a
+    blown-up flow would leave it) makes env_step return CH_ERR_DIVERGED with
+    the outputs still written; the handle stays usable and a finite state
+    steps normally again."""
+    native = native_gpu
+    env = native.env_create(native.params(**MINIMAL))
+    try:
+        fields = si.perturbed_poiseuille(16, 65, 16, 2, 0.1, 4)
+        bad = {k: np.array(v, copy=True) for k, v in fields.items()}
+        bad["v"][3, 1, 2] = np.nan
+        native.env_set_state(env, 0, native.pack_state(bad, 16, 65, 16))
+        act = np.ascontiguousarray(si.wall_action(16, 16, 5, 0.05 * 180 / 2800))
+        obs, tau, rew = np.full((2, 16, 16), 7.0), np.zeros(1), np.zeros(1)
+        assert native.env_step(env, act, obs, tau, rew) == native.CH_ERR_DIVERGED
+        assert not np.isfinite(tau[0]) and not np.isfinite(rew[0])
+        assert not np.isfinite(obs).all()
+        native.env_set_state(env, 0, native.pack_state(fields, 16, 65, 16))
+        assert native.env_step(env, act, obs, tau, rew) == native.CH_OK
+        assert np.isfinite(obs).all() and np.isfinite(tau[0])
+    finally:
+        native.env_destroy(env)
 
 
 def test_invalid_arguments_are_rejected(native_gpu):
