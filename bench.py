@@ -206,6 +206,31 @@ FP64_PEAK_SOURCE = ("FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 FLOP x 2.07 GHz (nom
                     "FMA probe measured 1.19 at 1.96 GHz)")
 
 
+def measure_fp64_peak() -> dict:
+    """FP64 throughput of a plain library GEMM on this GPU, in this run:
+    torch.matmul on 4096 x 4096 float64 operands (cuBLAS DGEMM, 2 n^3 FLOP),
+    best of 5 after a warm-up, CUDA events.  The denominator of the FP64
+    rooflines, as the copy test and the bf16 GEMM are for the others."""
+    import torch
+    n = 4096
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    torch.matmul(a, b)
+    torch.cuda.synchronize()
+    best = None
+    for _ in range(5):
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        torch.matmul(a, b)
+        e.record()
+        torch.cuda.synchronize()
+        ms = s.elapsed_time(e)
+        best = ms if best is None else min(best, ms)
+    del a, b
+    return {"tflops": 2.0 * n ** 3 / (best * 1e-3) / 1e12, "ms": best,
+            "how": "torch.matmul float64 4096^3 (cuBLAS DGEMM), best of 5, CUDA events, this run"}
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons during the timed region."""
 
@@ -544,7 +569,7 @@ class Handle:
         self.native.env_destroy(self.env)
 
 
-def roofline_of(workload: str, kern: dict) -> dict:
+def roofline_of(workload: str, kern: dict, fp64_peak: dict | None = None) -> dict:
     """Roofline of the kernel that bounds the workload: the FP64 plane kernel
     (all-FP64 handles) or the implicit half of the stage (mixed handles, FP64
     tau solves), against the FP64 FMA peak, with algorithmic work per launch
@@ -556,9 +581,13 @@ def roofline_of(workload: str, kern: dict) -> dict:
     avg_s = kern[kk]["ms_total"] * 1e-3 / max(kern[kk]["launches"], 1)
     flops = B * plane_kernel_flops(nx, ny, nz) if prec == 0 else implicit_half_fp64_flops(nx, ny, nz, B, mixed=True)
     achieved = flops / avg_s / 1e12
+    if fp64_peak:
+        peak, source = fp64_peak["tflops"], "of measured: " + fp64_peak["how"]
+    else:
+        peak, source = FP64_PEAK_TFLOPS, FP64_PEAK_SOURCE + " (derived)"
     r = {"kernel": kk, "dominant_kernel": dom, "bound": "alu", "unit": "TFLOP/s", "achieved": achieved,
-         "peak": FP64_PEAK_TFLOPS, "frac": achieved / FP64_PEAK_TFLOPS,
-         "peak_source": FP64_PEAK_SOURCE + " (derived; the measured peaks file has no FP64 figure)",
+         "peak": peak, "frac": achieved / peak, "peak_source": source,
+         "frac_of_derived_fma_peak": achieved / FP64_PEAK_TFLOPS,
          "flops_per_launch": flops, "avg_launch_ms": avg_s * 1e3,
          "traffic": TRAFFIC_BYTES.get((workload, kk))}
     if prec == 1:
@@ -576,7 +605,8 @@ def percentiles(ms: list) -> dict:
     return {"p50_ms": float(np.percentile(a, 50)), "p99_ms": float(np.percentile(a, 99))}
 
 
-def measure_handle(native, workload: str, args, rank: int, world: int, flush, dist, e2e: bool = True) -> dict:
+def measure_handle(native, workload: str, args, rank: int, world: int, flush, dist, e2e: bool = True,
+                   fp64_peak: dict | None = None) -> dict:
     """Graph-replay timing (value), a profiled pass (kernel breakdown and
     roofline) and the end-to-end host-buffer timing of one workload."""
     h = Handle(native, workload, rank, autotune=not args.no_autotune)
@@ -590,7 +620,7 @@ def measure_handle(native, workload: str, args, rank: int, world: int, flush, di
                "warmup": W, **percentiles(step_ms),
                "kernels_ms_per_step": {k: v["ms_total"] / K for k, v in kern.items()},
                "profiled_ms_per_step": sum(prof_ms) / K,
-               "roofline": roofline_of(workload, kern),
+               "roofline": roofline_of(workload, kern, fp64_peak),
                "gpu_launches": K * h.info.launches_per_step,
                "tiles": {"ppc_pre": h.info.ppc_pre, "ppc_post": h.info.ppc_post,
                          "post_batched": h.info.post_batched, "autotuned": bool(h.info.tuned),
@@ -766,11 +796,12 @@ def run_target(args, rank: int, world: int, native, dist, flush):
     """Default line: batched mixed 256 minimal channels vs the plain FP64
     single-environment minimal channel, the served form, the oracle check and
     the larger FP64 channel."""
+    fp64 = measure_fp64_peak()
     clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     clocks.start()
-    batched = measure_handle(native, TARGET_BATCHED, args, rank, world, flush, dist)
-    plain = measure_handle(native, TARGET_PLAIN, args, rank, world, flush, dist, e2e=False)
-    larger = measure_handle(native, "larger_fp64", args, rank, world, flush, dist, e2e=False)
+    batched = measure_handle(native, TARGET_BATCHED, args, rank, world, flush, dist, fp64_peak=fp64)
+    plain = measure_handle(native, TARGET_PLAIN, args, rank, world, flush, dist, e2e=False, fp64_peak=fp64)
+    larger = measure_handle(native, "larger_fp64", args, rank, world, flush, dist, e2e=False, fp64_peak=fp64)
     clk = clocks.stop()
     hb = batched.pop("_handle")
     for r in (plain, larger):
@@ -808,6 +839,7 @@ def run_target(args, rank: int, world: int, native, dist, flush):
         "profiled_ms_per_step": batched["profiled_ms_per_step"],
         "algorithmic_gbs_per_step": batched["algorithmic_gbs_per_step"],
         "roofline": batched["roofline"],
+        "fp64_peak_measured": fp64,
         "cpu_baseline": cpu,
         "e2e": batched["e2e"],
         "gpu_launches": batched["gpu_launches"],
@@ -826,9 +858,10 @@ def run_target(args, rank: int, world: int, native, dist, flush):
 
 def run_single(args, rank: int, world: int, native, dist, flush):
     """One single-handle workload as its own line."""
+    fp64 = measure_fp64_peak()
     clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     clocks.start()
-    r = measure_handle(native, args.workload, args, rank, world, flush, dist)
+    r = measure_handle(native, args.workload, args, rank, world, flush, dist, fp64_peak=fp64)
     clk = clocks.stop()
     h = r.pop("_handle")
     cpu = None
@@ -856,6 +889,7 @@ def run_single(args, rank: int, world: int, native, dist, flush):
             "mpts_rk3_steps_per_s": r["mpts_rk3_steps_per_s"], "kernels_ms_per_step": r["kernels_ms_per_step"],
             "profiled_ms_per_step": r["profiled_ms_per_step"],
             "algorithmic_gbs_per_step": r["algorithmic_gbs_per_step"], "roofline": r["roofline"],
+            "fp64_peak_measured": fp64,
             "cpu_baseline": cpu, "accuracy": r.get("accuracy"), "e2e": r["e2e"], "gpu_launches": r["gpu_launches"],
             "tiles": r["tiles"],
             "step_launch": "value: one captured CUDA graph per step; kernel times and roofline: a profiled pass "

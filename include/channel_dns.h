@@ -10,8 +10,10 @@
  * (TERMN).
  *
  * Numerical method (the readings of the paper that the library fixes):
- *   - closed channel y in [-1, 1], no slip at both walls; the action is the
- *     wall-normal velocity of the lower wall y = -1;
+ *   - channel y in [-1, 1]; the action is the wall-normal velocity of the
+ *     lower (no-slip) wall y = -1; the upper boundary is a no-slip wall
+ *     (closed channel, top_bc = 0) or free slip (the paper's open channel,
+ *     top_bc = 1);
  *   - velocity-vorticity (v, omega_y) form, 3/2-dealiased u x omega;
  *   - third-order low-storage Runge-Kutta for the nonlinear term and
  *     Crank-Nicolson for the viscous term (Sec. 3.1), coefficients
@@ -21,8 +23,9 @@
  *     correction for the four v wall conditions;
  *   - constant flow rate: the mean pressure gradient is set every stage so
  *     that the bulk velocity stays 1.
- * Units: half height 1, bulk velocity 1, nu = 1 / re_bulk,
- * u_tau = re_tau / re_bulk.
+ * Units: y in [-1, 1], bulk velocity 1, u_tau = re_tau / re_bulk; nu =
+ * 1 / re_bulk (closed channel: Reynolds numbers on the half height 1) or
+ * 2 / re_bulk (open channel: on its height 2).
  *
  * Conventions
  *   - All functions return 0 (CH_OK) on success or a negative CH_ERR_* code;
@@ -70,7 +73,12 @@ typedef struct ch_params {
     double dt;               /* time step in h / U_b                                   */
     int steps_per_action;    /* solver steps per env_step (actuation interval, Sec. 3.2) */
     double y_sense_plus;     /* sensing height in wall units; rounded up to a node (Sec. 3.2) */
-    int top_bc;              /* 0: no-slip upper wall (only value built)               */
+    int top_bc;              /* 0: closed channel, no-slip upper wall at y = +1; 1: open
+                                channel of the paper (Sec. 3.1), free-slip top: v = 0,
+                                D^2 v = 0, D omega_y = 0, DU = DW = 0 at y = +1, and Re_b,
+                                Re_tau based on the whole height 2 (nu = 2 / re_bulk,
+                                y+ = (1 + y) re_tau / 2); built for ny <= 65, larger ny
+                                return CH_ERR_UNSUPPORTED                                  */
     int precision;           /* 0: all FP64; 1: mixed -- the dealiased nonlinear term
                                 (Chebyshev synthesis/analysis, padded FFTs, products)
                                 in FP32, the tau solves, influence-matrix correction
@@ -244,7 +252,7 @@ const char* ch_strerror(int code);
 
 /* Host only (no GPU): write the env_reset initial state of one environment
  * into `buf` (same layout as env_get_state).  With p->top_bc = 1 (free-slip
- * top, not yet stepped by the library) the perturbation shapes are
+ * top) the perturbation shapes are
  * v ~ (1+y)^2 (1-y) (2-y) / 2 and omega_y ~ (1+y) (3-y) / 4 and the mean flow is
  * the half-Poiseuille 1.5 (2s - s^2), s = (1+y)/2, which meet the free-slip
  * conditions exactly. */

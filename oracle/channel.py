@@ -43,7 +43,7 @@ Open channel (``top_bc = 1``; Sec. 3.1: an open channel of height h with a
 free-slip top): ``y in [-1, 1]`` is the whole channel, so Re_b and Re_tau
 are based on the height 2 (``nu = 2 / Re_b``, ``y+ = (1 + y) Re_tau / 2``),
 and the top rows become ``Dg(+1) = 0``, ``D^2 v(+1) = 0`` (with ``v(+1) = 0``),
-``DU(+1) = DW(+1) = 0``.  The library does not implement it yet.
+``DU(+1) = DW(+1) = 0``.
 
 Wall action (Sec. 3.2): clipped to ``[-u_tau, u_tau]``, plane mean removed
 (zero net mass flux, Sec. 4.1), ramped linearly from the previous action over

@@ -91,6 +91,27 @@ std::vector<double> host_solve(int N, int sig, const std::vector<double>& r, con
   return f;
 }
 
+// the tau rows n >= 2 only: f_i = P_i with the lowest coefficient f_0 = 0
+std::vector<double> host_affine(int N, int sig, const std::vector<double>& r, const Factor& F) {
+  const int M = (N - sig) / 2 + 1;
+  std::vector<double> f(M, 0.0);
+  double anext = 0.0;
+  for (int i = M - 1; i >= 1; --i) {
+    const int n = 2 * i + sig;
+    double R = cA(n) * r[i - 1] - cB(n, N) * r[i];
+    if (i + 1 < M) R += cC(n, N) * r[i + 1];
+    const double a = F.e[i] * R - F.h[i] * anext;
+    f[i] = a;
+    anext = a;
+  }
+  double Pp = 0.0;
+  for (int i = 1; i < M; ++i) {
+    Pp = f[i] + F.b[i] * Pp;
+    f[i] = Pp;
+  }
+  return f;
+}
+
 bool fft_plan(int n, FftPlan* pl) {
   pl->n = n;
   pl->nst = 0;
@@ -118,10 +139,14 @@ std::vector<double2> twiddles(int n) {
   return t;
 }
 
-int sensing_node(int N, double re_tau, double y_plus) {
+// Re_b and Re_tau are based on the half height 1 of the closed channel and on
+// the whole height 2 of the open channel (free-slip top): y+ = (1 + y) Re_tau / height
+double channel_height(const ch_params_t* p) { return p->top_bc == 1 ? 2.0 : 1.0; }
+
+int sensing_node(int N, double re_tau, double y_plus, double height) {
   for (int j = N; j >= 0; --j) {
     const double yj = std::cos(M_PI * j / N);
-    if ((1.0 + yj) * re_tau >= y_plus) return j;
+    if ((1.0 + yj) * re_tau / height >= y_plus) return j;
   }
   return 0;
 }
@@ -154,7 +179,10 @@ int check_params(const ch_params_t* p) {
   if (p->steps_per_action < 1) return CH_ERR_ARG;
   if (p->control < 0 || p->control > 2) return CH_ERR_ARG;
   if (p->autotune != 0 && p->autotune != 1) return CH_ERR_ARG;
-  if (p->top_bc != 0 || (p->precision != 0 && p->precision != 1)) return CH_ERR_UNSUPPORTED;
+  if (p->top_bc != 0 && p->top_bc != 1) return CH_ERR_ARG;
+  if (p->precision != 0 && p->precision != 1) return CH_ERR_UNSUPPORTED;
+  // the free-slip top's stage kernels are built for ny <= 65 (one parity <= 33 unknowns)
+  if (p->top_bc == 1 && p->ny > 65) return CH_ERR_UNSUPPORTED;
   FftPlan a, b;
   if (!fft_plan(3 * p->nx / 2, &a) || !fft_plan(3 * p->nz / 2, &b)) return CH_ERR_UNSUPPORTED;
   if ((3 * p->nx / 2) % 2 || (3 * p->nz / 2) % 2) return CH_ERR_UNSUPPORTED;
@@ -345,6 +373,9 @@ int build_tables(ch_env* env) {
   std::vector<double> pois((size_t)2 * 4 * Mh * P, 0.0), pois_isq((size_t)2 * P, 0.0);
   std::vector<double> vh((size_t)3 * 2 * Mh * P, 0.0), vh_idv((size_t)3 * 2 * P, 0.0);
   std::vector<double> u1((size_t)3 * Mh, 0.0), u1_iflux(3, 0.0);
+  // free-slip top: sum Q, sum n^2 Q per parity; A, B of vh per parity
+  std::vector<double> helm_top((size_t)3 * 2 * 2 * P, 0.0), vh_top((size_t)3 * 2 * 2 * P, 0.0);
+  const bool top = p.top_bc == 1;
   auto put = [&](std::vector<double>& tab, size_t base, const Factor& F, int M, int pp) {
     for (int i = 0; i < M; ++i) {
       tab[base + ((size_t)0 * Mh + i) * P + pp] = F.e[i];
@@ -367,17 +398,31 @@ int build_tables(ch_env* env) {
         const size_t slot = (size_t)(k * 2 + sig);
         put(helm, slot * 4 * Mh * P, Fh, M, pp);
         helm_isq[slot * P + pp] = Fh.isq;
+        {
+          double sq = 0.0, sq2 = 0.0;
+          for (int i = 0; i < M; ++i) {
+            const double n = 2 * i + sig;
+            sq += Fh.Q[i];
+            sq2 += n * n * Fh.Q[i];
+          }
+          helm_top[(slot * 2 + 0) * P + pp] = sq;
+          helm_top[(slot * 2 + 1) * P + pp] = sq2;
+        }
         // homogeneous solution of this parity: phi_h = 1 on the wall row, r = 0
         const std::vector<double> zero(M, 0.0);
         const std::vector<double> phih = host_solve(N, sig, zero, Fh, 1.0);
         const std::vector<double> vhp = host_solve(N, sig, phih, Fp, 0.0);
-        double d = 0.0;
+        double d = 0.0, a2 = 0.0;
         for (int i = 0; i < M; ++i) {
           const int n = 2 * i + sig;
+          const double nn = (double)n * n;
           vh[(slot * Mh + i) * P + pp] = vhp[i];
-          d += (double)n * n * vhp[i];
+          d += nn * vhp[i];
+          a2 += nn * (nn - 1.0) / 3.0 * vhp[i];   // T_n''(+1) = n^2 (n^2 - 1) / 3
         }
         vh_idv[slot * P + pp] = (d != 0.0 && std::isfinite(d)) ? 1.0 / d : 0.0;
+        vh_top[(slot * 2 + 0) * P + pp] = a2;
+        vh_top[(slot * 2 + 1) * P + pp] = d;
       }
     }
   }
@@ -388,7 +433,9 @@ int build_tables(ch_env* env) {
     const int M = N / 2 + 1;
     std::vector<double> r(M, 0.0);
     r[0] = 1.0;
-    const std::vector<double> uu = host_solve(N, 0, r, F, 0.0);
+    // no-slip: the response with zero wall values; free-slip top: the affine
+    // particular response (lowest coefficient 0), closed on the device
+    const std::vector<double> uu = top ? host_affine(N, 0, r, F) : host_solve(N, 0, r, F, 0.0);
     const double cforce = (a + b) / (b * env->nu);
     double flux = 0.0;
     for (int i = 0; i < M; ++i) {
@@ -397,7 +444,7 @@ int build_tables(ch_env* env) {
       u1[(size_t)k * Mh + i] = v;
       flux += 2.0 / (1.0 - (double)n * n) * v;
     }
-    u1_iflux[k] = 1.0 / flux;
+    u1_iflux[k] = top ? 0.0 : 1.0 / flux;
   }
   // tau row constants per n
   std::vector<double> rowc((size_t)3 * ny, 0.0);
@@ -433,7 +480,10 @@ int build_tables(ch_env* env) {
   RC(dupload(env, &env->tab.tau.vh_idv, vh_idv));
   RC(dupload(env, &env->tab.tau.u1, u1));
   RC(dupload(env, &env->tab.tau.u1_iflux, u1_iflux));
+  RC(dupload(env, &env->tab.tau.helm_top, helm_top));
+  RC(dupload(env, &env->tab.tau.vh_top, vh_top));
   env->tab.tau.Mh = Mh;
+  env->tab.tau.top_bc = top ? 1 : 0;
   RC(dupload(env, &env->tab.tw_nx, twiddles(g.nx)));
   RC(dupload(env, &env->tab.tw_nz, twiddles(g.nz)));
   RC(dupload(env, &env->tab.tw_cheb, twiddles(g.N)));
@@ -692,11 +742,12 @@ bool tiles_valid(const ch_env* env, int smem_max, int ppc_pre, int ppc_post, int
   const size_t node = env->prm.precision == 1 ? sizeof(float2) : sizeof(double2);
   auto pow2 = [](int v, int hi) { return v >= 1 && v <= hi && (v & (v - 1)) == 0; };
   if (!pow2(ppc_pre, 8) || stage_pre_smem(g, ppc_pre, node) > (size_t)smem_max) return false;
-  if (post_batched == 1) return pow2(ppc_post, 16) && stage_post_batched_smem(g, ppc_post) <= (size_t)smem_max;
+  const int top = env->prm.top_bc;
+  if (post_batched == 1) return pow2(ppc_post, 16) && stage_post_batched_smem(g, ppc_post, top) <= (size_t)smem_max;
   if (post_batched != 0) return false;
   // the per-tile form runs 8 ppc threads and any tile width up to 8 (widths
   // that are not powers of two fill the resident CTA slots more evenly)
-  return ppc_post >= 1 && ppc_post <= 8 && stage_post_smem(g, env->tab.tau.Mh, ppc_post) <= (size_t)smem_max;
+  return ppc_post >= 1 && ppc_post <= 8 && stage_post_smem(g, env->tab.tau.Mh, ppc_post, top) <= (size_t)smem_max;
 }
 
 int drop_graphs(ch_env* env) {
@@ -861,7 +912,7 @@ size_t env_footprint(const ch_params_t* p) {
   const size_t state = B * (4 * ny * P * 16 + 4 * ny * 8 + 9 * ny * P * 16 + 3 * P * 16 + 8 +
                             (size_t)p->nz * p->nx * 8 + (2 * (size_t)p->nz * p->nx + 2) * 8);
   const size_t tables = (3 * 2 * 4 * Mh * P + 3 * 2 * P + 2 * 4 * Mh * P + 2 * P + 3 * 2 * Mh * P + 3 * 2 * P +
-                         3 * Mh + 3 + 3 * ny + ny) * 8 + ny * ny * 12 + (nxh + p->nz) * 8;
+                         3 * Mh + 3 + 3 * ny + ny + 2 * 3 * 2 * 2 * P) * 8 + ny * ny * 12 + (nxh + p->nz) * 8;
   return state + tables + ((size_t)4 << 20);  // plus twiddles and rounding slack
 }
 }  // namespace chdns
@@ -916,10 +967,10 @@ int env_create(const ch_params_t* p, ch_env_t** out) {
   Grid& g = env->g;
   g.nx = p->nx; g.ny = p->ny; g.nz = p->nz; g.nxh = p->nx / 2; g.P = g.nz * g.nxh; g.N = p->ny - 1;
   g.mx = 3 * p->nx / 2; g.mz = 3 * p->nz / 2;
-  env->nu = 1.0 / p->re_bulk;
+  env->nu = channel_height(p) / p->re_bulk;
   env->u_tau = p->re_tau / p->re_bulk;
   env->tau_ref = p->tau_ref > 0 ? p->tau_ref : env->u_tau * env->u_tau;
-  env->js = sensing_node(g.N, p->re_tau, p->y_sense_plus);
+  env->js = sensing_node(g.N, p->re_tau, p->y_sense_plus, channel_height(p));
   env->t.assign(env->B, 0.0);
   env->steps.assign(env->B, 0.0);
   int rc = CH_OK;
@@ -950,27 +1001,26 @@ int env_create(const ch_params_t* p, ch_env_t** out) {
         cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
       return fail(CH_ERR_CUDA);
     env->ppc_post = 8;
-    while (env->ppc_post > 1 && stage_post_smem(g, env->tab.tau.Mh, env->ppc_post) > (size_t)smem_max)
+    while (env->ppc_post > 1 && stage_post_smem(g, env->tab.tau.Mh, env->ppc_post, p->top_bc) > (size_t)smem_max)
       env->ppc_post /= 2;
     env->ppc_pre = 8;
     while (env->ppc_pre > 1 && stage_pre_smem(g, env->ppc_pre, sizeof(double2)) > (size_t)smem_max) env->ppc_pre /= 2;
-    if (stage_post_smem(g, env->tab.tau.Mh, env->ppc_post) > (size_t)smem_max) return fail(CH_ERR_UNSUPPORTED);
+    if (stage_post_smem(g, env->tab.tau.Mh, env->ppc_post, p->top_bc) > (size_t)smem_max) return fail(CH_ERR_UNSUPPORTED);
     // The batched form of stage_post runs four threads per mode, each with
     // the same work; it pays once the batch supplies at least two such warps
     // per SM sub-partition (B P / 8 >= 2 x 4 x SMs).
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return fail(CH_ERR_CUDA);
-    if ((size_t)B * P >= (size_t)64 * sms && stage_post_batched_smem(g, 8) <= (size_t)smem_max) {
+    if ((size_t)B * P >= (size_t)64 * sms && stage_post_batched_smem(g, 8, p->top_bc) <= (size_t)smem_max) {
       env->post_batched = true;
       env->ppc_post = 16;  // 64 threads; 8 when the tile would leave fewer than 3 CTAs per SM
-      if (stage_post_batched_smem(g, 16) > (size_t)76 * 1024) env->ppc_post = 8;
+      if (stage_post_batched_smem(g, 16, p->top_bc) > (size_t)76 * 1024) env->ppc_post = 8;
     }
     if (p->autotune && (rc = autotune_tiles(env, smem_max))) return fail(rc);
   }
-  // laminar Poiseuille, zero wall action
+  // laminar Poiseuille (the half-Poiseuille profile under a free-slip top), zero wall action
   std::vector<double> st(ch_state_bytes(p) / sizeof(double), 0.0);
-  st[(size_t)4 * ny * P + 0] = 0.75;
-  st[(size_t)4 * ny * P + 2] = -0.75;
+  fill_seed_state(p, 0, 0.0, 0, st.data());
   for (int e = 0; e < env->B; ++e)
     if ((rc = set_state_dev(env, e, st.data()))) return fail(rc);
   if (cudaMemset(pb.vw_old, 0, B * P * sizeof(double2)) != cudaSuccess) return fail(CH_ERR_CUDA);
@@ -1070,7 +1120,7 @@ int env_info(const ch_env_t* env, ch_info_t* info) {
   if (!env || !info) return CH_ERR_ARG;
   std::memset(info, 0, sizeof(*info));
   info->j_sense = env->js;
-  info->y_plus_sense = (1.0 + std::cos(M_PI * env->js / env->g.N)) * env->prm.re_tau;
+  info->y_plus_sense = (1.0 + std::cos(M_PI * env->js / env->g.N)) * env->prm.re_tau / channel_height(&env->prm);
   info->nu = env->nu;
   info->u_tau = env->u_tau;
   info->tau_ref = env->tau_ref;

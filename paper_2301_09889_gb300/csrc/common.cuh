@@ -438,7 +438,11 @@ struct TauTables {
   const double* u1;        // [3][Mh]           mean response to unit forcing (even parity)
   const double* u1_iflux;  // [3]               1 / int u1 dy
   const double* rowc;      // [3][ny]           tau row constants cA_n, cB_n, cC_n
+  // free-slip top (top_bc = 1): the wall rows couple the parities
+  const double* helm_top;  // [3][2][2][P]      sum Q, sum n^2 Q of the stage's factorisation, per parity
+  const double* vh_top;    // [3][2][2][P]      A = sum n^2 (n^2 - 1) / 3 vh_n, B = sum n^2 vh_n, per parity
   int Mh;
+  int top_bc;              // 0 no-slip upper wall; 1 free slip (u1 then holds the affine forcing response)
 };
 
 struct StageCoef {

@@ -38,8 +38,8 @@ struct DevTables {
 
 // fused wall-normal halves of a stage (stage.cu); ppc = modes per CTA
 size_t stage_pre_smem(const Grid& g, int ppc, size_t node_bytes);  // node_bytes: one complex node value
-size_t stage_post_smem(const Grid& g, int Mh, int ppc);
-size_t stage_post_batched_smem(const Grid& g, int ppc);
+size_t stage_post_smem(const Grid& g, int Mh, int ppc, int top);
+size_t stage_post_batched_smem(const Grid& g, int ppc, int top);
 template <typename RN>
 cudaError_t launch_stage_pre(const Grid& g, int B, const PencilBufs& pb, const DevTables& t,
                              typename cpx<RN>::T* q, int ppc, cudaStream_t st);

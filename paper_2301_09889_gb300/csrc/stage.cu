@@ -20,10 +20,15 @@ size_t stage_pre_smem(const Grid& g, int ppc, size_t node_bytes) {
   return (size_t)8 * g.ny * ppc * node_bytes + (size_t)12 * ppc * sizeof(double2);
 }
 // (both with six complex values per mode for the FP64 fast analysis; the
-// coefficient tile is smaller in FP32 node precision, the FP64 size bounds both)
-size_t stage_post_batched_smem(const Grid& g, int ppc) { return ((size_t)3 * g.ny + 6) * ppc * sizeof(double2); }
-size_t stage_post_smem(const Grid& g, int Mh, int ppc) {
-  return ((size_t)7 * g.ny + 6) * ppc * sizeof(double2) + ((size_t)18 * Mh * ppc + 6 * ppc) * sizeof(double);
+// coefficient tile is smaller in FP32 node precision, the FP64 size bounds both;
+// a free-slip top adds the exchange slots of the parity closures: six values
+// per thread, two rounds in the batched form)
+size_t stage_post_batched_smem(const Grid& g, int ppc, int top) {
+  return ((size_t)3 * g.ny + 6) * ppc * sizeof(double2) + (top ? (size_t)2 * 4 * ppc * 6 * sizeof(double) : 0);
+}
+size_t stage_post_smem(const Grid& g, int Mh, int ppc, int top) {
+  return ((size_t)7 * g.ny + 6) * ppc * sizeof(double2) + ((size_t)18 * Mh * ppc + 6 * ppc) * sizeof(double) +
+         (top ? (size_t)8 * ppc * 6 * sizeof(double) : 0);
 }
 
 template <typename RN>
@@ -47,28 +52,51 @@ template <typename RN>
 cudaError_t launch_stage_post(const Grid& g, int B, const PencilBufs& pb, const DevTables& t,
                               const typename cpx<RN>::T* h, const StageCoef& sc, int ppc, bool batched,
                               cudaStream_t st) {
-  if (batched) {
-    const size_t smem = stage_post_batched_smem(g, ppc);
-    switch (mh_bucket(g.N / 2 + 1)) {
-      case 5: return post_batched_mh<RN, 5>(g, B, pb, t, h, sc, ppc, smem, st);
-      case 9: return post_batched_mh<RN, 9>(g, B, pb, t, h, sc, ppc, smem, st);
-      case 17: return post_batched_mh<RN, 17>(g, B, pb, t, h, sc, ppc, smem, st);
-      case 33: return post_batched_mh<RN, 33>(g, B, pb, t, h, sc, ppc, smem, st);
-      case 49: return post_batched_mh<RN, 49>(g, B, pb, t, h, sc, ppc, smem, st);
-      case 65: return post_batched_mh<RN, 65>(g, B, pb, t, h, sc, ppc, smem, st);
-      case 101: return post_batched_mh<RN, 101>(g, B, pb, t, h, sc, ppc, smem, st);
+  const int top = t.tau.top_bc;
+  const int mh = mh_bucket(g.N / 2 + 1);
+  if (top) {
+    // free-slip top: built for MH <= 33 (ny <= 65)
+    if (batched) {
+      const size_t smem = stage_post_batched_smem(g, ppc, 1);
+      switch (mh) {
+        case 5: return post_batched_mh<RN, 5, 1>(g, B, pb, t, h, sc, ppc, smem, st);
+        case 9: return post_batched_mh<RN, 9, 1>(g, B, pb, t, h, sc, ppc, smem, st);
+        case 17: return post_batched_mh<RN, 17, 1>(g, B, pb, t, h, sc, ppc, smem, st);
+        case 33: return post_batched_mh<RN, 33, 1>(g, B, pb, t, h, sc, ppc, smem, st);
+        default: return cudaErrorInvalidValue;
+      }
+    }
+    const size_t smem = stage_post_smem(g, t.tau.Mh, ppc, 1);
+    switch (mh) {
+      case 5: return post_mh<RN, 5, 1>(g, B, pb, t, h, sc, ppc, smem, st);
+      case 9: return post_mh<RN, 9, 1>(g, B, pb, t, h, sc, ppc, smem, st);
+      case 17: return post_mh<RN, 17, 1>(g, B, pb, t, h, sc, ppc, smem, st);
+      case 33: return post_mh<RN, 33, 1>(g, B, pb, t, h, sc, ppc, smem, st);
       default: return cudaErrorInvalidValue;
     }
   }
-  const size_t smem = stage_post_smem(g, t.tau.Mh, ppc);
-  switch (mh_bucket(g.N / 2 + 1)) {
-    case 5: return post_mh<RN, 5>(g, B, pb, t, h, sc, ppc, smem, st);
-    case 9: return post_mh<RN, 9>(g, B, pb, t, h, sc, ppc, smem, st);
-    case 17: return post_mh<RN, 17>(g, B, pb, t, h, sc, ppc, smem, st);
-    case 33: return post_mh<RN, 33>(g, B, pb, t, h, sc, ppc, smem, st);
-    case 49: return post_mh<RN, 49>(g, B, pb, t, h, sc, ppc, smem, st);
-    case 65: return post_mh<RN, 65>(g, B, pb, t, h, sc, ppc, smem, st);
-    case 101: return post_mh<RN, 101>(g, B, pb, t, h, sc, ppc, smem, st);
+  if (batched) {
+    const size_t smem = stage_post_batched_smem(g, ppc, 0);
+    switch (mh) {
+      case 5: return post_batched_mh<RN, 5, 0>(g, B, pb, t, h, sc, ppc, smem, st);
+      case 9: return post_batched_mh<RN, 9, 0>(g, B, pb, t, h, sc, ppc, smem, st);
+      case 17: return post_batched_mh<RN, 17, 0>(g, B, pb, t, h, sc, ppc, smem, st);
+      case 33: return post_batched_mh<RN, 33, 0>(g, B, pb, t, h, sc, ppc, smem, st);
+      case 49: return post_batched_mh<RN, 49, 0>(g, B, pb, t, h, sc, ppc, smem, st);
+      case 65: return post_batched_mh<RN, 65, 0>(g, B, pb, t, h, sc, ppc, smem, st);
+      case 101: return post_batched_mh<RN, 101, 0>(g, B, pb, t, h, sc, ppc, smem, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  const size_t smem = stage_post_smem(g, t.tau.Mh, ppc, 0);
+  switch (mh) {
+    case 5: return post_mh<RN, 5, 0>(g, B, pb, t, h, sc, ppc, smem, st);
+    case 9: return post_mh<RN, 9, 0>(g, B, pb, t, h, sc, ppc, smem, st);
+    case 17: return post_mh<RN, 17, 0>(g, B, pb, t, h, sc, ppc, smem, st);
+    case 33: return post_mh<RN, 33, 0>(g, B, pb, t, h, sc, ppc, smem, st);
+    case 49: return post_mh<RN, 49, 0>(g, B, pb, t, h, sc, ppc, smem, st);
+    case 65: return post_mh<RN, 65, 0>(g, B, pb, t, h, sc, ppc, smem, st);
+    case 101: return post_mh<RN, 101, 0>(g, B, pb, t, h, sc, ppc, smem, st);
     default: return cudaErrorInvalidValue;
   }
 }

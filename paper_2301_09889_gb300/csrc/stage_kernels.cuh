@@ -102,6 +102,113 @@ __device__ __forceinline__ void tau_seq(int N, int ny, int sig, const double (&r
     if (i < M) f[i] += T.Q(i) * f0;
 }
 
+// ---------------------------------------------------------------------------
+// Free-slip top (open channel, top_bc = 1; paper Sec. 3.1).  The tau rows
+// n >= 2 are those of the no-slip channel, so elimination still leaves each
+// parity affine in its lowest coefficient, f = P + x Q (P_0 = 0, Q_0 = 1, Q
+// the precomputed products of b); only the wall rows change, and they couple
+// the two parities, which live in the two class threads of a mode:
+//   omega_y, W:  f(-1) = S_e - S_o,  Df(+1) = S2_e + S2_o
+//                (S = sum over the parity of f_n, S2 = sum of n^2 f_n);
+//   U:           the same two rows and the flow rate, with the response to
+//                the unknown forcing (even parity);
+//   v:           v(+-1) stay Dirichlet per parity; phi = P + c vh per parity,
+//                and D^2 v(+1) = A_e + A_o, Dv(-1) = -B_e + B_o
+//                (A = sum n^2 (n^2 - 1) / 3 v_n, B = sum n^2 v_n) fix c_e, c_o.
+// With the shifted unknowns f' = f + cc f_old every row's value is cc times
+// that row applied to the old field.  Each thread of a pair publishes the
+// sums of its parity; after a barrier both solve the same closure, summing
+// in parity order, so both find the same coefficients.
+// ---------------------------------------------------------------------------
+
+// The affine family of one parity: f_i = P_i (i >= 1), f_0 = 0, with
+// sp = sum P and sp2 = sum n^2 P (the same elimination as tau_seq).
+template <int MH, class Tab>
+__device__ __forceinline__ void tau_affine(int N, int ny, int sig, const double (&r)[MH], double (&f)[MH],
+                                           const Tab& T, const double* __restrict__ rowc, double& sp, double& sp2) {
+  const int M = (N - sig) / 2 + 1;
+  double anext = 0.0;
+#pragma unroll
+  for (int i = MH - 1; i >= 1; --i) {
+    if (i < M) {
+      const int n = 2 * i + sig;
+      double R = rowc[n] * r[i - 1] - rowc[ny + n] * r[i];
+      if (i + 1 < MH && i + 1 < M) R += rowc[2 * ny + n] * r[i + 1 < MH ? i + 1 : i];
+      const double a = T.e(i) * R - T.h(i) * anext;
+      f[i] = a;
+      anext = a;
+    }
+  }
+  double Pp = 0.0;
+  sp = 0.0;
+  sp2 = 0.0;
+#pragma unroll
+  for (int i = 1; i < MH; ++i) {
+    if (i < M) {
+      const double n = 2 * i + sig;
+      Pp = f[i] + T.b(i) * Pp;
+      f[i] = Pp;
+      sp += Pp;
+      sp2 += n * n * Pp;
+    }
+  }
+  f[0] = 0.0;
+}
+
+// f = P + x Q
+template <int MH, class Tab>
+__device__ __forceinline__ void tau_close(int N, int sig, double (&f)[MH], const Tab& T, double x) {
+  const int M = (N - sig) / 2 + 1;
+  f[0] = x;
+#pragma unroll
+  for (int i = 1; i < MH; ++i)
+    if (i < M) f[i] += T.Q(i) * x;
+}
+
+// a11 x1 + a12 x2 = b1, a21 x1 + a22 x2 = b2 (Cramer's rule)
+__device__ __forceinline__ void solve2(double a11, double a12, double a21, double a22, double b1, double b2,
+                                       double* x1, double* x2) {
+  const double id = 1.0 / (a11 * a22 - a12 * a21);
+  *x1 = (b1 * a22 - a12 * b2) * id;
+  *x2 = (a11 * b2 - a21 * b1) * id;
+}
+
+// Dirichlet bottom and Neumann top rows over the two parities of omega_y or W.
+// se, so: {sum P, sum n^2 P, sum f_old, sum n^2 f_old} of the even and odd
+// parity; q*: the table sums sum Q and sum n^2 Q.
+__device__ __forceinline__ void close_neumann_top(const double* se, const double* so, double qe, double qo,
+                                                  double q2e, double q2o, double cc, double* xe, double* xo) {
+  solve2(qe, -qo, q2e, q2o, cc * (se[2] - so[2]) - (se[0] - so[0]), cc * (se[3] + so[3]) - (se[1] + so[1]), xe, xo);
+}
+
+// Influence coefficients of v: se, so = {A_p, B_p, A_old, B_old}; a*, b*: A
+// and B of the homogeneous solutions vh of the two parities.
+__device__ __forceinline__ void close_free_slip_v(const double* se, const double* so, double ae, double ao,
+                                                  double be, double bo, double cc, double* ce, double* co) {
+  solve2(ae, ao, -be, bo, cc * (se[2] + so[2]) - (se[0] + so[0]), cc * (so[3] - se[3]) - (so[1] - se[1]), ce, co);
+}
+
+// Mean U at constant flow rate: unknowns (x_e, x_o, forcing).  se = {sum P,
+// sum n^2 P, sum U_old, sum n^2 U_old, int P, int U_old}, so = the first four
+// of the odd parity; q*: sum Q, sum n^2 Q; wq: int Q_e; u*: sum, sum n^2 and
+// int of the forcing response (even).  int = sum of 2 / (1 - n^2) x_n.
+__device__ __forceinline__ void close_free_slip_mean(const double* se, const double* so, double qe, double qo,
+                                                     double q2e, double q2o, double wq, double us, double u2,
+                                                     double uw, double cc, double flux, double* xe, double* xo,
+                                                     double* fc) {
+  const double a11 = qe, a12 = -qo, a13 = us;
+  const double a21 = q2e, a22 = q2o, a23 = u2;
+  const double a31 = wq, a32 = 0.0, a33 = uw;
+  const double b1 = cc * (se[2] - so[2]) - (se[0] - so[0]);
+  const double b2 = cc * (se[3] + so[3]) - (se[1] + so[1]);
+  const double b3 = flux + cc * se[5] - se[4];
+  const double m1 = a22 * a33 - a23 * a32, m2 = a21 * a33 - a23 * a31, m3 = a21 * a32 - a22 * a31;
+  const double id = 1.0 / (a11 * m1 - a12 * m2 + a13 * m3);
+  *xe = (b1 * m1 - a12 * (b2 * a33 - a23 * b3) + a13 * (b2 * a32 - a22 * b3)) * id;
+  *xo = (a11 * (b2 * a33 - a23 * b3) - b1 * m2 + a13 * (a21 * b3 - b2 * a31)) * id;
+  *fc = (a11 * (a22 * b3 - b2 * a32) - a12 * (a21 * b3 - b2 * a31) + b1 * m3) * id;
+}
+
 // Right-hand side of the v equation of parity sv and component r, one walk
 // from n = N down to 0 carrying Dv, D^2 v, t = i kx H_x + i kz H_z and Dt;
 // also stores h_v for the next stage.  Iteration i runs the other-parity step
@@ -637,7 +744,7 @@ __global__ void __launch_bounds__(128) stage_pre_kernel(Grid g, int B, PencilBuf
 // 1-c, e = 1 v on parity c.  The mean mode solves U at constant flow rate
 // (e = 0) and W (e = 1) on parity c, real component only.
 // ---------------------------------------------------------------------------
-template <typename RN, int MH>
+template <typename RN, int MH, int TOP>
 __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBufs pb, DevTables t,
                                                         const typename cpx<RN>::T* __restrict__ hn, StageCoef sc,
                                                         int ppc) {
@@ -766,13 +873,158 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
     __syncthreads();
   }
 
-  // ---- implicit solves
-  const int pl = tid % ppc;
-  const int combo = tid / ppc;
-  const int p = p0 + pl;
-  if (p < P && combo < 8) {
+  if constexpr (TOP == 0) {
+    // ---- implicit solves
+    const int pl = tid % ppc;
+    const int combo = tid / ppc;
+    const int p = p0 + pl;
+    if (p < P && combo < 8) {
+      const int c = combo & 1, r = (combo >> 1) & 1, e = combo >> 2;
+      const int row = p / g.nxh, ix = p % g.nxh;
+      const double cc = sc.alpha / sc.beta;
+      const double ibdn = 1.0 / (sc.beta * sc.dt * sc.nu);
+      const double* rowc = t.tau.rowc;
+      const CN* Hx = reinterpret_cast<const CN*>(sH) + pl;
+      const CN* Hy = Hx + ny * ppc;
+      const CN* Hz = Hy + ny * ppc;
+      auto helm = [&](int sig) { return TabSm{sh + sig * 4 * Mh * ppc + pl, Mh, ppc}; };
+      auto comp = [](auto z, int qd) { return qd == 0 ? z.x : z.y; };
+      const RN dtn = (RN)sc.dt, gan = (RN)sc.gamma, zen = (RN)sc.zeta;
+      if (row == g.nz / 2) {
+        // Nyquist row stays zero
+      } else if (p == 0) {
+        if (r == 0) {
+          const int s = c;
+          const int M = (N - s) / 2 + 1;
+          double* X = (e == 0 ? pb.UM : pb.WM) + (size_t)b * ny;
+          double* XP = (e == 0 ? pb.HXP : pb.HZP) + (size_t)b * ny;
+          const CN* Hm = (e == 0) ? Hx : Hz;
+          double rhs[MH], f[MH];
+          double sum = 0.0, flux_old = 0.0;
+  #pragma unroll
+          for (int i = 0; i < MH; ++i) {
+            rhs[i] = 0.0;
+            if (i < M) {
+              const int n = 2 * i + s;
+              const double xn = X[n];
+              const double hv = (double)Hm[n * ppc].x;
+              const double hp = XP[n];
+              XP[n] = hv;
+              rhs[i] = -((1.0 + cc) * xn + sc.dt * (sc.gamma * hv + sc.zeta * hp)) * ibdn;
+              sum += xn;
+              if (s == 0) flux_old += 2.0 / (1.0 - (double)n * n) * xn;
+            }
+          }
+          tau_seq<MH>(N, ny, s, rhs, f, helm(s), ss[(0 * 2 + s) * ppc + pl], cc * sum, rowc);
+          double fc = 0.0;
+          if (e == 0 && s == 0) {
+            double flux = 0.0;
+  #pragma unroll
+            for (int i = 0; i < MH; ++i)
+              if (i < M) flux += 2.0 / (1.0 - 4.0 * (double)i * i) * f[i];
+            fc = (sc.flux + cc * flux_old - flux) * t.tau.u1_iflux[sc.k];
+          }
+  #pragma unroll
+          for (int i = 0; i < MH; ++i) {
+            if (i < M) {
+              const int n = 2 * i + s;
+              double v = f[i] - cc * X[n];
+              if (e == 0 && s == 0) v += fc * t.tau.u1[(size_t)sc.k * Mh + i];
+              X[n] = v;
+            }
+          }
+        }
+      } else {
+        const double kx = t.kx[ix], kz = t.kz[row], k2 = kx * kx + kz * kz;
+        const double sgn = (r == 0) ? -1.0 : 1.0;
+        const int ra = 1 - r;
+        if (e == 0) {
+          // wall-normal vorticity, parity 1 - c
+          const int sq = 1 - c;
+          const int M = (N - sq) / 2 + 1;
+          const CompS Gc{reinterpret_cast<double*>(sG) + 2 * pl + r, 2 * ppc};
+          const CompT<RN> HGc{reinterpret_cast<RN*>(sHG) + 2 * pl + r, 2 * ppc};
+          const RN sgnn = (RN)sgn, kxn = (RN)kx, kzn = (RN)kz;
+          double rhs[MH], f[MH];
+          double sum = 0.0;
+  #pragma unroll
+          for (int i = 0; i < MH; ++i) {
+            rhs[i] = 0.0;
+            if (i < M) {
+              const int n = 2 * i + sq;
+              const double gn = Gc[n];
+              // nonlinear part in the node precision
+              const RN hg = sgnn * (kzn * comp(Hx[n * ppc], ra) - kxn * comp(Hz[n * ppc], ra));
+              const RN hp = HGc[n];
+              HGc[n] = hg;
+              const RN q = dtn * (gan * hg + zen * hp);
+              rhs[i] = -((1.0 + cc) * gn + (double)q) * ibdn;
+              sum += gn;
+            }
+          }
+          tau_seq<MH>(N, ny, sq, rhs, f, helm(sq), ss[(0 * 2 + sq) * ppc + pl], cc * sum, rowc);
+  #pragma unroll
+          for (int i = 0; i < MH; ++i)
+            if (i < M) {
+              const int n = 2 * i + sq;
+              Gc[n] = f[i] - cc * Gc[n];
+            }
+        } else {
+          // wall-normal velocity, parity c
+          const int sv = c;
+          const int M = (N - sv) / 2 + 1;
+          const CompS Vc{reinterpret_cast<double*>(sV) + 2 * pl + r, 2 * ppc};
+          const CompT<RN> HVc{reinterpret_cast<RN*>(sHV) + 2 * pl + r, 2 * ppc};
+          double S0 = 0.0, S2 = 0.0;
+          double rhs[MH];
+  #pragma unroll
+          for (int i = 0; i < MH; ++i) rhs[i] = 0.0;
+          for (int i = 0; i < M; ++i) {
+            const int n = 2 * i + sv;
+            const double vn = Vc[n];
+            S0 += vn;
+            S2 += (double)n * n * vn;
+          }
+          // one walk from n = N down to 0: Dv, D^2 v, t = i kx H_x + i kz H_z, Dt
+          v_walk<MH, RN>(N, ny, ppc, sv, Vc, HVc, HVc, Hx, Hy, Hz, r, sgn, kx, kz, k2, cc, ibdn, sc, rhs);
+          double f[MH];
+          tau_seq<MH>(N, ny, sv, rhs, f, helm(sv), ss[(0 * 2 + sv) * ppc + pl], 0.0, rowc);
+          const size_t vo = (size_t)b * P + p;
+          const double vw =
+              comp(pb.vw_old[vo], r) + sc.theta * (comp(pb.vw_new[vo], r) - comp(pb.vw_old[vo], r));
+          const double s = ((sv == 0) ? 0.5 : -0.5) * vw + cc * S0;
+          const TabSm TP{sp + sv * 4 * Mh * ppc + pl, Mh, ppc};
+          tau_seq<MH>(N, ny, sv, f, rhs, TP, ss[(1 * 2 + sv) * ppc + pl], s, rowc);
+          double dp = 0.0;
+  #pragma unroll
+          for (int i = 0; i < MH; ++i)
+            if (i < M) {
+              const double n = 2 * i + sv;
+              dp += n * n * rhs[i];
+            }
+          const double cI = (cc * S2 - dp) * ss[(2 * 2 + sv) * ppc + pl];
+          const double* vh = svh + sv * Mh * ppc + pl;
+  #pragma unroll
+          for (int i = 0; i < MH; ++i)
+            if (i < M) {
+              const int n = 2 * i + sv;
+              Vc[n] = rhs[i] + cI * vh[i * ppc] - cc * Vc[n];
+            }
+        }
+      }
+    }
+  } else {
+    // ---- implicit solves under a free-slip top: each thread forms the
+    // affine family of its parity and publishes its sums; the closure follows
+    // the barrier.  Thread (mode, class c, component r, equation e) as above;
+    // its partner of the other parity is class 1 - c.
+    double* xch = reinterpret_cast<double*>(ss + 6 * ppc) + 12 * ppc;  // [8 ppc threads][6]
+    const int pl = tid % ppc;
+    const int combo = tid / ppc;
+    const int p = p0 + pl;
     const int c = combo & 1, r = (combo >> 1) & 1, e = combo >> 2;
     const int row = p / g.nxh, ix = p % g.nxh;
+    const bool live = p < P && combo < 8 && row != g.nz / 2 && !(p == 0 && r == 1);
     const double cc = sc.alpha / sc.beta;
     const double ibdn = 1.0 / (sc.beta * sc.dt * sc.nu);
     const double* rowc = t.tau.rowc;
@@ -782,124 +1034,168 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
     auto helm = [&](int sig) { return TabSm{sh + sig * 4 * Mh * ppc + pl, Mh, ppc}; };
     auto comp = [](auto z, int qd) { return qd == 0 ? z.x : z.y; };
     const RN dtn = (RN)sc.dt, gan = (RN)sc.gamma, zen = (RN)sc.zeta;
-    if (row == g.nz / 2) {
-      // Nyquist row stays zero
-    } else if (p == 0) {
-      if (r == 0) {
-        const int s = c;
-        const int M = (N - s) / 2 + 1;
+    const int pc = min(p, P - 1);
+    // table sums of both parities: sum Q, sum n^2 Q of this stage; A, B of vh
+    auto qs = [&](int sig, int w) { return t.tau.helm_top[((size_t)(sc.k * 2 + sig) * 2 + w) * P + pc]; };
+    auto vs = [&](int sig, int w) { return t.tau.vh_top[((size_t)(sc.k * 2 + sig) * 2 + w) * P + pc]; };
+    double* mine = xch + tid * 6;
+    const double* other = xch + ((combo ^ 1) * ppc + pl) * 6;
+    double f[MH], rhs[MH];
+    int sig = 0;
+    if (live) {
+      if (p == 0) {
+        // mean mode: U (e = 0) at constant flow rate, W (e = 1), parity c
+        sig = c;
+        const int M = (N - sig) / 2 + 1;
         double* X = (e == 0 ? pb.UM : pb.WM) + (size_t)b * ny;
         double* XP = (e == 0 ? pb.HXP : pb.HZP) + (size_t)b * ny;
         const CN* Hm = (e == 0) ? Hx : Hz;
-        double rhs[MH], f[MH];
-        double sum = 0.0, flux_old = 0.0;
+        double so = 0.0, so2 = 0.0, wo = 0.0;
 #pragma unroll
         for (int i = 0; i < MH; ++i) {
           rhs[i] = 0.0;
           if (i < M) {
-            const int n = 2 * i + s;
+            const int n = 2 * i + sig;
             const double xn = X[n];
             const double hv = (double)Hm[n * ppc].x;
             const double hp = XP[n];
             XP[n] = hv;
             rhs[i] = -((1.0 + cc) * xn + sc.dt * (sc.gamma * hv + sc.zeta * hp)) * ibdn;
-            sum += xn;
-            if (s == 0) flux_old += 2.0 / (1.0 - (double)n * n) * xn;
+            so += xn;
+            so2 += (double)n * n * xn;
+            if (sig == 0) wo += 2.0 / (1.0 - (double)n * n) * xn;
           }
         }
-        tau_seq<MH>(N, ny, s, rhs, f, helm(s), ss[(0 * 2 + s) * ppc + pl], cc * sum, rowc);
-        double fc = 0.0;
-        if (e == 0 && s == 0) {
-          double flux = 0.0;
+        double psum, psum2;
+        tau_affine<MH>(N, ny, sig, rhs, f, helm(sig), rowc, psum, psum2);
+        double wp = 0.0;
+        if (sig == 0) {
 #pragma unroll
           for (int i = 0; i < MH; ++i)
-            if (i < M) flux += 2.0 / (1.0 - 4.0 * (double)i * i) * f[i];
-          fc = (sc.flux + cc * flux_old - flux) * t.tau.u1_iflux[sc.k];
+            if (i < M) wp += 2.0 / (1.0 - 4.0 * (double)i * i) * f[i];
         }
-#pragma unroll
-        for (int i = 0; i < MH; ++i) {
-          if (i < M) {
-            const int n = 2 * i + s;
-            double v = f[i] - cc * X[n];
-            if (e == 0 && s == 0) v += fc * t.tau.u1[(size_t)sc.k * Mh + i];
-            X[n] = v;
-          }
-        }
-      }
-    } else {
-      const double kx = t.kx[ix], kz = t.kz[row], k2 = kx * kx + kz * kz;
-      const double sgn = (r == 0) ? -1.0 : 1.0;
-      const int ra = 1 - r;
-      if (e == 0) {
+        mine[0] = psum; mine[1] = psum2; mine[2] = so; mine[3] = so2; mine[4] = wp; mine[5] = wo;
+      } else if (e == 0) {
         // wall-normal vorticity, parity 1 - c
-        const int sq = 1 - c;
-        const int M = (N - sq) / 2 + 1;
+        sig = 1 - c;
+        const int M = (N - sig) / 2 + 1;
         const CompS Gc{reinterpret_cast<double*>(sG) + 2 * pl + r, 2 * ppc};
         const CompT<RN> HGc{reinterpret_cast<RN*>(sHG) + 2 * pl + r, 2 * ppc};
-        const RN sgnn = (RN)sgn, kxn = (RN)kx, kzn = (RN)kz;
-        double rhs[MH], f[MH];
-        double sum = 0.0;
+        const double sgn = (r == 0) ? -1.0 : 1.0;
+        const int ra = 1 - r;
+        const RN sgnn = (RN)sgn, kxn = (RN)t.kx[ix], kzn = (RN)t.kz[row];
+        double so = 0.0, so2 = 0.0;
 #pragma unroll
         for (int i = 0; i < MH; ++i) {
           rhs[i] = 0.0;
           if (i < M) {
-            const int n = 2 * i + sq;
+            const int n = 2 * i + sig;
             const double gn = Gc[n];
-            // nonlinear part in the node precision
             const RN hg = sgnn * (kzn * comp(Hx[n * ppc], ra) - kxn * comp(Hz[n * ppc], ra));
             const RN hp = HGc[n];
             HGc[n] = hg;
             const RN q = dtn * (gan * hg + zen * hp);
             rhs[i] = -((1.0 + cc) * gn + (double)q) * ibdn;
-            sum += gn;
+            so += gn;
+            so2 += (double)n * n * gn;
           }
         }
-        tau_seq<MH>(N, ny, sq, rhs, f, helm(sq), ss[(0 * 2 + sq) * ppc + pl], cc * sum, rowc);
-#pragma unroll
-        for (int i = 0; i < MH; ++i)
-          if (i < M) {
-            const int n = 2 * i + sq;
-            Gc[n] = f[i] - cc * Gc[n];
-          }
+        double psum, psum2;
+        tau_affine<MH>(N, ny, sig, rhs, f, helm(sig), rowc, psum, psum2);
+        mine[0] = psum; mine[1] = psum2; mine[2] = so; mine[3] = so2;
       } else {
-        // wall-normal velocity, parity c
-        const int sv = c;
-        const int M = (N - sv) / 2 + 1;
+        // wall-normal velocity, parity c: phi_p and v_p as in the no-slip
+        // channel (Dirichlet rows of both), then the sums of the free-slip rows
+        sig = c;
+        const int M = (N - sig) / 2 + 1;
+        const double kx = t.kx[ix], kz = t.kz[row], k2 = kx * kx + kz * kz;
+        const double sgn = (r == 0) ? -1.0 : 1.0;
         const CompS Vc{reinterpret_cast<double*>(sV) + 2 * pl + r, 2 * ppc};
         const CompT<RN> HVc{reinterpret_cast<RN*>(sHV) + 2 * pl + r, 2 * ppc};
-        double S0 = 0.0, S2 = 0.0;
-        double rhs[MH];
+        double S0 = 0.0, Bo = 0.0, Ao = 0.0;
 #pragma unroll
         for (int i = 0; i < MH; ++i) rhs[i] = 0.0;
         for (int i = 0; i < M; ++i) {
-          const int n = 2 * i + sv;
-          const double vn = Vc[n];
+          const double n = 2 * i + sig;
+          const double vn = Vc[2 * i + sig];
           S0 += vn;
-          S2 += (double)n * n * vn;
+          Bo += n * n * vn;
+          Ao += n * n * (n * n - 1.0) / 3.0 * vn;
         }
-        // one walk from n = N down to 0: Dv, D^2 v, t = i kx H_x + i kz H_z, Dt
-        v_walk<MH, RN>(N, ny, ppc, sv, Vc, HVc, HVc, Hx, Hy, Hz, r, sgn, kx, kz, k2, cc, ibdn, sc, rhs);
-        double f[MH];
-        tau_seq<MH>(N, ny, sv, rhs, f, helm(sv), ss[(0 * 2 + sv) * ppc + pl], 0.0, rowc);
+        v_walk<MH, RN>(N, ny, ppc, sig, Vc, HVc, HVc, Hx, Hy, Hz, r, sgn, kx, kz, k2, cc, ibdn, sc, rhs);
+        tau_seq<MH>(N, ny, sig, rhs, f, helm(sig), ss[(0 * 2 + sig) * ppc + pl], 0.0, rowc);
         const size_t vo = (size_t)b * P + p;
         const double vw =
             comp(pb.vw_old[vo], r) + sc.theta * (comp(pb.vw_new[vo], r) - comp(pb.vw_old[vo], r));
-        const double s = ((sv == 0) ? 0.5 : -0.5) * vw + cc * S0;
-        const TabSm TP{sp + sv * 4 * Mh * ppc + pl, Mh, ppc};
-        tau_seq<MH>(N, ny, sv, f, rhs, TP, ss[(1 * 2 + sv) * ppc + pl], s, rowc);
-        double dp = 0.0;
+        const double s = ((sig == 0) ? 0.5 : -0.5) * vw + cc * S0;
+        const TabSm TP{sp + sig * 4 * Mh * ppc + pl, Mh, ppc};
+        tau_seq<MH>(N, ny, sig, f, rhs, TP, ss[(1 * 2 + sig) * ppc + pl], s, rowc);
+        double Ap = 0.0, Bp = 0.0;
 #pragma unroll
         for (int i = 0; i < MH; ++i)
           if (i < M) {
-            const double n = 2 * i + sv;
-            dp += n * n * rhs[i];
+            const double n = 2 * i + sig;
+            Bp += n * n * rhs[i];
+            Ap += n * n * (n * n - 1.0) / 3.0 * rhs[i];
           }
-        const double cI = (cc * S2 - dp) * ss[(2 * 2 + sv) * ppc + pl];
-        const double* vh = svh + sv * Mh * ppc + pl;
+        mine[0] = Ap; mine[1] = Bp; mine[2] = Ao; mine[3] = Bo;
+      }
+    }
+    __syncthreads();
+    if (live) {
+      const double* se = sig == 0 ? mine : other;
+      const double* so = sig == 0 ? other : mine;
+      const int M = (N - sig) / 2 + 1;
+      if (p == 0) {
+        double* X = (e == 0 ? pb.UM : pb.WM) + (size_t)b * ny;
+        double xe, xo, fc = 0.0;
+        if (e == 1) {
+          close_neumann_top(se, so, qs(0, 0), qs(1, 0), qs(0, 1), qs(1, 1), cc, &xe, &xo);
+        } else {
+          // forcing response (even parity) and int Q_e
+          const double* u1 = t.tau.u1 + (size_t)sc.k * Mh;
+          const TabSm He = helm(0);
+          double us = 0.0, u2 = 0.0, uw = 0.0, wq = 0.0;
+          for (int i = 0; i < N / 2 + 1; ++i) {
+            const double n = 2 * i, w = 2.0 / (1.0 - n * n);
+            us += u1[i];
+            u2 += n * n * u1[i];
+            uw += w * u1[i];
+            wq += w * (i == 0 ? 1.0 : He.Q(i));
+          }
+          close_free_slip_mean(se, so, qs(0, 0), qs(1, 0), qs(0, 1), qs(1, 1), wq, us, u2, uw, cc, sc.flux, &xe,
+                               &xo, &fc);
+        }
+        tau_close<MH>(N, sig, f, helm(sig), sig == 0 ? xe : xo);
 #pragma unroll
         for (int i = 0; i < MH; ++i)
           if (i < M) {
-            const int n = 2 * i + sv;
+            const int n = 2 * i + sig;
+            double v = f[i] - cc * X[n];
+            if (e == 0 && sig == 0) v += fc * t.tau.u1[(size_t)sc.k * Mh + i];
+            X[n] = v;
+          }
+      } else if (e == 0) {
+        const CompS Gc{reinterpret_cast<double*>(sG) + 2 * pl + r, 2 * ppc};
+        double xe, xo;
+        close_neumann_top(se, so, qs(0, 0), qs(1, 0), qs(0, 1), qs(1, 1), cc, &xe, &xo);
+        tau_close<MH>(N, sig, f, helm(sig), sig == 0 ? xe : xo);
+#pragma unroll
+        for (int i = 0; i < MH; ++i)
+          if (i < M) {
+            const int n = 2 * i + sig;
+            Gc[n] = f[i] - cc * Gc[n];
+          }
+      } else {
+        const CompS Vc{reinterpret_cast<double*>(sV) + 2 * pl + r, 2 * ppc};
+        double ce, co;
+        close_free_slip_v(se, so, vs(0, 0), vs(1, 0), vs(0, 1), vs(1, 1), cc, &ce, &co);
+        const double cI = sig == 0 ? ce : co;
+        const double* vh = svh + sig * Mh * ppc + pl;
+#pragma unroll
+        for (int i = 0; i < MH; ++i)
+          if (i < M) {
+            const int n = 2 * i + sig;
             Vc[n] = rhs[i] + cI * vh[i * ppc] - cc * Vc[n];
           }
       }
@@ -933,7 +1229,7 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
 // analysis runs field by field with four threads per mode (n = q + 4k); each
 // coefficient is accumulated in the same order as in the per-tile form.
 // ---------------------------------------------------------------------------
-template <typename RN, int MH>
+template <typename RN, int MH, int TOP>
 __global__ void __launch_bounds__(64) stage_post_batched_kernel(Grid g, int B, PencilBufs pb, DevTables t,
                                                                 const typename cpx<RN>::T* __restrict__ hn,
                                                                 StageCoef sc, int ppc) {
@@ -1021,142 +1317,334 @@ __global__ void __launch_bounds__(64) stage_post_batched_kernel(Grid g, int B, P
     __syncthreads();
   }
 
-  // ---- implicit solves (no barrier below)
-  const int p = p0 + pl;
-  if (p >= P) return;
-  const int row = p / g.nxh, ix = p % g.nxh;
-  if (row == g.nz / 2) return;  // Nyquist row stays zero
-  const double cc = sc.alpha / sc.beta;
-  const double ibdn = 1.0 / (sc.beta * sc.dt * sc.nu);
-  const double* rowc = t.tau.rowc;
-  const CN* Hx = sN + pl;
-  const CN* Hy = Hx + ny * ppc;
-  const CN* Hz = Hy + ny * ppc;
-  auto comp = [](auto z, int qq) { return qq == 0 ? z.x : z.y; };
-  const RN dtn = (RN)sc.dt, gan = (RN)sc.gamma, zen = (RN)sc.zeta;
-  auto helm = [&](int sig) { return TabSm{t.tau.helm + (size_t)(sc.k * 2 + sig) * 4 * Mh * P + p, Mh, P}; };
-  auto helm_isq = [&](int sig) { return t.tau.helm_isq[(size_t)(sc.k * 2 + sig) * P + p]; };
-  if (p == 0) {
-    // mean mode: U (r = 0) at constant flow rate and W (r = 1), parity c
-    const int e = r, s = c;
-    const int M = (N - s) / 2 + 1;
-    double* X = (e == 0 ? pb.UM : pb.WM) + (size_t)b * ny;
-    double* XP = (e == 0 ? pb.HXP : pb.HZP) + (size_t)b * ny;
-    const CN* Hm = (e == 0) ? Hx : Hz;
-    double rhs[MH], f[MH];
-    double sum = 0.0, flux_old = 0.0;
-#pragma unroll
-    for (int i = 0; i < MH; ++i) {
-      rhs[i] = 0.0;
-      if (i < M) {
-        const int n = 2 * i + s;
-        const double xn = X[n];
-        const double hv = (double)Hm[n * ppc].x;
-        const double hp = XP[n];
-        XP[n] = hv;
-        rhs[i] = -((1.0 + cc) * xn + sc.dt * (sc.gamma * hv + sc.zeta * hp)) * ibdn;
-        sum += xn;
-        if (s == 0) flux_old += 2.0 / (1.0 - (double)n * n) * xn;
+  if constexpr (TOP == 0) {
+    // ---- implicit solves (no barrier below)
+    const int p = p0 + pl;
+    if (p >= P) return;
+    const int row = p / g.nxh, ix = p % g.nxh;
+    if (row == g.nz / 2) return;  // Nyquist row stays zero
+    const double cc = sc.alpha / sc.beta;
+    const double ibdn = 1.0 / (sc.beta * sc.dt * sc.nu);
+    const double* rowc = t.tau.rowc;
+    const CN* Hx = sN + pl;
+    const CN* Hy = Hx + ny * ppc;
+    const CN* Hz = Hy + ny * ppc;
+    auto comp = [](auto z, int qq) { return qq == 0 ? z.x : z.y; };
+    const RN dtn = (RN)sc.dt, gan = (RN)sc.gamma, zen = (RN)sc.zeta;
+    auto helm = [&](int sig) { return TabSm{t.tau.helm + (size_t)(sc.k * 2 + sig) * 4 * Mh * P + p, Mh, P}; };
+    auto helm_isq = [&](int sig) { return t.tau.helm_isq[(size_t)(sc.k * 2 + sig) * P + p]; };
+    if (p == 0) {
+      // mean mode: U (r = 0) at constant flow rate and W (r = 1), parity c
+      const int e = r, s = c;
+      const int M = (N - s) / 2 + 1;
+      double* X = (e == 0 ? pb.UM : pb.WM) + (size_t)b * ny;
+      double* XP = (e == 0 ? pb.HXP : pb.HZP) + (size_t)b * ny;
+      const CN* Hm = (e == 0) ? Hx : Hz;
+      double rhs[MH], f[MH];
+      double sum = 0.0, flux_old = 0.0;
+  #pragma unroll
+      for (int i = 0; i < MH; ++i) {
+        rhs[i] = 0.0;
+        if (i < M) {
+          const int n = 2 * i + s;
+          const double xn = X[n];
+          const double hv = (double)Hm[n * ppc].x;
+          const double hp = XP[n];
+          XP[n] = hv;
+          rhs[i] = -((1.0 + cc) * xn + sc.dt * (sc.gamma * hv + sc.zeta * hp)) * ibdn;
+          sum += xn;
+          if (s == 0) flux_old += 2.0 / (1.0 - (double)n * n) * xn;
+        }
       }
+      tau_seq<MH>(N, ny, s, rhs, f, helm(s), helm_isq(s), cc * sum, rowc);
+      double fc = 0.0;
+      if (e == 0 && s == 0) {
+        double flux = 0.0;
+  #pragma unroll
+        for (int i = 0; i < MH; ++i)
+          if (i < M) flux += 2.0 / (1.0 - 4.0 * (double)i * i) * f[i];
+        fc = (sc.flux + cc * flux_old - flux) * t.tau.u1_iflux[sc.k];
+      }
+  #pragma unroll
+      for (int i = 0; i < MH; ++i) {
+        if (i < M) {
+          const int n = 2 * i + s;
+          double v = f[i] - cc * X[n];
+          if (e == 0 && s == 0) v += fc * t.tau.u1[(size_t)sc.k * Mh + i];
+          X[n] = v;
+        }
+      }
+      return;
     }
-    tau_seq<MH>(N, ny, s, rhs, f, helm(s), helm_isq(s), cc * sum, rowc);
-    double fc = 0.0;
-    if (e == 0 && s == 0) {
-      double flux = 0.0;
-#pragma unroll
+    const double kx = t.kx[ix], kz = t.kz[row], k2 = kx * kx + kz * kz;
+    const double sgn = (r == 0) ? -1.0 : 1.0;
+    const int ra = 1 - r;
+    const size_t base = 2 * ((size_t)b * ny * P + p) + r;  // component r of element n at base + 2 P n
+    {
+      // wall-normal vorticity, parity 1 - c
+      const int sq = 1 - c;
+      const int M = (N - sq) / 2 + 1;
+      const CompS Gc{reinterpret_cast<double*>(pb.G) + base, 2 * P};
+      // previous right-hand sides are stored in the node precision
+      const CompT<RN> HGc{reinterpret_cast<RN*>(pb.HGP) + base, 2 * P};
+      const CompT<RN> HGr = kStageH ? CompT<RN>{reinterpret_cast<RN*>(sHGt) + 2 * pl + r, 2 * ppc} : HGc;
+      const RN sgnn = (RN)sgn, kxn = (RN)kx, kzn = (RN)kz;
+      double rhs[MH], f[MH];
+      double sum = 0.0;
+  #pragma unroll
+      for (int i = 0; i < MH; ++i) {
+        rhs[i] = 0.0;
+        if (i < M) {
+          const int n = 2 * i + sq;
+          const double gn = Gc[n];
+          const RN hg = sgnn * (kzn * comp(Hx[n * ppc], ra) - kxn * comp(Hz[n * ppc], ra));
+          const RN hp = HGr[n];
+          HGc[n] = hg;
+          const RN q = dtn * (gan * hg + zen * hp);
+          rhs[i] = -((1.0 + cc) * gn + (double)q) * ibdn;
+          sum += gn;
+        }
+      }
+      tau_seq<MH>(N, ny, sq, rhs, f, helm(sq), helm_isq(sq), cc * sum, rowc);
+  #pragma unroll
       for (int i = 0; i < MH; ++i)
-        if (i < M) flux += 2.0 / (1.0 - 4.0 * (double)i * i) * f[i];
-      fc = (sc.flux + cc * flux_old - flux) * t.tau.u1_iflux[sc.k];
+        if (i < M) {
+          const int n = 2 * i + sq;
+          Gc[n] = f[i] - cc * Gc[n];
+        }
     }
-#pragma unroll
-    for (int i = 0; i < MH; ++i) {
-      if (i < M) {
-        const int n = 2 * i + s;
-        double v = f[i] - cc * X[n];
-        if (e == 0 && s == 0) v += fc * t.tau.u1[(size_t)sc.k * Mh + i];
-        X[n] = v;
-      }
-    }
-    return;
-  }
-  const double kx = t.kx[ix], kz = t.kz[row], k2 = kx * kx + kz * kz;
-  const double sgn = (r == 0) ? -1.0 : 1.0;
-  const int ra = 1 - r;
-  const size_t base = 2 * ((size_t)b * ny * P + p) + r;  // component r of element n at base + 2 P n
-  {
-    // wall-normal vorticity, parity 1 - c
-    const int sq = 1 - c;
-    const int M = (N - sq) / 2 + 1;
-    const CompS Gc{reinterpret_cast<double*>(pb.G) + base, 2 * P};
-    // previous right-hand sides are stored in the node precision
-    const CompT<RN> HGc{reinterpret_cast<RN*>(pb.HGP) + base, 2 * P};
-    const CompT<RN> HGr = kStageH ? CompT<RN>{reinterpret_cast<RN*>(sHGt) + 2 * pl + r, 2 * ppc} : HGc;
-    const RN sgnn = (RN)sgn, kxn = (RN)kx, kzn = (RN)kz;
-    double rhs[MH], f[MH];
-    double sum = 0.0;
-#pragma unroll
-    for (int i = 0; i < MH; ++i) {
-      rhs[i] = 0.0;
-      if (i < M) {
-        const int n = 2 * i + sq;
-        const double gn = Gc[n];
-        const RN hg = sgnn * (kzn * comp(Hx[n * ppc], ra) - kxn * comp(Hz[n * ppc], ra));
-        const RN hp = HGr[n];
-        HGc[n] = hg;
-        const RN q = dtn * (gan * hg + zen * hp);
-        rhs[i] = -((1.0 + cc) * gn + (double)q) * ibdn;
-        sum += gn;
-      }
-    }
-    tau_seq<MH>(N, ny, sq, rhs, f, helm(sq), helm_isq(sq), cc * sum, rowc);
-#pragma unroll
-    for (int i = 0; i < MH; ++i)
-      if (i < M) {
-        const int n = 2 * i + sq;
-        Gc[n] = f[i] - cc * Gc[n];
-      }
-  }
-  {
-    // wall-normal velocity, parity c
-    const int sv = c;
-    const int M = (N - sv) / 2 + 1;
-    const CompS Vc{reinterpret_cast<double*>(pb.V) + base, 2 * P};
-    const CompT<RN> HVc{reinterpret_cast<RN*>(pb.HVP) + base, 2 * P};
-    const CompT<RN> HVr = kStageH ? CompT<RN>{reinterpret_cast<RN*>(sHVt) + 2 * pl + r, 2 * ppc} : HVc;
-    double S0 = 0.0, S2 = 0.0;
-    double rhs[MH];
-#pragma unroll
-    for (int i = 0; i < MH; ++i) rhs[i] = 0.0;
-    for (int i = 0; i < M; ++i) {
-      const int n = 2 * i + sv;
-      const double vn = Vc[n];
-      S0 += vn;
-      S2 += (double)n * n * vn;
-    }
-    v_walk<MH, RN>(N, ny, ppc, sv, Vc, HVr, HVc, Hx, Hy, Hz, r, sgn, kx, kz, k2, cc, ibdn, sc, rhs);
-    double f[MH];
-    tau_seq<MH>(N, ny, sv, rhs, f, helm(sv), helm_isq(sv), 0.0, rowc);
-    const size_t vo = (size_t)b * P + p;
-    const double vw =
-        comp(pb.vw_old[vo], r) + sc.theta * (comp(pb.vw_new[vo], r) - comp(pb.vw_old[vo], r));
-    const double s = ((sv == 0) ? 0.5 : -0.5) * vw + cc * S0;
-    const TabSm TP{t.tau.pois + (size_t)sv * 4 * Mh * P + p, Mh, P};
-    tau_seq<MH>(N, ny, sv, f, rhs, TP, t.tau.pois_isq[(size_t)sv * P + p], s, rowc);
-    double dp = 0.0;
-#pragma unroll
-    for (int i = 0; i < MH; ++i)
-      if (i < M) {
-        const double n = 2 * i + sv;
-        dp += n * n * rhs[i];
-      }
-    const double cI = (cc * S2 - dp) * t.tau.vh_idv[(size_t)(sc.k * 2 + sv) * P + p];
-    const double* vh = t.tau.vh + (size_t)(sc.k * 2 + sv) * Mh * P + p;
-#pragma unroll
-    for (int i = 0; i < MH; ++i)
-      if (i < M) {
+    {
+      // wall-normal velocity, parity c
+      const int sv = c;
+      const int M = (N - sv) / 2 + 1;
+      const CompS Vc{reinterpret_cast<double*>(pb.V) + base, 2 * P};
+      const CompT<RN> HVc{reinterpret_cast<RN*>(pb.HVP) + base, 2 * P};
+      const CompT<RN> HVr = kStageH ? CompT<RN>{reinterpret_cast<RN*>(sHVt) + 2 * pl + r, 2 * ppc} : HVc;
+      double S0 = 0.0, S2 = 0.0;
+      double rhs[MH];
+  #pragma unroll
+      for (int i = 0; i < MH; ++i) rhs[i] = 0.0;
+      for (int i = 0; i < M; ++i) {
         const int n = 2 * i + sv;
-        Vc[n] = rhs[i] + cI * vh[(size_t)i * P] - cc * Vc[n];
+        const double vn = Vc[n];
+        S0 += vn;
+        S2 += (double)n * n * vn;
       }
+      v_walk<MH, RN>(N, ny, ppc, sv, Vc, HVr, HVc, Hx, Hy, Hz, r, sgn, kx, kz, k2, cc, ibdn, sc, rhs);
+      double f[MH];
+      tau_seq<MH>(N, ny, sv, rhs, f, helm(sv), helm_isq(sv), 0.0, rowc);
+      const size_t vo = (size_t)b * P + p;
+      const double vw =
+          comp(pb.vw_old[vo], r) + sc.theta * (comp(pb.vw_new[vo], r) - comp(pb.vw_old[vo], r));
+      const double s = ((sv == 0) ? 0.5 : -0.5) * vw + cc * S0;
+      const TabSm TP{t.tau.pois + (size_t)sv * 4 * Mh * P + p, Mh, P};
+      tau_seq<MH>(N, ny, sv, f, rhs, TP, t.tau.pois_isq[(size_t)sv * P + p], s, rowc);
+      double dp = 0.0;
+  #pragma unroll
+      for (int i = 0; i < MH; ++i)
+        if (i < M) {
+          const double n = 2 * i + sv;
+          dp += n * n * rhs[i];
+        }
+      const double cI = (cc * S2 - dp) * t.tau.vh_idv[(size_t)(sc.k * 2 + sv) * P + p];
+      const double* vh = t.tau.vh + (size_t)(sc.k * 2 + sv) * Mh * P + p;
+  #pragma unroll
+      for (int i = 0; i < MH; ++i)
+        if (i < M) {
+          const int n = 2 * i + sv;
+          Vc[n] = rhs[i] + cI * vh[(size_t)i * P] - cc * Vc[n];
+        }
+    }
+  } else {
+    // ---- implicit solves under a free-slip top, in two rounds (omega_y or
+    // the mean flow, then v), each closed after a barrier by the pair of class
+    // threads (c, 1 - c) of a (mode, component); every thread reaches both
+    // barriers
+    double* xch = reinterpret_cast<double*>(smem_raw + (size_t)(3 * ny + 6) * ppc * sizeof(double2));  // [2][4 ppc][6]
+    const int p = p0 + pl;
+    const int pc = min(p, P - 1);
+    const int row = pc / g.nxh, ix = pc % g.nxh;
+    const bool live = p < P && row != g.nz / 2;
+    const bool mean = p == 0;
+    const int mate = (1 - c) * 2 * ppc + tid % (2 * ppc);
+    const double cc = sc.alpha / sc.beta;
+    const double ibdn = 1.0 / (sc.beta * sc.dt * sc.nu);
+    const double* rowc = t.tau.rowc;
+    const CN* Hx = sN + pl;
+    const CN* Hy = Hx + ny * ppc;
+    const CN* Hz = Hy + ny * ppc;
+    auto comp = [](auto z, int qq) { return qq == 0 ? z.x : z.y; };
+    const RN dtn = (RN)sc.dt, gan = (RN)sc.gamma, zen = (RN)sc.zeta;
+    auto helm = [&](int sig) { return TabSm{t.tau.helm + (size_t)(sc.k * 2 + sig) * 4 * Mh * P + pc, Mh, P}; };
+    auto helm_isq = [&](int sig) { return t.tau.helm_isq[(size_t)(sc.k * 2 + sig) * P + pc]; };
+    auto qs = [&](int sig, int w) { return t.tau.helm_top[((size_t)(sc.k * 2 + sig) * 2 + w) * P + pc]; };
+    auto vs = [&](int sig, int w) { return t.tau.vh_top[((size_t)(sc.k * 2 + sig) * 2 + w) * P + pc]; };
+    const size_t base = 2 * ((size_t)b * ny * P + pc) + r;  // component r of element n at base + 2 P n
+    const double sgn = (r == 0) ? -1.0 : 1.0;
+    const int ra = 1 - r;
+    double f[MH], rhs[MH];
+    // round 1: the mean mode (U for r = 0, W for r = 1) on parity c, or
+    // omega_y on parity 1 - c
+    {
+      const int sig = mean ? c : 1 - c;
+      const int M = (N - sig) / 2 + 1;
+      double* mine = xch + tid * 6;
+      const double* other = xch + mate * 6;
+      if (live) {
+        if (mean) {
+          double* X = (r == 0 ? pb.UM : pb.WM) + (size_t)b * ny;
+          double* XP = (r == 0 ? pb.HXP : pb.HZP) + (size_t)b * ny;
+          const CN* Hm = (r == 0) ? Hx : Hz;
+          double so = 0.0, so2 = 0.0, wo = 0.0;
+#pragma unroll
+          for (int i = 0; i < MH; ++i) {
+            rhs[i] = 0.0;
+            if (i < M) {
+              const int n = 2 * i + sig;
+              const double xn = X[n];
+              const double hv = (double)Hm[n * ppc].x;
+              const double hp = XP[n];
+              XP[n] = hv;
+              rhs[i] = -((1.0 + cc) * xn + sc.dt * (sc.gamma * hv + sc.zeta * hp)) * ibdn;
+              so += xn;
+              so2 += (double)n * n * xn;
+              if (sig == 0) wo += 2.0 / (1.0 - (double)n * n) * xn;
+            }
+          }
+          double psum, psum2;
+          tau_affine<MH>(N, ny, sig, rhs, f, helm(sig), rowc, psum, psum2);
+          double wp = 0.0;
+          if (sig == 0) {
+#pragma unroll
+            for (int i = 0; i < MH; ++i)
+              if (i < M) wp += 2.0 / (1.0 - 4.0 * (double)i * i) * f[i];
+          }
+          mine[0] = psum; mine[1] = psum2; mine[2] = so; mine[3] = so2; mine[4] = wp; mine[5] = wo;
+        } else {
+          const CompS Gc{reinterpret_cast<double*>(pb.G) + base, 2 * P};
+          const CompT<RN> HGc{reinterpret_cast<RN*>(pb.HGP) + base, 2 * P};
+          const CompT<RN> HGr = kStageH ? CompT<RN>{reinterpret_cast<RN*>(sHGt) + 2 * pl + r, 2 * ppc} : HGc;
+          const RN sgnn = (RN)sgn, kxn = (RN)t.kx[ix], kzn = (RN)t.kz[row];
+          double so = 0.0, so2 = 0.0;
+#pragma unroll
+          for (int i = 0; i < MH; ++i) {
+            rhs[i] = 0.0;
+            if (i < M) {
+              const int n = 2 * i + sig;
+              const double gn = Gc[n];
+              const RN hg = sgnn * (kzn * comp(Hx[n * ppc], ra) - kxn * comp(Hz[n * ppc], ra));
+              const RN hp = HGr[n];
+              HGc[n] = hg;
+              const RN q = dtn * (gan * hg + zen * hp);
+              rhs[i] = -((1.0 + cc) * gn + (double)q) * ibdn;
+              so += gn;
+              so2 += (double)n * n * gn;
+            }
+          }
+          double psum, psum2;
+          tau_affine<MH>(N, ny, sig, rhs, f, helm(sig), rowc, psum, psum2);
+          mine[0] = psum; mine[1] = psum2; mine[2] = so; mine[3] = so2;
+        }
+      }
+      __syncthreads();
+      if (live) {
+        const double* se = sig == 0 ? mine : other;
+        const double* so = sig == 0 ? other : mine;
+        double xe, xo, fc = 0.0;
+        if (mean && r == 0) {
+          const double* u1 = t.tau.u1 + (size_t)sc.k * Mh;
+          const TabSm He = helm(0);
+          double us = 0.0, u2 = 0.0, uw = 0.0, wq = 0.0;
+          for (int i = 0; i < N / 2 + 1; ++i) {
+            const double n = 2 * i, w = 2.0 / (1.0 - n * n);
+            us += u1[i];
+            u2 += n * n * u1[i];
+            uw += w * u1[i];
+            wq += w * (i == 0 ? 1.0 : He.Q(i));
+          }
+          close_free_slip_mean(se, so, qs(0, 0), qs(1, 0), qs(0, 1), qs(1, 1), wq, us, u2, uw, cc, sc.flux, &xe,
+                               &xo, &fc);
+        } else {
+          close_neumann_top(se, so, qs(0, 0), qs(1, 0), qs(0, 1), qs(1, 1), cc, &xe, &xo);
+        }
+        tau_close<MH>(N, sig, f, helm(sig), sig == 0 ? xe : xo);
+        if (mean) {
+          double* X = (r == 0 ? pb.UM : pb.WM) + (size_t)b * ny;
+#pragma unroll
+          for (int i = 0; i < MH; ++i)
+            if (i < M) {
+              const int n = 2 * i + sig;
+              double v = f[i] - cc * X[n];
+              if (r == 0 && sig == 0) v += fc * t.tau.u1[(size_t)sc.k * Mh + i];
+              X[n] = v;
+            }
+        } else {
+          const CompS Gc{reinterpret_cast<double*>(pb.G) + base, 2 * P};
+#pragma unroll
+          for (int i = 0; i < MH; ++i)
+            if (i < M) {
+              const int n = 2 * i + sig;
+              Gc[n] = f[i] - cc * Gc[n];
+            }
+        }
+      }
+    }
+    // round 2: v on parity c (every mode but the mean)
+    {
+      const int sig = c;
+      const int M = (N - sig) / 2 + 1;
+      double* mine = xch + (4 * ppc + tid) * 6;
+      const double* other = xch + (4 * ppc + mate) * 6;
+      const bool on = live && !mean;
+      const CompS Vc{reinterpret_cast<double*>(pb.V) + base, 2 * P};
+      if (on) {
+        const double kx = t.kx[ix], kz = t.kz[row], k2 = kx * kx + kz * kz;
+        const CompT<RN> HVc{reinterpret_cast<RN*>(pb.HVP) + base, 2 * P};
+        const CompT<RN> HVr = kStageH ? CompT<RN>{reinterpret_cast<RN*>(sHVt) + 2 * pl + r, 2 * ppc} : HVc;
+        double S0 = 0.0, Bo = 0.0, Ao = 0.0;
+#pragma unroll
+        for (int i = 0; i < MH; ++i) rhs[i] = 0.0;
+        for (int i = 0; i < M; ++i) {
+          const double n = 2 * i + sig;
+          const double vn = Vc[2 * i + sig];
+          S0 += vn;
+          Bo += n * n * vn;
+          Ao += n * n * (n * n - 1.0) / 3.0 * vn;
+        }
+        v_walk<MH, RN>(N, ny, ppc, sig, Vc, HVr, HVc, Hx, Hy, Hz, r, sgn, kx, kz, k2, cc, ibdn, sc, rhs);
+        tau_seq<MH>(N, ny, sig, rhs, f, helm(sig), helm_isq(sig), 0.0, rowc);
+        const size_t vo = (size_t)b * P + pc;
+        const double vw =
+            comp(pb.vw_old[vo], r) + sc.theta * (comp(pb.vw_new[vo], r) - comp(pb.vw_old[vo], r));
+        const double s = ((sig == 0) ? 0.5 : -0.5) * vw + cc * S0;
+        const TabSm TP{t.tau.pois + (size_t)sig * 4 * Mh * P + pc, Mh, P};
+        tau_seq<MH>(N, ny, sig, f, rhs, TP, t.tau.pois_isq[(size_t)sig * P + pc], s, rowc);
+        double Ap = 0.0, Bp = 0.0;
+#pragma unroll
+        for (int i = 0; i < MH; ++i)
+          if (i < M) {
+            const double n = 2 * i + sig;
+            Bp += n * n * rhs[i];
+            Ap += n * n * (n * n - 1.0) / 3.0 * rhs[i];
+          }
+        mine[0] = Ap; mine[1] = Bp; mine[2] = Ao; mine[3] = Bo;
+      }
+      __syncthreads();
+      if (on) {
+        const double* se = sig == 0 ? mine : other;
+        const double* so = sig == 0 ? other : mine;
+        double ce, co;
+        close_free_slip_v(se, so, vs(0, 0), vs(1, 0), vs(0, 1), vs(1, 1), cc, &ce, &co);
+        const double cI = sig == 0 ? ce : co;
+        const double* vh = t.tau.vh + (size_t)(sc.k * 2 + sig) * Mh * P + pc;
+#pragma unroll
+        for (int i = 0; i < MH; ++i)
+          if (i < M) {
+            const int n = 2 * i + sig;
+            Vc[n] = rhs[i] + cI * vh[(size_t)i * P] - cc * Vc[n];
+          }
+      }
+    }
   }
 }
 
@@ -1173,25 +1661,25 @@ cudaError_t pre_mh(const Grid& g, int B, const PencilBufs& pb, const DevTables& 
                                         st, g, B, pb, t, q, ppc);
 }
 
-template <typename RN, int MH>
+template <typename RN, int MH, int TOP>
 cudaError_t post_mh(const Grid& g, int B, const PencilBufs& pb, const DevTables& t,
                            const typename cpx<RN>::T* h, const StageCoef& sc, int ppc, size_t smem,
                            cudaStream_t st) {
   static SmemLimit lim;
-  const cudaError_t e = raise_smem_limit(stage_post_kernel<RN, MH>, &lim, smem);
+  const cudaError_t e = raise_smem_limit(stage_post_kernel<RN, MH, TOP>, &lim, smem);
   if (e != cudaSuccess) return e;
-  return launch_pdl_if<sizeof(RN) == 4>(stage_post_kernel<RN, MH>, dim3((g.P + ppc - 1) / ppc, B), dim3(8 * ppc),
-                                        smem, st, g, B, pb, t, h, sc, ppc);
+  return launch_pdl_if<sizeof(RN) == 4>(stage_post_kernel<RN, MH, TOP>, dim3((g.P + ppc - 1) / ppc, B),
+                                        dim3(8 * ppc), smem, st, g, B, pb, t, h, sc, ppc);
 }
 
-template <typename RN, int MH>
+template <typename RN, int MH, int TOP>
 cudaError_t post_batched_mh(const Grid& g, int B, const PencilBufs& pb, const DevTables& t,
                                    const typename cpx<RN>::T* h, const StageCoef& sc, int ppc, size_t smem,
                                    cudaStream_t st) {
   static SmemLimit lim;
-  const cudaError_t e = raise_smem_limit(stage_post_batched_kernel<RN, MH>, &lim, smem);
+  const cudaError_t e = raise_smem_limit(stage_post_batched_kernel<RN, MH, TOP>, &lim, smem);
   if (e != cudaSuccess) return e;
-  return launch_pdl_if<sizeof(RN) == 4>(stage_post_batched_kernel<RN, MH>, dim3((g.P + ppc - 1) / ppc, B),
+  return launch_pdl_if<sizeof(RN) == 4>(stage_post_batched_kernel<RN, MH, TOP>, dim3((g.P + ppc - 1) / ppc, B),
                                         dim3(4 * ppc), smem, st, g, B, pb, t, h, sc, ppc);
 }
 
@@ -1206,18 +1694,25 @@ cudaError_t post_batched_mh(const Grid& g, int B, const PencilBufs& pb, const De
   template cudaError_t pre_mh<float, MH>(const Grid&, int, const PencilBufs&, const DevTables&, float2*, int,    \
                                          size_t, cudaStream_t);                                                \
   }
-#define CH_STAGE_POST(MH)                                                                                      \
+#define CH_STAGE_POST_TOP(MH, TOP)                                                                             \
   namespace chdns {                                                                                            \
-  template cudaError_t post_mh<double, MH>(const Grid&, int, const PencilBufs&, const DevTables&, const double2*, \
-                                           const StageCoef&, int, size_t, cudaStream_t);                       \
-  template cudaError_t post_mh<float, MH>(const Grid&, int, const PencilBufs&, const DevTables&, const float2*,   \
-                                          const StageCoef&, int, size_t, cudaStream_t);                        \
+  template cudaError_t post_mh<double, MH, TOP>(const Grid&, int, const PencilBufs&, const DevTables&,          \
+                                                const double2*, const StageCoef&, int, size_t, cudaStream_t);  \
+  template cudaError_t post_mh<float, MH, TOP>(const Grid&, int, const PencilBufs&, const DevTables&,           \
+                                               const float2*, const StageCoef&, int, size_t, cudaStream_t);    \
   }
-#define CH_STAGE_POST_BATCHED(MH)                                                                              \
+#define CH_STAGE_POST_BATCHED_TOP(MH, TOP)                                                                     \
   namespace chdns {                                                                                            \
-  template cudaError_t post_batched_mh<double, MH>(const Grid&, int, const PencilBufs&, const DevTables&,        \
-                                                   const double2*, const StageCoef&, int, size_t, cudaStream_t); \
-  template cudaError_t post_batched_mh<float, MH>(const Grid&, int, const PencilBufs&, const DevTables&,         \
-                                                  const float2*, const StageCoef&, int, size_t, cudaStream_t);  \
+  template cudaError_t post_batched_mh<double, MH, TOP>(const Grid&, int, const PencilBufs&, const DevTables&,  \
+                                                        const double2*, const StageCoef&, int, size_t,         \
+                                                        cudaStream_t);                                         \
+  template cudaError_t post_batched_mh<float, MH, TOP>(const Grid&, int, const PencilBufs&, const DevTables&,   \
+                                                       const float2*, const StageCoef&, int, size_t,           \
+                                                       cudaStream_t);                                          \
   }
+// no-slip upper wall (TOP = 0) for every bucket; the free-slip top (TOP = 1)
+// is instantiated for MH <= 33 (ny <= 65) in translation units of its own
+#define CH_STAGE_POST(MH) CH_STAGE_POST_TOP(MH, 0)
+#define CH_STAGE_POST_BATCHED(MH) CH_STAGE_POST_BATCHED_TOP(MH, 0)
 #define CH_STAGE_INSTANTIATE(MH) CH_STAGE_PRE(MH) CH_STAGE_POST(MH) CH_STAGE_POST_BATCHED(MH)
+#define CH_STAGE_INSTANTIATE_OPEN(MH) CH_STAGE_POST_TOP(MH, 1) CH_STAGE_POST_BATCHED_TOP(MH, 1)

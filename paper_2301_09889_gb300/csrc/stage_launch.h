@@ -13,10 +13,10 @@ namespace chdns {
 template <typename RN, int MH>
 cudaError_t pre_mh(const Grid& g, int B, const PencilBufs& pb, const DevTables& t, typename cpx<RN>::T* q, int ppc,
                    size_t smem, cudaStream_t st);
-template <typename RN, int MH>
+template <typename RN, int MH, int TOP>
 cudaError_t post_mh(const Grid& g, int B, const PencilBufs& pb, const DevTables& t, const typename cpx<RN>::T* h,
                     const StageCoef& sc, int ppc, size_t smem, cudaStream_t st);
-template <typename RN, int MH>
+template <typename RN, int MH, int TOP>
 cudaError_t post_batched_mh(const Grid& g, int B, const PencilBufs& pb, const DevTables& t,
                             const typename cpx<RN>::T* h, const StageCoef& sc, int ppc, size_t smem,
                             cudaStream_t st);

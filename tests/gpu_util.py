@@ -17,7 +17,7 @@ def rel_l2(a, b) -> float:
 
 def oracle_params(**kw) -> channel.Params:
     keys = ("nx", "ny", "nz", "lx", "lz", "re_tau", "re_bulk", "dt", "steps_per_action",
-            "y_sense_plus", "control", "alpha", "tau_ref")
+            "y_sense_plus", "control", "alpha", "tau_ref", "top_bc")
     return channel.Params(**{k: kw[k] for k in keys if k in kw})
 
 
@@ -37,7 +37,7 @@ def run_pair(native, kw: dict, nsteps: int, seed: int = 0, amp: float = 0.1, kma
     ops = channel.Operators(op)
     env = native.env_create(p)
     try:
-        fields = si.perturbed_poiseuille(op.nx, op.ny, op.nz, seed, amp, kmax)
+        fields = si.perturbed_poiseuille(op.nx, op.ny, op.nz, seed, amp, kmax, top_bc=op.top_bc)
         native.env_set_state(env, 0, native.pack_state(fields, op.nx, op.ny, op.nz))
         ost = channel.new_state(fields, op)
         lib_out, ora_out = [], []
@@ -81,7 +81,7 @@ def run_batch_pair(native, kw: dict, B: int, slots, nsteps: int, seed0: int = 30
         if tiles is not None:
             native.env_set_tiles(env, *tiles)
         info = native.env_info(env)
-        fields = [si.perturbed_poiseuille(nx, ny, nz, seed0 + e, amp, kmax) for e in range(B)]
+        fields = [si.perturbed_poiseuille(nx, ny, nz, seed0 + e, amp, kmax, top_bc=op.top_bc) for e in range(B)]
         for e in range(B):
             native.env_set_state(env, e, native.pack_state(fields[e], nx, ny, nz))
         acts = []

@@ -16,24 +16,27 @@ from oracle import channel
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-11   # relative L2, all-FP64 path
+# The wall shear nu sum_n (-1)^(n+1) n^2 U_n weighs the coefficients of U by
+# n^2: relative to the state its condition number nu ||n^2||_2 ||U||_2 / tau_w
+# is about 5e3 at 65 nodes and 2e4 at 129, so rounding-level state errors
+# (1e-15 .. 3e-14 measured) reach it as 1e-11 .. 1e-10.  Its bar, and the
+# reward's, is 1e-9 relative in the all-FP64 path.
+TAU_TOL = 1e-9
 
 MINIMAL = dict(nx=16, ny=65, nz=16, lx=2.67, lz=0.8, re_tau=180.0, re_bulk=2800.0, dt=0.005)
 LARGER = dict(nx=64, ny=65, nz=64, lx=2 * math.pi, lz=math.pi, re_tau=180.0, re_bulk=2800.0, dt=0.005)
 
 
-def _check_outputs(lib_out, ora_out, ost, kw, tol=TOL):
-    """Observation planes, wall shear and reward to `tol`, relative.  The
-    reward 1 - tau_w / tau_ref is measured against the size of its tau_w term
-    (the reward itself may be near zero).  (A looser bound follows from the
-    state tolerance alone: tau_w = nu sum_n (-1)^(n+1) n^2 U_n, so by
-    Cauchy-Schwarz |d tau_w| <= nu ||n^2||_2 tol ||U||_2; the measured errors
-    are far below it.)"""
+def _check_outputs(lib_out, ora_out, ost, kw, tol=TOL, tau_tol=TAU_TOL):
+    """Observation planes to `tol`, wall shear and reward to `tau_tol`,
+    relative.  The reward 1 - tau_w / tau_ref is measured against the size of
+    its tau_w term (the reward itself may be near zero)."""
     u_tau = kw["re_tau"] / kw["re_bulk"]
     tau_ref = kw.get("tau_ref", 0.0) or u_tau ** 2
     for (lo, lt, lr), (oo, ot, orr) in zip(lib_out, ora_out):
         assert rel_l2(lo, oo) < tol
-        assert abs(lt - ot) <= tol * abs(ot), (lt, ot)
-        assert abs(lr - orr) <= tol * max(abs(orr), abs(ot) / tau_ref), (lr, orr)
+        assert abs(lt - ot) <= tau_tol * abs(ot), (lt, ot)
+        assert abs(lr - orr) <= tau_tol * max(abs(orr), abs(ot) / tau_ref), (lr, orr)
 
 
 def test_single_step_minimal_channel(native_gpu):

@@ -77,9 +77,11 @@ def test_host_argument_checks(native):
 
 def test_env_create_rejects_unsupported_parameters_before_any_device_work(native):
     """Parameter checks run before env_create touches the device, so they hold
-    on a machine without a GPU: the free-slip top (top_bc = 1) is refused until
-    the library steps it, and malformed grids or modes are argument errors."""
-    cases = [(dict(top_bc=1), native.CH_ERR_UNSUPPORTED), (dict(precision=2), native.CH_ERR_UNSUPPORTED),
+    on a machine without a GPU: the free-slip top (top_bc = 1) is built for up
+    to 65 nodes, other wall conditions do not exist, and malformed grids or
+    modes are argument errors."""
+    cases = [(dict(top_bc=1, ny=129), native.CH_ERR_UNSUPPORTED), (dict(top_bc=2), native.CH_ERR_ARG),
+             (dict(precision=2), native.CH_ERR_UNSUPPORTED),
              (dict(control=3), native.CH_ERR_ARG), (dict(nx=15), native.CH_ERR_ARG),
              (dict(ny=5), native.CH_ERR_ARG), (dict(steps_per_action=0), native.CH_ERR_ARG),
              (dict(dt=0.0), native.CH_ERR_ARG)]
