@@ -101,7 +101,11 @@ typedef struct ch_info {
     double nu, u_tau, tau_ref;
     size_t state_bytes;      /* bytes of one environment's serialised state                */
     size_t device_bytes;     /* device memory held by the handle                           */
-    int plane_cluster;       /* CTAs cooperating on one y-plane of the nonlinear term       */
+    int plane_cluster;       /* CTAs of a thread-block cluster cooperating on one y-plane of
+                                the nonlinear term; 0: no cluster holds the plane (FP64
+                                planes of 256 x 256 modes), the term runs in three passes
+                                through a global scratch array (z inverse, x transforms and
+                                products, z forward)                                     */
     int launches_per_step;   /* kernels launched by one env_step                            */
     int post_batched;        /* 1: the implicit half of a stage runs one thread per (mode,
                                 class, component); 0: eight threads per mode on a tile  */
@@ -278,7 +282,8 @@ typedef struct ch_server ch_server_t;
 
 typedef struct ch_srv_stats {
     uint64_t completed;      /* requests completed since creation / last reset   */
-    double p50_us, p99_us, mean_us, max_us;  /* submit -> completion latency       */
+    double p50_us, p99_us, mean_us, max_us;  /* submit -> completion latency over the
+                                                last 2^20 completed requests            */
     double env_steps_per_s;  /* completed / wall time since creation / last reset */
     int classes, envs, pending;
     size_t hbm_used, hbm_budget;  /* device bytes held by the class handles      */
@@ -333,9 +338,10 @@ int srv_destroy(ch_server_t* s);
  *       at each node, of u, v, w, omega_x, omega_y, omega_z;
  *   d_h [B][3][ny][nz][nx/2] complex: Fourier coefficients of the kept modes
  *       of H = u x omega evaluated on the 3nx/2 x 3nz/2 grid.
- * Uses the handle's twiddle tables; allocates nothing.  CH_ERR_UNSUPPORTED
- * where the FP64 padded plane does not fit a cluster's shared memory
- * (e.g. 256 x 256 Fourier modes; mixed-precision handles of that size run). */
+ * Uses the handle's twiddle tables (and, for FP64 handles of 256 x 256
+ * modes, their three-pass scratch array); allocates nothing.
+ * CH_ERR_UNSUPPORTED for mixed-precision handles whose FP64 padded plane
+ * does not fit a cluster's shared memory (256 x 256 modes). */
 int ch_nonlinear(ch_env_t* env, const double* d_q, double* d_h);
 
 /* Chebyshev-tau Dirichlet problems (D^2 - lam_m) f = r (coefficient rows

@@ -313,7 +313,30 @@ int setup_plane(ch_env* env, PlaneArgs<R>* a, size_t* smem) {
   // a 16-CTA cluster (non-portable opt-in) only where no portable size fits
   if (!nf && g.mz % 16 == 0 && (g.mz / 16) % 2 == 0 && (size_t)6 * (g.mz / 16) * g.nxh * csz <= 160 * 1024)
     feasible[nf++] = 16;
-  if (!nf) return CH_ERR_UNSUPPORTED;
+  if (!nf) {
+    // FP64 planes of 256 x 256 modes: three passes through a global scratch
+    // array (only for handles that step in FP64)
+    if (sizeof(R) != 8 || env->prm.precision != 0 || !two_pass_shape_ok(g.mx, g.mz, g.nxh)) return CH_ERR_UNSUPPORTED;
+    a->two_pass = 1;
+    a->S = 1;
+    a->Lz = g.mz;
+    a->NP = 0;
+    *smem = 0;
+    C* y = nullptr;
+    RC(dalloc(env, &y, (size_t)env->B * g.ny * 6 * g.mz * g.nxh));
+    a->y = y;
+    if (!fft_plan(g.mx, &a->px) || !fft_plan(g.mz, &a->pz)) return CH_ERR_UNSUPPORTED;
+    auto cast2 = [](const std::vector<double2>& v) {
+      std::vector<C> o(v.size());
+      for (size_t i = 0; i < v.size(); ++i) o[i] = mk((R)v[i].x, (R)v[i].y);
+      return o;
+    };
+    RC(dupload(env, &a->tw_x, cast2(twiddles(g.mx))));
+    RC(dupload(env, &a->tw_z, cast2(twiddles(g.mz))));
+    RC(dupload(env, &a->tw_mz, cast2(twiddles(g.mz))));
+    a->scale = (R)(1.0 / ((double)g.mx * g.mz));
+    return CH_OK;
+  }
   int S = feasible[nf - 1];
   for (int k = 0; k < nf; ++k)
     if ((long)g.ny * env->B * feasible[k] >= nsm) { S = feasible[k]; break; }
@@ -743,7 +766,7 @@ bool tiles_valid(const ch_env* env, int smem_max, int ppc_pre, int ppc_post, int
   auto pow2 = [](int v, int hi) { return v >= 1 && v <= hi && (v & (v - 1)) == 0; };
   if (!pow2(ppc_pre, 8) || stage_pre_smem(g, ppc_pre, node) > (size_t)smem_max) return false;
   const int top = env->prm.top_bc;
-  if (post_batched == 1) return pow2(ppc_post, 16) && stage_post_batched_smem(g, ppc_post, top) <= (size_t)smem_max;
+  if (post_batched == 1) return pow2(ppc_post, 16) && stage_post_batched_smem(g, ppc_post, top, node) <= (size_t)smem_max;
   if (post_batched != 0) return false;
   // the per-tile form runs 8 ppc threads and any tile width up to 8 (widths
   // that are not powers of two fill the resident CTA slots more evenly)
@@ -913,7 +936,11 @@ size_t env_footprint(const ch_params_t* p) {
                             (size_t)p->nz * p->nx * 8 + (2 * (size_t)p->nz * p->nx + 2) * 8);
   const size_t tables = (3 * 2 * 4 * Mh * P + 3 * 2 * P + 2 * 4 * Mh * P + 2 * P + 3 * 2 * Mh * P + 3 * 2 * P +
                          3 * Mh + 3 + 3 * ny + ny + 2 * 3 * 2 * 2 * P) * 8 + ny * ny * 12 + (nxh + p->nz) * 8;
-  return state + tables + ((size_t)4 << 20);  // plus twiddles and rounding slack
+  // FP64 planes of 256 x 256 modes: the scratch of the three-pass nonlinear term
+  const size_t mx = 3 * (size_t)p->nx / 2, mz = 3 * (size_t)p->nz / 2;
+  const size_t two_pass = (p->precision == 0 && two_pass_shape_ok((int)mx, (int)mz, (int)nxh))
+                              ? B * ny * 6 * mz * nxh * 16 : 0;
+  return state + tables + two_pass + ((size_t)4 << 20);  // plus twiddles and rounding slack
 }
 }  // namespace chdns
 
@@ -1011,10 +1038,11 @@ int env_create(const ch_params_t* p, ch_env_t** out) {
     // per SM sub-partition (B P / 8 >= 2 x 4 x SMs).
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return fail(CH_ERR_CUDA);
-    if ((size_t)B * P >= (size_t)64 * sms && stage_post_batched_smem(g, 8, p->top_bc) <= (size_t)smem_max) {
+    const size_t node = p->precision == 1 ? sizeof(float2) : sizeof(double2);
+    if ((size_t)B * P >= (size_t)64 * sms && stage_post_batched_smem(g, 8, p->top_bc, node) <= (size_t)smem_max) {
       env->post_batched = true;
       env->ppc_post = 16;  // 64 threads; 8 when the tile would leave fewer than 3 CTAs per SM
-      if (stage_post_batched_smem(g, 16, p->top_bc) > (size_t)76 * 1024) env->ppc_post = 8;
+      if (stage_post_batched_smem(g, 16, p->top_bc, node) > (size_t)76 * 1024) env->ppc_post = 8;
     }
     if (p->autotune && (rc = autotune_tiles(env, smem_max))) return fail(rc);
   }
@@ -1126,7 +1154,7 @@ int env_info(const ch_env_t* env, ch_info_t* info) {
   info->tau_ref = env->tau_ref;
   info->state_bytes = ch_state_bytes(&env->prm);
   info->device_bytes = env->device_bytes;
-  info->plane_cluster = env->prm.precision == 1 ? env->plane_f.S : env->plane.S;
+  info->plane_cluster = env->prm.precision == 1 ? env->plane_f.S : (env->plane.two_pass ? 0 : env->plane.S);
   info->launches_per_step = env->launches_per_step;
   info->post_batched = env->post_batched ? 1 : 0;
   info->ppc_pre = env->ppc_pre;

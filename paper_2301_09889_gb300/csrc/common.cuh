@@ -3,6 +3,8 @@
 // passed from the host code to the kernels.
 #pragma once
 
+#include <cmath>
+
 #include <cuda_runtime.h>
 #include <cstddef>
 #include <cstdint>
@@ -25,12 +27,46 @@ template <> struct cpx<float> { using T = float2; };
 __host__ __device__ __forceinline__ double2 mk(double x, double y) { return make_double2(x, y); }
 __host__ __device__ __forceinline__ float2 mk(float x, float y) { return make_float2(x, y); }
 
+// Round-to-nearest multiply and fused multiply-add that the compiler never
+// contracts or splits.  An expression such as a*b - c*d may be fused either
+// way, and the choice can differ between kernels that inline the same code;
+// the arithmetic that several kernel forms share (so that their results agree
+// bit for bit) is written with these.
+__host__ __device__ __forceinline__ double fma_rn(double a, double b, double c) {
+#ifdef __CUDA_ARCH__
+  return __fma_rn(a, b, c);
+#else
+  return std::fma(a, b, c);
+#endif
+}
+__host__ __device__ __forceinline__ float fma_rn(float a, float b, float c) {
+#ifdef __CUDA_ARCH__
+  return __fmaf_rn(a, b, c);
+#else
+  return std::fma(a, b, c);
+#endif
+}
+__host__ __device__ __forceinline__ double mul_rn(double a, double b) {
+#ifdef __CUDA_ARCH__
+  return __dmul_rn(a, b);
+#else
+  return a * b;
+#endif
+}
+__host__ __device__ __forceinline__ float mul_rn(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fmul_rn(a, b);
+#else
+  return a * b;
+#endif
+}
+
 #define CH_CPX_OPS(C, R)                                                                   \
   __host__ __device__ __forceinline__ C operator+(C a, C b) { return mk(a.x + b.x, a.y + b.y); } \
   __host__ __device__ __forceinline__ C operator-(C a, C b) { return mk(a.x - b.x, a.y - b.y); } \
   __host__ __device__ __forceinline__ C operator*(R s, C a) { return mk(s * a.x, s * a.y); }     \
   __host__ __device__ __forceinline__ C cmul(C a, C b) {                                  \
-    return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);                              \
+    return mk(fma_rn(a.x, b.x, -mul_rn(a.y, b.y)), fma_rn(a.x, b.y, mul_rn(a.y, b.x)));    \
   }                                                                                       \
   __host__ __device__ __forceinline__ C cconj(C a) { return mk(a.x, -a.y); }                \
   /* i * s * a */                                                                         \
@@ -424,6 +460,10 @@ struct PlaneArgs {
   FftPlan px, pz;
   R scale;             // 1 / (mx mz)
   const int* active;   // [B] slots to process (nullptr: all)
+  // planes that fit no cluster's shared memory: three passes through global
+  // memory (z inverse, x transforms and products, z forward)
+  int two_pass;
+  C* y;                // [B][ny][6][mz][nxh] scratch: z-transformed columns, then H in fields 0..2
 };
 
 // Per-mode tau tables (device), mode index fastest so that threads owning
@@ -444,6 +484,16 @@ struct TauTables {
   int Mh;
   int top_bc;              // 0 no-slip upper wall; 1 free slip (u1 then holds the affine forcing response)
 };
+
+// Shared memory of the batched implicit half before its exchange slots: the
+// tile of H, [3][ny][ppc] complex in the node precision, then for FP32 nodes
+// the staged previous right-hand sides [2][ny][ppc] (FP32 pairs), for FP64
+// nodes six more complex values per mode (scratch of the fast analysis);
+// 16-byte aligned.
+__host__ __device__ inline size_t stage_post_batched_tile_bytes(int ny, int ppc, size_t node_bytes) {
+  const size_t b = node_bytes == 8 ? (size_t)5 * ny * ppc * 8 : ((size_t)3 * ny + 6) * ppc * 16;
+  return (b + 15) & ~(size_t)15;
+}
 
 struct StageCoef {
   double alpha, beta, gamma, zeta, dt, nu, theta, flux;

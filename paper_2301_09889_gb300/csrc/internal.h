@@ -11,6 +11,10 @@ template <typename R>
 cudaError_t launch_plane(const PlaneArgs<R>& a, int B, size_t smem, cudaStream_t st);
 template <typename R>
 cudaError_t plane_max_clusters(const PlaneArgs<R>& a, size_t smem, int* clusters);
+// nonlinear term in three passes through global memory (plane2.cu), FP64
+bool two_pass_shape_ok(int mx, int mz, int nxh);
+template <typename R>
+cudaError_t launch_plane_two_pass(const PlaneArgs<R>& a, int B, cudaStream_t st);
 
 struct PencilBufs {
   double2 *V, *G;               // [B][ny][P]
@@ -39,7 +43,7 @@ struct DevTables {
 // fused wall-normal halves of a stage (stage.cu); ppc = modes per CTA
 size_t stage_pre_smem(const Grid& g, int ppc, size_t node_bytes);  // node_bytes: one complex node value
 size_t stage_post_smem(const Grid& g, int Mh, int ppc, int top);
-size_t stage_post_batched_smem(const Grid& g, int ppc, int top);
+size_t stage_post_batched_smem(const Grid& g, int ppc, int top, size_t node_bytes);
 template <typename RN>
 cudaError_t launch_stage_pre(const Grid& g, int B, const PencilBufs& pb, const DevTables& t,
                              typename cpx<RN>::T* q, int ppc, cudaStream_t st);

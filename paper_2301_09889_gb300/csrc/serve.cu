@@ -70,6 +70,7 @@ struct Class {
   cudaEvent_t ev = nullptr;
   cudaStream_t stream = nullptr;  // prioritised stream the class's ticks run on
   bool busy = false;
+  bool stuck = false;   // its stream did not drain after a failed enqueue: no further ticks
   std::vector<uint64_t> running;  // request per slot in the current tick (0 none)
 };
 
@@ -110,7 +111,19 @@ struct ch_server {
   std::map<uint64_t, Request> reqs;
   int next_env = 1;
   uint64_t next_req = 1;
+  // submit-to-completion latencies of the last kLatencyWindow completed
+  // requests since creation or the last srv_stats reset (a ring buffer)
+  static constexpr size_t kLatencyWindow = (size_t)1 << 20;
   std::vector<double> latencies_us;
+  size_t latency_next = 0;
+  void record_latency(double us) {
+    if (latencies_us.size() < kLatencyWindow) {
+      latencies_us.push_back(us);
+    } else {
+      latencies_us[latency_next] = us;
+      latency_next = (latency_next + 1) % kLatencyWindow;
+    }
+  }
   Clock::time_point t0 = Clock::now();
   uint64_t completed = 0;
   int worker_error = CH_OK;
@@ -243,24 +256,37 @@ void ch_server::run() {
                                          cudaMemcpyDeviceToHost, st) != cudaSuccess)
         rc = CH_ERR_CUDA;
       if (rc == CH_OK && cudaEventRecord(c->ev, st) != cudaSuccess) rc = CH_ERR_CUDA;
+      bool drained = true;
+      if (rc != CH_OK) {
+        // copies and kernels queued before the failure may still read the
+        // pinned action and mask buffers: wait (bounded, about 5 s) for the
+        // class stream before a later tick may rewrite them
+        drained = false;
+        for (int it = 0; it < 100000 && !drained; ++it) {
+          if (cudaStreamQuery(st) != cudaErrorNotReady) drained = true;
+          else std::this_thread::sleep_for(std::chrono::microseconds(50));
+        }
+      }
       lk.lock();
       if (rc != CH_OK) {
-        worker_error = rc;
+        worker_error = drained ? rc : CH_ERR_TIMEOUT;
         for (int sl = 0; sl < c->slots; ++sl)
           if (c->running[sl]) {
             Request& r = reqs[c->running[sl]];
             r.state = 2;
             r.status = rc;
             r.done_at = Clock::now();
+            c->running[sl] = 0;
           }
-        c->busy = false;
+        c->busy = !drained;
+        c->stuck = !drained;
         cv_done.notify_all();
       }
     }
     // complete finished ticks
     for (size_t ci = 0; ci < classes.size(); ++ci) {
       Class* c = classes[ci].get();
-      if (!c || !c->busy) continue;
+      if (!c || !c->busy || c->stuck) continue;
       const cudaError_t q = cudaEventQuery(c->ev);
       if (q == cudaErrorNotReady) {
         any_busy = true;
@@ -278,7 +304,7 @@ void ch_server::run() {
         r.status = (q != cudaSuccess) ? CH_ERR_CUDA : (std::isfinite(r.tau) ? CH_OK : CH_ERR_DIVERGED);
         r.state = 2;
         r.done_at = now;
-        latencies_us.push_back(std::chrono::duration<double, std::micro>(now - r.submit).count());
+        record_latency(std::chrono::duration<double, std::micro>(now - r.submit).count());
         ++completed;
         c->running[sl] = 0;
       }
@@ -482,6 +508,7 @@ int srv_stats(ch_server_t* s, ch_srv_stats_t* st, int reset) {
   st->worker_status = s->worker_error;
   if (reset) {
     s->latencies_us.clear();
+    s->latency_next = 0;
     s->completed = 0;
     s->t0 = Clock::now();
   }

@@ -23,8 +23,8 @@ size_t stage_pre_smem(const Grid& g, int ppc, size_t node_bytes) {
 // coefficient tile is smaller in FP32 node precision, the FP64 size bounds both;
 // a free-slip top adds the exchange slots of the parity closures: six values
 // per thread, two rounds in the batched form)
-size_t stage_post_batched_smem(const Grid& g, int ppc, int top) {
-  return ((size_t)3 * g.ny + 6) * ppc * sizeof(double2) + (top ? (size_t)2 * 4 * ppc * 6 * sizeof(double) : 0);
+size_t stage_post_batched_smem(const Grid& g, int ppc, int top, size_t node_bytes) {
+  return stage_post_batched_tile_bytes(g.ny, ppc, node_bytes) + (top ? (size_t)2 * 4 * ppc * 6 * sizeof(double) : 0);
 }
 size_t stage_post_smem(const Grid& g, int Mh, int ppc, int top) {
   return ((size_t)7 * g.ny + 6) * ppc * sizeof(double2) + ((size_t)18 * Mh * ppc + 6 * ppc) * sizeof(double) +
@@ -57,7 +57,7 @@ cudaError_t launch_stage_post(const Grid& g, int B, const PencilBufs& pb, const 
   if (top) {
     // free-slip top: built for MH <= 33 (ny <= 65)
     if (batched) {
-      const size_t smem = stage_post_batched_smem(g, ppc, 1);
+      const size_t smem = stage_post_batched_smem(g, ppc, 1, sizeof(typename cpx<RN>::T));
       switch (mh) {
         case 5: return post_batched_mh<RN, 5, 1>(g, B, pb, t, h, sc, ppc, smem, st);
         case 9: return post_batched_mh<RN, 9, 1>(g, B, pb, t, h, sc, ppc, smem, st);
@@ -76,7 +76,7 @@ cudaError_t launch_stage_post(const Grid& g, int B, const PencilBufs& pb, const 
     }
   }
   if (batched) {
-    const size_t smem = stage_post_batched_smem(g, ppc, 0);
+    const size_t smem = stage_post_batched_smem(g, ppc, 0, sizeof(typename cpx<RN>::T));
     switch (mh) {
       case 5: return post_batched_mh<RN, 5, 0>(g, B, pb, t, h, sc, ppc, smem, st);
       case 9: return post_batched_mh<RN, 9, 0>(g, B, pb, t, h, sc, ppc, smem, st);

@@ -79,9 +79,9 @@ __device__ __forceinline__ void tau_seq(int N, int ny, int sig, const double (&r
   for (int i = MH - 1; i >= 1; --i) {
     if (i < M) {
       const int n = 2 * i + sig;
-      double R = rowc[n] * r[i - 1] - rowc[ny + n] * r[i];
-      if (i + 1 < MH && i + 1 < M) R += rowc[2 * ny + n] * r[i + 1 < MH ? i + 1 : i];
-      const double a = T.e(i) * R - T.h(i) * anext;
+      double R = fma_rn(-rowc[ny + n], r[i], mul_rn(rowc[n], r[i - 1]));
+      if (i + 1 < MH && i + 1 < M) R = fma_rn(rowc[2 * ny + n], r[i + 1 < MH ? i + 1 : i], R);
+      const double a = fma_rn(-T.h(i), anext, mul_rn(T.e(i), R));
       f[i] = a;
       anext = a;
     }
@@ -90,16 +90,16 @@ __device__ __forceinline__ void tau_seq(int N, int ny, int sig, const double (&r
 #pragma unroll
   for (int i = 1; i < MH; ++i) {
     if (i < M) {
-      Pp = f[i] + T.b(i) * Pp;
+      Pp = fma_rn(T.b(i), Pp, f[i]);
       f[i] = Pp;
       sum += Pp;
     }
   }
-  const double f0 = isq * (s - sum);
+  const double f0 = mul_rn(isq, s - sum);
   f[0] = f0;
 #pragma unroll
   for (int i = 1; i < MH; ++i)
-    if (i < M) f[i] += T.Q(i) * f0;
+    if (i < M) f[i] = fma_rn(T.Q(i), f0, f[i]);
 }
 
 // ---------------------------------------------------------------------------
@@ -132,9 +132,9 @@ __device__ __forceinline__ void tau_affine(int N, int ny, int sig, const double 
   for (int i = MH - 1; i >= 1; --i) {
     if (i < M) {
       const int n = 2 * i + sig;
-      double R = rowc[n] * r[i - 1] - rowc[ny + n] * r[i];
-      if (i + 1 < MH && i + 1 < M) R += rowc[2 * ny + n] * r[i + 1 < MH ? i + 1 : i];
-      const double a = T.e(i) * R - T.h(i) * anext;
+      double R = fma_rn(-rowc[ny + n], r[i], mul_rn(rowc[n], r[i - 1]));
+      if (i + 1 < MH && i + 1 < M) R = fma_rn(rowc[2 * ny + n], r[i + 1 < MH ? i + 1 : i], R);
+      const double a = fma_rn(-T.h(i), anext, mul_rn(T.e(i), R));
       f[i] = a;
       anext = a;
     }
@@ -146,10 +146,10 @@ __device__ __forceinline__ void tau_affine(int N, int ny, int sig, const double 
   for (int i = 1; i < MH; ++i) {
     if (i < M) {
       const double n = 2 * i + sig;
-      Pp = f[i] + T.b(i) * Pp;
+      Pp = fma_rn(T.b(i), Pp, f[i]);
       f[i] = Pp;
       sp += Pp;
-      sp2 += n * n * Pp;
+      sp2 = fma_rn(n * n, Pp, sp2);
     }
   }
   f[0] = 0.0;
@@ -162,15 +162,15 @@ __device__ __forceinline__ void tau_close(int N, int sig, double (&f)[MH], const
   f[0] = x;
 #pragma unroll
   for (int i = 1; i < MH; ++i)
-    if (i < M) f[i] += T.Q(i) * x;
+    if (i < M) f[i] = fma_rn(T.Q(i), x, f[i]);
 }
 
 // a11 x1 + a12 x2 = b1, a21 x1 + a22 x2 = b2 (Cramer's rule)
 __device__ __forceinline__ void solve2(double a11, double a12, double a21, double a22, double b1, double b2,
                                        double* x1, double* x2) {
-  const double id = 1.0 / (a11 * a22 - a12 * a21);
-  *x1 = (b1 * a22 - a12 * b2) * id;
-  *x2 = (a11 * b2 - a21 * b1) * id;
+  const double id = 1.0 / fma_rn(a11, a22, -mul_rn(a12, a21));
+  *x1 = mul_rn(fma_rn(b1, a22, -mul_rn(a12, b2)), id);
+  *x2 = mul_rn(fma_rn(a11, b2, -mul_rn(a21, b1)), id);
 }
 
 // Dirichlet bottom and Neumann top rows over the two parities of omega_y or W.
@@ -178,14 +178,16 @@ __device__ __forceinline__ void solve2(double a11, double a12, double a21, doubl
 // parity; q*: the table sums sum Q and sum n^2 Q.
 __device__ __forceinline__ void close_neumann_top(const double* se, const double* so, double qe, double qo,
                                                   double q2e, double q2o, double cc, double* xe, double* xo) {
-  solve2(qe, -qo, q2e, q2o, cc * (se[2] - so[2]) - (se[0] - so[0]), cc * (se[3] + so[3]) - (se[1] + so[1]), xe, xo);
+  solve2(qe, -qo, q2e, q2o, fma_rn(cc, se[2] - so[2], -(se[0] - so[0])), fma_rn(cc, se[3] + so[3], -(se[1] + so[1])),
+         xe, xo);
 }
 
 // Influence coefficients of v: se, so = {A_p, B_p, A_old, B_old}; a*, b*: A
 // and B of the homogeneous solutions vh of the two parities.
 __device__ __forceinline__ void close_free_slip_v(const double* se, const double* so, double ae, double ao,
                                                   double be, double bo, double cc, double* ce, double* co) {
-  solve2(ae, ao, -be, bo, cc * (se[2] + so[2]) - (se[0] + so[0]), cc * (so[3] - se[3]) - (so[1] - se[1]), ce, co);
+  solve2(ae, ao, -be, bo, fma_rn(cc, se[2] + so[2], -(se[0] + so[0])), fma_rn(cc, so[3] - se[3], -(so[1] - se[1])),
+         ce, co);
 }
 
 // Mean U at constant flow rate: unknowns (x_e, x_o, forcing).  se = {sum P,
@@ -199,14 +201,16 @@ __device__ __forceinline__ void close_free_slip_mean(const double* se, const dou
   const double a11 = qe, a12 = -qo, a13 = us;
   const double a21 = q2e, a22 = q2o, a23 = u2;
   const double a31 = wq, a32 = 0.0, a33 = uw;
-  const double b1 = cc * (se[2] - so[2]) - (se[0] - so[0]);
-  const double b2 = cc * (se[3] + so[3]) - (se[1] + so[1]);
-  const double b3 = flux + cc * se[5] - se[4];
-  const double m1 = a22 * a33 - a23 * a32, m2 = a21 * a33 - a23 * a31, m3 = a21 * a32 - a22 * a31;
-  const double id = 1.0 / (a11 * m1 - a12 * m2 + a13 * m3);
-  *xe = (b1 * m1 - a12 * (b2 * a33 - a23 * b3) + a13 * (b2 * a32 - a22 * b3)) * id;
-  *xo = (a11 * (b2 * a33 - a23 * b3) - b1 * m2 + a13 * (a21 * b3 - b2 * a31)) * id;
-  *fc = (a11 * (a22 * b3 - b2 * a32) - a12 * (a21 * b3 - b2 * a31) + b1 * m3) * id;
+  const double b1 = fma_rn(cc, se[2] - so[2], -(se[0] - so[0]));
+  const double b2 = fma_rn(cc, se[3] + so[3], -(se[1] + so[1]));
+  const double b3 = fma_rn(cc, se[5], flux) - se[4];
+  // 2 x 2 minors (x y - z w, fused on the first product)
+  auto det2 = [](double x, double y, double z, double w) { return fma_rn(x, y, -mul_rn(z, w)); };
+  const double m1 = det2(a22, a33, a23, a32), m2 = det2(a21, a33, a23, a31), m3 = det2(a21, a32, a22, a31);
+  const double id = 1.0 / fma_rn(a13, m3, fma_rn(a11, m1, -mul_rn(a12, m2)));
+  *xe = mul_rn(fma_rn(a13, det2(b2, a32, a22, b3), fma_rn(b1, m1, -mul_rn(a12, det2(b2, a33, a23, b3)))), id);
+  *xo = mul_rn(fma_rn(a13, det2(a21, b3, b2, a31), fma_rn(a11, det2(b2, a33, a23, b3), -mul_rn(b1, m2))), id);
+  *fc = mul_rn(fma_rn(b1, m3, fma_rn(a11, det2(a22, b3, b2, a32), -mul_rn(a12, det2(a21, b3, b2, a31)))), id);
 }
 
 // Right-hand side of the v equation of parity sv and component r, one walk
@@ -240,23 +244,23 @@ __device__ __forceinline__ void v_walk(int N, int ny, int ppc, int sv, const Com
     const int no = 2 * i + sv + 1;
     if (no <= N) {
       const double vn1 = (no + 1 <= N) ? Vc[no + 1] : 0.0;
-      dv = dv + ((double)(4 * i + 4) + dsv) * vn1;  // 2 (no + 1)
-      tt = sgnn * (kxn * comp(Hx[no * ppc], ra) + kzn * comp(Hz[no * ppc], ra));
+      dv = fma_rn((double)(4 * i + 4) + dsv, vn1, dv);  // 2 (no + 1)
+      tt = mul_rn(sgnn, fma_rn(kxn, comp(Hx[no * ppc], ra), mul_rn(kzn, comp(Hz[no * ppc], ra))));
     }
     const int n = 2 * i + sv;
     if (n <= N) {
       const double fac = (double)(4 * i + 2) + dsv;  // 2 (n + 1)
       const RN facn = (RN)(4 * i + 2) + dsvn;
-      const double t1 = d2v + fac * dv;
-      const RN t2 = dtt + facn * ((n + 1 <= N) ? tt : (RN)0);
+      const double t1 = fma_rn(fac, dv, d2v);
+      const RN t2 = fma_rn(facn, (n + 1 <= N) ? tt : (RN)0, dtt);
       d2v = (n == 0) ? 0.5 * t1 : t1;
       dtt = (n == 0) ? (RN)0.5 * t2 : t2;
-      const double phi = d2v - k2 * Vc[n];
-      const RN hv = -k2n * comp(Hy[n * ppc], r) - dtt;
+      const double phi = fma_rn(-k2, Vc[n], d2v);
+      const RN hv = fma_rn(-k2n, comp(Hy[n * ppc], r), -dtt);
       const RN hp = HVr[n];
       HVw[n] = hv;
-      const RN q = dtn * (gan * hv + zen * hp);
-      rhs[i] = -((1.0 + cc) * phi + (double)q) * ibdn;
+      const RN q = mul_rn(dtn, fma_rn(gan, hv, mul_rn(zen, hp)));
+      rhs[i] = mul_rn(fma_rn(1.0 + cc, phi, (double)q), -ibdn);
     }
   }
 }
@@ -910,9 +914,9 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
               const double hv = (double)Hm[n * ppc].x;
               const double hp = XP[n];
               XP[n] = hv;
-              rhs[i] = -((1.0 + cc) * xn + sc.dt * (sc.gamma * hv + sc.zeta * hp)) * ibdn;
+              rhs[i] = mul_rn(fma_rn(1.0 + cc, xn, mul_rn(sc.dt, fma_rn(sc.gamma, hv, mul_rn(sc.zeta, hp)))), -ibdn);
               sum += xn;
-              if (s == 0) flux_old += 2.0 / (1.0 - (double)n * n) * xn;
+              if (s == 0) flux_old = fma_rn(2.0 / (1.0 - (double)n * n), xn, flux_old);
             }
           }
           tau_seq<MH>(N, ny, s, rhs, f, helm(s), ss[(0 * 2 + s) * ppc + pl], cc * sum, rowc);
@@ -921,15 +925,15 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
             double flux = 0.0;
   #pragma unroll
             for (int i = 0; i < MH; ++i)
-              if (i < M) flux += 2.0 / (1.0 - 4.0 * (double)i * i) * f[i];
-            fc = (sc.flux + cc * flux_old - flux) * t.tau.u1_iflux[sc.k];
+              if (i < M) flux = fma_rn(2.0 / (1.0 - 4.0 * (double)i * i), f[i], flux);
+            fc = mul_rn(fma_rn(cc, flux_old, sc.flux) - flux, t.tau.u1_iflux[sc.k]);
           }
   #pragma unroll
           for (int i = 0; i < MH; ++i) {
             if (i < M) {
               const int n = 2 * i + s;
-              double v = f[i] - cc * X[n];
-              if (e == 0 && s == 0) v += fc * t.tau.u1[(size_t)sc.k * Mh + i];
+              double v = fma_rn(-cc, X[n], f[i]);
+              if (e == 0 && s == 0) v = fma_rn(fc, t.tau.u1[(size_t)sc.k * Mh + i], v);
               X[n] = v;
             }
           }
@@ -954,11 +958,11 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
               const int n = 2 * i + sq;
               const double gn = Gc[n];
               // nonlinear part in the node precision
-              const RN hg = sgnn * (kzn * comp(Hx[n * ppc], ra) - kxn * comp(Hz[n * ppc], ra));
+              const RN hg = mul_rn(sgnn, fma_rn(-kxn, comp(Hz[n * ppc], ra), mul_rn(kzn, comp(Hx[n * ppc], ra))));
               const RN hp = HGc[n];
               HGc[n] = hg;
-              const RN q = dtn * (gan * hg + zen * hp);
-              rhs[i] = -((1.0 + cc) * gn + (double)q) * ibdn;
+              const RN q = mul_rn(dtn, fma_rn(gan, hg, mul_rn(zen, hp)));
+              rhs[i] = mul_rn(fma_rn(1.0 + cc, gn, (double)q), -ibdn);
               sum += gn;
             }
           }
@@ -967,7 +971,7 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
           for (int i = 0; i < MH; ++i)
             if (i < M) {
               const int n = 2 * i + sq;
-              Gc[n] = f[i] - cc * Gc[n];
+              Gc[n] = fma_rn(-cc, Gc[n], f[i]);
             }
         } else {
           // wall-normal velocity, parity c
@@ -983,7 +987,7 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
             const int n = 2 * i + sv;
             const double vn = Vc[n];
             S0 += vn;
-            S2 += (double)n * n * vn;
+            S2 = fma_rn((double)n * n, vn, S2);
           }
           // one walk from n = N down to 0: Dv, D^2 v, t = i kx H_x + i kz H_z, Dt
           v_walk<MH, RN>(N, ny, ppc, sv, Vc, HVc, HVc, Hx, Hy, Hz, r, sgn, kx, kz, k2, cc, ibdn, sc, rhs);
@@ -991,8 +995,8 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
           tau_seq<MH>(N, ny, sv, rhs, f, helm(sv), ss[(0 * 2 + sv) * ppc + pl], 0.0, rowc);
           const size_t vo = (size_t)b * P + p;
           const double vw =
-              comp(pb.vw_old[vo], r) + sc.theta * (comp(pb.vw_new[vo], r) - comp(pb.vw_old[vo], r));
-          const double s = ((sv == 0) ? 0.5 : -0.5) * vw + cc * S0;
+              fma_rn(sc.theta, comp(pb.vw_new[vo], r) - comp(pb.vw_old[vo], r), comp(pb.vw_old[vo], r));
+          const double s = fma_rn(cc, S0, ((sv == 0) ? 0.5 : -0.5) * vw);
           const TabSm TP{sp + sv * 4 * Mh * ppc + pl, Mh, ppc};
           tau_seq<MH>(N, ny, sv, f, rhs, TP, ss[(1 * 2 + sv) * ppc + pl], s, rowc);
           double dp = 0.0;
@@ -1000,15 +1004,15 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
           for (int i = 0; i < MH; ++i)
             if (i < M) {
               const double n = 2 * i + sv;
-              dp += n * n * rhs[i];
+              dp = fma_rn(n * n, rhs[i], dp);
             }
-          const double cI = (cc * S2 - dp) * ss[(2 * 2 + sv) * ppc + pl];
+          const double cI = mul_rn(fma_rn(cc, S2, -dp), ss[(2 * 2 + sv) * ppc + pl]);
           const double* vh = svh + sv * Mh * ppc + pl;
   #pragma unroll
           for (int i = 0; i < MH; ++i)
             if (i < M) {
               const int n = 2 * i + sv;
-              Vc[n] = rhs[i] + cI * vh[i * ppc] - cc * Vc[n];
+              Vc[n] = fma_rn(-cc, Vc[n], fma_rn(cI, vh[i * ppc], rhs[i]));
             }
         }
       }
@@ -1060,10 +1064,10 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
             const double hv = (double)Hm[n * ppc].x;
             const double hp = XP[n];
             XP[n] = hv;
-            rhs[i] = -((1.0 + cc) * xn + sc.dt * (sc.gamma * hv + sc.zeta * hp)) * ibdn;
+            rhs[i] = mul_rn(fma_rn(1.0 + cc, xn, mul_rn(sc.dt, fma_rn(sc.gamma, hv, mul_rn(sc.zeta, hp)))), -ibdn);
             so += xn;
-            so2 += (double)n * n * xn;
-            if (sig == 0) wo += 2.0 / (1.0 - (double)n * n) * xn;
+            so2 = fma_rn((double)n * n, xn, so2);
+            if (sig == 0) wo = fma_rn(2.0 / (1.0 - (double)n * n), xn, wo);
           }
         }
         double psum, psum2;
@@ -1072,7 +1076,7 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
         if (sig == 0) {
 #pragma unroll
           for (int i = 0; i < MH; ++i)
-            if (i < M) wp += 2.0 / (1.0 - 4.0 * (double)i * i) * f[i];
+            if (i < M) wp = fma_rn(2.0 / (1.0 - 4.0 * (double)i * i), f[i], wp);
         }
         mine[0] = psum; mine[1] = psum2; mine[2] = so; mine[3] = so2; mine[4] = wp; mine[5] = wo;
       } else if (e == 0) {
@@ -1091,13 +1095,13 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
           if (i < M) {
             const int n = 2 * i + sig;
             const double gn = Gc[n];
-            const RN hg = sgnn * (kzn * comp(Hx[n * ppc], ra) - kxn * comp(Hz[n * ppc], ra));
+            const RN hg = mul_rn(sgnn, fma_rn(-kxn, comp(Hz[n * ppc], ra), mul_rn(kzn, comp(Hx[n * ppc], ra))));
             const RN hp = HGc[n];
             HGc[n] = hg;
-            const RN q = dtn * (gan * hg + zen * hp);
-            rhs[i] = -((1.0 + cc) * gn + (double)q) * ibdn;
+            const RN q = mul_rn(dtn, fma_rn(gan, hg, mul_rn(zen, hp)));
+            rhs[i] = mul_rn(fma_rn(1.0 + cc, gn, (double)q), -ibdn);
             so += gn;
-            so2 += (double)n * n * gn;
+            so2 = fma_rn((double)n * n, gn, so2);
           }
         }
         double psum, psum2;
@@ -1119,15 +1123,15 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
           const double n = 2 * i + sig;
           const double vn = Vc[2 * i + sig];
           S0 += vn;
-          Bo += n * n * vn;
-          Ao += n * n * (n * n - 1.0) / 3.0 * vn;
+          Bo = fma_rn(n * n, vn, Bo);
+          Ao = fma_rn(n * n * (n * n - 1.0) / 3.0, vn, Ao);
         }
         v_walk<MH, RN>(N, ny, ppc, sig, Vc, HVc, HVc, Hx, Hy, Hz, r, sgn, kx, kz, k2, cc, ibdn, sc, rhs);
         tau_seq<MH>(N, ny, sig, rhs, f, helm(sig), ss[(0 * 2 + sig) * ppc + pl], 0.0, rowc);
         const size_t vo = (size_t)b * P + p;
         const double vw =
-            comp(pb.vw_old[vo], r) + sc.theta * (comp(pb.vw_new[vo], r) - comp(pb.vw_old[vo], r));
-        const double s = ((sig == 0) ? 0.5 : -0.5) * vw + cc * S0;
+            fma_rn(sc.theta, comp(pb.vw_new[vo], r) - comp(pb.vw_old[vo], r), comp(pb.vw_old[vo], r));
+        const double s = fma_rn(cc, S0, ((sig == 0) ? 0.5 : -0.5) * vw);
         const TabSm TP{sp + sig * 4 * Mh * ppc + pl, Mh, ppc};
         tau_seq<MH>(N, ny, sig, f, rhs, TP, ss[(1 * 2 + sig) * ppc + pl], s, rowc);
         double Ap = 0.0, Bp = 0.0;
@@ -1135,8 +1139,8 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
         for (int i = 0; i < MH; ++i)
           if (i < M) {
             const double n = 2 * i + sig;
-            Bp += n * n * rhs[i];
-            Ap += n * n * (n * n - 1.0) / 3.0 * rhs[i];
+            Bp = fma_rn(n * n, rhs[i], Bp);
+            Ap = fma_rn(n * n * (n * n - 1.0) / 3.0, rhs[i], Ap);
           }
         mine[0] = Ap; mine[1] = Bp; mine[2] = Ao; mine[3] = Bo;
       }
@@ -1159,9 +1163,9 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
           for (int i = 0; i < N / 2 + 1; ++i) {
             const double n = 2 * i, w = 2.0 / (1.0 - n * n);
             us += u1[i];
-            u2 += n * n * u1[i];
-            uw += w * u1[i];
-            wq += w * (i == 0 ? 1.0 : He.Q(i));
+            u2 = fma_rn(n * n, u1[i], u2);
+            uw = fma_rn(w, u1[i], uw);
+            wq = fma_rn(w, i == 0 ? 1.0 : He.Q(i), wq);
           }
           close_free_slip_mean(se, so, qs(0, 0), qs(1, 0), qs(0, 1), qs(1, 1), wq, us, u2, uw, cc, sc.flux, &xe,
                                &xo, &fc);
@@ -1171,8 +1175,8 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
         for (int i = 0; i < MH; ++i)
           if (i < M) {
             const int n = 2 * i + sig;
-            double v = f[i] - cc * X[n];
-            if (e == 0 && sig == 0) v += fc * t.tau.u1[(size_t)sc.k * Mh + i];
+            double v = fma_rn(-cc, X[n], f[i]);
+            if (e == 0 && sig == 0) v = fma_rn(fc, t.tau.u1[(size_t)sc.k * Mh + i], v);
             X[n] = v;
           }
       } else if (e == 0) {
@@ -1184,7 +1188,7 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
         for (int i = 0; i < MH; ++i)
           if (i < M) {
             const int n = 2 * i + sig;
-            Gc[n] = f[i] - cc * Gc[n];
+            Gc[n] = fma_rn(-cc, Gc[n], f[i]);
           }
       } else {
         const CompS Vc{reinterpret_cast<double*>(sV) + 2 * pl + r, 2 * ppc};
@@ -1196,7 +1200,7 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
         for (int i = 0; i < MH; ++i)
           if (i < M) {
             const int n = 2 * i + sig;
-            Vc[n] = rhs[i] + cI * vh[i * ppc] - cc * Vc[n];
+            Vc[n] = fma_rn(-cc, Vc[n], fma_rn(cI, vh[i * ppc], rhs[i]));
           }
       }
     }
@@ -1244,8 +1248,8 @@ __global__ void __launch_bounds__(64) stage_post_batched_kernel(Grid g, int B, P
   if (pb.active && !pb.active[b]) return;
   const int tid = threadIdx.x, nt = blockDim.x;
   // FP32 nodes: the previous right-hand sides (FP32 pairs) are staged in shared
-  // memory by one coalesced load, behind the node tile within the space the
-  // FP64 coefficient tile takes; the new ones go straight to global memory
+  // memory by one coalesced load behind the node tile, issued before the wait
+  // for H; the new ones go straight to global memory
   constexpr bool kStageH = sizeof(RN) == 4;
   CN* sHVt = sN + 3 * ny * ppc;
   CN* sHGt = sHVt + ny * ppc;
@@ -1333,134 +1337,143 @@ __global__ void __launch_bounds__(64) stage_post_batched_kernel(Grid g, int B, P
     const RN dtn = (RN)sc.dt, gan = (RN)sc.gamma, zen = (RN)sc.zeta;
     auto helm = [&](int sig) { return TabSm{t.tau.helm + (size_t)(sc.k * 2 + sig) * 4 * Mh * P + p, Mh, P}; };
     auto helm_isq = [&](int sig) { return t.tau.helm_isq[(size_t)(sc.k * 2 + sig) * P + p]; };
-    if (p == 0) {
-      // mean mode: U (r = 0) at constant flow rate and W (r = 1), parity c
-      const int e = r, s = c;
-      const int M = (N - s) / 2 + 1;
-      double* X = (e == 0 ? pb.UM : pb.WM) + (size_t)b * ny;
-      double* XP = (e == 0 ? pb.HXP : pb.HZP) + (size_t)b * ny;
-      const CN* Hm = (e == 0) ? Hx : Hz;
-      double rhs[MH], f[MH];
-      double sum = 0.0, flux_old = 0.0;
-  #pragma unroll
-      for (int i = 0; i < MH; ++i) {
-        rhs[i] = 0.0;
-        if (i < M) {
-          const int n = 2 * i + s;
-          const double xn = X[n];
-          const double hv = (double)Hm[n * ppc].x;
-          const double hp = XP[n];
-          XP[n] = hv;
-          rhs[i] = -((1.0 + cc) * xn + sc.dt * (sc.gamma * hv + sc.zeta * hp)) * ibdn;
-          sum += xn;
-          if (s == 0) flux_old += 2.0 / (1.0 - (double)n * n) * xn;
+    // The class c is uniform over each warp for tiles of 16 or more modes, so
+    // the solve is compiled once per class: every parity-dependent factor
+    // (2 (n + 1), n^2, the row bounds) becomes a constant.  The arithmetic is
+    // the same as with a run-time class (the factors are exact small integers).
+    auto solve = [&](auto cls) {
+      constexpr int c = decltype(cls)::value;
+      if (p == 0) {
+        // mean mode: U (r = 0) at constant flow rate and W (r = 1), parity c
+        const int e = r, s = c;
+        const int M = (N - s) / 2 + 1;
+        double* X = (e == 0 ? pb.UM : pb.WM) + (size_t)b * ny;
+        double* XP = (e == 0 ? pb.HXP : pb.HZP) + (size_t)b * ny;
+        const CN* Hm = (e == 0) ? Hx : Hz;
+        double rhs[MH], f[MH];
+        double sum = 0.0, flux_old = 0.0;
+    #pragma unroll
+        for (int i = 0; i < MH; ++i) {
+          rhs[i] = 0.0;
+          if (i < M) {
+            const int n = 2 * i + s;
+            const double xn = X[n];
+            const double hv = (double)Hm[n * ppc].x;
+            const double hp = XP[n];
+            XP[n] = hv;
+            rhs[i] = mul_rn(fma_rn(1.0 + cc, xn, mul_rn(sc.dt, fma_rn(sc.gamma, hv, mul_rn(sc.zeta, hp)))), -ibdn);
+            sum += xn;
+            if (s == 0) flux_old = fma_rn(2.0 / (1.0 - (double)n * n), xn, flux_old);
+          }
         }
+        tau_seq<MH>(N, ny, s, rhs, f, helm(s), helm_isq(s), cc * sum, rowc);
+        double fc = 0.0;
+        if (e == 0 && s == 0) {
+          double flux = 0.0;
+    #pragma unroll
+          for (int i = 0; i < MH; ++i)
+            if (i < M) flux = fma_rn(2.0 / (1.0 - 4.0 * (double)i * i), f[i], flux);
+          fc = mul_rn(fma_rn(cc, flux_old, sc.flux) - flux, t.tau.u1_iflux[sc.k]);
+        }
+    #pragma unroll
+        for (int i = 0; i < MH; ++i) {
+          if (i < M) {
+            const int n = 2 * i + s;
+            double v = fma_rn(-cc, X[n], f[i]);
+            if (e == 0 && s == 0) v = fma_rn(fc, t.tau.u1[(size_t)sc.k * Mh + i], v);
+            X[n] = v;
+          }
+        }
+        return;
       }
-      tau_seq<MH>(N, ny, s, rhs, f, helm(s), helm_isq(s), cc * sum, rowc);
-      double fc = 0.0;
-      if (e == 0 && s == 0) {
-        double flux = 0.0;
-  #pragma unroll
+      const double kx = t.kx[ix], kz = t.kz[row], k2 = kx * kx + kz * kz;
+      const double sgn = (r == 0) ? -1.0 : 1.0;
+      const int ra = 1 - r;
+      const size_t base = 2 * ((size_t)b * ny * P + p) + r;  // component r of element n at base + 2 P n
+      {
+        // wall-normal vorticity, parity 1 - c
+        const int sq = 1 - c;
+        const int M = (N - sq) / 2 + 1;
+        const CompS Gc{reinterpret_cast<double*>(pb.G) + base, 2 * P};
+        // previous right-hand sides are stored in the node precision
+        const CompT<RN> HGc{reinterpret_cast<RN*>(pb.HGP) + base, 2 * P};
+        const CompT<RN> HGr = kStageH ? CompT<RN>{reinterpret_cast<RN*>(sHGt) + 2 * pl + r, 2 * ppc} : HGc;
+        const RN sgnn = (RN)sgn, kxn = (RN)kx, kzn = (RN)kz;
+        double rhs[MH], f[MH];
+        double sum = 0.0;
+    #pragma unroll
+        for (int i = 0; i < MH; ++i) {
+          rhs[i] = 0.0;
+          if (i < M) {
+            const int n = 2 * i + sq;
+            const double gn = Gc[n];
+            const RN hg = mul_rn(sgnn, fma_rn(-kxn, comp(Hz[n * ppc], ra), mul_rn(kzn, comp(Hx[n * ppc], ra))));
+            const RN hp = HGr[n];
+            HGc[n] = hg;
+            const RN q = mul_rn(dtn, fma_rn(gan, hg, mul_rn(zen, hp)));
+            rhs[i] = mul_rn(fma_rn(1.0 + cc, gn, (double)q), -ibdn);
+            sum += gn;
+          }
+        }
+        tau_seq<MH>(N, ny, sq, rhs, f, helm(sq), helm_isq(sq), cc * sum, rowc);
+    #pragma unroll
         for (int i = 0; i < MH; ++i)
-          if (i < M) flux += 2.0 / (1.0 - 4.0 * (double)i * i) * f[i];
-        fc = (sc.flux + cc * flux_old - flux) * t.tau.u1_iflux[sc.k];
+          if (i < M) {
+            const int n = 2 * i + sq;
+            Gc[n] = fma_rn(-cc, Gc[n], f[i]);
+          }
       }
-  #pragma unroll
-      for (int i = 0; i < MH; ++i) {
-        if (i < M) {
-          const int n = 2 * i + s;
-          double v = f[i] - cc * X[n];
-          if (e == 0 && s == 0) v += fc * t.tau.u1[(size_t)sc.k * Mh + i];
-          X[n] = v;
-        }
-      }
-      return;
-    }
-    const double kx = t.kx[ix], kz = t.kz[row], k2 = kx * kx + kz * kz;
-    const double sgn = (r == 0) ? -1.0 : 1.0;
-    const int ra = 1 - r;
-    const size_t base = 2 * ((size_t)b * ny * P + p) + r;  // component r of element n at base + 2 P n
-    {
-      // wall-normal vorticity, parity 1 - c
-      const int sq = 1 - c;
-      const int M = (N - sq) / 2 + 1;
-      const CompS Gc{reinterpret_cast<double*>(pb.G) + base, 2 * P};
-      // previous right-hand sides are stored in the node precision
-      const CompT<RN> HGc{reinterpret_cast<RN*>(pb.HGP) + base, 2 * P};
-      const CompT<RN> HGr = kStageH ? CompT<RN>{reinterpret_cast<RN*>(sHGt) + 2 * pl + r, 2 * ppc} : HGc;
-      const RN sgnn = (RN)sgn, kxn = (RN)kx, kzn = (RN)kz;
-      double rhs[MH], f[MH];
-      double sum = 0.0;
-  #pragma unroll
-      for (int i = 0; i < MH; ++i) {
-        rhs[i] = 0.0;
-        if (i < M) {
-          const int n = 2 * i + sq;
-          const double gn = Gc[n];
-          const RN hg = sgnn * (kzn * comp(Hx[n * ppc], ra) - kxn * comp(Hz[n * ppc], ra));
-          const RN hp = HGr[n];
-          HGc[n] = hg;
-          const RN q = dtn * (gan * hg + zen * hp);
-          rhs[i] = -((1.0 + cc) * gn + (double)q) * ibdn;
-          sum += gn;
-        }
-      }
-      tau_seq<MH>(N, ny, sq, rhs, f, helm(sq), helm_isq(sq), cc * sum, rowc);
-  #pragma unroll
-      for (int i = 0; i < MH; ++i)
-        if (i < M) {
-          const int n = 2 * i + sq;
-          Gc[n] = f[i] - cc * Gc[n];
-        }
-    }
-    {
-      // wall-normal velocity, parity c
-      const int sv = c;
-      const int M = (N - sv) / 2 + 1;
-      const CompS Vc{reinterpret_cast<double*>(pb.V) + base, 2 * P};
-      const CompT<RN> HVc{reinterpret_cast<RN*>(pb.HVP) + base, 2 * P};
-      const CompT<RN> HVr = kStageH ? CompT<RN>{reinterpret_cast<RN*>(sHVt) + 2 * pl + r, 2 * ppc} : HVc;
-      double S0 = 0.0, S2 = 0.0;
-      double rhs[MH];
-  #pragma unroll
-      for (int i = 0; i < MH; ++i) rhs[i] = 0.0;
-      for (int i = 0; i < M; ++i) {
-        const int n = 2 * i + sv;
-        const double vn = Vc[n];
-        S0 += vn;
-        S2 += (double)n * n * vn;
-      }
-      v_walk<MH, RN>(N, ny, ppc, sv, Vc, HVr, HVc, Hx, Hy, Hz, r, sgn, kx, kz, k2, cc, ibdn, sc, rhs);
-      double f[MH];
-      tau_seq<MH>(N, ny, sv, rhs, f, helm(sv), helm_isq(sv), 0.0, rowc);
-      const size_t vo = (size_t)b * P + p;
-      const double vw =
-          comp(pb.vw_old[vo], r) + sc.theta * (comp(pb.vw_new[vo], r) - comp(pb.vw_old[vo], r));
-      const double s = ((sv == 0) ? 0.5 : -0.5) * vw + cc * S0;
-      const TabSm TP{t.tau.pois + (size_t)sv * 4 * Mh * P + p, Mh, P};
-      tau_seq<MH>(N, ny, sv, f, rhs, TP, t.tau.pois_isq[(size_t)sv * P + p], s, rowc);
-      double dp = 0.0;
-  #pragma unroll
-      for (int i = 0; i < MH; ++i)
-        if (i < M) {
-          const double n = 2 * i + sv;
-          dp += n * n * rhs[i];
-        }
-      const double cI = (cc * S2 - dp) * t.tau.vh_idv[(size_t)(sc.k * 2 + sv) * P + p];
-      const double* vh = t.tau.vh + (size_t)(sc.k * 2 + sv) * Mh * P + p;
-  #pragma unroll
-      for (int i = 0; i < MH; ++i)
-        if (i < M) {
+      {
+        // wall-normal velocity, parity c
+        const int sv = c;
+        const int M = (N - sv) / 2 + 1;
+        const CompS Vc{reinterpret_cast<double*>(pb.V) + base, 2 * P};
+        const CompT<RN> HVc{reinterpret_cast<RN*>(pb.HVP) + base, 2 * P};
+        const CompT<RN> HVr = kStageH ? CompT<RN>{reinterpret_cast<RN*>(sHVt) + 2 * pl + r, 2 * ppc} : HVc;
+        double S0 = 0.0, S2 = 0.0;
+        double rhs[MH];
+    #pragma unroll
+        for (int i = 0; i < MH; ++i) rhs[i] = 0.0;
+        for (int i = 0; i < M; ++i) {
           const int n = 2 * i + sv;
-          Vc[n] = rhs[i] + cI * vh[(size_t)i * P] - cc * Vc[n];
+          const double vn = Vc[n];
+          S0 += vn;
+          S2 = fma_rn((double)n * n, vn, S2);
         }
-    }
+        v_walk<MH, RN>(N, ny, ppc, sv, Vc, HVr, HVc, Hx, Hy, Hz, r, sgn, kx, kz, k2, cc, ibdn, sc, rhs);
+        double f[MH];
+        tau_seq<MH>(N, ny, sv, rhs, f, helm(sv), helm_isq(sv), 0.0, rowc);
+        const size_t vo = (size_t)b * P + p;
+        const double vw =
+            fma_rn(sc.theta, comp(pb.vw_new[vo], r) - comp(pb.vw_old[vo], r), comp(pb.vw_old[vo], r));
+        const double s = fma_rn(cc, S0, ((sv == 0) ? 0.5 : -0.5) * vw);
+        const TabSm TP{t.tau.pois + (size_t)sv * 4 * Mh * P + p, Mh, P};
+        tau_seq<MH>(N, ny, sv, f, rhs, TP, t.tau.pois_isq[(size_t)sv * P + p], s, rowc);
+        double dp = 0.0;
+    #pragma unroll
+        for (int i = 0; i < MH; ++i)
+          if (i < M) {
+            const double n = 2 * i + sv;
+            dp = fma_rn(n * n, rhs[i], dp);
+          }
+        const double cI = mul_rn(fma_rn(cc, S2, -dp), t.tau.vh_idv[(size_t)(sc.k * 2 + sv) * P + p]);
+        const double* vh = t.tau.vh + (size_t)(sc.k * 2 + sv) * Mh * P + p;
+    #pragma unroll
+        for (int i = 0; i < MH; ++i)
+          if (i < M) {
+            const int n = 2 * i + sv;
+            Vc[n] = fma_rn(-cc, Vc[n], fma_rn(cI, vh[(size_t)i * P], rhs[i]));
+          }
+      }
+    };
+    if (c == 0) solve(std::integral_constant<int, 0>{});
+    else solve(std::integral_constant<int, 1>{});
   } else {
     // ---- implicit solves under a free-slip top, in two rounds (omega_y or
     // the mean flow, then v), each closed after a barrier by the pair of class
     // threads (c, 1 - c) of a (mode, component); every thread reaches both
     // barriers
-    double* xch = reinterpret_cast<double*>(smem_raw + (size_t)(3 * ny + 6) * ppc * sizeof(double2));  // [2][4 ppc][6]
+    double* xch = reinterpret_cast<double*>(smem_raw + stage_post_batched_tile_bytes(ny, ppc, sizeof(CN)));  // [2][4 ppc][6]
     const int p = p0 + pl;
     const int pc = min(p, P - 1);
     const int row = pc / g.nxh, ix = pc % g.nxh;
@@ -1505,10 +1518,10 @@ __global__ void __launch_bounds__(64) stage_post_batched_kernel(Grid g, int B, P
               const double hv = (double)Hm[n * ppc].x;
               const double hp = XP[n];
               XP[n] = hv;
-              rhs[i] = -((1.0 + cc) * xn + sc.dt * (sc.gamma * hv + sc.zeta * hp)) * ibdn;
+              rhs[i] = mul_rn(fma_rn(1.0 + cc, xn, mul_rn(sc.dt, fma_rn(sc.gamma, hv, mul_rn(sc.zeta, hp)))), -ibdn);
               so += xn;
-              so2 += (double)n * n * xn;
-              if (sig == 0) wo += 2.0 / (1.0 - (double)n * n) * xn;
+              so2 = fma_rn((double)n * n, xn, so2);
+              if (sig == 0) wo = fma_rn(2.0 / (1.0 - (double)n * n), xn, wo);
             }
           }
           double psum, psum2;
@@ -1517,7 +1530,7 @@ __global__ void __launch_bounds__(64) stage_post_batched_kernel(Grid g, int B, P
           if (sig == 0) {
 #pragma unroll
             for (int i = 0; i < MH; ++i)
-              if (i < M) wp += 2.0 / (1.0 - 4.0 * (double)i * i) * f[i];
+              if (i < M) wp = fma_rn(2.0 / (1.0 - 4.0 * (double)i * i), f[i], wp);
           }
           mine[0] = psum; mine[1] = psum2; mine[2] = so; mine[3] = so2; mine[4] = wp; mine[5] = wo;
         } else {
@@ -1532,13 +1545,13 @@ __global__ void __launch_bounds__(64) stage_post_batched_kernel(Grid g, int B, P
             if (i < M) {
               const int n = 2 * i + sig;
               const double gn = Gc[n];
-              const RN hg = sgnn * (kzn * comp(Hx[n * ppc], ra) - kxn * comp(Hz[n * ppc], ra));
+              const RN hg = mul_rn(sgnn, fma_rn(-kxn, comp(Hz[n * ppc], ra), mul_rn(kzn, comp(Hx[n * ppc], ra))));
               const RN hp = HGr[n];
               HGc[n] = hg;
-              const RN q = dtn * (gan * hg + zen * hp);
-              rhs[i] = -((1.0 + cc) * gn + (double)q) * ibdn;
+              const RN q = mul_rn(dtn, fma_rn(gan, hg, mul_rn(zen, hp)));
+              rhs[i] = mul_rn(fma_rn(1.0 + cc, gn, (double)q), -ibdn);
               so += gn;
-              so2 += (double)n * n * gn;
+              so2 = fma_rn((double)n * n, gn, so2);
             }
           }
           double psum, psum2;
@@ -1558,9 +1571,9 @@ __global__ void __launch_bounds__(64) stage_post_batched_kernel(Grid g, int B, P
           for (int i = 0; i < N / 2 + 1; ++i) {
             const double n = 2 * i, w = 2.0 / (1.0 - n * n);
             us += u1[i];
-            u2 += n * n * u1[i];
-            uw += w * u1[i];
-            wq += w * (i == 0 ? 1.0 : He.Q(i));
+            u2 = fma_rn(n * n, u1[i], u2);
+            uw = fma_rn(w, u1[i], uw);
+            wq = fma_rn(w, i == 0 ? 1.0 : He.Q(i), wq);
           }
           close_free_slip_mean(se, so, qs(0, 0), qs(1, 0), qs(0, 1), qs(1, 1), wq, us, u2, uw, cc, sc.flux, &xe,
                                &xo, &fc);
@@ -1574,8 +1587,8 @@ __global__ void __launch_bounds__(64) stage_post_batched_kernel(Grid g, int B, P
           for (int i = 0; i < MH; ++i)
             if (i < M) {
               const int n = 2 * i + sig;
-              double v = f[i] - cc * X[n];
-              if (r == 0 && sig == 0) v += fc * t.tau.u1[(size_t)sc.k * Mh + i];
+              double v = fma_rn(-cc, X[n], f[i]);
+              if (r == 0 && sig == 0) v = fma_rn(fc, t.tau.u1[(size_t)sc.k * Mh + i], v);
               X[n] = v;
             }
         } else {
@@ -1584,7 +1597,7 @@ __global__ void __launch_bounds__(64) stage_post_batched_kernel(Grid g, int B, P
           for (int i = 0; i < MH; ++i)
             if (i < M) {
               const int n = 2 * i + sig;
-              Gc[n] = f[i] - cc * Gc[n];
+              Gc[n] = fma_rn(-cc, Gc[n], f[i]);
             }
         }
       }
@@ -1608,15 +1621,15 @@ __global__ void __launch_bounds__(64) stage_post_batched_kernel(Grid g, int B, P
           const double n = 2 * i + sig;
           const double vn = Vc[2 * i + sig];
           S0 += vn;
-          Bo += n * n * vn;
-          Ao += n * n * (n * n - 1.0) / 3.0 * vn;
+          Bo = fma_rn(n * n, vn, Bo);
+          Ao = fma_rn(n * n * (n * n - 1.0) / 3.0, vn, Ao);
         }
         v_walk<MH, RN>(N, ny, ppc, sig, Vc, HVr, HVc, Hx, Hy, Hz, r, sgn, kx, kz, k2, cc, ibdn, sc, rhs);
         tau_seq<MH>(N, ny, sig, rhs, f, helm(sig), helm_isq(sig), 0.0, rowc);
         const size_t vo = (size_t)b * P + pc;
         const double vw =
-            comp(pb.vw_old[vo], r) + sc.theta * (comp(pb.vw_new[vo], r) - comp(pb.vw_old[vo], r));
-        const double s = ((sig == 0) ? 0.5 : -0.5) * vw + cc * S0;
+            fma_rn(sc.theta, comp(pb.vw_new[vo], r) - comp(pb.vw_old[vo], r), comp(pb.vw_old[vo], r));
+        const double s = fma_rn(cc, S0, ((sig == 0) ? 0.5 : -0.5) * vw);
         const TabSm TP{t.tau.pois + (size_t)sig * 4 * Mh * P + pc, Mh, P};
         tau_seq<MH>(N, ny, sig, f, rhs, TP, t.tau.pois_isq[(size_t)sig * P + pc], s, rowc);
         double Ap = 0.0, Bp = 0.0;
@@ -1624,8 +1637,8 @@ __global__ void __launch_bounds__(64) stage_post_batched_kernel(Grid g, int B, P
         for (int i = 0; i < MH; ++i)
           if (i < M) {
             const double n = 2 * i + sig;
-            Bp += n * n * rhs[i];
-            Ap += n * n * (n * n - 1.0) / 3.0 * rhs[i];
+            Bp = fma_rn(n * n, rhs[i], Bp);
+            Ap = fma_rn(n * n * (n * n - 1.0) / 3.0, rhs[i], Ap);
           }
         mine[0] = Ap; mine[1] = Bp; mine[2] = Ao; mine[3] = Bo;
       }
@@ -1641,7 +1654,7 @@ __global__ void __launch_bounds__(64) stage_post_batched_kernel(Grid g, int B, P
         for (int i = 0; i < MH; ++i)
           if (i < M) {
             const int n = 2 * i + sig;
-            Vc[n] = rhs[i] + cI * vh[(size_t)i * P] - cc * Vc[n];
+            Vc[n] = fma_rn(-cc, Vc[n], fma_rn(cI, vh[(size_t)i * P], rhs[i]));
           }
       }
     }

@@ -9,13 +9,14 @@ constant flow rate.  Reported, over the window after the transient:
   the channels still turbulent when the copies branch (wall shear above twice
   the laminar 3 nu U_b / h), with the spread of the per-channel values;
 * the laminar upper bound 1 - tau_lam / <tau_w>_uncontrolled (Sec. 3.2 quotes
-  73.9 % at its Reynolds number);
+  73.9 % at its Reynolds number; tau_lam = 3 / Re_b in both geometries);
 * on the sensing plane, the rms of u' and v' in wall units of the uncontrolled
   flow and the fractions of the four quadrants of (u', v') (Q2 ejections,
   Q4 sweeps; Sec. 4.2-4.3 discuss how control changes them).
 
 The paper reports DR of 26 % (minimal channel) and 20 % (larger channel) for
-opposition control at y+ = 15, after an initial transient of t+ = 500.
+opposition control at y+ = 15, after an initial transient of t+ = 500, in
+its open channel (--top-bc 1 here; the default is the closed channel).
 Every step runs through the C ABI; this module only averages its outputs.
 
     python -m paper_2301_09889_gb300.validate --grid minimal --batch 16
@@ -78,15 +79,19 @@ def _step(env, act, obs, tau, rew):
 
 
 def run(grid: str = "minimal", batch: int = 16, precision: int = 0, seed: int = 0, amplitude: float = 1.0,
-        kmax: int = 4, t_spin: float = 300.0, t_trans: float = 43.2, t_avg: float = 300.0, spa: int = 20,
+        kmax: int = 4, t_spin: float = 300.0, t_trans: float | None = None, t_avg: float = 300.0, spa: int = 20,
         alpha: float = 1.0, y_plus: float = 15.0, dt: float = 0.005, re_tau: float = 180.0,
-        re_bulk: float = 2800.0) -> dict:
-    """Times in bulk units (h / U_b); t_trans = 43.2 is t+ = 500 at Re_tau 180,
-    Re_b 2800.  spa: solver steps per env_step call (wall shear averaged over
-    them)."""
+        re_bulk: float = 2800.0, top_bc: int = 0) -> dict:
+    """Times in bulk units (U_b and the unit of y); the transient defaults to
+    t+ = 500, t = 500 nu / u_tau^2 (43.2 in the closed channel at Re_tau 180,
+    Re_b 2800; 86.4 in the open channel, top_bc = 1, whose nu is 2 / Re_b).
+    spa: solver steps per env_step call (wall shear averaged over them)."""
     t0 = time.perf_counter()
+    nu = (2.0 if top_bc == 1 else 1.0) / re_bulk
+    if t_trans is None:
+        t_trans = 500.0 * nu / (re_tau / re_bulk) ** 2
     base = dict(GRIDS[grid], re_tau=re_tau, re_bulk=re_bulk, dt=dt, precision=precision, batch=batch,
-                steps_per_action=spa, y_sense_plus=y_plus, alpha=alpha)
+                steps_per_action=spa, y_sense_plus=y_plus, alpha=alpha, top_bc=top_bc)
     nz, nx = base["nz"], base["nx"]
     t_call = spa * dt
     zero = np.zeros((batch, nz, nx))
@@ -124,6 +129,7 @@ def run(grid: str = "minimal", batch: int = 16, precision: int = 0, seed: int = 
             native.env_destroy(ctl)
     out = {
         "grid": grid, "nx_ny_nz": [nx, base["ny"], nz], "precision": "f64" if precision == 0 else "mixed",
+        "geometry": "open channel, free-slip top" if top_bc == 1 else "closed channel",
         "batch": batch, "seed": seed, "amplitude": amplitude, "kmax": kmax, "dt": dt, "steps_per_call": spa,
         "t_spin": t_spin, "t_transient": t_trans, "t_average": t_avg, "alpha": alpha,
         "sensing_node": int(info.j_sense), "sensing_y_plus": float(info.y_plus_sense),
@@ -156,14 +162,16 @@ def main(argv=None):
     ap.add_argument("--amplitude", type=float, default=1.0)
     ap.add_argument("--kmax", type=int, default=4)
     ap.add_argument("--t-spin", type=float, default=300.0)
-    ap.add_argument("--t-transient", type=float, default=43.2)
+    ap.add_argument("--t-transient", type=float, default=None, help="default: t+ = 500")
     ap.add_argument("--t-average", type=float, default=300.0)
     ap.add_argument("--steps-per-call", type=int, default=20)
     ap.add_argument("--alpha", type=float, default=1.0)
     ap.add_argument("--y-plus", type=float, default=15.0)
+    ap.add_argument("--top-bc", type=int, choices=(0, 1), default=0,
+                    help="1: the paper's open channel (free-slip top, sensing node y+ = 15.17 at 65 nodes)")
     a = ap.parse_args(argv)
     res = run(a.grid, a.batch, a.precision, a.seed, a.amplitude, a.kmax, a.t_spin, a.t_transient, a.t_average,
-              a.steps_per_call, a.alpha, a.y_plus)
+              a.steps_per_call, a.alpha, a.y_plus, top_bc=a.top_bc)
     print(json.dumps(res))
 
 

@@ -287,13 +287,12 @@ def test_re550_grid_mixed_wall_spectrum_and_boundary_conditions(native_gpu):
     assert info.plane_cluster == 16
 
 
-def test_re550_grid_fp64_is_reported_unsupported(native_gpu):
-    """The FP64 padded plane of 256x256 modes exceeds the shared memory of any
-    cluster: env_create refuses it with CH_ERR_UNSUPPORTED."""
-    native = native_gpu
-    with pytest.raises(native.ChannelError) as exc:
-        native.env_create(native.params(**RE550, precision=0))
-    assert exc.value.code == -8
+def test_re550_grid_fp64_wall_spectrum_and_boundary_conditions(native_gpu):
+    """256x193x256 channel at Re_tau 550 in FP64: the padded plane fits no
+    cluster's shared memory, so the nonlinear term runs in three passes
+    through global memory (plane_cluster reported 0)."""
+    info = _large_grid_step_checks(native_gpu, RE550, 0, 6, 8)
+    assert info.plane_cluster == 0
 
 
 def test_batched_implicit_half_against_oracle(native_gpu):
