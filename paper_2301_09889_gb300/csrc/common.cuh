@@ -66,6 +66,11 @@ __host__ __device__ __forceinline__ float mul_rn(float a, float b) {
   __host__ __device__ __forceinline__ C operator-(C a, C b) { return mk(a.x - b.x, a.y - b.y); } \
   __host__ __device__ __forceinline__ C operator*(R s, C a) { return mk(s * a.x, s * a.y); }     \
   __host__ __device__ __forceinline__ C cmul(C a, C b) {                                  \
+    return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);                              \
+  }                                                                                       \
+  /* the same product with its fused multiply-adds pinned (code shared by several     */ \
+  /* kernel forms whose results must agree bit for bit)                                */ \
+  __host__ __device__ __forceinline__ C cmul_rn(C a, C b) {                               \
     return mk(fma_rn(a.x, b.x, -mul_rn(a.y, b.y)), fma_rn(a.x, b.y, mul_rn(a.y, b.x)));    \
   }                                                                                       \
   __host__ __device__ __forceinline__ C cconj(C a) { return mk(a.x, -a.y); }                \

@@ -310,7 +310,7 @@ __device__ __forceinline__ void lines_dif(double2* buf, const double2* tw, int n
 #pragma unroll
       for (int u = 0; u < r; ++u) {
         double2 y = x[u];
-        if (u > 0 && q > 0) y = cmul(y, tw[q * u * tstep]);
+        if (u > 0 && q > 0) y = cmul_rn(y, tw[q * u * tstep]);
         base[(i0 + u * m) * G] = y;
       }
     }
