@@ -196,7 +196,10 @@ def measured_peaks() -> dict:
 # under profiles/); absent where no capture of the current kernel exists
 TRAFFIC_BYTES = {
     ("larger_fp64", "nonlinear_plane"): 12.639232e6,
-    ("minimal_batch256_mixed", "stage_post"): (151.807488 + 41.975552) * 1e6,
+    ("minimal_batch256_mixed", "stage_post"): (151.877632 + 43.473408) * 1e6,
+    # the three passes of one FP64 256x256-mode stage (z inverse + x pass + z forward)
+    ("large550_fp64", "nonlinear_plane"): (604.911872 + 852.392448 + 910.863872 + 413.775360 + 455.520000
+                                           + 259.116544) * 1e6,
 }
 
 # FP64 FMA rate: 152 SMs x 2 FP64 FMA/clk/SM x 2 FLOP x 2.07 GHz; an FMA-chain probe

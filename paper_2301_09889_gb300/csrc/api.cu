@@ -419,7 +419,12 @@ int build_tables(ch_env* env) {
         const double ibdn = 1.0 / (rk_beta(k) * p.dt * env->nu);
         const Factor Fh = host_factor(N, sig, k2 + ibdn);
         const size_t slot = (size_t)(k * 2 + sig);
-        put(helm, slot * 4 * Mh * P, Fh, M, pp);
+        // every Helmholtz right-hand side of the stage carries the factor
+        // -1/(beta dt nu); the solve is linear in it, so the device tables take
+        // it in the elimination factor e and the kernels leave it out
+        Factor Fs = Fh;
+        for (double& e : Fs.e) e *= -ibdn;
+        put(helm, slot * 4 * Mh * P, Fs, M, pp);
         helm_isq[slot * P + pp] = Fh.isq;
         {
           double sq = 0.0, sq2 = 0.0;

@@ -9,7 +9,7 @@ namespace chdns {
 // launchers
 // ---------------------------------------------------------------------------
 static int mh_bucket(int need) {
-  const int b[] = {5, 9, 17, 33, 49, 65, 101};
+  const int b[] = {5, 9, 17, 33, 49, 65, 97, 101};
   for (int v : b)
     if (need <= v) return v;
   return 0;
@@ -43,6 +43,7 @@ cudaError_t launch_stage_pre(const Grid& g, int B, const PencilBufs& pb, const D
     case 33: return pre_mh<RN, 33>(g, B, pb, t, q, ppc, smem, st);
     case 49: return pre_mh<RN, 49>(g, B, pb, t, q, ppc, smem, st);
     case 65: return pre_mh<RN, 65>(g, B, pb, t, q, ppc, smem, st);
+    case 97: return pre_mh<RN, 97>(g, B, pb, t, q, ppc, smem, st);
     case 101: return pre_mh<RN, 101>(g, B, pb, t, q, ppc, smem, st);
     default: return cudaErrorInvalidValue;
   }
@@ -84,6 +85,7 @@ cudaError_t launch_stage_post(const Grid& g, int B, const PencilBufs& pb, const 
       case 33: return post_batched_mh<RN, 33, 0>(g, B, pb, t, h, sc, ppc, smem, st);
       case 49: return post_batched_mh<RN, 49, 0>(g, B, pb, t, h, sc, ppc, smem, st);
       case 65: return post_batched_mh<RN, 65, 0>(g, B, pb, t, h, sc, ppc, smem, st);
+      case 97: return post_batched_mh<RN, 97, 0>(g, B, pb, t, h, sc, ppc, smem, st);
       case 101: return post_batched_mh<RN, 101, 0>(g, B, pb, t, h, sc, ppc, smem, st);
       default: return cudaErrorInvalidValue;
     }
@@ -96,6 +98,7 @@ cudaError_t launch_stage_post(const Grid& g, int B, const PencilBufs& pb, const 
     case 33: return post_mh<RN, 33, 0>(g, B, pb, t, h, sc, ppc, smem, st);
     case 49: return post_mh<RN, 49, 0>(g, B, pb, t, h, sc, ppc, smem, st);
     case 65: return post_mh<RN, 65, 0>(g, B, pb, t, h, sc, ppc, smem, st);
+    case 97: return post_mh<RN, 97, 0>(g, B, pb, t, h, sc, ppc, smem, st);
     case 101: return post_mh<RN, 101, 0>(g, B, pb, t, h, sc, ppc, smem, st);
     default: return cudaErrorInvalidValue;
   }

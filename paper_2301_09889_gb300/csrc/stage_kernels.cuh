@@ -102,6 +102,11 @@ __device__ __forceinline__ void tau_seq(int N, int ny, int sig, const double (&r
     if (i < M) f[i] = fma_rn(T.Q(i), f0, f[i]);
 }
 
+// symmetry class of a solve compiled for one class (a constant) or for both
+template <int V>
+__device__ __forceinline__ constexpr int class_of(std::integral_constant<int, V>) { return V; }
+__device__ __forceinline__ int class_of(int v) { return v; }
+
 // ---------------------------------------------------------------------------
 // Free-slip top (open channel, top_bc = 1; paper Sec. 3.1).  The tau rows
 // n >= 2 are those of the no-slip channel, so elimination still leaves each
@@ -229,7 +234,7 @@ __device__ __forceinline__ void v_walk(int N, int ny, int ppc, int sv, const Com
                                        const CompT<RN>& HVw,
                                        const typename cpx<RN>::T* Hx, const typename cpx<RN>::T* Hy,
                                        const typename cpx<RN>::T* Hz, int r, double sgn, double kx, double kz,
-                                       double k2, double cc, double ibdn, const StageCoef& sc, double (&rhs)[MH]) {
+                                       double k2, double cc, const StageCoef& sc, double (&rhs)[MH]) {
   using CN = typename cpx<RN>::T;
   const int ra = 1 - r;
   auto comp = [](const CN z, int qd) { return qd == 0 ? z.x : z.y; };
@@ -260,7 +265,7 @@ __device__ __forceinline__ void v_walk(int N, int ny, int ppc, int sv, const Com
       const RN hp = HVr[n];
       HVw[n] = hv;
       const RN q = mul_rn(dtn, fma_rn(gan, hv, mul_rn(zen, hp)));
-      rhs[i] = mul_rn(fma_rn(1.0 + cc, phi, (double)q), -ibdn);
+      rhs[i] = fma_rn(1.0 + cc, phi, (double)q);
     }
   }
 }
@@ -740,9 +745,13 @@ __global__ void __launch_bounds__(128) stage_pre_kernel(Grid g, int B, PencilBuf
 //   (D^2 - k^2) v'   = phi',   phi = (D^2 - k^2) v^{k-1},
 // lam = k^2 + 1/(beta dt nu).  (D^2 - k^2) X = (D^2 - lam) X + X/(beta dt nu)
 // holds for every coefficient row, so this is the same tau discretisation as
-// the plain form without derivatives of the old fields.  The wall rows of g'
-// and v' carry c times the old wall values; the influence matrix fixes
-// Dv'(+-1) = c Dv^{k-1}(+-1).  Then g^k = g' - c g^{k-1}, v^k = v' - c v^{k-1}.
+// the plain form without derivatives of the old fields.  The solve is linear
+// in its right-hand side, so the factor -1/(beta dt nu), the same for every
+// coefficient of a stage, is folded into the elimination factors e of the
+// Helmholtz tables on the host: the kernels form (1 + c) g + dt (...) only.
+// The wall rows of g' and v' carry c times the old wall values; the influence
+// matrix fixes Dv'(+-1) = c Dv^{k-1}(+-1).  Then g^k = g' - c g^{k-1},
+// v^k = v' - c v^{k-1}.
 //   h_g = i kz H_x - i kx H_z,  h_v = -k^2 H_y - D(i kx H_x + i kz H_z).
 // Thread (mode, class c, component r, equation e): e = 0 omega_y on parity
 // 1-c, e = 1 v on parity c.  The mean mode solves U at constant flow rate
@@ -886,7 +895,6 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
       const int c = combo & 1, r = (combo >> 1) & 1, e = combo >> 2;
       const int row = p / g.nxh, ix = p % g.nxh;
       const double cc = sc.alpha / sc.beta;
-      const double ibdn = 1.0 / (sc.beta * sc.dt * sc.nu);
       const double* rowc = t.tau.rowc;
       const CN* Hx = reinterpret_cast<const CN*>(sH) + pl;
       const CN* Hy = Hx + ny * ppc;
@@ -914,7 +922,7 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
               const double hv = (double)Hm[n * ppc].x;
               const double hp = XP[n];
               XP[n] = hv;
-              rhs[i] = mul_rn(fma_rn(1.0 + cc, xn, mul_rn(sc.dt, fma_rn(sc.gamma, hv, mul_rn(sc.zeta, hp)))), -ibdn);
+              rhs[i] = fma_rn(1.0 + cc, xn, mul_rn(sc.dt, fma_rn(sc.gamma, hv, mul_rn(sc.zeta, hp))));
               sum += xn;
               if (s == 0) flux_old = fma_rn(2.0 / (1.0 - (double)n * n), xn, flux_old);
             }
@@ -962,7 +970,7 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
               const RN hp = HGc[n];
               HGc[n] = hg;
               const RN q = mul_rn(dtn, fma_rn(gan, hg, mul_rn(zen, hp)));
-              rhs[i] = mul_rn(fma_rn(1.0 + cc, gn, (double)q), -ibdn);
+              rhs[i] = fma_rn(1.0 + cc, gn, (double)q);
               sum += gn;
             }
           }
@@ -990,7 +998,7 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
             S2 = fma_rn((double)n * n, vn, S2);
           }
           // one walk from n = N down to 0: Dv, D^2 v, t = i kx H_x + i kz H_z, Dt
-          v_walk<MH, RN>(N, ny, ppc, sv, Vc, HVc, HVc, Hx, Hy, Hz, r, sgn, kx, kz, k2, cc, ibdn, sc, rhs);
+          v_walk<MH, RN>(N, ny, ppc, sv, Vc, HVc, HVc, Hx, Hy, Hz, r, sgn, kx, kz, k2, cc, sc, rhs);
           double f[MH];
           tau_seq<MH>(N, ny, sv, rhs, f, helm(sv), ss[(0 * 2 + sv) * ppc + pl], 0.0, rowc);
           const size_t vo = (size_t)b * P + p;
@@ -1030,7 +1038,6 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
     const int row = p / g.nxh, ix = p % g.nxh;
     const bool live = p < P && combo < 8 && row != g.nz / 2 && !(p == 0 && r == 1);
     const double cc = sc.alpha / sc.beta;
-    const double ibdn = 1.0 / (sc.beta * sc.dt * sc.nu);
     const double* rowc = t.tau.rowc;
     const CN* Hx = reinterpret_cast<const CN*>(sH) + pl;
     const CN* Hy = Hx + ny * ppc;
@@ -1064,7 +1071,7 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
             const double hv = (double)Hm[n * ppc].x;
             const double hp = XP[n];
             XP[n] = hv;
-            rhs[i] = mul_rn(fma_rn(1.0 + cc, xn, mul_rn(sc.dt, fma_rn(sc.gamma, hv, mul_rn(sc.zeta, hp)))), -ibdn);
+            rhs[i] = fma_rn(1.0 + cc, xn, mul_rn(sc.dt, fma_rn(sc.gamma, hv, mul_rn(sc.zeta, hp))));
             so += xn;
             so2 = fma_rn((double)n * n, xn, so2);
             if (sig == 0) wo = fma_rn(2.0 / (1.0 - (double)n * n), xn, wo);
@@ -1099,7 +1106,7 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
             const RN hp = HGc[n];
             HGc[n] = hg;
             const RN q = mul_rn(dtn, fma_rn(gan, hg, mul_rn(zen, hp)));
-            rhs[i] = mul_rn(fma_rn(1.0 + cc, gn, (double)q), -ibdn);
+            rhs[i] = fma_rn(1.0 + cc, gn, (double)q);
             so += gn;
             so2 = fma_rn((double)n * n, gn, so2);
           }
@@ -1126,7 +1133,7 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
           Bo = fma_rn(n * n, vn, Bo);
           Ao = fma_rn(n * n * (n * n - 1.0) / 3.0, vn, Ao);
         }
-        v_walk<MH, RN>(N, ny, ppc, sig, Vc, HVc, HVc, Hx, Hy, Hz, r, sgn, kx, kz, k2, cc, ibdn, sc, rhs);
+        v_walk<MH, RN>(N, ny, ppc, sig, Vc, HVc, HVc, Hx, Hy, Hz, r, sgn, kx, kz, k2, cc, sc, rhs);
         tau_seq<MH>(N, ny, sig, rhs, f, helm(sig), ss[(0 * 2 + sig) * ppc + pl], 0.0, rowc);
         const size_t vo = (size_t)b * P + p;
         const double vw =
@@ -1328,7 +1335,6 @@ __global__ void __launch_bounds__(64) stage_post_batched_kernel(Grid g, int B, P
     const int row = p / g.nxh, ix = p % g.nxh;
     if (row == g.nz / 2) return;  // Nyquist row stays zero
     const double cc = sc.alpha / sc.beta;
-    const double ibdn = 1.0 / (sc.beta * sc.dt * sc.nu);
     const double* rowc = t.tau.rowc;
     const CN* Hx = sN + pl;
     const CN* Hy = Hx + ny * ppc;
@@ -1338,11 +1344,13 @@ __global__ void __launch_bounds__(64) stage_post_batched_kernel(Grid g, int B, P
     auto helm = [&](int sig) { return TabSm{t.tau.helm + (size_t)(sc.k * 2 + sig) * 4 * Mh * P + p, Mh, P}; };
     auto helm_isq = [&](int sig) { return t.tau.helm_isq[(size_t)(sc.k * 2 + sig) * P + p]; };
     // The class c is uniform over each warp for tiles of 16 or more modes, so
-    // the solve is compiled once per class: every parity-dependent factor
-    // (2 (n + 1), n^2, the row bounds) becomes a constant.  The arithmetic is
-    // the same as with a run-time class (the factors are exact small integers).
+    // for up to 65 nodes (MH <= 33) the solve is compiled once per class: every
+    // parity-dependent factor (2 (n + 1), n^2, the row bounds) becomes a
+    // constant.  Larger buckets keep one run-time class (their unrolled code
+    // would double).  The arithmetic is the same either way: the factors are
+    // exact small integers and every fused operation is pinned.
     auto solve = [&](auto cls) {
-      constexpr int c = decltype(cls)::value;
+      const int c = class_of(cls);
       if (p == 0) {
         // mean mode: U (r = 0) at constant flow rate and W (r = 1), parity c
         const int e = r, s = c;
@@ -1361,7 +1369,7 @@ __global__ void __launch_bounds__(64) stage_post_batched_kernel(Grid g, int B, P
             const double hv = (double)Hm[n * ppc].x;
             const double hp = XP[n];
             XP[n] = hv;
-            rhs[i] = mul_rn(fma_rn(1.0 + cc, xn, mul_rn(sc.dt, fma_rn(sc.gamma, hv, mul_rn(sc.zeta, hp)))), -ibdn);
+            rhs[i] = fma_rn(1.0 + cc, xn, mul_rn(sc.dt, fma_rn(sc.gamma, hv, mul_rn(sc.zeta, hp))));
             sum += xn;
             if (s == 0) flux_old = fma_rn(2.0 / (1.0 - (double)n * n), xn, flux_old);
           }
@@ -1411,7 +1419,7 @@ __global__ void __launch_bounds__(64) stage_post_batched_kernel(Grid g, int B, P
             const RN hp = HGr[n];
             HGc[n] = hg;
             const RN q = mul_rn(dtn, fma_rn(gan, hg, mul_rn(zen, hp)));
-            rhs[i] = mul_rn(fma_rn(1.0 + cc, gn, (double)q), -ibdn);
+            rhs[i] = fma_rn(1.0 + cc, gn, (double)q);
             sum += gn;
           }
         }
@@ -1440,7 +1448,7 @@ __global__ void __launch_bounds__(64) stage_post_batched_kernel(Grid g, int B, P
           S0 += vn;
           S2 = fma_rn((double)n * n, vn, S2);
         }
-        v_walk<MH, RN>(N, ny, ppc, sv, Vc, HVr, HVc, Hx, Hy, Hz, r, sgn, kx, kz, k2, cc, ibdn, sc, rhs);
+        v_walk<MH, RN>(N, ny, ppc, sv, Vc, HVr, HVc, Hx, Hy, Hz, r, sgn, kx, kz, k2, cc, sc, rhs);
         double f[MH];
         tau_seq<MH>(N, ny, sv, rhs, f, helm(sv), helm_isq(sv), 0.0, rowc);
         const size_t vo = (size_t)b * P + p;
@@ -1466,8 +1474,12 @@ __global__ void __launch_bounds__(64) stage_post_batched_kernel(Grid g, int B, P
           }
       }
     };
-    if (c == 0) solve(std::integral_constant<int, 0>{});
-    else solve(std::integral_constant<int, 1>{});
+    if constexpr (MH <= 33) {
+      if (c == 0) solve(std::integral_constant<int, 0>{});
+      else solve(std::integral_constant<int, 1>{});
+    } else {
+      solve(c);
+    }
   } else {
     // ---- implicit solves under a free-slip top, in two rounds (omega_y or
     // the mean flow, then v), each closed after a barrier by the pair of class
@@ -1481,7 +1493,6 @@ __global__ void __launch_bounds__(64) stage_post_batched_kernel(Grid g, int B, P
     const bool mean = p == 0;
     const int mate = (1 - c) * 2 * ppc + tid % (2 * ppc);
     const double cc = sc.alpha / sc.beta;
-    const double ibdn = 1.0 / (sc.beta * sc.dt * sc.nu);
     const double* rowc = t.tau.rowc;
     const CN* Hx = sN + pl;
     const CN* Hy = Hx + ny * ppc;
@@ -1518,7 +1529,7 @@ __global__ void __launch_bounds__(64) stage_post_batched_kernel(Grid g, int B, P
               const double hv = (double)Hm[n * ppc].x;
               const double hp = XP[n];
               XP[n] = hv;
-              rhs[i] = mul_rn(fma_rn(1.0 + cc, xn, mul_rn(sc.dt, fma_rn(sc.gamma, hv, mul_rn(sc.zeta, hp)))), -ibdn);
+              rhs[i] = fma_rn(1.0 + cc, xn, mul_rn(sc.dt, fma_rn(sc.gamma, hv, mul_rn(sc.zeta, hp))));
               so += xn;
               so2 = fma_rn((double)n * n, xn, so2);
               if (sig == 0) wo = fma_rn(2.0 / (1.0 - (double)n * n), xn, wo);
@@ -1549,7 +1560,7 @@ __global__ void __launch_bounds__(64) stage_post_batched_kernel(Grid g, int B, P
               const RN hp = HGr[n];
               HGc[n] = hg;
               const RN q = mul_rn(dtn, fma_rn(gan, hg, mul_rn(zen, hp)));
-              rhs[i] = mul_rn(fma_rn(1.0 + cc, gn, (double)q), -ibdn);
+              rhs[i] = fma_rn(1.0 + cc, gn, (double)q);
               so += gn;
               so2 = fma_rn((double)n * n, gn, so2);
             }
@@ -1624,7 +1635,7 @@ __global__ void __launch_bounds__(64) stage_post_batched_kernel(Grid g, int B, P
           Bo = fma_rn(n * n, vn, Bo);
           Ao = fma_rn(n * n * (n * n - 1.0) / 3.0, vn, Ao);
         }
-        v_walk<MH, RN>(N, ny, ppc, sig, Vc, HVr, HVc, Hx, Hy, Hz, r, sgn, kx, kz, k2, cc, ibdn, sc, rhs);
+        v_walk<MH, RN>(N, ny, ppc, sig, Vc, HVr, HVc, Hx, Hy, Hz, r, sgn, kx, kz, k2, cc, sc, rhs);
         tau_seq<MH>(N, ny, sig, rhs, f, helm(sig), helm_isq(sig), 0.0, rowc);
         const size_t vo = (size_t)b * P + pc;
         const double vw =

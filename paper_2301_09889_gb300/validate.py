@@ -90,7 +90,14 @@ def run(grid: str = "minimal", batch: int = 16, precision: int = 0, seed: int = 
     nu = (2.0 if top_bc == 1 else 1.0) / re_bulk
     if t_trans is None:
         t_trans = 500.0 * nu / (re_tau / re_bulk) ** 2
-    base = dict(GRIDS[grid], re_tau=re_tau, re_bulk=re_bulk, dt=dt, precision=precision, batch=batch,
+    box = dict(GRIDS[grid])
+    if top_bc == 1:
+        # the paper's boxes are given in units of the channel height h; in the
+        # open-channel reading h is the whole height, 2 in units of y, so the
+        # lengths double (the minimal box 2.67h x h x 0.8h is 5.34 x 2 x 1.6)
+        box["lx"] *= 2.0
+        box["lz"] *= 2.0
+    base = dict(box, re_tau=re_tau, re_bulk=re_bulk, dt=dt, precision=precision, batch=batch,
                 steps_per_action=spa, y_sense_plus=y_plus, alpha=alpha, top_bc=top_bc)
     nz, nx = base["nz"], base["nx"]
     t_call = spa * dt
@@ -128,7 +135,8 @@ def run(grid: str = "minimal", batch: int = 16, precision: int = 0, seed: int = 
         if ctl is not None:
             native.env_destroy(ctl)
     out = {
-        "grid": grid, "nx_ny_nz": [nx, base["ny"], nz], "precision": "f64" if precision == 0 else "mixed",
+        "grid": grid, "nx_ny_nz": [nx, base["ny"], nz], "lx_lz": [base["lx"], base["lz"]],
+        "precision": "f64" if precision == 0 else "mixed",
         "geometry": "open channel, free-slip top" if top_bc == 1 else "closed channel",
         "batch": batch, "seed": seed, "amplitude": amplitude, "kmax": kmax, "dt": dt, "steps_per_call": spa,
         "t_spin": t_spin, "t_transient": t_trans, "t_average": t_avg, "alpha": alpha,

@@ -94,3 +94,18 @@ def test_quadrant_fractions_and_fluctuation_removal():
     st2.add(np.array([1.0]), obs, np.array([True]))
     assert st2.summary(1.0)["quadrants_Q1_Q2_Q3_Q4"] == [0.5, 0.0, 0.5, 0.0]
     assert st2.summary(2.0)["uv_plus"] == pytest.approx(1.0 / 4.0)
+
+
+def test_open_channel_run_uses_the_papers_box_and_transient(monkeypatch):
+    """top_bc = 1: the boxes are given in units of the channel height, which
+    is 2 in units of y, so the lengths double; the default transient is
+    t+ = 500 with nu = 2 / Re_b."""
+    fake = FakeBinding()
+    monkeypatch.setattr(validate, "native", fake)
+    out = validate.run("minimal", batch=3, t_spin=1.0, t_avg=1.0, spa=10, top_bc=1)
+    p = fake.handles[0].p
+    assert p.top_bc == 1 and fake.handles[1].p.top_bc == 1
+    assert p.lx == pytest.approx(2 * 2.67) and p.lz == pytest.approx(2 * 0.8)
+    assert out["lx_lz"] == [pytest.approx(5.34), pytest.approx(1.6)]
+    assert out["t_transient"] == pytest.approx(500 * (2 / 2800) / (180 / 2800) ** 2)
+    assert out["geometry"] == "open channel, free-slip top"
