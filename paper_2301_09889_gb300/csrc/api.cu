@@ -355,6 +355,16 @@ int setup_plane(ch_env* env, PlaneArgs<R>* a, size_t* smem) {
     *smem = zb + (size_t)6 * np * g.mx * csz;
   }
   if (!a->S) return CH_ERR_UNSUPPORTED;
+  // planes of 16 x 16 modes run one plane per team of threads with the line
+  // transforms in registers once the batch supplies enough planes to fill
+  // the SMs (four per SM, two per CTA); fewer planes keep the cluster split,
+  // which spreads each plane over S CTAs
+  a->team16 = 0;
+  if (plane16_shape(g.mx, g.mz, g.nxh, g.nz) && (long)g.ny * env->B >= 4L * nsm) {
+    a->team16 = 1;
+    a->S = 1;
+    a->Lz = g.mz;
+  }
   if (!fft_plan(g.mx, &a->px) || !fft_plan(a->Lz, &a->pz)) return CH_ERR_UNSUPPORTED;
   if (a->S > 8) {
     int clusters = 0;

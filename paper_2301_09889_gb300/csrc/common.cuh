@@ -465,6 +465,9 @@ struct PlaneArgs {
   FftPlan px, pz;
   R scale;             // 1 / (mx mz)
   const int* active;   // [B] slots to process (nullptr: all)
+  // planes of 16 x 16 modes in batches that fill the GPU: one plane per team
+  // of threads, line transforms in registers (plane_small.cu)
+  int team16;
   // planes that fit no cluster's shared memory: three passes through global
   // memory (z inverse, x transforms and products, z forward)
   int two_pass;

@@ -11,6 +11,10 @@ template <typename R>
 cudaError_t launch_plane(const PlaneArgs<R>& a, int B, size_t smem, cudaStream_t st);
 template <typename R>
 cudaError_t plane_max_clusters(const PlaneArgs<R>& a, size_t smem, int* clusters);
+// nonlinear term of planes of 16 x 16 modes, line transforms in registers (plane_small.cu)
+bool plane16_shape(int mx, int mz, int nxh, int nz);
+template <typename R>
+cudaError_t launch_plane16(const PlaneArgs<R>& a, int B, cudaStream_t st);
 // nonlinear term in three passes through global memory (plane2.cu), FP64
 bool two_pass_shape_ok(int mx, int mz, int nxh);
 template <typename R>

@@ -371,6 +371,7 @@ static SmemLimit& generic_limit() {
 
 template <typename R>
 cudaError_t launch_plane(const PlaneArgs<R>& a, int B, size_t smem, cudaStream_t st) {
+  if (a.team16) return launch_plane16<R>(a, B, st);
   if constexpr (sizeof(R) == 8) {
     if (a.two_pass) return launch_plane_two_pass<R>(a, B, st);
     CH_PLANE_CT(24, 6, 8, 3)
