@@ -102,8 +102,8 @@ typedef struct ch_info {
     size_t state_bytes;      /* bytes of one environment's serialised state                */
     size_t device_bytes;     /* device memory held by the handle                           */
     int plane_cluster;       /* CTAs of a thread-block cluster cooperating on one y-plane of
-                                the nonlinear term; 0: no cluster holds the plane (FP64
-                                planes of 256 x 256 modes), the term runs in three passes
+                                the nonlinear term; 0: no portable cluster holds the plane
+                                (planes of 256 x 256 modes), the term runs in three passes
                                 through a global scratch array (z inverse, x transforms and
                                 products, z forward)                                     */
     int launches_per_step;   /* kernels launched by one env_step                            */
@@ -112,6 +112,10 @@ typedef struct ch_info {
     int ppc_pre, ppc_post;   /* Fourier modes per CTA of the explicit and implicit halves */
     int tuned;               /* 1 if the tile shapes were chosen by timing (autotune)    */
     double tune_ms;          /* host time env_create spent timing candidates            */
+    int plane_team;          /* 1: planes of 16 x 16 modes in a batch of at least four
+                                planes per SM; each padded 24 x 24 plane is owned by a team
+                                of 96 threads that transforms its 24-point lines in
+                                registers (plane_cluster is then 1); 0 otherwise          */
 } ch_info_t;
 
 typedef struct ch_env ch_env_t;

@@ -310,13 +310,11 @@ int setup_plane(ch_env* env, PlaneArgs<R>* a, size_t* smem) {
     if ((size_t)6 * (g.mz / S) * g.nxh * csz > 160 * 1024) continue;
     feasible[nf++] = S;
   }
-  // a 16-CTA cluster (non-portable opt-in) only where no portable size fits
-  if (!nf && g.mz % 16 == 0 && (g.mz / 16) % 2 == 0 && (size_t)6 * (g.mz / 16) * g.nxh * csz <= 160 * 1024)
-    feasible[nf++] = 16;
-  if (!nf) {
-    // FP64 planes of 256 x 256 modes: three passes through a global scratch
-    // array (only for handles that step in FP64)
-    if (sizeof(R) != 8 || env->prm.precision != 0 || !two_pass_shape_ok(g.mx, g.mz, g.nxh)) return CH_ERR_UNSUPPORTED;
+  // planes of 256 x 256 modes, whose padded z-slab fits no portable cluster
+  // in either precision: three passes through a global scratch array, whose
+  // traffic costs less than the serialisation of a 16-CTA cluster over the
+  // few such clusters the device holds at once
+  if (!nf && two_pass_shape_ok(g.mx, g.mz, g.nxh)) {
     a->two_pass = 1;
     a->S = 1;
     a->Lz = g.mz;
@@ -337,6 +335,10 @@ int setup_plane(ch_env* env, PlaneArgs<R>* a, size_t* smem) {
     a->scale = (R)(1.0 / ((double)g.mx * g.mz));
     return CH_OK;
   }
+  // a 16-CTA cluster (non-portable opt-in) only where no portable size fits
+  if (!nf && g.mz % 16 == 0 && (g.mz / 16) % 2 == 0 && (size_t)6 * (g.mz / 16) * g.nxh * csz <= 160 * 1024)
+    feasible[nf++] = 16;
+  if (!nf) return CH_ERR_UNSUPPORTED;
   int S = feasible[nf - 1];
   for (int k = 0; k < nf; ++k)
     if ((long)g.ny * env->B * feasible[k] >= nsm) { S = feasible[k]; break; }
@@ -711,6 +713,17 @@ int run_stage(ch_env* env, int k, double theta) {
   return CH_OK;
 }
 
+// kernels of one env_step: the action or control kernels, per RK step three
+// stages of (stage_pre, nonlinear term, implicit half) and the wall shear,
+// then the outputs; the nonlinear term takes three launches where it runs in
+// passes, the implicit half two in its wide form
+static void set_launch_count(ch_env* env) {
+  const ch_params_t* p = &env->prm;
+  const bool passes = p->precision == 1 ? env->plane_f.two_pass : env->plane.two_pass;
+  const int stage = 1 + (passes ? 3 : 1) + stage_post_launches(env->g, p->top_bc, env->post_batched);
+  env->launches_per_step = (p->control == 0 ? 2 : p->control == 1 ? 1 : 5) + p->steps_per_action * (3 * stage + 1) + 3;
+}
+
 // The kernels of one environment step, in stream order.
 int launch_step(ch_env* env, const double* d_action, double* d_out, const int* d_active) {
   const Grid& g = env->g;
@@ -951,10 +964,11 @@ size_t env_footprint(const ch_params_t* p) {
                             (size_t)p->nz * p->nx * 8 + (2 * (size_t)p->nz * p->nx + 2) * 8);
   const size_t tables = (3 * 2 * 4 * Mh * P + 3 * 2 * P + 2 * 4 * Mh * P + 2 * P + 3 * 2 * Mh * P + 3 * 2 * P +
                          3 * Mh + 3 + 3 * ny + ny + 2 * 3 * 2 * 2 * P) * 8 + ny * ny * 12 + (nxh + p->nz) * 8;
-  // FP64 planes of 256 x 256 modes: the scratch of the three-pass nonlinear term
+  // planes of 256 x 256 modes: the scratch of the three-pass nonlinear term
+  // (complex values of the plane's precision)
   const size_t mx = 3 * (size_t)p->nx / 2, mz = 3 * (size_t)p->nz / 2;
-  const size_t two_pass = (p->precision == 0 && two_pass_shape_ok((int)mx, (int)mz, (int)nxh))
-                              ? B * ny * 6 * mz * nxh * 16 : 0;
+  const size_t two_pass = two_pass_shape_ok((int)mx, (int)mz, (int)nxh)
+                              ? B * ny * 6 * mz * nxh * (p->precision == 0 ? 16 : 8) : 0;
   return state + tables + two_pass + ((size_t)4 << 20);  // plus twiddles and rounding slack
 }
 }  // namespace chdns
@@ -1069,7 +1083,7 @@ int env_create(const ch_params_t* p, ch_env_t** out) {
   if (cudaMemset(pb.vw_old, 0, B * P * sizeof(double2)) != cudaSuccess) return fail(CH_ERR_CUDA);
   if (cudaMemset(pb.tau_acc, 0, B * sizeof(double)) != cudaSuccess) return fail(CH_ERR_CUDA);
   if (cudaDeviceSynchronize() != cudaSuccess) return fail(CH_ERR_CUDA);
-  env->launches_per_step = (p->control == 0 ? 2 : p->control == 1 ? 1 : 5) + p->steps_per_action * (3 * 3 + 1) + 3;
+  set_launch_count(env);
   *out = env;
   return CH_OK;
 }
@@ -1169,13 +1183,15 @@ int env_info(const ch_env_t* env, ch_info_t* info) {
   info->tau_ref = env->tau_ref;
   info->state_bytes = ch_state_bytes(&env->prm);
   info->device_bytes = env->device_bytes;
-  info->plane_cluster = env->prm.precision == 1 ? env->plane_f.S : (env->plane.two_pass ? 0 : env->plane.S);
+  info->plane_cluster = env->prm.precision == 1 ? (env->plane_f.two_pass ? 0 : env->plane_f.S)
+                                               : (env->plane.two_pass ? 0 : env->plane.S);
   info->launches_per_step = env->launches_per_step;
   info->post_batched = env->post_batched ? 1 : 0;
   info->ppc_pre = env->ppc_pre;
   info->ppc_post = env->ppc_post;
   info->tuned = env->tuned ? 1 : 0;
   info->tune_ms = env->tune_ms;
+  info->plane_team = env->prm.precision == 1 ? env->plane_f.team16 : env->plane.team16;
   return CH_OK;
 }
 
@@ -1191,6 +1207,7 @@ int env_set_tiles(ch_env_t* env, int ppc_pre, int ppc_post, int post_batched) {
   env->ppc_post = ppc_post;
   env->post_batched = post_batched == 1;
   env->tuned = false;
+  set_launch_count(env);
   return CH_OK;
 }
 

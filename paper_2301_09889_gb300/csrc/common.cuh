@@ -498,8 +498,10 @@ struct TauTables {
 // the staged previous right-hand sides [2][ny][ppc] (FP32 pairs), for FP64
 // nodes six more complex values per mode (scratch of the fast analysis);
 // 16-byte aligned.
+constexpr bool kPostStageHV = true, kPostStageHG = true;
 __host__ __device__ inline size_t stage_post_batched_tile_bytes(int ny, int ppc, size_t node_bytes) {
-  const size_t b = node_bytes == 8 ? (size_t)5 * ny * ppc * 8 : ((size_t)3 * ny + 6) * ppc * 16;
+  const size_t staged = (size_t)kPostStageHV + (size_t)kPostStageHG;
+  const size_t b = node_bytes == 8 ? (3 + staged) * ny * ppc * 8 : ((size_t)3 * ny + 6) * ppc * 16;
   return (b + 15) & ~(size_t)15;
 }
 

@@ -48,6 +48,8 @@ struct DevTables {
 size_t stage_pre_smem(const Grid& g, int ppc, size_t node_bytes);  // node_bytes: one complex node value
 size_t stage_post_smem(const Grid& g, int Mh, int ppc, int top);
 size_t stage_post_batched_smem(const Grid& g, int ppc, int top, size_t node_bytes);
+// kernels one launch_stage_post issues (the batched form above 65 nodes: two)
+int stage_post_launches(const Grid& g, int top, bool batched);
 template <typename RN>
 cudaError_t launch_stage_pre(const Grid& g, int B, const PencilBufs& pb, const DevTables& t,
                              typename cpx<RN>::T* q, int ppc, cudaStream_t st);

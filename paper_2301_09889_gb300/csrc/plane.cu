@@ -372,8 +372,8 @@ static SmemLimit& generic_limit() {
 template <typename R>
 cudaError_t launch_plane(const PlaneArgs<R>& a, int B, size_t smem, cudaStream_t st) {
   if (a.team16) return launch_plane16<R>(a, B, st);
+  if (a.two_pass) return launch_plane_two_pass<R>(a, B, st);
   if constexpr (sizeof(R) == 8) {
-    if (a.two_pass) return launch_plane_two_pass<R>(a, B, st);
     CH_PLANE_CT(24, 6, 8, 3)
     CH_PLANE_CT(24, 24, 8, 12)
     CH_PLANE_CT_NT(96, 24, 32, 3, 512)
@@ -385,7 +385,6 @@ cudaError_t launch_plane(const PlaneArgs<R>& a, int B, size_t smem, cudaStream_t
     CH_PLANE_CT(96, 24, 32, 12)
     CH_PLANE_CT(48, 12, 16, 6)
     CH_PLANE_CT_NT(192, 48, 64, 8, 1024)
-    CH_PLANE_CT_NT(384, 24, 128, 4, 1024)
   }
   return launch_with(plane_kernel<R>, a, B, smem, st, &generic_limit<R>());
 }

@@ -1,7 +1,9 @@
 // Dealiased nonlinear term H = u x omega for planes whose padded z-slabs fit no
-// cluster's shared memory (the FP64 plane of 256 x 256 modes: 295 KB per CTA
-// even split over 16 CTAs).  The same 3/2-rule transforms as plane.cu, in
-// three passes through a global scratch array y[B][ny][6][mz][nxh]:
+// portable cluster's shared memory: the plane of 256 x 256 modes takes 295 KB
+// per CTA in FP64 even split over 16 CTAs, and 147 KB in FP32 over a 16-CTA
+// cluster, of which the device holds only a few at once.  The same 3/2-rule
+// transforms as plane.cu, in three passes through a global scratch array
+// y[B][ny][6][mz][nxh]:
 //   1. z inverse: per tile of CW kx columns of one field, zero-pad the kz
 //      spectrum to mz points and transform along z (DIF, digit-reversed rows);
 //   2. x pass: per pair of physical z rows, pack the two real rows of each
@@ -180,5 +182,6 @@ cudaError_t launch_plane_two_pass(const PlaneArgs<R>& a, int B, cudaStream_t st)
 }
 
 template cudaError_t launch_plane_two_pass<double>(const PlaneArgs<double>&, int, cudaStream_t);
+template cudaError_t launch_plane_two_pass<float>(const PlaneArgs<float>&, int, cudaStream_t);
 
 }  // namespace chdns

@@ -270,6 +270,271 @@ __device__ __forceinline__ void v_walk(int N, int ny, int ppc, int sv, const Com
   }
 }
 
+// ---------------------------------------------------------------------------
+// The implicit solves of the no-slip channel with one register array per
+// thread.  tau_fused is tau_seq with the right-hand side produced on the fly:
+// rhs(i) is called once per coefficient, for i = M-1 down to 0, and row i of
+// the elimination runs as soon as r_{i-1} exists, so no array of right-hand
+// sides is held.  A solve may read its right-hand side from f itself (the
+// second solve of v): f[i] is read at step i and written at step i - 1.
+// The wall value s is asked for after the last call of rhs, so the sums that
+// rhs accumulates are complete.  The row arithmetic is tau_seq's.  f is a
+// per-thread array of MH doubles: registers (RegArr), or a column of shared
+// memory (SmemArr) where MH doubles per thread exceed the register file.
+// ---------------------------------------------------------------------------
+template <int MH>
+struct RegArr {
+  double v[MH];
+  __device__ __forceinline__ double& operator[](int i) { return v[i]; }
+};
+struct SmemArr {
+  double* p;
+  int stride;
+  __device__ __forceinline__ double& operator[](int i) const { return p[i * stride]; }
+};
+
+template <int MH, class Arr, class Tab, class Rhs, class Wall>
+__device__ __forceinline__ void tau_fused(int N, int ny, int sig, Rhs&& rhs, Arr& f, const Tab& T, double isq,
+                                          Wall&& wall, const double* __restrict__ rowc) {
+  const int M = (N - sig) / 2 + 1;
+  double r1 = 0.0, r2 = 0.0, anext = 0.0;  // r_{i+1}, r_{i+2}, a_{i+2}
+#pragma unroll
+  for (int i = MH - 1; i >= 0; --i) {
+    double r0 = 0.0;
+    if (i < M) r0 = rhs(i);
+    const int j = i + 1;  // row j needs r_{j-1} = r0, r_j = r1, r_{j+1} = r2
+    if (j < MH && j < M) {
+      const int n = 2 * j + sig;
+      double R = fma_rn(-rowc[ny + n], r1, mul_rn(rowc[n], r0));
+      if (j + 1 < M) R = fma_rn(rowc[2 * ny + n], r2, R);
+      const double a = fma_rn(-T.h(j), anext, mul_rn(T.e(j), R));
+      f[j] = a;
+      anext = a;
+    }
+    r2 = r1;
+    r1 = r0;
+  }
+  double Pp = 0.0, sum = 0.0;
+#pragma unroll
+  for (int i = 1; i < MH; ++i) {
+    if (i < M) {
+      Pp = fma_rn(T.b(i), Pp, f[i]);
+      f[i] = Pp;
+      sum += Pp;
+    }
+  }
+  const double f0 = mul_rn(isq, wall() - sum);
+  f[0] = f0;
+#pragma unroll
+  for (int i = 1; i < MH; ++i)
+    if (i < M) f[i] = fma_rn(T.Q(i), f0, f[i]);
+}
+
+// omega_y of parity sq: (D^2 - lam) g' = -((1 + cc) g + dt (gamma h_g + zeta
+// h_g'))/(beta dt nu), the factor -1/(beta dt nu) folded into the table's e;
+// wall row sum g' = cc sum g; g <- g' - cc g.  h_g = sgn (-kx H_z + kz H_x) of
+// the other component, in the node precision; h_g' is read through HGr and
+// the new h_g written through HGw.
+template <int MH, typename RN, class Arr, class GV, class HR, class HW, class Tab>
+__device__ __forceinline__ void omega_solve(Arr& f, int N, int ny, int ppc, int sq, const GV& Gc, const HR& HGr,
+                                            const HW& HGw, const typename cpx<RN>::T* Hx,
+                                            const typename cpx<RN>::T* Hz, int r, double sgn, double kx, double kz,
+                                            double cc, const StageCoef& sc, const Tab& T, double isq,
+                                            const double* __restrict__ rowc) {
+  using CN = typename cpx<RN>::T;
+  const int ra = 1 - r;
+  auto comp = [](const CN z, int qd) { return qd == 0 ? z.x : z.y; };
+  const RN sgnn = (RN)sgn, kxn = (RN)kx, kzn = (RN)kz;
+  const RN dtn = (RN)sc.dt, gan = (RN)sc.gamma, zen = (RN)sc.zeta;
+  const int M = (N - sq) / 2 + 1;
+  double sum = 0.0;
+  tau_fused<MH>(
+      N, ny, sq,
+      [&](int i) {
+        const int n = 2 * i + sq;
+        const double gn = Gc[n];
+        const RN hg = mul_rn(sgnn, fma_rn(-kxn, comp(Hz[n * ppc], ra), mul_rn(kzn, comp(Hx[n * ppc], ra))));
+        const RN hp = HGr[n];
+        HGw[n] = hg;
+        const RN q = mul_rn(dtn, fma_rn(gan, hg, mul_rn(zen, hp)));
+        sum += gn;
+        return fma_rn(1.0 + cc, gn, (double)q);
+      },
+      f, T, isq, [&] { return mul_rn(cc, sum); }, rowc);
+#pragma unroll
+  for (int i = 0; i < MH; ++i)
+    if (i < M) {
+      const int n = 2 * i + sq;
+      Gc[n] = fma_rn(-cc, Gc[n], f[i]);
+    }
+}
+
+// v of parity sv: the walk of v_walk (Dv, D^2 v, t, Dt from n = N down)
+// feeds the phi solve row by row; the wall sums S0 = sum v, S2 = sum n^2 v
+// of the old field are taken on the way down.  Then the Dirichlet solve of
+// (D^2 - k^2) v_p = phi with v_p(+-1) = cc v(+-1) + (wall velocity), reading
+// phi from the same array, and the influence correction c_I vh that fixes
+// Dv at the wall: v <- v_p + c_I vh - cc v.
+template <int MH, typename RN, class Arr, class VV, class HR, class HW, class Tab, class TabP, class VH>
+__device__ __forceinline__ void v_solve(Arr& f, int N, int ny, int ppc, int sv, const VV& Vc, const HR& HVr,
+                                        const HW& HVw,
+                                        const typename cpx<RN>::T* Hx, const typename cpx<RN>::T* Hy,
+                                        const typename cpx<RN>::T* Hz, int r, double sgn, double kx, double kz,
+                                        double k2, double cc, const StageCoef& sc, const Tab& Th, double isq_h,
+                                        const TabP& Tp, double isq_p, const VH& vh, double idv, double vw,
+                                        const double* __restrict__ rowc) {
+  using CN = typename cpx<RN>::T;
+  const int ra = 1 - r;
+  auto comp = [](const CN z, int qd) { return qd == 0 ? z.x : z.y; };
+  const double dsv = 2.0 * sv;
+  const RN dsvn = (RN)(2 * sv);
+  const RN sgnn = (RN)sgn, kxn = (RN)kx, kzn = (RN)kz, k2n = (RN)k2;
+  const RN dtn = (RN)sc.dt, gan = (RN)sc.gamma, zen = (RN)sc.zeta;
+  const int M = (N - sv) / 2 + 1;
+  double dv = 0.0, d2v = 0.0, S0 = 0.0, S2 = 0.0;
+  RN tt = 0, dtt = 0;
+  tau_fused<MH>(
+      N, ny, sv,
+      [&](int i) {
+        const int no = 2 * i + sv + 1;
+        if (no <= N) {
+          const double vn1 = (no + 1 <= N) ? Vc[no + 1] : 0.0;
+          dv = fma_rn((double)(4 * i + 4) + dsv, vn1, dv);  // 2 (no + 1)
+          tt = mul_rn(sgnn, fma_rn(kxn, comp(Hx[no * ppc], ra), mul_rn(kzn, comp(Hz[no * ppc], ra))));
+        }
+        const int n = 2 * i + sv;
+        const double fac = (double)(4 * i + 2) + dsv;  // 2 (n + 1)
+        const RN facn = (RN)(4 * i + 2) + dsvn;
+        const double t1 = fma_rn(fac, dv, d2v);
+        const RN t2 = fma_rn(facn, (n + 1 <= N) ? tt : (RN)0, dtt);
+        d2v = (n == 0) ? 0.5 * t1 : t1;
+        dtt = (n == 0) ? (RN)0.5 * t2 : t2;
+        const double vn = Vc[n];
+        S0 += vn;
+        S2 = fma_rn((double)n * n, vn, S2);
+        const double phi = fma_rn(-k2, vn, d2v);
+        const RN hv = fma_rn(-k2n, comp(Hy[n * ppc], r), -dtt);
+        const RN hp = HVr[n];
+        HVw[n] = hv;
+        const RN q = mul_rn(dtn, fma_rn(gan, hv, mul_rn(zen, hp)));
+        return fma_rn(1.0 + cc, phi, (double)q);
+      },
+      f, Th, isq_h, [] { return 0.0; }, rowc);
+  const double s = fma_rn(cc, S0, ((sv == 0) ? 0.5 : -0.5) * vw);
+  tau_fused<MH>(N, ny, sv, [&](int i) { return f[i]; }, f, Tp, isq_p, [&] { return s; }, rowc);
+  double dp = 0.0;
+#pragma unroll
+  for (int i = 0; i < MH; ++i)
+    if (i < M) {
+      const double n = 2 * i + sv;
+      dp = fma_rn(n * n, f[i], dp);
+    }
+  const double cI = mul_rn(fma_rn(cc, S2, -dp), idv);
+#pragma unroll
+  for (int i = 0; i < MH; ++i)
+    if (i < M) {
+      const int n = 2 * i + sv;
+      Vc[n] = fma_rn(-cc, Vc[n], fma_rn(cI, vh(i), f[i]));
+    }
+}
+
+// mean flow of parity s: U (e = 0, at constant flow rate through the
+// response u1 to a unit forcing) or W (e = 1); X the coefficients, XP the
+// previous plane means of H_x or H_z (FP64), Hm the new plane mean.
+template <int MH, typename RN, class Arr, class Tab>
+__device__ __forceinline__ void mean_solve(Arr& f, int N, int ny, int ppc, int s, int e, double* X, double* XP,
+                                           const typename cpx<RN>::T* Hm, double cc, const StageCoef& sc,
+                                           const Tab& T, double isq, const double* __restrict__ rowc,
+                                           const double* __restrict__ u1, double u1_iflux) {
+  const int M = (N - s) / 2 + 1;
+  double sum = 0.0, flux_old = 0.0;
+  tau_fused<MH>(
+      N, ny, s,
+      [&](int i) {
+        const int n = 2 * i + s;
+        const double xn = X[n];
+        const double hv = (double)Hm[n * ppc].x;
+        const double hp = XP[n];
+        XP[n] = hv;
+        sum += xn;
+        if (s == 0) flux_old = fma_rn(2.0 / (1.0 - (double)n * n), xn, flux_old);
+        return fma_rn(1.0 + cc, xn, mul_rn(sc.dt, fma_rn(sc.gamma, hv, mul_rn(sc.zeta, hp))));
+      },
+      f, T, isq, [&] { return mul_rn(cc, sum); }, rowc);
+  double fc = 0.0;
+  if (e == 0 && s == 0) {
+    double flux = 0.0;
+#pragma unroll
+    for (int i = 0; i < MH; ++i)
+      if (i < M) flux = fma_rn(2.0 / (1.0 - 4.0 * (double)i * i), f[i], flux);
+    fc = mul_rn(fma_rn(cc, flux_old, sc.flux) - flux, u1_iflux);
+  }
+#pragma unroll
+  for (int i = 0; i < MH; ++i) {
+    if (i < M) {
+      const int n = 2 * i + s;
+      double v = fma_rn(-cc, X[n], f[i]);
+      if (e == 0 && s == 0) v = fma_rn(fc, u1[i], v);
+      X[n] = v;
+    }
+  }
+}
+
+
+// One (mode p, class, component r) thread's implicit solves under the no-slip
+// top: the mean flow (p = 0), else omega_y of parity 1 - c and v of parity c.
+// H_x, H_y, H_z: Chebyshev coefficients of the mode, element n at n * hs;
+// HGr, HVr: the previous nonlinear right-hand sides (node precision); the new
+// ones go to the pencil buffers.  f: the thread's array of MH doubles.
+template <int MH, typename RN, class Arr, class Cls>
+__device__ __forceinline__ void post_solve_noslip(Arr& f, Cls cls, const Grid& g, const PencilBufs& pb,
+                                                  const DevTables& t, const StageCoef& sc, int b, int p, int r,
+                                                  const typename cpx<RN>::T* Hx, const typename cpx<RN>::T* Hy,
+                                                  const typename cpx<RN>::T* Hz, int hs, const CompT<RN>& HGr,
+                                                  const CompT<RN>& HVr) {
+  const int c = class_of(cls);
+  const int P = g.P, ny = g.ny, N = g.N, Mh = t.tau.Mh;
+  const double cc = sc.alpha / sc.beta;
+  const double* rowc = t.tau.rowc;
+  auto comp = [](auto z, int qq) { return qq == 0 ? z.x : z.y; };
+  auto helm = [&](int sig) { return TabSm{t.tau.helm + (size_t)(sc.k * 2 + sig) * 4 * Mh * P + p, Mh, P}; };
+  auto helm_isq = [&](int sig) { return t.tau.helm_isq[(size_t)(sc.k * 2 + sig) * P + p]; };
+  if (p == 0) {
+    // mean mode: U (r = 0) at constant flow rate and W (r = 1), parity c
+    const int e = r;
+    mean_solve<MH, RN>(f, N, ny, hs, c, e, (e == 0 ? pb.UM : pb.WM) + (size_t)b * ny,
+                       (e == 0 ? pb.HXP : pb.HZP) + (size_t)b * ny, (e == 0) ? Hx : Hz, cc, sc, helm(c),
+                       helm_isq(c), rowc, t.tau.u1 + (size_t)sc.k * Mh, t.tau.u1_iflux[sc.k]);
+    return;
+  }
+  const int row = p / g.nxh, ix = p % g.nxh;
+  const double kx = t.kx[ix], kz = t.kz[row], k2 = kx * kx + kz * kz;
+  const double sgn = (r == 0) ? -1.0 : 1.0;
+  const size_t base = 2 * ((size_t)b * ny * P + p) + r;  // component r of element n at base + 2 P n
+  {
+    // wall-normal vorticity, parity 1 - c; previous right-hand sides are
+    // stored in the node precision
+    const int sq = 1 - c;
+    const CompS Gc{reinterpret_cast<double*>(pb.G) + base, 2 * P};
+    const CompT<RN> HGc{reinterpret_cast<RN*>(pb.HGP) + base, 2 * P};
+    omega_solve<MH, RN>(f, N, ny, hs, sq, Gc, HGr, HGc, Hx, Hz, r, sgn, kx, kz, cc, sc, helm(sq), helm_isq(sq),
+                        rowc);
+  }
+  {
+    // wall-normal velocity, parity c
+    const int sv = c;
+    const CompS Vc{reinterpret_cast<double*>(pb.V) + base, 2 * P};
+    const CompT<RN> HVc{reinterpret_cast<RN*>(pb.HVP) + base, 2 * P};
+    const size_t vo = (size_t)b * P + p;
+    const double vw = fma_rn(sc.theta, comp(pb.vw_new[vo], r) - comp(pb.vw_old[vo], r), comp(pb.vw_old[vo], r));
+    const TabSm TP{t.tau.pois + (size_t)sv * 4 * Mh * P + p, Mh, P};
+    const double* vh = t.tau.vh + (size_t)(sc.k * 2 + sv) * Mh * P + p;
+    v_solve<MH, RN>(f, N, ny, hs, sv, Vc, HVr, HVc, Hx, Hy, Hz, r, sgn, kx, kz, k2, cc, sc, helm(sv), helm_isq(sv),
+                    TP, t.tau.pois_isq[(size_t)sv * P + p], [&](int i) { return vh[(size_t)i * P]; },
+                    t.tau.vh_idv[(size_t)(sc.k * 2 + sv) * P + p], vw, rowc);
+  }
+}
+
 // cos(pi j n / N) table in the node precision
 template <typename RN>
 __device__ __forceinline__ const RN* cheb_table(const DevTables& t);
@@ -277,6 +542,39 @@ template <>
 __device__ __forceinline__ const double* cheb_table<double>(const DevTables& t) { return t.cheb; }
 template <>
 __device__ __forceinline__ const float* cheb_table<float>(const DevTables& t) { return t.cheb_f; }
+
+// Chebyshev coefficients a_n, n = n0 + dn k (k < KN, all of one parity), of
+// one field of one mode from its nodal values col[j * stride], j = 0..N, by the
+// direct sums a_n = (2 / (N c_n)) sum_j'' f_j cos(pi j n / N) over the folded
+// pairs f_j + (-1)^n f_{N-j} (sg = (-1)^n), accumulated over j in ascending
+// order; c_0 = c_N = 2, the end nodes weigh 1/2.
+template <typename RN, int KN>
+__device__ __forceinline__ void analysis_sums(const typename cpx<RN>::T* col, int stride, int N, int ny,
+                                              const RN* __restrict__ cheb, int n0, int dn, RN sg,
+                                              typename cpx<RN>::T (&acc)[KN]) {
+  using CN = typename cpx<RN>::T;
+  CN a[KN];
+  const CN w0 = (RN)0.5 * (col[0] + sg * col[N * stride]);  // j = 0 and j = N weigh 1/2
+#pragma unroll
+  for (int k = 0; k < KN; ++k) a[k] = w0;
+  for (int j = 1; 2 * j < N; ++j) {
+    const CN fold = col[j * stride] + sg * col[(N - j) * stride];
+#pragma unroll
+    for (int k = 0; k < KN; ++k) {
+      const int n = n0 + dn * k;
+      a[k] = a[k] + cheb[(size_t)min(n, N) * ny + j] * fold;
+    }
+  }
+  const RN s0 = (RN)2.0 / (RN)N;
+#pragma unroll
+  for (int k = 0; k < KN; ++k) {
+    const int n = n0 + dn * k;
+    const RN cbn = (n == 0 || n == N) ? (RN)2.0 : (RN)1.0;
+    CN v = a[k];
+    if ((N & 1) == 0) v = v + cheb[(size_t)min(n, N) * ny + N / 2] * col[(N / 2) * stride];
+    acc[k] = (s0 / cbn) * v;
+  }
+}
 
 template <typename C> __device__ __forceinline__ C to_node(double2 v);
 template <> __device__ __forceinline__ double2 to_node<double2>(double2 v) { return v; }
@@ -901,127 +1199,40 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
       const CN* Hz = Hy + ny * ppc;
       auto helm = [&](int sig) { return TabSm{sh + sig * 4 * Mh * ppc + pl, Mh, ppc}; };
       auto comp = [](auto z, int qd) { return qd == 0 ? z.x : z.y; };
-      const RN dtn = (RN)sc.dt, gan = (RN)sc.gamma, zen = (RN)sc.zeta;
       if (row == g.nz / 2) {
         // Nyquist row stays zero
       } else if (p == 0) {
         if (r == 0) {
-          const int s = c;
-          const int M = (N - s) / 2 + 1;
-          double* X = (e == 0 ? pb.UM : pb.WM) + (size_t)b * ny;
-          double* XP = (e == 0 ? pb.HXP : pb.HZP) + (size_t)b * ny;
-          const CN* Hm = (e == 0) ? Hx : Hz;
-          double rhs[MH], f[MH];
-          double sum = 0.0, flux_old = 0.0;
-  #pragma unroll
-          for (int i = 0; i < MH; ++i) {
-            rhs[i] = 0.0;
-            if (i < M) {
-              const int n = 2 * i + s;
-              const double xn = X[n];
-              const double hv = (double)Hm[n * ppc].x;
-              const double hp = XP[n];
-              XP[n] = hv;
-              rhs[i] = fma_rn(1.0 + cc, xn, mul_rn(sc.dt, fma_rn(sc.gamma, hv, mul_rn(sc.zeta, hp))));
-              sum += xn;
-              if (s == 0) flux_old = fma_rn(2.0 / (1.0 - (double)n * n), xn, flux_old);
-            }
-          }
-          tau_seq<MH>(N, ny, s, rhs, f, helm(s), ss[(0 * 2 + s) * ppc + pl], cc * sum, rowc);
-          double fc = 0.0;
-          if (e == 0 && s == 0) {
-            double flux = 0.0;
-  #pragma unroll
-            for (int i = 0; i < MH; ++i)
-              if (i < M) flux = fma_rn(2.0 / (1.0 - 4.0 * (double)i * i), f[i], flux);
-            fc = mul_rn(fma_rn(cc, flux_old, sc.flux) - flux, t.tau.u1_iflux[sc.k]);
-          }
-  #pragma unroll
-          for (int i = 0; i < MH; ++i) {
-            if (i < M) {
-              const int n = 2 * i + s;
-              double v = fma_rn(-cc, X[n], f[i]);
-              if (e == 0 && s == 0) v = fma_rn(fc, t.tau.u1[(size_t)sc.k * Mh + i], v);
-              X[n] = v;
-            }
-          }
+          RegArr<MH> f;
+          mean_solve<MH, RN>(f, N, ny, ppc, c, e, (e == 0 ? pb.UM : pb.WM) + (size_t)b * ny,
+                             (e == 0 ? pb.HXP : pb.HZP) + (size_t)b * ny, (e == 0) ? Hx : Hz, cc, sc, helm(c),
+                             ss[(0 * 2 + c) * ppc + pl], rowc, t.tau.u1 + (size_t)sc.k * Mh, t.tau.u1_iflux[sc.k]);
         }
       } else {
         const double kx = t.kx[ix], kz = t.kz[row], k2 = kx * kx + kz * kz;
         const double sgn = (r == 0) ? -1.0 : 1.0;
-        const int ra = 1 - r;
         if (e == 0) {
           // wall-normal vorticity, parity 1 - c
           const int sq = 1 - c;
-          const int M = (N - sq) / 2 + 1;
           const CompS Gc{reinterpret_cast<double*>(sG) + 2 * pl + r, 2 * ppc};
           const CompT<RN> HGc{reinterpret_cast<RN*>(sHG) + 2 * pl + r, 2 * ppc};
-          const RN sgnn = (RN)sgn, kxn = (RN)kx, kzn = (RN)kz;
-          double rhs[MH], f[MH];
-          double sum = 0.0;
-  #pragma unroll
-          for (int i = 0; i < MH; ++i) {
-            rhs[i] = 0.0;
-            if (i < M) {
-              const int n = 2 * i + sq;
-              const double gn = Gc[n];
-              // nonlinear part in the node precision
-              const RN hg = mul_rn(sgnn, fma_rn(-kxn, comp(Hz[n * ppc], ra), mul_rn(kzn, comp(Hx[n * ppc], ra))));
-              const RN hp = HGc[n];
-              HGc[n] = hg;
-              const RN q = mul_rn(dtn, fma_rn(gan, hg, mul_rn(zen, hp)));
-              rhs[i] = fma_rn(1.0 + cc, gn, (double)q);
-              sum += gn;
-            }
-          }
-          tau_seq<MH>(N, ny, sq, rhs, f, helm(sq), ss[(0 * 2 + sq) * ppc + pl], cc * sum, rowc);
-  #pragma unroll
-          for (int i = 0; i < MH; ++i)
-            if (i < M) {
-              const int n = 2 * i + sq;
-              Gc[n] = fma_rn(-cc, Gc[n], f[i]);
-            }
+          RegArr<MH> f;
+          omega_solve<MH, RN>(f, N, ny, ppc, sq, Gc, HGc, HGc, Hx, Hz, r, sgn, kx, kz, cc, sc, helm(sq),
+                              ss[(0 * 2 + sq) * ppc + pl], rowc);
         } else {
           // wall-normal velocity, parity c
           const int sv = c;
-          const int M = (N - sv) / 2 + 1;
           const CompS Vc{reinterpret_cast<double*>(sV) + 2 * pl + r, 2 * ppc};
           const CompT<RN> HVc{reinterpret_cast<RN*>(sHV) + 2 * pl + r, 2 * ppc};
-          double S0 = 0.0, S2 = 0.0;
-          double rhs[MH];
-  #pragma unroll
-          for (int i = 0; i < MH; ++i) rhs[i] = 0.0;
-          for (int i = 0; i < M; ++i) {
-            const int n = 2 * i + sv;
-            const double vn = Vc[n];
-            S0 += vn;
-            S2 = fma_rn((double)n * n, vn, S2);
-          }
-          // one walk from n = N down to 0: Dv, D^2 v, t = i kx H_x + i kz H_z, Dt
-          v_walk<MH, RN>(N, ny, ppc, sv, Vc, HVc, HVc, Hx, Hy, Hz, r, sgn, kx, kz, k2, cc, sc, rhs);
-          double f[MH];
-          tau_seq<MH>(N, ny, sv, rhs, f, helm(sv), ss[(0 * 2 + sv) * ppc + pl], 0.0, rowc);
           const size_t vo = (size_t)b * P + p;
           const double vw =
               fma_rn(sc.theta, comp(pb.vw_new[vo], r) - comp(pb.vw_old[vo], r), comp(pb.vw_old[vo], r));
-          const double s = fma_rn(cc, S0, ((sv == 0) ? 0.5 : -0.5) * vw);
           const TabSm TP{sp + sv * 4 * Mh * ppc + pl, Mh, ppc};
-          tau_seq<MH>(N, ny, sv, f, rhs, TP, ss[(1 * 2 + sv) * ppc + pl], s, rowc);
-          double dp = 0.0;
-  #pragma unroll
-          for (int i = 0; i < MH; ++i)
-            if (i < M) {
-              const double n = 2 * i + sv;
-              dp = fma_rn(n * n, rhs[i], dp);
-            }
-          const double cI = mul_rn(fma_rn(cc, S2, -dp), ss[(2 * 2 + sv) * ppc + pl]);
           const double* vh = svh + sv * Mh * ppc + pl;
-  #pragma unroll
-          for (int i = 0; i < MH; ++i)
-            if (i < M) {
-              const int n = 2 * i + sv;
-              Vc[n] = fma_rn(-cc, Vc[n], fma_rn(cI, vh[i * ppc], rhs[i]));
-            }
+          RegArr<MH> f;
+          v_solve<MH, RN>(f, N, ny, ppc, sv, Vc, HVc, HVc, Hx, Hy, Hz, r, sgn, kx, kz, k2, cc, sc, helm(sv),
+                          ss[(0 * 2 + sv) * ppc + pl], TP, ss[(1 * 2 + sv) * ppc + pl],
+                          [&](int i) { return vh[i * ppc]; }, ss[(2 * 2 + sv) * ppc + pl], vw, rowc);
         }
       }
     }
@@ -1240,8 +1451,14 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
 // analysis runs field by field with four threads per mode (n = q + 4k); each
 // coefficient is accumulated in the same order as in the per-tile form.
 // ---------------------------------------------------------------------------
+// Five CTAs per SM for the no-slip solve with up to 65 nodes: the register
+// budget (168) holds its one array of coefficients, and the shared tile
+// (41.6 KB at 65 nodes in FP32) allows five.
+template <int MH, int TOP>
+constexpr int post_batched_min_ctas() { return (TOP == 0 && MH <= 33) ? 5 : 1; }
+
 template <typename RN, int MH, int TOP>
-__global__ void __launch_bounds__(64) stage_post_batched_kernel(Grid g, int B, PencilBufs pb, DevTables t,
+__global__ void __launch_bounds__(64, post_batched_min_ctas<MH, TOP>()) stage_post_batched_kernel(Grid g, int B, PencilBufs pb, DevTables t,
                                                                 const typename cpx<RN>::T* __restrict__ hn,
                                                                 StageCoef sc, int ppc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1257,15 +1474,15 @@ __global__ void __launch_bounds__(64) stage_post_batched_kernel(Grid g, int B, P
   // FP32 nodes: the previous right-hand sides (FP32 pairs) are staged in shared
   // memory by one coalesced load behind the node tile, issued before the wait
   // for H; the new ones go straight to global memory
-  constexpr bool kStageH = sizeof(RN) == 4;
+  constexpr bool kStageHV = sizeof(RN) == 4 && kPostStageHV, kStageHG = sizeof(RN) == 4 && kPostStageHG;
   CN* sHVt = sN + 3 * ny * ppc;
-  CN* sHGt = sHVt + ny * ppc;
-  if (kStageH) {
+  CN* sHGt = sHVt + (kStageHV ? ny * ppc : 0);
+  if (kStageHV || kStageHG) {
     for (int w = tid; w < ny * ppc; w += nt) {
       const int pl = w % ppc, n = w / ppc;
       const size_t o = ((size_t)b * ny + n) * P + min(p0 + pl, P - 1);
-      sHVt[w] = reinterpret_cast<const CN*>(pb.HVP)[o];
-      sHGt[w] = reinterpret_cast<const CN*>(pb.HGP)[o];
+      if (kStageHV) sHVt[w] = reinterpret_cast<const CN*>(pb.HVP)[o];
+      if (kStageHG) sHGt[w] = reinterpret_cast<const CN*>(pb.HGP)[o];
     }
   }
   pdl_wait_then_release();  // H comes from the preceding kernel
@@ -1294,30 +1511,9 @@ __global__ void __launch_bounds__(64) stage_post_batched_kernel(Grid g, int B, P
     const int qd = r + 2 * c;             // n = qd + 4k, parity of n = r
     const RN* cheb = cheb_table<RN>(t);
     const RN sg = r ? (RN)-1.0 : (RN)1.0;
-    const RN s0 = (RN)2.0 / (RN)N;
     for (int f = 2; f >= 0; --f) {
-      const CN* col = sN + (size_t)f * ny * ppc + pl;
-      CN a[KN];
-      const CN w0 = (RN)0.5 * (col[0] + sg * col[N * ppc]);  // j = 0 and j = N weigh 1/2
-#pragma unroll
-      for (int k = 0; k < KN; ++k) a[k] = w0;
-      for (int j = 1; 2 * j < N; ++j) {
-        const CN fold = col[j * ppc] + sg * col[(N - j) * ppc];
-#pragma unroll
-        for (int k = 0; k < KN; ++k) {
-          const int n = qd + 4 * k;
-          a[k] = a[k] + cheb[(size_t)min(n, N) * ny + j] * fold;
-        }
-      }
       CN acc[KN];
-#pragma unroll
-      for (int k = 0; k < KN; ++k) {
-        const int n = qd + 4 * k;
-        const RN cbn = (n == 0 || n == N) ? (RN)2.0 : (RN)1.0;
-        CN v = a[k];
-        if ((N & 1) == 0) v = v + cheb[(size_t)min(n, N) * ny + N / 2] * col[(N / 2) * ppc];
-        acc[k] = (s0 / cbn) * v;
-      }
+      analysis_sums<RN, KN>(sN + (size_t)f * ny * ppc + pl, ppc, N, ny, cheb, qd, 4, sg, acc);
       __syncthreads();
 #pragma unroll
       for (int k = 0; k < KN; ++k) {
@@ -1332,17 +1528,15 @@ __global__ void __launch_bounds__(64) stage_post_batched_kernel(Grid g, int B, P
     // ---- implicit solves (no barrier below)
     const int p = p0 + pl;
     if (p >= P) return;
-    const int row = p / g.nxh, ix = p % g.nxh;
-    if (row == g.nz / 2) return;  // Nyquist row stays zero
-    const double cc = sc.alpha / sc.beta;
-    const double* rowc = t.tau.rowc;
+    if (p / g.nxh == g.nz / 2) return;  // Nyquist row stays zero
     const CN* Hx = sN + pl;
     const CN* Hy = Hx + ny * ppc;
     const CN* Hz = Hy + ny * ppc;
-    auto comp = [](auto z, int qq) { return qq == 0 ? z.x : z.y; };
-    const RN dtn = (RN)sc.dt, gan = (RN)sc.gamma, zen = (RN)sc.zeta;
-    auto helm = [&](int sig) { return TabSm{t.tau.helm + (size_t)(sc.k * 2 + sig) * 4 * Mh * P + p, Mh, P}; };
-    auto helm_isq = [&](int sig) { return t.tau.helm_isq[(size_t)(sc.k * 2 + sig) * P + p]; };
+    const size_t base = 2 * ((size_t)b * ny * P + p) + r;  // component r of element n at base + 2 P n
+    const CompT<RN> HGr = kStageHG ? CompT<RN>{reinterpret_cast<RN*>(sHGt) + 2 * pl + r, 2 * ppc}
+                                   : CompT<RN>{reinterpret_cast<RN*>(pb.HGP) + base, 2 * P};
+    const CompT<RN> HVr = kStageHV ? CompT<RN>{reinterpret_cast<RN*>(sHVt) + 2 * pl + r, 2 * ppc}
+                                   : CompT<RN>{reinterpret_cast<RN*>(pb.HVP) + base, 2 * P};
     // The class c is uniform over each warp for tiles of 16 or more modes, so
     // for up to 65 nodes (MH <= 33) the solve is compiled once per class: every
     // parity-dependent factor (2 (n + 1), n^2, the row bounds) becomes a
@@ -1350,129 +1544,8 @@ __global__ void __launch_bounds__(64) stage_post_batched_kernel(Grid g, int B, P
     // would double).  The arithmetic is the same either way: the factors are
     // exact small integers and every fused operation is pinned.
     auto solve = [&](auto cls) {
-      const int c = class_of(cls);
-      if (p == 0) {
-        // mean mode: U (r = 0) at constant flow rate and W (r = 1), parity c
-        const int e = r, s = c;
-        const int M = (N - s) / 2 + 1;
-        double* X = (e == 0 ? pb.UM : pb.WM) + (size_t)b * ny;
-        double* XP = (e == 0 ? pb.HXP : pb.HZP) + (size_t)b * ny;
-        const CN* Hm = (e == 0) ? Hx : Hz;
-        double rhs[MH], f[MH];
-        double sum = 0.0, flux_old = 0.0;
-    #pragma unroll
-        for (int i = 0; i < MH; ++i) {
-          rhs[i] = 0.0;
-          if (i < M) {
-            const int n = 2 * i + s;
-            const double xn = X[n];
-            const double hv = (double)Hm[n * ppc].x;
-            const double hp = XP[n];
-            XP[n] = hv;
-            rhs[i] = fma_rn(1.0 + cc, xn, mul_rn(sc.dt, fma_rn(sc.gamma, hv, mul_rn(sc.zeta, hp))));
-            sum += xn;
-            if (s == 0) flux_old = fma_rn(2.0 / (1.0 - (double)n * n), xn, flux_old);
-          }
-        }
-        tau_seq<MH>(N, ny, s, rhs, f, helm(s), helm_isq(s), cc * sum, rowc);
-        double fc = 0.0;
-        if (e == 0 && s == 0) {
-          double flux = 0.0;
-    #pragma unroll
-          for (int i = 0; i < MH; ++i)
-            if (i < M) flux = fma_rn(2.0 / (1.0 - 4.0 * (double)i * i), f[i], flux);
-          fc = mul_rn(fma_rn(cc, flux_old, sc.flux) - flux, t.tau.u1_iflux[sc.k]);
-        }
-    #pragma unroll
-        for (int i = 0; i < MH; ++i) {
-          if (i < M) {
-            const int n = 2 * i + s;
-            double v = fma_rn(-cc, X[n], f[i]);
-            if (e == 0 && s == 0) v = fma_rn(fc, t.tau.u1[(size_t)sc.k * Mh + i], v);
-            X[n] = v;
-          }
-        }
-        return;
-      }
-      const double kx = t.kx[ix], kz = t.kz[row], k2 = kx * kx + kz * kz;
-      const double sgn = (r == 0) ? -1.0 : 1.0;
-      const int ra = 1 - r;
-      const size_t base = 2 * ((size_t)b * ny * P + p) + r;  // component r of element n at base + 2 P n
-      {
-        // wall-normal vorticity, parity 1 - c
-        const int sq = 1 - c;
-        const int M = (N - sq) / 2 + 1;
-        const CompS Gc{reinterpret_cast<double*>(pb.G) + base, 2 * P};
-        // previous right-hand sides are stored in the node precision
-        const CompT<RN> HGc{reinterpret_cast<RN*>(pb.HGP) + base, 2 * P};
-        const CompT<RN> HGr = kStageH ? CompT<RN>{reinterpret_cast<RN*>(sHGt) + 2 * pl + r, 2 * ppc} : HGc;
-        const RN sgnn = (RN)sgn, kxn = (RN)kx, kzn = (RN)kz;
-        double rhs[MH], f[MH];
-        double sum = 0.0;
-    #pragma unroll
-        for (int i = 0; i < MH; ++i) {
-          rhs[i] = 0.0;
-          if (i < M) {
-            const int n = 2 * i + sq;
-            const double gn = Gc[n];
-            const RN hg = mul_rn(sgnn, fma_rn(-kxn, comp(Hz[n * ppc], ra), mul_rn(kzn, comp(Hx[n * ppc], ra))));
-            const RN hp = HGr[n];
-            HGc[n] = hg;
-            const RN q = mul_rn(dtn, fma_rn(gan, hg, mul_rn(zen, hp)));
-            rhs[i] = fma_rn(1.0 + cc, gn, (double)q);
-            sum += gn;
-          }
-        }
-        tau_seq<MH>(N, ny, sq, rhs, f, helm(sq), helm_isq(sq), cc * sum, rowc);
-    #pragma unroll
-        for (int i = 0; i < MH; ++i)
-          if (i < M) {
-            const int n = 2 * i + sq;
-            Gc[n] = fma_rn(-cc, Gc[n], f[i]);
-          }
-      }
-      {
-        // wall-normal velocity, parity c
-        const int sv = c;
-        const int M = (N - sv) / 2 + 1;
-        const CompS Vc{reinterpret_cast<double*>(pb.V) + base, 2 * P};
-        const CompT<RN> HVc{reinterpret_cast<RN*>(pb.HVP) + base, 2 * P};
-        const CompT<RN> HVr = kStageH ? CompT<RN>{reinterpret_cast<RN*>(sHVt) + 2 * pl + r, 2 * ppc} : HVc;
-        double S0 = 0.0, S2 = 0.0;
-        double rhs[MH];
-    #pragma unroll
-        for (int i = 0; i < MH; ++i) rhs[i] = 0.0;
-        for (int i = 0; i < M; ++i) {
-          const int n = 2 * i + sv;
-          const double vn = Vc[n];
-          S0 += vn;
-          S2 = fma_rn((double)n * n, vn, S2);
-        }
-        v_walk<MH, RN>(N, ny, ppc, sv, Vc, HVr, HVc, Hx, Hy, Hz, r, sgn, kx, kz, k2, cc, sc, rhs);
-        double f[MH];
-        tau_seq<MH>(N, ny, sv, rhs, f, helm(sv), helm_isq(sv), 0.0, rowc);
-        const size_t vo = (size_t)b * P + p;
-        const double vw =
-            fma_rn(sc.theta, comp(pb.vw_new[vo], r) - comp(pb.vw_old[vo], r), comp(pb.vw_old[vo], r));
-        const double s = fma_rn(cc, S0, ((sv == 0) ? 0.5 : -0.5) * vw);
-        const TabSm TP{t.tau.pois + (size_t)sv * 4 * Mh * P + p, Mh, P};
-        tau_seq<MH>(N, ny, sv, f, rhs, TP, t.tau.pois_isq[(size_t)sv * P + p], s, rowc);
-        double dp = 0.0;
-    #pragma unroll
-        for (int i = 0; i < MH; ++i)
-          if (i < M) {
-            const double n = 2 * i + sv;
-            dp = fma_rn(n * n, rhs[i], dp);
-          }
-        const double cI = mul_rn(fma_rn(cc, S2, -dp), t.tau.vh_idv[(size_t)(sc.k * 2 + sv) * P + p]);
-        const double* vh = t.tau.vh + (size_t)(sc.k * 2 + sv) * Mh * P + p;
-    #pragma unroll
-        for (int i = 0; i < MH; ++i)
-          if (i < M) {
-            const int n = 2 * i + sv;
-            Vc[n] = fma_rn(-cc, Vc[n], fma_rn(cI, vh[(size_t)i * P], rhs[i]));
-          }
-      }
+      RegArr<MH> f;
+      post_solve_noslip<MH, RN>(f, cls, g, pb, t, sc, b, p, r, Hx, Hy, Hz, ppc, HGr, HVr);
     };
     if constexpr (MH <= 33) {
       if (c == 0) solve(std::integral_constant<int, 0>{});
@@ -1547,7 +1620,7 @@ __global__ void __launch_bounds__(64) stage_post_batched_kernel(Grid g, int B, P
         } else {
           const CompS Gc{reinterpret_cast<double*>(pb.G) + base, 2 * P};
           const CompT<RN> HGc{reinterpret_cast<RN*>(pb.HGP) + base, 2 * P};
-          const CompT<RN> HGr = kStageH ? CompT<RN>{reinterpret_cast<RN*>(sHGt) + 2 * pl + r, 2 * ppc} : HGc;
+          const CompT<RN> HGr = kStageHG ? CompT<RN>{reinterpret_cast<RN*>(sHGt) + 2 * pl + r, 2 * ppc} : HGc;
           const RN sgnn = (RN)sgn, kxn = (RN)t.kx[ix], kzn = (RN)t.kz[row];
           double so = 0.0, so2 = 0.0;
 #pragma unroll
@@ -1624,7 +1697,7 @@ __global__ void __launch_bounds__(64) stage_post_batched_kernel(Grid g, int B, P
       if (on) {
         const double kx = t.kx[ix], kz = t.kz[row], k2 = kx * kx + kz * kz;
         const CompT<RN> HVc{reinterpret_cast<RN*>(pb.HVP) + base, 2 * P};
-        const CompT<RN> HVr = kStageH ? CompT<RN>{reinterpret_cast<RN*>(sHVt) + 2 * pl + r, 2 * ppc} : HVc;
+        const CompT<RN> HVr = kStageHV ? CompT<RN>{reinterpret_cast<RN*>(sHVt) + 2 * pl + r, 2 * ppc} : HVc;
         double S0 = 0.0, Bo = 0.0, Ao = 0.0;
 #pragma unroll
         for (int i = 0; i < MH; ++i) rhs[i] = 0.0;
@@ -1673,6 +1746,107 @@ __global__ void __launch_bounds__(64) stage_post_batched_kernel(Grid g, int B, P
 }
 
 // ---------------------------------------------------------------------------
+// The implicit half for more than 65 nodes (no-slip top), in two launches.
+// One parity of one unknown then holds up to 101 coefficients, more than a
+// thread's registers next to the rest of the solve, and the node tile of H
+// (3 ny ppc values) would leave one or two CTAs per SM.  So:
+//   stage_post_analysis_kernel: the Chebyshev analysis of H, a tile of modes
+//     at a time, written over the nodal values in place (a CTA reads all the
+//     nodes of its modes before it writes their coefficients);
+//   stage_post_wide_kernel: one thread per (mode, class, component) as in the
+//     batched form, reading the coefficients of H from global memory and
+//     keeping its array of coefficients in a column of shared memory.
+// The per-output arithmetic of both halves is that of the batched form.
+// ---------------------------------------------------------------------------
+template <typename RN, int MH>
+__global__ void __launch_bounds__(256) stage_post_analysis_kernel(Grid g, int B, PencilBufs pb, DevTables t,
+                                                                  typename cpx<RN>::T* __restrict__ hn, int ppc) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  using CN = typename cpx<RN>::T;
+  const int P = g.P, ny = g.ny, N = g.N;
+  const int p0 = blockIdx.x * ppc;
+  const int b = blockIdx.y;
+  if (pb.active && !pb.active[b]) return;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  pdl_wait_then_release();  // H comes from the nonlinear term
+  CN* hb = hn + (size_t)b * 3 * ny * P;
+  constexpr int NF = 2 * (MH - 1);
+  if constexpr (std::is_same<RN, double>::value && ct_plan_ok(NF)) {
+    if (N == NF) {
+      // FFT form over the three fields of the tile, coefficients straight to hn
+      double2* X = reinterpret_cast<double2*>(smem_raw);  // [3][ny][ppc]
+      for (int w = tid; w < 3 * ny * ppc; w += nt) {
+        const int pl = w % ppc, fn = w / ppc;
+        X[w] = hb[(size_t)fn * P + min(p0 + pl, P - 1)];
+      }
+      __syncthreads();
+      analysis_fft<NF>(X, ppc, ny, P, p0, X + 3 * ny * ppc, t.cheb, t.tw_cheb, hb + p0);
+      return;
+    }
+  }
+  // direct sums, one field at a time: thread (mode pl, group gq of 8) forms
+  // the coefficients n = gq + 8 k
+  constexpr int KN = (2 * MH + 7) / 8;
+  CN* col0 = reinterpret_cast<CN*>(smem_raw);  // [ny][ppc]
+  const int pl = tid % ppc, gq = tid / ppc;
+  const RN* cheb = cheb_table<RN>(t);
+  const RN sg = (gq & 1) ? (RN)-1.0 : (RN)1.0;
+  for (int f = 0; f < 3; ++f) {
+    CN* hf = hb + (size_t)f * ny * P;
+    for (int w = tid; w < ny * ppc; w += nt) {
+      const int q = w % ppc, n = w / ppc;
+      col0[w] = hf[(size_t)n * P + min(p0 + q, P - 1)];
+    }
+    __syncthreads();
+    if (gq < 8) {
+      CN acc[KN];
+      analysis_sums<RN, KN>(col0 + pl, ppc, N, ny, cheb, gq, 8, sg, acc);
+      if (p0 + pl < P) {
+#pragma unroll
+        for (int k = 0; k < KN; ++k) {
+          const int n = gq + 8 * k;
+          if (n <= N) hf[(size_t)n * P + p0 + pl] = acc[k];
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename RN, int MH>
+__global__ void __launch_bounds__(64) stage_post_wide_kernel(Grid g, int B, PencilBufs pb, DevTables t,
+                                                             const typename cpx<RN>::T* __restrict__ hc,
+                                                             StageCoef sc, int ppc) {
+  extern __shared__ __align__(16) double sarr[];  // [MH][blockDim.x]
+  using CN = typename cpx<RN>::T;
+  const int P = g.P, ny = g.ny;
+  const int p0 = blockIdx.x * ppc;
+  const int b = blockIdx.y;
+  if (pb.active && !pb.active[b]) return;
+  pdl_wait_then_release();  // the coefficients of H come from the analysis
+  const int tid = threadIdx.x;
+  const int r = tid & 1, pl = (tid >> 1) % ppc, c = tid / (2 * ppc);
+  const int p = p0 + pl;
+  if (p >= P) return;  // no barrier in this kernel
+  if (p / g.nxh == g.nz / 2) return;  // Nyquist row stays zero
+  const CN* Hx = hc + (size_t)b * 3 * ny * P + p;
+  const CN* Hy = Hx + (size_t)ny * P;
+  const CN* Hz = Hy + (size_t)ny * P;
+  const size_t base = 2 * ((size_t)b * ny * P + p) + r;
+  const CompT<RN> HGr{reinterpret_cast<RN*>(pb.HGP) + base, 2 * P};
+  const CompT<RN> HVr{reinterpret_cast<RN*>(pb.HVP) + base, 2 * P};
+  SmemArr f{sarr + tid, (int)blockDim.x};
+  post_solve_noslip<MH, RN>(f, c, g, pb, t, sc, b, p, r, Hx, Hy, Hz, P, HGr, HVr);
+}
+
+// modes per CTA of the analysis half: 32 with direct sums (256 threads), 8
+// with the FP64 FFT form (three fields of the tile in shared memory)
+template <typename RN, int MH>
+constexpr int post_analysis_ppc() {
+  return (std::is_same<RN, double>::value && ct_plan_ok(2 * (MH - 1))) ? 8 : 32;
+}
+
+// ---------------------------------------------------------------------------
 // per-MH launchers, instantiated in the stage_mh*.cu translation units
 // ---------------------------------------------------------------------------
 template <typename RN, int MH>
@@ -1700,11 +1874,31 @@ template <typename RN, int MH, int TOP>
 cudaError_t post_batched_mh(const Grid& g, int B, const PencilBufs& pb, const DevTables& t,
                                    const typename cpx<RN>::T* h, const StageCoef& sc, int ppc, size_t smem,
                                    cudaStream_t st) {
-  static SmemLimit lim;
-  const cudaError_t e = raise_smem_limit(stage_post_batched_kernel<RN, MH, TOP>, &lim, smem);
-  if (e != cudaSuccess) return e;
-  return launch_pdl_if<sizeof(RN) == 4>(stage_post_batched_kernel<RN, MH, TOP>, dim3((g.P + ppc - 1) / ppc, B),
-                                        dim3(4 * ppc), smem, st, g, B, pb, t, h, sc, ppc);
+  using CN = typename cpx<RN>::T;
+  if constexpr (TOP == 0 && MH > 33) {
+    // two launches; the analysis replaces the nodal values of H, which no
+    // later kernel of the stage reads, by their coefficients
+    constexpr int apc = post_analysis_ppc<RN, MH>();
+    const size_t sa = std::is_same<RN, double>::value && apc == 8
+                          ? ((size_t)3 * g.ny + 6) * apc * sizeof(double2)
+                          : (size_t)g.ny * apc * sizeof(CN);
+    const int na = apc == 8 ? 128 : 8 * apc;
+    static SmemLimit lim_a, lim_w;
+    cudaError_t e = raise_smem_limit(stage_post_analysis_kernel<RN, MH>, &lim_a, sa);
+    if (e != cudaSuccess) return e;
+    if ((e = raise_smem_limit(stage_post_wide_kernel<RN, MH>, &lim_w, smem)) != cudaSuccess) return e;
+    e = launch_pdl_if<sizeof(RN) == 4>(stage_post_analysis_kernel<RN, MH>, dim3((g.P + apc - 1) / apc, B), dim3(na),
+                                       sa, st, g, B, pb, t, const_cast<CN*>(h), apc);
+    if (e != cudaSuccess) return e;
+    return launch_pdl_if<sizeof(RN) == 4>(stage_post_wide_kernel<RN, MH>, dim3((g.P + ppc - 1) / ppc, B),
+                                          dim3(4 * ppc), smem, st, g, B, pb, t, h, sc, ppc);
+  } else {
+    static SmemLimit lim;
+    const cudaError_t e = raise_smem_limit(stage_post_batched_kernel<RN, MH, TOP>, &lim, smem);
+    if (e != cudaSuccess) return e;
+    return launch_pdl_if<sizeof(RN) == 4>(stage_post_batched_kernel<RN, MH, TOP>, dim3((g.P + ppc - 1) / ppc, B),
+                                          dim3(4 * ppc), smem, st, g, B, pb, t, h, sc, ppc);
+  }
 }
 
 }  // namespace chdns

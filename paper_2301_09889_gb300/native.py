@@ -66,6 +66,7 @@ class ChInfo(ctypes.Structure):
         ("ppc_pre", ctypes.c_int), ("ppc_post", ctypes.c_int),
         ("tuned", ctypes.c_int),
         ("tune_ms", ctypes.c_double),
+        ("plane_team", ctypes.c_int),
     ]
 
 

@@ -103,10 +103,21 @@ def test_mixed_batch_equals_single(native_gpu):
         native.env_destroy(envb)
 
 
+def test_mixed_wide_form_against_oracle(native_gpu):
+    """80 channels of 129 nodes, mixed precision, in the two-launch batched
+    form of the implicit half: sampled slots against the FP64 oracle."""
+    kw = dict(MINIMAL, ny=129)
+    info, res = run_batch_pair(native_gpu, kw, 80, (0, 79), 2, tiles=(8, 16, 1))
+    assert info.post_batched == 1
+    for e, (lo, oo, ls, os_) in res.items():
+        _report(f"16x129x16 x80 wide form, slot {e}, 2 steps", _check(lo, oo, ls, os_, kw))
+
+
 def test_mixed_batched_implicit_half(native_gpu):
     """80 minimal channels, mixed precision, batched form of the implicit half:
     sampled slots against the FP64 oracle."""
     info, res = run_batch_pair(native_gpu, MINIMAL, 80, (0, 79), 2, tiles=(8, 16, 1))
     assert info.post_batched == 1
+    assert info.plane_team == 1
     for e, (lo, oo, ls, os_) in res.items():
         _report(f"minimal x80 batched, slot {e}, 2 steps", _check(lo, oo, ls, os_, MINIMAL))

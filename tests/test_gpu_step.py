@@ -134,6 +134,47 @@ def test_batch_equals_single_runs(native_gpu):
         assert rel_l2(ob[e], o1[0]) < 1e-13 and abs(tb[e] - t1[0]) < 1e-13 * abs(t1[0]) * 1e3
 
 
+def _run_batch_info(native, kw, seeds, acts, nsteps):
+    B = len(seeds)
+    env = native.env_create(native.params(**kw, batch=B))
+    try:
+        info = native.env_info(env)
+        for e, sd in enumerate(seeds):
+            native.env_set_state(env, e, native.pack_state(si.perturbed_poiseuille(16, 65, 16, sd, 0.2, 99), 16, 65, 16))
+        obs, tau, rew = np.zeros((B, 2, 16, 16)), np.zeros(B), np.zeros(B)
+        for _ in range(nsteps):
+            assert native.env_step(env, np.ascontiguousarray(acts), obs, tau, rew) == 0
+        return info, [native.env_get_state(env, e) for e in range(B)], obs.copy(), tau.copy()
+    finally:
+        native.env_destroy(env)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_register_plane_batch_slot_independent_and_equal_to_single(native_gpu, precision):
+    """A batch of 16 minimal channels (1040 planes, at least four per SM) runs
+    the nonlinear term with the register line transforms, one team of threads
+    per plane.  A slot's result is bit-identical whatever its neighbours hold,
+    and agrees to rounding with a single channel, which runs the cluster
+    kernel."""
+    native = native_gpu
+    kw = dict(MINIMAL, precision=precision)
+    B = 16
+    a = np.stack([si.wall_action(16, 16, 100 + e, 0.05 * 180 / 2800) for e in range(B)])
+    b = a.copy()
+    b[1:] = np.stack([si.wall_action(16, 16, 900 + e, 0.2 * 180 / 2800) for e in range(B - 1)])
+    info, sa, oa, ta = _run_batch_info(native, kw, list(range(10, 10 + B)), a, 3)
+    assert info.plane_team == 1 and info.plane_cluster == 1
+    _, sb, ob, tb = _run_batch_info(native, kw, [10] + list(range(70, 70 + B - 1)), b, 3)
+    assert np.array_equal(sa[0], sb[0]) and np.array_equal(oa[0], ob[0]) and ta[0] == tb[0]
+    tol = 1e-13 if precision == 0 else 1e-6
+    for e in (0, B - 1):
+        i1, s1, o1, t1 = _run_batch_info(native, kw, [10 + e], a[e:e + 1], 3)
+        assert i1.plane_team == 0
+        assert rel_l2(sa[e], s1[0]) < tol, e
+        assert rel_l2(oa[e], o1[0]) < tol
+        assert abs(ta[e] - t1[0]) < tol * 1e3 * abs(t1[0])
+
+
 def test_env_reset_matches_generator(native_gpu):
     native = native_gpu
     p = native.params(**MINIMAL, batch=2)
@@ -282,9 +323,9 @@ def test_re395_grid_wall_spectrum_and_boundary_conditions(native_gpu, precision)
 
 def test_re550_grid_mixed_wall_spectrum_and_boundary_conditions(native_gpu):
     """256x193x256 channel at Re_tau 550, mixed precision: the padded FP32
-    plane is split over a 16-CTA cluster."""
+    plane runs in three passes through global memory."""
     info = _large_grid_step_checks(native_gpu, RE550, 1, 6, 8)
-    assert info.plane_cluster == 16
+    assert info.plane_cluster == 0
 
 
 def test_re550_grid_fp64_wall_spectrum_and_boundary_conditions(native_gpu):
@@ -301,6 +342,7 @@ def test_batched_implicit_half_against_oracle(native_gpu):
     sampled slots, including the first and the last, against the oracle."""
     info, res = run_batch_pair(native_gpu, MINIMAL, 80, (0, 41, 79), 2, tiles=(8, 16, 1))
     assert info.post_batched == 1
+    assert info.plane_team == 1  # 80 x 65 planes: register line transforms
     for e, (lo, oo, ls, os_) in res.items():
         compare_states(ls, os_, TOL)
         _check_outputs(lo, oo, os_, MINIMAL)
@@ -375,6 +417,52 @@ def test_tile_shapes_give_identical_results(native_gpu, precision):
             ref = got
         else:
             assert all(np.array_equal(a, b) for a, b in zip(ref, got)), (pre, post, bat)
+
+
+TALL = dict(nx=16, ny=129, nz=16, lx=2.67, lz=0.8, re_tau=180.0, re_bulk=2800.0, dt=0.005)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_wide_form_tile_shapes_give_identical_results(native_gpu, precision):
+    """Above 65 nodes the batched implicit half runs in two launches (analysis
+    of H in place, then the solves with their arrays in shared memory).  It
+    gives the same bits as the per-tile form, for every width."""
+    native = native_gpu
+    B = 3
+    kw = dict(TALL, precision=precision, autotune=0)
+    acts = np.stack([si.wall_action(16, 16, 710 + e, 0.5 * 180 / 2800) for e in range(B)])
+    ref = None
+    for pre, post, bat in [(8, 4, 0), (4, 3, 0), (8, 16, 1), (4, 8, 1), (2, 2, 1)]:
+        env = native.env_create(native.params(**kw, batch=B))
+        try:
+            native.env_set_tiles(env, pre, post, bat)
+            info = native.env_info(env)
+            assert (info.ppc_post, info.post_batched) == (post, bat)
+            # per RK step: 3 x (pre, plane, post [+ analysis]) + wall shear; action and outputs
+            assert info.launches_per_step == 2 + 3 * (3 + bat) + 1 + 3
+            for e in range(B):
+                native.env_set_state(env, e, native.pack_state(
+                    si.perturbed_poiseuille(16, 129, 16, 80 + e, 0.2, 99), 16, 129, 16))
+            obs, tau, rew = np.zeros((B, 2, 16, 16)), np.zeros(B), np.zeros(B)
+            for _ in range(2):
+                assert native.env_step(env, acts, obs, tau, rew) == 0
+            got = (np.concatenate([native.env_get_state(env, e) for e in range(B)]), obs.copy(), tau.copy())
+        finally:
+            native.env_destroy(env)
+        if ref is None:
+            ref = got
+        else:
+            assert all(np.array_equal(a, b) for a, b in zip(ref, got)), (pre, post, bat)
+
+
+def test_wide_form_against_oracle(native_gpu):
+    """80 channels of 129 nodes in the two-launch batched form: sampled slots
+    against the oracle."""
+    info, res = run_batch_pair(native_gpu, TALL, 80, (0, 79), 2, tiles=(8, 16, 1))
+    assert info.post_batched == 1
+    for e, (lo, oo, ls, os_) in res.items():
+        compare_states(ls, os_, TOL)
+        _check_outputs(lo, oo, os_, TALL)
 
 
 def test_autotune_picks_a_candidate_and_rejects_bad_shapes(native_gpu):
