@@ -161,8 +161,8 @@ __device__ __forceinline__ void tau_affine(int N, int ny, int sig, const double 
 }
 
 // f = P + x Q
-template <int MH, class Tab>
-__device__ __forceinline__ void tau_close(int N, int sig, double (&f)[MH], const Tab& T, double x) {
+template <int MH, class Arr, class Tab>
+__device__ __forceinline__ void tau_close(int N, int sig, Arr& f, const Tab& T, double x) {
   const int M = (N - sig) / 2 + 1;
   f[0] = x;
 #pragma unroll
@@ -282,10 +282,10 @@ __device__ __forceinline__ void v_walk(int N, int ny, int ppc, int sv, const Com
 // per-thread array of MH doubles: registers (RegArr), or a column of shared
 // memory (SmemArr) where MH doubles per thread exceed the register file.
 // ---------------------------------------------------------------------------
-template <int MH>
+template <int MH, class V = double>
 struct RegArr {
-  double v[MH];
-  __device__ __forceinline__ double& operator[](int i) { return v[i]; }
+  V v[MH];
+  __device__ __forceinline__ V& operator[](int i) { return v[i]; }
 };
 struct SmemArr {
   double* p;
@@ -296,34 +296,35 @@ struct SmemArr {
 template <int MH, class Arr, class Tab, class Rhs, class Wall>
 __device__ __forceinline__ void tau_fused(int N, int ny, int sig, Rhs&& rhs, Arr& f, const Tab& T, double isq,
                                           Wall&& wall, const double* __restrict__ rowc) {
+  using V = std::decay_t<decltype(f[0])>;  // double, or a Pair of components
   const int M = (N - sig) / 2 + 1;
-  double r1 = 0.0, r2 = 0.0, anext = 0.0;  // r_{i+1}, r_{i+2}, a_{i+2}
+  V r1{}, r2{}, anext{};  // r_{i+1}, r_{i+2}, a_{i+2}
 #pragma unroll
   for (int i = MH - 1; i >= 0; --i) {
-    double r0 = 0.0;
+    V r0{};
     if (i < M) r0 = rhs(i);
     const int j = i + 1;  // row j needs r_{j-1} = r0, r_j = r1, r_{j+1} = r2
     if (j < MH && j < M) {
       const int n = 2 * j + sig;
-      double R = fma_rn(-rowc[ny + n], r1, mul_rn(rowc[n], r0));
+      V R = fma_rn(-rowc[ny + n], r1, mul_rn(rowc[n], r0));
       if (j + 1 < M) R = fma_rn(rowc[2 * ny + n], r2, R);
-      const double a = fma_rn(-T.h(j), anext, mul_rn(T.e(j), R));
+      const V a = fma_rn(-T.h(j), anext, mul_rn(T.e(j), R));
       f[j] = a;
       anext = a;
     }
     r2 = r1;
     r1 = r0;
   }
-  double Pp = 0.0, sum = 0.0;
+  V Pp{}, sum{};
 #pragma unroll
   for (int i = 1; i < MH; ++i) {
     if (i < M) {
       Pp = fma_rn(T.b(i), Pp, f[i]);
       f[i] = Pp;
-      sum += Pp;
+      sum = sum + Pp;
     }
   }
-  const double f0 = mul_rn(isq, wall() - sum);
+  const V f0 = mul_rn(isq, wall() - sum);
   f[0] = f0;
 #pragma unroll
   for (int i = 1; i < MH; ++i)
@@ -438,6 +439,186 @@ __device__ __forceinline__ void v_solve(Arr& f, int N, int ny, int ppc, int sv, 
     }
 }
 
+// ---------------------------------------------------------------------------
+// The affine families of the free-slip top with the right-hand sides produced
+// on the fly, as in tau_fused.  tau_affine_fused leaves f_i = P_i (i >= 1),
+// f_0 = 0, with sp = sum P and sp2 = sum n^2 P; tau_close then adds x Q.
+// The wall sums of the old field are taken on the way down.
+// ---------------------------------------------------------------------------
+template <int MH, class Arr, class Tab, class Rhs>
+__device__ __forceinline__ void tau_affine_fused(int N, int ny, int sig, Rhs&& rhs, Arr& f, const Tab& T,
+                                                 const double* __restrict__ rowc, double& sp, double& sp2) {
+  const int M = (N - sig) / 2 + 1;
+  double r1 = 0.0, r2 = 0.0, anext = 0.0;
+#pragma unroll
+  for (int i = MH - 1; i >= 0; --i) {
+    double r0 = 0.0;
+    if (i < M) r0 = rhs(i);
+    const int j = i + 1;
+    if (j < MH && j < M) {
+      const int n = 2 * j + sig;
+      double R = fma_rn(-rowc[ny + n], r1, mul_rn(rowc[n], r0));
+      if (j + 1 < M) R = fma_rn(rowc[2 * ny + n], r2, R);
+      const double a = fma_rn(-T.h(j), anext, mul_rn(T.e(j), R));
+      f[j] = a;
+      anext = a;
+    }
+    r2 = r1;
+    r1 = r0;
+  }
+  double Pp = 0.0;
+  sp = 0.0;
+  sp2 = 0.0;
+#pragma unroll
+  for (int i = 1; i < MH; ++i) {
+    if (i < M) {
+      const double n = 2 * i + sig;
+      Pp = fma_rn(T.b(i), Pp, f[i]);
+      f[i] = Pp;
+      sp += Pp;
+      sp2 = fma_rn(n * n, Pp, sp2);
+    }
+  }
+  f[0] = 0.0;
+}
+
+// omega_y of parity sq under the free-slip top: the affine family and
+// out = {sum P, sum n^2 P, sum g, sum n^2 g} for the closure
+template <int MH, typename RN, class Arr, class GV, class HR, class HW, class Tab>
+__device__ __forceinline__ void omega_open_affine(Arr& f, int N, int ny, int ppc, int sq, const GV& Gc,
+                                                  const HR& HGr, const HW& HGw, const typename cpx<RN>::T* Hx,
+                                                  const typename cpx<RN>::T* Hz, int r, double sgn, double kx,
+                                                  double kz, double cc, const StageCoef& sc, const Tab& T,
+                                                  const double* __restrict__ rowc, double* out) {
+  using CN = typename cpx<RN>::T;
+  const int ra = 1 - r;
+  auto comp = [](const CN z, int qd) { return qd == 0 ? z.x : z.y; };
+  const RN sgnn = (RN)sgn, kxn = (RN)kx, kzn = (RN)kz;
+  const RN dtn = (RN)sc.dt, gan = (RN)sc.gamma, zen = (RN)sc.zeta;
+  double so = 0.0, so2 = 0.0, sp, sp2;
+  tau_affine_fused<MH>(
+      N, ny, sq,
+      [&](int i) {
+        const int n = 2 * i + sq;
+        const double gn = Gc[n];
+        const RN hg = mul_rn(sgnn, fma_rn(-kxn, comp(Hz[n * ppc], ra), mul_rn(kzn, comp(Hx[n * ppc], ra))));
+        const RN hp = HGr[n];
+        HGw[n] = hg;
+        const RN q = mul_rn(dtn, fma_rn(gan, hg, mul_rn(zen, hp)));
+        so += gn;
+        so2 = fma_rn((double)n * n, gn, so2);
+        return fma_rn(1.0 + cc, gn, (double)q);
+      },
+      f, T, rowc, sp, sp2);
+  out[0] = sp;
+  out[1] = sp2;
+  out[2] = so;
+  out[3] = so2;
+}
+
+// mean flow of parity s under the free-slip top (U: e = 0, W: e = 1): the
+// affine family and out = {sum P, sum n^2 P, sum X, sum n^2 X, int P, int X}
+// (int x = sum 2 / (1 - n^2) x_n, even parity only)
+template <int MH, typename RN, class Arr, class Tab>
+__device__ __forceinline__ void mean_open_affine(Arr& f, int N, int ny, int ppc, int s, double* X, double* XP,
+                                                 const typename cpx<RN>::T* Hm, double cc, const StageCoef& sc,
+                                                 const Tab& T, const double* __restrict__ rowc, double* out) {
+  const int M = (N - s) / 2 + 1;
+  double so = 0.0, so2 = 0.0, wo = 0.0, sp, sp2;
+  tau_affine_fused<MH>(
+      N, ny, s,
+      [&](int i) {
+        const int n = 2 * i + s;
+        const double xn = X[n];
+        const double hv = (double)Hm[n * ppc].x;
+        const double hp = XP[n];
+        XP[n] = hv;
+        so += xn;
+        so2 = fma_rn((double)n * n, xn, so2);
+        if (s == 0) wo = fma_rn(2.0 / (1.0 - (double)n * n), xn, wo);
+        return fma_rn(1.0 + cc, xn, mul_rn(sc.dt, fma_rn(sc.gamma, hv, mul_rn(sc.zeta, hp))));
+      },
+      f, T, rowc, sp, sp2);
+  double wp = 0.0;
+  if (s == 0) {
+#pragma unroll
+    for (int i = 0; i < MH; ++i)
+      if (i < M) wp = fma_rn(2.0 / (1.0 - 4.0 * (double)i * i), f[i], wp);
+  }
+  out[0] = sp;
+  out[1] = sp2;
+  out[2] = so;
+  out[3] = so2;
+  out[4] = wp;
+  out[5] = wo;
+}
+
+// v of parity sv under the free-slip top: phi and v_p with the Dirichlet rows
+// of the no-slip channel (f = v_p on return), then out = {A_p, B_p, A_old,
+// B_old} of the free-slip rows (A = sum n^2 (n^2 - 1) / 3 v_n, B = sum n^2
+// v_n); vw is the wall velocity of this component
+template <int MH, typename RN, class Arr, class VV, class HR, class HW, class Tab, class TabP>
+__device__ __forceinline__ void v_open_part(Arr& f, int N, int ny, int ppc, int sv, const VV& Vc, const HR& HVr,
+                                            const HW& HVw, const typename cpx<RN>::T* Hx,
+                                            const typename cpx<RN>::T* Hy, const typename cpx<RN>::T* Hz, int r,
+                                            double sgn, double kx, double kz, double k2, double cc,
+                                            const StageCoef& sc, const Tab& Th, double isq_h, const TabP& Tp,
+                                            double isq_p, double vw, const double* __restrict__ rowc, double* out) {
+  using CN = typename cpx<RN>::T;
+  const int ra = 1 - r;
+  auto comp = [](const CN z, int qd) { return qd == 0 ? z.x : z.y; };
+  const double dsv = 2.0 * sv;
+  const RN dsvn = (RN)(2 * sv);
+  const RN sgnn = (RN)sgn, kxn = (RN)kx, kzn = (RN)kz, k2n = (RN)k2;
+  const RN dtn = (RN)sc.dt, gan = (RN)sc.gamma, zen = (RN)sc.zeta;
+  const int M = (N - sv) / 2 + 1;
+  double dv = 0.0, d2v = 0.0, S0 = 0.0, Bo = 0.0, Ao = 0.0;
+  RN tt = 0, dtt = 0;
+  tau_fused<MH>(
+      N, ny, sv,
+      [&](int i) {
+        const int no = 2 * i + sv + 1;
+        if (no <= N) {
+          const double vn1 = (no + 1 <= N) ? Vc[no + 1] : 0.0;
+          dv = fma_rn((double)(4 * i + 4) + dsv, vn1, dv);  // 2 (no + 1)
+          tt = mul_rn(sgnn, fma_rn(kxn, comp(Hx[no * ppc], ra), mul_rn(kzn, comp(Hz[no * ppc], ra))));
+        }
+        const int n = 2 * i + sv;
+        const double fac = (double)(4 * i + 2) + dsv;  // 2 (n + 1)
+        const RN facn = (RN)(4 * i + 2) + dsvn;
+        const double t1 = fma_rn(fac, dv, d2v);
+        const RN t2 = fma_rn(facn, (n + 1 <= N) ? tt : (RN)0, dtt);
+        d2v = (n == 0) ? 0.5 * t1 : t1;
+        dtt = (n == 0) ? (RN)0.5 * t2 : t2;
+        const double vn = Vc[n];
+        const double nn = (double)n * n;
+        S0 += vn;
+        Bo = fma_rn(nn, vn, Bo);
+        Ao = fma_rn(nn * (nn - 1.0) / 3.0, vn, Ao);
+        const double phi = fma_rn(-k2, vn, d2v);
+        const RN hv = fma_rn(-k2n, comp(Hy[n * ppc], r), -dtt);
+        const RN hp = HVr[n];
+        HVw[n] = hv;
+        const RN q = mul_rn(dtn, fma_rn(gan, hv, mul_rn(zen, hp)));
+        return fma_rn(1.0 + cc, phi, (double)q);
+      },
+      f, Th, isq_h, [] { return 0.0; }, rowc);
+  const double s = fma_rn(cc, S0, ((sv == 0) ? 0.5 : -0.5) * vw);
+  tau_fused<MH>(N, ny, sv, [&](int i) { return f[i]; }, f, Tp, isq_p, [&] { return s; }, rowc);
+  double Ap = 0.0, Bp = 0.0;
+#pragma unroll
+  for (int i = 0; i < MH; ++i)
+    if (i < M) {
+      const double n = 2 * i + sv;
+      Bp = fma_rn(n * n, f[i], Bp);
+      Ap = fma_rn(n * n * (n * n - 1.0) / 3.0, f[i], Ap);
+    }
+  out[0] = Ap;
+  out[1] = Bp;
+  out[2] = Ao;
+  out[3] = Bo;
+}
+
 // mean flow of parity s: U (e = 0, at constant flow rate through the
 // response u1 to a unit forcing) or W (e = 1); X the coefficients, XP the
 // previous plane means of H_x or H_z (FP64), Hm the new plane mean.
@@ -485,9 +666,11 @@ __device__ __forceinline__ void mean_solve(Arr& f, int N, int ny, int ppc, int s
 // top: the mean flow (p = 0), else omega_y of parity 1 - c and v of parity c.
 // H_x, H_y, H_z: Chebyshev coefficients of the mode, element n at n * hs;
 // HGr, HVr: the previous nonlinear right-hand sides (node precision); the new
-// ones go to the pencil buffers.  f: the thread's array of MH doubles.
-template <int MH, typename RN, class Arr, class Cls>
-__device__ __forceinline__ void post_solve_noslip(Arr& f, Cls cls, const Grid& g, const PencilBufs& pb,
+// ones go to the pencil buffers.  Each solve keeps its array of MH doubles in
+// registers (col = nullptr) or in the thread's column of shared memory,
+// col[i * cs].
+template <int MH, typename RN, bool SMEM, class Cls>
+__device__ __forceinline__ void post_solve_noslip(double* col, int cs, Cls cls, const Grid& g, const PencilBufs& pb,
                                                   const DevTables& t, const StageCoef& sc, int b, int p, int r,
                                                   const typename cpx<RN>::T* Hx, const typename cpx<RN>::T* Hy,
                                                   const typename cpx<RN>::T* Hz, int hs, const CompT<RN>& HGr,
@@ -502,9 +685,18 @@ __device__ __forceinline__ void post_solve_noslip(Arr& f, Cls cls, const Grid& g
   if (p == 0) {
     // mean mode: U (r = 0) at constant flow rate and W (r = 1), parity c
     const int e = r;
-    mean_solve<MH, RN>(f, N, ny, hs, c, e, (e == 0 ? pb.UM : pb.WM) + (size_t)b * ny,
+    auto run = [&](auto& f) {
+      mean_solve<MH, RN>(f, N, ny, hs, c, e, (e == 0 ? pb.UM : pb.WM) + (size_t)b * ny,
                        (e == 0 ? pb.HXP : pb.HZP) + (size_t)b * ny, (e == 0) ? Hx : Hz, cc, sc, helm(c),
                        helm_isq(c), rowc, t.tau.u1 + (size_t)sc.k * Mh, t.tau.u1_iflux[sc.k]);
+    };
+    if constexpr (SMEM) {
+      SmemArr f{col, cs};
+      run(f);
+    } else {
+      RegArr<MH> f;
+      run(f);
+    }
     return;
   }
   const int row = p / g.nxh, ix = p % g.nxh;
@@ -517,8 +709,17 @@ __device__ __forceinline__ void post_solve_noslip(Arr& f, Cls cls, const Grid& g
     const int sq = 1 - c;
     const CompS Gc{reinterpret_cast<double*>(pb.G) + base, 2 * P};
     const CompT<RN> HGc{reinterpret_cast<RN*>(pb.HGP) + base, 2 * P};
-    omega_solve<MH, RN>(f, N, ny, hs, sq, Gc, HGr, HGc, Hx, Hz, r, sgn, kx, kz, cc, sc, helm(sq), helm_isq(sq),
-                        rowc);
+    auto run = [&](auto& f) {
+      omega_solve<MH, RN>(f, N, ny, hs, sq, Gc, HGr, HGc, Hx, Hz, r, sgn, kx, kz, cc, sc, helm(sq), helm_isq(sq),
+                          rowc);
+    };
+    if constexpr (SMEM) {
+      SmemArr f{col, cs};
+      run(f);
+    } else {
+      RegArr<MH> f;
+      run(f);
+    }
   }
   {
     // wall-normal velocity, parity c
@@ -529,9 +730,18 @@ __device__ __forceinline__ void post_solve_noslip(Arr& f, Cls cls, const Grid& g
     const double vw = fma_rn(sc.theta, comp(pb.vw_new[vo], r) - comp(pb.vw_old[vo], r), comp(pb.vw_old[vo], r));
     const TabSm TP{t.tau.pois + (size_t)sv * 4 * Mh * P + p, Mh, P};
     const double* vh = t.tau.vh + (size_t)(sc.k * 2 + sv) * Mh * P + p;
-    v_solve<MH, RN>(f, N, ny, hs, sv, Vc, HVr, HVc, Hx, Hy, Hz, r, sgn, kx, kz, k2, cc, sc, helm(sv), helm_isq(sv),
-                    TP, t.tau.pois_isq[(size_t)sv * P + p], [&](int i) { return vh[(size_t)i * P]; },
-                    t.tau.vh_idv[(size_t)(sc.k * 2 + sv) * P + p], vw, rowc);
+    auto run = [&](auto& f) {
+      v_solve<MH, RN>(f, N, ny, hs, sv, Vc, HVr, HVc, Hx, Hy, Hz, r, sgn, kx, kz, k2, cc, sc, helm(sv),
+                      helm_isq(sv), TP, t.tau.pois_isq[(size_t)sv * P + p], [&](int i) { return vh[(size_t)i * P]; },
+                      t.tau.vh_idv[(size_t)(sc.k * 2 + sv) * P + p], vw, rowc);
+    };
+    if constexpr (SMEM) {
+      SmemArr f{col, cs};
+      run(f);
+    } else {
+      RegArr<MH> f;
+      run(f);
+    }
   }
 }
 
@@ -1255,112 +1465,42 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
     const CN* Hz = Hy + ny * ppc;
     auto helm = [&](int sig) { return TabSm{sh + sig * 4 * Mh * ppc + pl, Mh, ppc}; };
     auto comp = [](auto z, int qd) { return qd == 0 ? z.x : z.y; };
-    const RN dtn = (RN)sc.dt, gan = (RN)sc.gamma, zen = (RN)sc.zeta;
     const int pc = min(p, P - 1);
     // table sums of both parities: sum Q, sum n^2 Q of this stage; A, B of vh
     auto qs = [&](int sig, int w) { return t.tau.helm_top[((size_t)(sc.k * 2 + sig) * 2 + w) * P + pc]; };
     auto vs = [&](int sig, int w) { return t.tau.vh_top[((size_t)(sc.k * 2 + sig) * 2 + w) * P + pc]; };
     double* mine = xch + tid * 6;
     const double* other = xch + ((combo ^ 1) * ppc + pl) * 6;
-    double f[MH], rhs[MH];
+    RegArr<MH> f;
     int sig = 0;
     if (live) {
       if (p == 0) {
         // mean mode: U (e = 0) at constant flow rate, W (e = 1), parity c
         sig = c;
-        const int M = (N - sig) / 2 + 1;
-        double* X = (e == 0 ? pb.UM : pb.WM) + (size_t)b * ny;
-        double* XP = (e == 0 ? pb.HXP : pb.HZP) + (size_t)b * ny;
-        const CN* Hm = (e == 0) ? Hx : Hz;
-        double so = 0.0, so2 = 0.0, wo = 0.0;
-#pragma unroll
-        for (int i = 0; i < MH; ++i) {
-          rhs[i] = 0.0;
-          if (i < M) {
-            const int n = 2 * i + sig;
-            const double xn = X[n];
-            const double hv = (double)Hm[n * ppc].x;
-            const double hp = XP[n];
-            XP[n] = hv;
-            rhs[i] = fma_rn(1.0 + cc, xn, mul_rn(sc.dt, fma_rn(sc.gamma, hv, mul_rn(sc.zeta, hp))));
-            so += xn;
-            so2 = fma_rn((double)n * n, xn, so2);
-            if (sig == 0) wo = fma_rn(2.0 / (1.0 - (double)n * n), xn, wo);
-          }
-        }
-        double psum, psum2;
-        tau_affine<MH>(N, ny, sig, rhs, f, helm(sig), rowc, psum, psum2);
-        double wp = 0.0;
-        if (sig == 0) {
-#pragma unroll
-          for (int i = 0; i < MH; ++i)
-            if (i < M) wp = fma_rn(2.0 / (1.0 - 4.0 * (double)i * i), f[i], wp);
-        }
-        mine[0] = psum; mine[1] = psum2; mine[2] = so; mine[3] = so2; mine[4] = wp; mine[5] = wo;
+        mean_open_affine<MH, RN>(f, N, ny, ppc, sig, (e == 0 ? pb.UM : pb.WM) + (size_t)b * ny,
+                                 (e == 0 ? pb.HXP : pb.HZP) + (size_t)b * ny, (e == 0) ? Hx : Hz, cc, sc, helm(sig),
+                                 rowc, mine);
       } else if (e == 0) {
         // wall-normal vorticity, parity 1 - c
         sig = 1 - c;
-        const int M = (N - sig) / 2 + 1;
         const CompS Gc{reinterpret_cast<double*>(sG) + 2 * pl + r, 2 * ppc};
         const CompT<RN> HGc{reinterpret_cast<RN*>(sHG) + 2 * pl + r, 2 * ppc};
-        const double sgn = (r == 0) ? -1.0 : 1.0;
-        const int ra = 1 - r;
-        const RN sgnn = (RN)sgn, kxn = (RN)t.kx[ix], kzn = (RN)t.kz[row];
-        double so = 0.0, so2 = 0.0;
-#pragma unroll
-        for (int i = 0; i < MH; ++i) {
-          rhs[i] = 0.0;
-          if (i < M) {
-            const int n = 2 * i + sig;
-            const double gn = Gc[n];
-            const RN hg = mul_rn(sgnn, fma_rn(-kxn, comp(Hz[n * ppc], ra), mul_rn(kzn, comp(Hx[n * ppc], ra))));
-            const RN hp = HGc[n];
-            HGc[n] = hg;
-            const RN q = mul_rn(dtn, fma_rn(gan, hg, mul_rn(zen, hp)));
-            rhs[i] = fma_rn(1.0 + cc, gn, (double)q);
-            so += gn;
-            so2 = fma_rn((double)n * n, gn, so2);
-          }
-        }
-        double psum, psum2;
-        tau_affine<MH>(N, ny, sig, rhs, f, helm(sig), rowc, psum, psum2);
-        mine[0] = psum; mine[1] = psum2; mine[2] = so; mine[3] = so2;
+        omega_open_affine<MH, RN>(f, N, ny, ppc, sig, Gc, HGc, HGc, Hx, Hz, r, (r == 0) ? -1.0 : 1.0, t.kx[ix],
+                                  t.kz[row], cc, sc, helm(sig), rowc, mine);
       } else {
         // wall-normal velocity, parity c: phi_p and v_p as in the no-slip
         // channel (Dirichlet rows of both), then the sums of the free-slip rows
         sig = c;
-        const int M = (N - sig) / 2 + 1;
         const double kx = t.kx[ix], kz = t.kz[row], k2 = kx * kx + kz * kz;
-        const double sgn = (r == 0) ? -1.0 : 1.0;
         const CompS Vc{reinterpret_cast<double*>(sV) + 2 * pl + r, 2 * ppc};
         const CompT<RN> HVc{reinterpret_cast<RN*>(sHV) + 2 * pl + r, 2 * ppc};
-        double S0 = 0.0, Bo = 0.0, Ao = 0.0;
-#pragma unroll
-        for (int i = 0; i < MH; ++i) rhs[i] = 0.0;
-        for (int i = 0; i < M; ++i) {
-          const double n = 2 * i + sig;
-          const double vn = Vc[2 * i + sig];
-          S0 += vn;
-          Bo = fma_rn(n * n, vn, Bo);
-          Ao = fma_rn(n * n * (n * n - 1.0) / 3.0, vn, Ao);
-        }
-        v_walk<MH, RN>(N, ny, ppc, sig, Vc, HVc, HVc, Hx, Hy, Hz, r, sgn, kx, kz, k2, cc, sc, rhs);
-        tau_seq<MH>(N, ny, sig, rhs, f, helm(sig), ss[(0 * 2 + sig) * ppc + pl], 0.0, rowc);
         const size_t vo = (size_t)b * P + p;
         const double vw =
             fma_rn(sc.theta, comp(pb.vw_new[vo], r) - comp(pb.vw_old[vo], r), comp(pb.vw_old[vo], r));
-        const double s = fma_rn(cc, S0, ((sig == 0) ? 0.5 : -0.5) * vw);
         const TabSm TP{sp + sig * 4 * Mh * ppc + pl, Mh, ppc};
-        tau_seq<MH>(N, ny, sig, f, rhs, TP, ss[(1 * 2 + sig) * ppc + pl], s, rowc);
-        double Ap = 0.0, Bp = 0.0;
-#pragma unroll
-        for (int i = 0; i < MH; ++i)
-          if (i < M) {
-            const double n = 2 * i + sig;
-            Bp = fma_rn(n * n, rhs[i], Bp);
-            Ap = fma_rn(n * n * (n * n - 1.0) / 3.0, rhs[i], Ap);
-          }
-        mine[0] = Ap; mine[1] = Bp; mine[2] = Ao; mine[3] = Bo;
+        v_open_part<MH, RN>(f, N, ny, ppc, sig, Vc, HVc, HVc, Hx, Hy, Hz, r, (r == 0) ? -1.0 : 1.0, kx, kz, k2, cc,
+                            sc, helm(sig), ss[(0 * 2 + sig) * ppc + pl], TP, ss[(1 * 2 + sig) * ppc + pl], vw, rowc,
+                            mine);
       }
     }
     __syncthreads();
@@ -1418,7 +1558,7 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
         for (int i = 0; i < MH; ++i)
           if (i < M) {
             const int n = 2 * i + sig;
-            Vc[n] = fma_rn(-cc, Vc[n], fma_rn(cI, vh[i * ppc], rhs[i]));
+            Vc[n] = fma_rn(-cc, Vc[n], fma_rn(cI, vh[i * ppc], f[i]));
           }
       }
     }
@@ -1544,8 +1684,7 @@ __global__ void __launch_bounds__(64, post_batched_min_ctas<MH, TOP>()) stage_po
     // would double).  The arithmetic is the same either way: the factors are
     // exact small integers and every fused operation is pinned.
     auto solve = [&](auto cls) {
-      RegArr<MH> f;
-      post_solve_noslip<MH, RN>(f, cls, g, pb, t, sc, b, p, r, Hx, Hy, Hz, ppc, HGr, HVr);
+      post_solve_noslip<MH, RN, false>(nullptr, 0, cls, g, pb, t, sc, b, p, r, Hx, Hy, Hz, ppc, HGr, HVr);
     };
     if constexpr (MH <= 33) {
       if (c == 0) solve(std::integral_constant<int, 0>{});
@@ -1571,15 +1710,13 @@ __global__ void __launch_bounds__(64, post_batched_min_ctas<MH, TOP>()) stage_po
     const CN* Hy = Hx + ny * ppc;
     const CN* Hz = Hy + ny * ppc;
     auto comp = [](auto z, int qq) { return qq == 0 ? z.x : z.y; };
-    const RN dtn = (RN)sc.dt, gan = (RN)sc.gamma, zen = (RN)sc.zeta;
     auto helm = [&](int sig) { return TabSm{t.tau.helm + (size_t)(sc.k * 2 + sig) * 4 * Mh * P + pc, Mh, P}; };
     auto helm_isq = [&](int sig) { return t.tau.helm_isq[(size_t)(sc.k * 2 + sig) * P + pc]; };
     auto qs = [&](int sig, int w) { return t.tau.helm_top[((size_t)(sc.k * 2 + sig) * 2 + w) * P + pc]; };
     auto vs = [&](int sig, int w) { return t.tau.vh_top[((size_t)(sc.k * 2 + sig) * 2 + w) * P + pc]; };
     const size_t base = 2 * ((size_t)b * ny * P + pc) + r;  // component r of element n at base + 2 P n
     const double sgn = (r == 0) ? -1.0 : 1.0;
-    const int ra = 1 - r;
-    double f[MH], rhs[MH];
+    RegArr<MH> f;
     // round 1: the mean mode (U for r = 0, W for r = 1) on parity c, or
     // omega_y on parity 1 - c
     {
@@ -1589,58 +1726,15 @@ __global__ void __launch_bounds__(64, post_batched_min_ctas<MH, TOP>()) stage_po
       const double* other = xch + mate * 6;
       if (live) {
         if (mean) {
-          double* X = (r == 0 ? pb.UM : pb.WM) + (size_t)b * ny;
-          double* XP = (r == 0 ? pb.HXP : pb.HZP) + (size_t)b * ny;
-          const CN* Hm = (r == 0) ? Hx : Hz;
-          double so = 0.0, so2 = 0.0, wo = 0.0;
-#pragma unroll
-          for (int i = 0; i < MH; ++i) {
-            rhs[i] = 0.0;
-            if (i < M) {
-              const int n = 2 * i + sig;
-              const double xn = X[n];
-              const double hv = (double)Hm[n * ppc].x;
-              const double hp = XP[n];
-              XP[n] = hv;
-              rhs[i] = fma_rn(1.0 + cc, xn, mul_rn(sc.dt, fma_rn(sc.gamma, hv, mul_rn(sc.zeta, hp))));
-              so += xn;
-              so2 = fma_rn((double)n * n, xn, so2);
-              if (sig == 0) wo = fma_rn(2.0 / (1.0 - (double)n * n), xn, wo);
-            }
-          }
-          double psum, psum2;
-          tau_affine<MH>(N, ny, sig, rhs, f, helm(sig), rowc, psum, psum2);
-          double wp = 0.0;
-          if (sig == 0) {
-#pragma unroll
-            for (int i = 0; i < MH; ++i)
-              if (i < M) wp = fma_rn(2.0 / (1.0 - 4.0 * (double)i * i), f[i], wp);
-          }
-          mine[0] = psum; mine[1] = psum2; mine[2] = so; mine[3] = so2; mine[4] = wp; mine[5] = wo;
+          mean_open_affine<MH, RN>(f, N, ny, ppc, sig, (r == 0 ? pb.UM : pb.WM) + (size_t)b * ny,
+                                   (r == 0 ? pb.HXP : pb.HZP) + (size_t)b * ny, (r == 0) ? Hx : Hz, cc, sc, helm(sig),
+                                   rowc, mine);
         } else {
           const CompS Gc{reinterpret_cast<double*>(pb.G) + base, 2 * P};
           const CompT<RN> HGc{reinterpret_cast<RN*>(pb.HGP) + base, 2 * P};
           const CompT<RN> HGr = kStageHG ? CompT<RN>{reinterpret_cast<RN*>(sHGt) + 2 * pl + r, 2 * ppc} : HGc;
-          const RN sgnn = (RN)sgn, kxn = (RN)t.kx[ix], kzn = (RN)t.kz[row];
-          double so = 0.0, so2 = 0.0;
-#pragma unroll
-          for (int i = 0; i < MH; ++i) {
-            rhs[i] = 0.0;
-            if (i < M) {
-              const int n = 2 * i + sig;
-              const double gn = Gc[n];
-              const RN hg = mul_rn(sgnn, fma_rn(-kxn, comp(Hz[n * ppc], ra), mul_rn(kzn, comp(Hx[n * ppc], ra))));
-              const RN hp = HGr[n];
-              HGc[n] = hg;
-              const RN q = mul_rn(dtn, fma_rn(gan, hg, mul_rn(zen, hp)));
-              rhs[i] = fma_rn(1.0 + cc, gn, (double)q);
-              so += gn;
-              so2 = fma_rn((double)n * n, gn, so2);
-            }
-          }
-          double psum, psum2;
-          tau_affine<MH>(N, ny, sig, rhs, f, helm(sig), rowc, psum, psum2);
-          mine[0] = psum; mine[1] = psum2; mine[2] = so; mine[3] = so2;
+          omega_open_affine<MH, RN>(f, N, ny, ppc, sig, Gc, HGr, HGc, Hx, Hz, r, sgn, t.kx[ix], t.kz[row], cc, sc,
+                                    helm(sig), rowc, mine);
         }
       }
       __syncthreads();
@@ -1698,33 +1792,12 @@ __global__ void __launch_bounds__(64, post_batched_min_ctas<MH, TOP>()) stage_po
         const double kx = t.kx[ix], kz = t.kz[row], k2 = kx * kx + kz * kz;
         const CompT<RN> HVc{reinterpret_cast<RN*>(pb.HVP) + base, 2 * P};
         const CompT<RN> HVr = kStageHV ? CompT<RN>{reinterpret_cast<RN*>(sHVt) + 2 * pl + r, 2 * ppc} : HVc;
-        double S0 = 0.0, Bo = 0.0, Ao = 0.0;
-#pragma unroll
-        for (int i = 0; i < MH; ++i) rhs[i] = 0.0;
-        for (int i = 0; i < M; ++i) {
-          const double n = 2 * i + sig;
-          const double vn = Vc[2 * i + sig];
-          S0 += vn;
-          Bo = fma_rn(n * n, vn, Bo);
-          Ao = fma_rn(n * n * (n * n - 1.0) / 3.0, vn, Ao);
-        }
-        v_walk<MH, RN>(N, ny, ppc, sig, Vc, HVr, HVc, Hx, Hy, Hz, r, sgn, kx, kz, k2, cc, sc, rhs);
-        tau_seq<MH>(N, ny, sig, rhs, f, helm(sig), helm_isq(sig), 0.0, rowc);
         const size_t vo = (size_t)b * P + pc;
         const double vw =
             fma_rn(sc.theta, comp(pb.vw_new[vo], r) - comp(pb.vw_old[vo], r), comp(pb.vw_old[vo], r));
-        const double s = fma_rn(cc, S0, ((sig == 0) ? 0.5 : -0.5) * vw);
         const TabSm TP{t.tau.pois + (size_t)sig * 4 * Mh * P + pc, Mh, P};
-        tau_seq<MH>(N, ny, sig, f, rhs, TP, t.tau.pois_isq[(size_t)sig * P + pc], s, rowc);
-        double Ap = 0.0, Bp = 0.0;
-#pragma unroll
-        for (int i = 0; i < MH; ++i)
-          if (i < M) {
-            const double n = 2 * i + sig;
-            Bp = fma_rn(n * n, rhs[i], Bp);
-            Ap = fma_rn(n * n * (n * n - 1.0) / 3.0, rhs[i], Ap);
-          }
-        mine[0] = Ap; mine[1] = Bp; mine[2] = Ao; mine[3] = Bo;
+        v_open_part<MH, RN>(f, N, ny, ppc, sig, Vc, HVr, HVc, Hx, Hy, Hz, r, sgn, kx, kz, k2, cc, sc, helm(sig),
+                            helm_isq(sig), TP, t.tau.pois_isq[(size_t)sig * P + pc], vw, rowc, mine);
       }
       __syncthreads();
       if (on) {
@@ -1738,7 +1811,7 @@ __global__ void __launch_bounds__(64, post_batched_min_ctas<MH, TOP>()) stage_po
         for (int i = 0; i < MH; ++i)
           if (i < M) {
             const int n = 2 * i + sig;
-            Vc[n] = fma_rn(-cc, Vc[n], fma_rn(cI, vh[(size_t)i * P], rhs[i]));
+            Vc[n] = fma_rn(-cc, Vc[n], fma_rn(cI, vh[(size_t)i * P], f[i]));
           }
       }
     }
@@ -1835,8 +1908,7 @@ __global__ void __launch_bounds__(64) stage_post_wide_kernel(Grid g, int B, Penc
   const size_t base = 2 * ((size_t)b * ny * P + p) + r;
   const CompT<RN> HGr{reinterpret_cast<RN*>(pb.HGP) + base, 2 * P};
   const CompT<RN> HVr{reinterpret_cast<RN*>(pb.HVP) + base, 2 * P};
-  SmemArr f{sarr + tid, (int)blockDim.x};
-  post_solve_noslip<MH, RN>(f, c, g, pb, t, sc, b, p, r, Hx, Hy, Hz, P, HGr, HVr);
+  post_solve_noslip<MH, RN, true>(sarr + tid, (int)blockDim.x, c, g, pb, t, sc, b, p, r, Hx, Hy, Hz, P, HGr, HVr);
 }
 
 // modes per CTA of the analysis half: 32 with direct sums (256 threads), 8
