@@ -660,24 +660,31 @@ def measure_handle(native, workload: str, args, rank: int, world: int, flush, di
 # serving
 # ---------------------------------------------------------------------------
 
-def served_run(native, workload: str, rate: float, duration: float, warm: float = 3.0) -> dict:
+def served_run(native, workload: str, rate: float, duration: float, warm: float = 3.0,
+               linger_us: int | None = None) -> dict:
     """Continuous-batching server driven by actor threads.
 
     Each actor thread drives a group of CH_SERVE_GROUP environments of one
     class (default per workload): it submits one action for every environment
-    of its group, waits for each result, thinks for an exponentially
+    of its group in one call (srv_submit_many), waits for the group's results
+    in one call (srv_wait_many), thinks for an exponentially
     distributed time of mean 1/rate (0: none, saturation) and repeats until
     the time budget is spent.  Groups larger than one keep the Python threads
     few, so that the host side does not limit the measured server.
-    Latencies are the server's own submit-to-completion clock."""
+    Latencies are the server's own submit-to-completion clock.  linger_us is
+    the server's batching window (srv_set_linger; default CH_SERVE_LINGER_US,
+    else 0)."""
     import random
     import threading
 
     groups, slots, group_default, name = SERVED[workload]
     budget = int(float(os.environ.get("CH_SERVE_BUDGET_GB", "64")) * (1 << 30))
     srv = native.srv_create(budget, slots)
+    if linger_us is None:
+        linger_us = int(os.environ.get("CH_SERVE_LINGER_US", "0"))
     envs = []
     try:
+        native.srv_set_linger(srv, linger_us)
         for prm, count in groups:
             p = native.params(**prm)
             for _ in range(count):
@@ -693,23 +700,23 @@ def served_run(native, workload: str, rate: float, duration: float, warm: float 
             nrng = np.random.default_rng(seed)
             nx, nz = prm["nx"], prm["nz"]
             u_tau = prm["re_tau"] / prm["re_bulk"]
-            obs = np.zeros((2, nz, nx))
+            obs = np.zeros((len(eids), 2, nz, nx))
             acts = nrng.standard_normal((16, nz, nx)) * 0.05 * u_tau
             acts -= acts.mean(axis=(1, 2), keepdims=True)
+            ids = np.asarray(eids, dtype=np.int32)
             mine = lat.setdefault(f"{nx}x{prm['ny']}x{nz}", [])
             i = 0
             try:
                 while not stop.is_set():
                     t0 = time.perf_counter()
-                    rids = [native.srv_submit(srv, eid, acts[(i + k) % 16] if prm["control"] == 0 else None)
-                            for k, eid in enumerate(eids)]
-                    for rid in rids:
-                        rc, *_ = native.srv_wait(srv, rid, 120000, obs)
-                        if rc != native.CH_OK:
-                            errors.append(rc)
-                            return
-                        if measuring.is_set():
-                            mine.append(time.perf_counter() - t0)
+                    a = acts[(i + np.arange(len(eids))) % 16] if prm["control"] == 0 else None
+                    rids = native.srv_submit_many(srv, ids, a)
+                    rc, _, _, st = native.srv_wait_many(srv, rids, 120000, obs)
+                    if rc != native.CH_OK or (st != native.CH_OK).any():
+                        errors.append(rc if rc != native.CH_OK else int(st[st != native.CH_OK][0]))
+                        return
+                    if measuring.is_set():
+                        mine.extend([time.perf_counter() - t0] * len(eids))
                     i += 1
                     if rate > 0:
                         time.sleep(rng.expovariate(rate))
@@ -750,7 +757,8 @@ def served_run(native, workload: str, rate: float, duration: float, warm: float 
                                 "p99_ms": float(np.percentile(a, 99))}
     return {"value": st.env_steps_per_s, "unit": UNIT, "completed": int(st.completed),
             "p50_ms": st.p50_us / 1e3, "p99_ms": st.p99_us / 1e3, "mean_ms": st.mean_us / 1e3,
-            "think_rate_per_s": rate, "seconds": duration, "envs": len(envs), "classes": st.classes,
+            "think_rate_per_s": rate, "linger_us": linger_us, "seconds": duration, "envs": len(envs),
+            "classes": st.classes,
             "slots_per_class": slots, "envs_per_actor_thread": group, "actor_threads": len(work),
             "hbm_used_gb": st.hbm_used / (1 << 30), "mpts_rk3_steps_per_s": st.env_steps_per_s * pts / 1e6,
             "per_class_actor_side": per_class, "errors": errors[:5], "workload": name}
@@ -773,7 +781,8 @@ def run_served(args):
         "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": r["workload"], "envs": r["envs"], "slots_per_class": r["slots_per_class"],
-                   "classes": r["classes"], "think_rate_per_s": rate, "envs_per_actor_thread": r["envs_per_actor_thread"],
+                   "classes": r["classes"], "think_rate_per_s": rate, "linger_us": r["linger_us"],
+                   "envs_per_actor_thread": r["envs_per_actor_thread"],
                    "actor_threads": r["actor_threads"], "seconds": duration, "hbm_used_gb": r["hbm_used_gb"]},
         "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"], "mean_ms": r["mean_ms"],
         "mpts_rk3_steps_per_s": r["mpts_rk3_steps_per_s"], "per_class_actor_side": r["per_class_actor_side"],

@@ -297,6 +297,14 @@ typedef struct ch_srv_stats {
 /* Server with a device-memory budget for its class handles.  No GPU work yet. */
 int srv_create(size_t hbm_budget_bytes, int slots_per_class, ch_server_t** out);
 
+/* Bounded batching window, in microseconds (0, the default, up to 10^6).
+ * While some of a class's environments have a request pending and others do
+ * not, the class's next tick waits until every environment has one or until
+ * linger_us have passed since the oldest pending request, whichever comes
+ * first.  Larger ticks raise throughput when actors submit at nearly the same
+ * time; a request waits at most linger_us longer.  CH_ERR_ARG out of range. */
+int srv_set_linger(ch_server_t* s, int linger_us);
+
 /* Admit one environment with the env_reset initial state (seed, amplitude,
  * kmax).  Uses a free slot of its class; otherwise creates the class, which
  * fails with CH_ERR_BUDGET if its footprint does not fit the budget (retry
@@ -313,6 +321,14 @@ int srv_evict(ch_server_t* s, int env_id);
  * Requests of one environment run in submission order. */
 int srv_submit(ch_server_t* s, int env_id, const double* action, uint64_t* req_id);
 
+/* srv_submit for n requests at once (an actor driving many environments):
+ * env_ids [n]; actions holds, in order, one [nz][nx] plane for every request
+ * whose environment takes external actions (NULL if none does); req_ids [n]
+ * receives the ids.  Every request is checked first (unknown environment,
+ * missing or non-finite action: CH_ERR_ARG) and then all are queued at once,
+ * so a refused batch queues nothing. */
+int srv_submit_many(ch_server_t* s, int n, const int* env_ids, const double* actions, uint64_t* req_ids);
+
 /* Result of a request: CH_PENDING while it runs; otherwise its status, with
  * obs [2][nz][nx], wall shear, reward and the submit-to-completion latency
  * written (any output pointer may be NULL) and the request released. */
@@ -322,6 +338,14 @@ int srv_poll(ch_server_t* s, uint64_t req_id, double* obs, double* wall_shear, d
 /* srv_poll that waits up to timeout_ms; CH_ERR_TIMEOUT if still running. */
 int srv_wait(ch_server_t* s, uint64_t req_id, int timeout_ms, double* obs, double* wall_shear,
              double* reward, double* latency_us);
+
+/* Wait up to timeout_ms for n requests to finish, then release them all:
+ * obs receives their [2][nz][nx] planes in order (may be NULL), wall_shear
+ * and reward [n] (may be NULL), status [n] each request's status.  CH_OK once
+ * all have finished (their statuses say how), CH_ERR_TIMEOUT with nothing
+ * released if some are still running, CH_ERR_ARG for an unknown id. */
+int srv_wait_many(ch_server_t* s, int n, const uint64_t* req_ids, int timeout_ms, double* obs, double* wall_shear,
+                  double* reward, int* status);
 
 /* State of an admitted environment (layout of env_get_state); waits for
  * its class to be idle.  srv_set_state requires no queued request. */

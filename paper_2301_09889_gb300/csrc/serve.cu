@@ -106,6 +106,10 @@ struct ch_server {
   bool stop = false;
   size_t budget = 0, used = 0;
   int slots_per_class = 0;
+  // bounded batching window: a class with some but not all of its
+  // environments pending waits up to this long after its oldest pending
+  // request before it launches (0: launch with whatever is pending)
+  std::chrono::microseconds linger{0};
   std::vector<std::unique_ptr<Class>> classes;
   std::unordered_map<int, Env> envs;
   std::map<uint64_t, Request> reqs;
@@ -219,10 +223,31 @@ void ch_server::run() {
   std::unique_lock<std::mutex> lk(mu);
   while (!stop) {
     bool launched = false, any_busy = false;
+    Clock::time_point wake = Clock::time_point::max();  // earliest end of a batching window
     // launch a tick on every idle class with pending requests
     for (size_t ci = 0; ci < classes.size(); ++ci) {
       Class* c = classes[ci].get();
       if (!c || c->busy) continue;
+      if (linger.count() > 0) {
+        // hold the tick while some of the class's environments have no
+        // request yet and the oldest pending one is younger than the window
+        int nenv = 0, nready = 0;
+        Clock::time_point oldest = Clock::time_point::max();
+        for (int sl = 0; sl < c->slots; ++sl) {
+          const int eid = c->slot_env[sl];
+          if (eid < 0) continue;
+          ++nenv;
+          const Env& e = envs[eid];
+          if (e.queue.empty()) continue;
+          ++nready;
+          oldest = std::min(oldest, reqs[e.queue.front()].submit);
+        }
+        if (nready == 0) continue;
+        if (nready < nenv && Clock::now() < oldest + linger) {
+          wake = std::min(wake, oldest + linger);
+          continue;
+        }
+      }
       int nact = 0;
       const size_t plane = (size_t)c->nz * c->nx;
       for (int sl = 0; sl < c->slots; ++sl) {
@@ -312,7 +337,9 @@ void ch_server::run() {
       cv_done.notify_all();
     }
     if (!launched && !any_busy) {
-      cv_work.wait_for(lk, std::chrono::milliseconds(50));
+      // new requests wake the worker; so does the end of a batching window
+      if (wake != Clock::time_point::max()) cv_work.wait_until(lk, wake);
+      else cv_work.wait_for(lk, std::chrono::milliseconds(50));
     } else if (!launched && any_busy) {
       // ticks in flight: poll their events again shortly
       lk.unlock();
@@ -347,6 +374,14 @@ int srv_create(size_t hbm_budget_bytes, int slots_per_class, ch_server_t** out) 
   }
   s->worker = std::thread([s] { s->run(); });
   *out = s;
+  return CH_OK;
+}
+
+int srv_set_linger(ch_server_t* s, int linger_us) {
+  if (!s || linger_us < 0 || linger_us > 1000000) return CH_ERR_ARG;
+  std::unique_lock<std::mutex> lk(s->mu);
+  s->linger = std::chrono::microseconds(linger_us);
+  s->cv_work.notify_all();
   return CH_OK;
 }
 
@@ -446,6 +481,44 @@ int srv_submit(ch_server_t* s, int env_id, const double* action, uint64_t* req_i
   return CH_OK;
 }
 
+int srv_submit_many(ch_server_t* s, int n, const int* env_ids, const double* actions, uint64_t* req_ids) {
+  if (!s || n < 0 || (n > 0 && (!env_ids || !req_ids))) return CH_ERR_ARG;
+  std::unique_lock<std::mutex> lk(s->mu);
+  // check every request first: a refused batch queues nothing
+  size_t off = 0;
+  for (int i = 0; i < n; ++i) {
+    auto it = s->envs.find(env_ids[i]);
+    if (it == s->envs.end()) return CH_ERR_ARG;
+    const Class* c = s->classes[it->second.cls].get();
+    if (c->key.control != 0) continue;
+    if (!actions) return CH_ERR_ARG;
+    const size_t m = (size_t)c->nz * c->nx;
+    for (size_t k = 0; k < m; ++k)
+      if (!std::isfinite(actions[off + k])) return CH_ERR_ARG;  // poisoned action
+    off += m;
+  }
+  off = 0;
+  const auto now = Clock::now();
+  for (int i = 0; i < n; ++i) {
+    Env& e = s->envs[env_ids[i]];
+    const Class* c = s->classes[e.cls].get();
+    Request r;
+    r.id = s->next_req++;
+    r.env_id = env_ids[i];
+    r.submit = now;
+    if (c->key.control == 0) {
+      const size_t m = (size_t)c->nz * c->nx;
+      r.action.assign(actions + off, actions + off + m);
+      off += m;
+    }
+    e.queue.push_back(r.id);
+    req_ids[i] = r.id;
+    s->reqs.emplace(r.id, std::move(r));
+  }
+  if (n > 0) s->cv_work.notify_one();
+  return CH_OK;
+}
+
 static int take_result(ch_server* s, std::map<uint64_t, Request>::iterator it, double* obs, double* wall_shear,
                        double* reward, double* latency_us) {
   Request& r = it->second;
@@ -481,6 +554,35 @@ int srv_wait(ch_server_t* s, uint64_t req_id, int timeout_ms, double* obs, doubl
   it = s->reqs.find(req_id);
   if (it == s->reqs.end()) return CH_ERR_ARG;
   return take_result(s, it, obs, wall_shear, reward, latency_us);
+}
+
+int srv_wait_many(ch_server_t* s, int n, const uint64_t* req_ids, int timeout_ms, double* obs, double* wall_shear,
+                  double* reward, int* status) {
+  if (!s || n < 0 || timeout_ms < 0 || (n > 0 && (!req_ids || !status))) return CH_ERR_ARG;
+  std::unique_lock<std::mutex> lk(s->mu);
+  for (int i = 0; i < n; ++i)
+    if (s->reqs.find(req_ids[i]) == s->reqs.end()) return CH_ERR_ARG;
+  const bool ok = s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] {
+    for (int i = 0; i < n; ++i) {
+      auto jt = s->reqs.find(req_ids[i]);
+      if (jt != s->reqs.end() && jt->second.state != 2) return false;
+    }
+    return true;
+  });
+  if (!ok) return CH_ERR_TIMEOUT;
+  size_t off = 0;
+  for (int i = 0; i < n; ++i) {
+    auto it = s->reqs.find(req_ids[i]);
+    if (it == s->reqs.end()) {  // taken meanwhile by another caller
+      status[i] = CH_ERR_ARG;
+      continue;
+    }
+    const size_t m = it->second.obs.size();
+    status[i] = take_result(s, it, obs ? obs + off : nullptr, wall_shear ? wall_shear + i : nullptr,
+                            reward ? reward + i : nullptr, nullptr);
+    off += m;
+  }
+  return CH_OK;
 }
 
 int srv_stats(ch_server_t* s, ch_srv_stats_t* st, int reset) {

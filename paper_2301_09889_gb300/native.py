@@ -34,6 +34,7 @@ EXPORTS = (
     "env_profile", "env_profile_read", "ch_tau_helmholtz_noalloc", "env_set_tiles",
     "srv_create", "srv_admit", "srv_evict", "srv_submit", "srv_poll", "srv_wait", "srv_get_state",
     "srv_set_state", "srv_stats", "srv_destroy", "env_set_policy", "env_get_action", "env_observe",
+    "srv_set_linger", "srv_submit_many", "srv_wait_many",
 )
 CH_PENDING = 1
 
@@ -132,6 +133,10 @@ def load() -> ctypes.CDLL:
         "env_profile": (ctypes.c_int, [vp, ctypes.c_int]),
         "env_set_tiles": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
         "srv_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, P(vp)]),
+        "srv_set_linger": (ctypes.c_int, [vp, ctypes.c_int]),
+        "srv_submit_many": (ctypes.c_int, [vp, ctypes.c_int, P(ctypes.c_int), dp, P(ctypes.c_uint64)]),
+        "srv_wait_many": (ctypes.c_int, [vp, ctypes.c_int, P(ctypes.c_uint64), ctypes.c_int, dp, dp, dp,
+                                         P(ctypes.c_int)]),
         "srv_admit": (ctypes.c_int, [vp, P(ChParams), ctypes.c_uint64, ctypes.c_double, ctypes.c_int,
                                      P(ctypes.c_int)]),
         "srv_evict": (ctypes.c_int, [vp, ctypes.c_int]),
@@ -371,6 +376,10 @@ def srv_create(hbm_budget_bytes: int, slots_per_class: int) -> ctypes.c_void_p:
     return h
 
 
+def srv_set_linger(srv, linger_us: int):
+    _check(load().srv_set_linger(srv, linger_us), "srv_set_linger")
+
+
 def srv_admit(srv, p: ChParams, seed: int, amplitude: float = 0.1, kmax: int = 4) -> int:
     eid = ctypes.c_int()
     _check(load().srv_admit(srv, ctypes.byref(p), seed, amplitude, kmax, ctypes.byref(eid)), "srv_admit")
@@ -405,6 +414,28 @@ def srv_wait(srv, req_id: int, timeout_ms: int, obs: np.ndarray):
     rc = load().srv_wait(srv, req_id, timeout_ms, _dptr(obs), ctypes.byref(tau), ctypes.byref(rew),
                          ctypes.byref(lat))
     return rc, tau.value, rew.value, lat.value
+
+
+def srv_submit_many(srv, env_ids, actions: np.ndarray | None) -> np.ndarray:
+    """Queue one request per environment of env_ids (actions [n][nz][nx] in
+    the same order, or None); returns the request ids."""
+    ids = np.ascontiguousarray(env_ids, dtype=np.int32)
+    out = np.zeros(len(ids), dtype=np.uint64)
+    act = None if actions is None else np.ascontiguousarray(actions, dtype=np.float64)
+    _check(load().srv_submit_many(srv, len(ids), ids.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                  None if act is None else _dptr(act), out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))),
+           "srv_submit_many")
+    return out
+
+
+def srv_wait_many(srv, req_ids: np.ndarray, timeout_ms: int, obs: np.ndarray):
+    """(rc, wall_shear [n], reward [n], status [n]); obs [n][2][nz][nx] is filled."""
+    ids = np.ascontiguousarray(req_ids, dtype=np.uint64)
+    n = len(ids)
+    tau, rew, st = np.zeros(n), np.zeros(n), np.zeros(n, dtype=np.int32)
+    rc = load().srv_wait_many(srv, n, ids.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), timeout_ms, _dptr(obs), _dptr(tau),
+                              _dptr(rew), st.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    return rc, tau, rew, st
 
 
 def srv_get_state(srv, env_id: int, nbytes: int) -> np.ndarray:

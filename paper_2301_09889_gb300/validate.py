@@ -11,8 +11,9 @@ constant flow rate.  Reported, over the window after the transient:
 * the laminar upper bound 1 - tau_lam / <tau_w>_uncontrolled (Sec. 3.2 quotes
   73.9 % at its Reynolds number; tau_lam = 3 / Re_b in both geometries);
 * on the sensing plane, the rms of u' and v' in wall units of the uncontrolled
-  flow and the fractions of the four quadrants of (u', v') (Q2 ejections,
-  Q4 sweeps; Sec. 4.2-4.3 discuss how control changes them).
+  flow, the fractions of the four quadrants of (u', v') (Q2 ejections,
+  Q4 sweeps), and the probability densities of u' and v' with their skewness
+  and flatness (Sec. 4.2-4.3 discuss how control changes them).
 
 The paper reports DR of 26 % (minimal channel) and 20 % (larger channel) for
 opposition control at y+ = 15, after an initial transient of t+ = 500, in
@@ -40,14 +41,28 @@ GRIDS = {
 
 
 class PlaneStats:
-    """Running sums of the wall shear and of the sensing-plane fluctuations."""
+    """Running sums of the wall shear and of the sensing-plane fluctuations.
 
-    def __init__(self, batch: int):
+    The densities of u' and v' are histograms on fixed bins in units of
+    `scale` (the nominal friction velocity): u' over +-U_RANGE scale and v'
+    over +-V_RANGE scale, BINS bins each; the summary converts them to wall
+    units of the measured friction velocity.  Samples outside the range are
+    counted in `outside`."""
+
+    BINS, U_RANGE, V_RANGE = 120, 12.0, 6.0
+
+    def __init__(self, batch: int, scale: float = 1.0):
         self.n = 0
         self.tau = np.zeros(batch)
         self.uu = self.vv = self.uv = 0.0
+        self.u3 = self.u4 = self.v3 = self.v4 = 0.0
         self.quad = np.zeros(4)
         self.points = 0
+        self.scale = scale
+        self.u_edges = np.linspace(-self.U_RANGE, self.U_RANGE, self.BINS + 1) * scale
+        self.v_edges = np.linspace(-self.V_RANGE, self.V_RANGE, self.BINS + 1) * scale
+        self.hu = np.zeros(self.BINS)
+        self.hv = np.zeros(self.BINS)
 
     def add(self, tau: np.ndarray, obs: np.ndarray, keep: np.ndarray):
         self.n += 1
@@ -60,15 +75,38 @@ class PlaneStats:
         self.uv += float((up * vp).sum())
         self.quad += [np.count_nonzero((up > 0) & (vp > 0)), np.count_nonzero((up < 0) & (vp > 0)),
                       np.count_nonzero((up < 0) & (vp < 0)), np.count_nonzero((up > 0) & (vp < 0))]
+        self.u3 += float((up ** 3).sum())
+        self.u4 += float((up ** 4).sum())
+        self.v3 += float((vp ** 3).sum())
+        self.v4 += float((vp ** 4).sum())
+        self.hu += np.histogram(up, self.u_edges)[0]
+        self.hv += np.histogram(vp, self.v_edges)[0]
         self.points += up.size
 
     def summary(self, u_tau0: float) -> dict:
         m = max(self.points, 1)
+
+        def pdf(h, edges):
+            # density per unit of the fluctuation in wall units of u_tau0
+            plus = edges / u_tau0
+            width = np.diff(plus)
+            return {"bin_centers_plus": (0.5 * (plus[1:] + plus[:-1])).round(4).tolist(),
+                    "density": (h / m / width).round(6).tolist(),
+                    "outside": float(1.0 - h.sum() / m)}
+
+        def shape(m2, m3, m4):
+            var = m2 / m
+            return (m3 / m / var ** 1.5 if var > 0 else 0.0, m4 / m / var ** 2 if var > 0 else 0.0)
+
+        su, fu = shape(self.uu, self.u3, self.u4)
+        sv, fv = shape(self.vv, self.v3, self.v4)
         return {
             "u_rms_plus": math.sqrt(self.uu / m) / u_tau0,
             "v_rms_plus": math.sqrt(self.vv / m) / u_tau0,
             "uv_plus": self.uv / m / u_tau0 ** 2,
             "quadrants_Q1_Q2_Q3_Q4": (self.quad / m).round(4).tolist(),
+            "u_skewness": su, "u_flatness": fu, "v_skewness": sv, "v_flatness": fv,
+            "pdf_u": pdf(self.hu, self.u_edges), "pdf_v": pdf(self.hv, self.v_edges),
         }
 
 
@@ -124,7 +162,7 @@ def run(grid: str = "minimal", batch: int = 16, precision: int = 0, seed: int = 
         n_trans, n_avg = round(t_trans / t_call), max(1, round(t_avg / t_call))
         stats = {}
         for name, env, act in (("uncontrolled", unc, zero), ("opposition", ctl, None)):
-            st = PlaneStats(batch)
+            st = PlaneStats(batch, re_tau / re_bulk)  # nominal u_tau in both geometries
             for i in range(n_trans + n_avg):
                 _step(env, act, obs, tau, rew)
                 if i >= n_trans and keep.any():

@@ -170,3 +170,97 @@ def test_faults_are_reported_not_hung(native_gpu):
             native.srv_submit(srv, eid, _actions(7, 1)[0])   # evicted id
     finally:
         native.srv_destroy(srv)
+
+
+def test_batching_window_fills_ticks_and_keeps_results(native_gpu):
+    """With a batching window the server holds a class's tick until all of its
+    environments have a request (or the window ends): the first request of
+    the first of four staggered actors waits for the last one, and every
+    result is the same as without a window.  Out-of-range windows are
+    refused."""
+    import time
+    native = native_gpu
+    acts = [_actions(20 + k, 4) for k in range(4)]
+
+    def run(linger_us):
+        srv = native.srv_create(8 * GB, 4)
+        try:
+            for bad in (-1, 2_000_000):
+                with pytest.raises(native.ChannelError):
+                    native.srv_set_linger(srv, bad)
+            native.srv_set_linger(srv, linger_us)
+            eids = [native.srv_admit(srv, native.params(**MINIMAL), seed=90 + k, amplitude=0.2, kmax=99)
+                    for k in range(4)]
+            outs, lats = [None] * 4, [None] * 4
+
+            def actor(k):
+                time.sleep(0.05 * k)
+                res, lat = [], []
+                for a in acts[k]:
+                    rid = native.srv_submit(srv, eids[k], a)
+                    obs = np.zeros((2, 16, 16))
+                    rc, tau, rew, us = native.srv_wait(srv, rid, 60000, obs)
+                    assert rc == native.CH_OK, rc
+                    res.append((obs, tau, rew))
+                    lat.append(us)
+                outs[k], lats[k] = res, lat
+
+            threads = [threading.Thread(target=actor, args=(k,)) for k in range(4)]
+            for t in threads:
+                t.start()
+            for t in threads:
+                t.join()
+            return outs, lats, native.srv_stats(srv)
+        finally:
+            native.srv_destroy(srv)
+
+    plain, lat0, _ = run(0)
+    held, lat1, st = run(500_000)
+    assert st.completed == 16 and st.worker_status == native.CH_OK
+    for a, b in zip(plain, held):
+        for (oa, ta, ra), (ob, tb, rb) in zip(a, b):
+            assert np.array_equal(oa, ob) and ta == tb and ra == rb
+    # the last actor starts 150 ms after the first: held, the first request
+    # waits for it; without a window it runs at once
+    assert lat1[0][0] > 100_000, lat1[0][0]
+    assert lat0[0][0] < 100_000, lat0[0][0]
+
+
+def test_submit_many_and_wait_many(native_gpu):
+    """Requests queued and collected in batches give the same results as one
+    at a time; a batch with an unknown environment or a poisoned action is
+    refused whole, queueing nothing."""
+    native = native_gpu
+    acts = [_actions(40 + k, 3) for k in range(3)]
+
+    def one_at_a_time():
+        srv = native.srv_create(8 * GB, 4)
+        try:
+            eids = [native.srv_admit(srv, native.params(**MINIMAL), seed=95 + k, amplitude=0.2, kmax=99)
+                    for k in range(3)]
+            return [_drive(native, srv, eids[k], acts[k]) for k in range(3)]
+        finally:
+            native.srv_destroy(srv)
+
+    ref = one_at_a_time()
+    srv = native.srv_create(8 * GB, 4)
+    try:
+        eids = [native.srv_admit(srv, native.params(**MINIMAL), seed=95 + k, amplitude=0.2, kmax=99)
+                for k in range(3)]
+        bad = np.stack([acts[k][0] for k in range(3)])
+        bad[1, 2, 3] = np.nan
+        with pytest.raises(native.ChannelError):
+            native.srv_submit_many(srv, eids, bad)
+        with pytest.raises(native.ChannelError):
+            native.srv_submit_many(srv, [eids[0], 9999], np.stack([acts[0][0], acts[1][0]]))
+        assert native.srv_stats(srv).pending == 0
+        obs = np.zeros((3, 2, 16, 16))
+        for t in range(3):
+            rids = native.srv_submit_many(srv, eids, np.stack([acts[k][t] for k in range(3)]))
+            rc, tau, rew, st = native.srv_wait_many(srv, rids, 60000, obs)
+            assert rc == native.CH_OK and (st == native.CH_OK).all()
+            for k in range(3):
+                o, ta, ra = ref[k][t]
+                assert np.array_equal(obs[k], o) and tau[k] == ta and rew[k] == ra
+    finally:
+        native.srv_destroy(srv)

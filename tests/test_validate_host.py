@@ -109,3 +109,37 @@ def test_open_channel_run_uses_the_papers_box_and_transient(monkeypatch):
     assert out["lx_lz"] == [pytest.approx(5.34), pytest.approx(1.6)]
     assert out["t_transient"] == pytest.approx(500 * (2 / 2800) / (180 / 2800) ** 2)
     assert out["geometry"] == "open channel, free-slip top"
+
+
+def test_fluctuation_densities_skewness_and_flatness():
+    """The densities integrate to one over wall units and put their mass
+    where the samples are; skewness and flatness follow from the moments."""
+    scale, u_tau0 = 0.05, 0.064
+    st = validate.PlaneStats(1, scale)
+    obs = np.zeros((1, 2, 4, 4))
+    rng = np.random.default_rng(3)
+    for _ in range(200):
+        obs[0, 0] = 2.0 + scale * rng.standard_normal((4, 4))
+        obs[0, 1] = np.where(rng.random((4, 4)) < 0.25, 3.0, -1.0) * scale   # skewed two-point law
+        st.add(np.array([1.0]), obs, np.array([True]))
+    s = st.summary(u_tau0)
+    for key in ("pdf_u", "pdf_v"):
+        c, d = np.array(s[key]["bin_centers_plus"]), np.array(s[key]["density"])
+        assert s[key]["outside"] == pytest.approx(0.0, abs=1e-3)
+        assert float((d * np.gradient(c)).sum()) == pytest.approx(1.0, rel=2e-3)
+    # the centred Gaussian u' (about each plane's mean): symmetric, flatness near 3
+    assert abs(s["u_skewness"]) < 0.2 and s["u_flatness"] == pytest.approx(3.0, abs=0.4)
+    # v' about each plane's mean of a +3 / -1 law with weights 1/4, 3/4: skewed
+    # positive, so the density has more mass above zero at large |v'|
+    assert s["v_skewness"] > 0.5
+    cv, dv = np.array(s["pdf_v"]["bin_centers_plus"]), np.array(s["pdf_v"]["density"])
+    assert dv[cv > 1.5 * scale / u_tau0].sum() > dv[cv < -1.5 * scale / u_tau0].sum()
+    # exact moments of a two-point law: +-1 in equal numbers has skewness 0, flatness 1
+    st2 = validate.PlaneStats(1, 1.0)
+    obs2 = np.zeros((1, 2, 2, 2))
+    obs2[0, 0] = [[1.0, -1.0], [-1.0, 1.0]]
+    obs2[0, 1] = [[2.0, -2.0], [2.0, -2.0]]
+    st2.add(np.array([1.0]), obs2, np.array([True]))
+    s2 = st2.summary(1.0)
+    assert s2["u_skewness"] == pytest.approx(0.0) and s2["u_flatness"] == pytest.approx(1.0)
+    assert s2["v_flatness"] == pytest.approx(1.0)
