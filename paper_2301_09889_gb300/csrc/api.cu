@@ -783,10 +783,11 @@ int capture_step(ch_env* env, int gi, const int* d_active) {
 }
 
 // ---------------------------------------------------------------------------
-// Tile shapes of the stage kernels.  Every candidate performs the same
-// floating-point operations per output (each mode's recurrences and sums run
-// in one fixed order whatever the number of modes per CTA or the thread
-// mapping), so the shapes change speed only, never results.
+// Tile shapes of the stage kernels.  Within a form of the implicit half every
+// candidate performs the same floating-point operations per output (each
+// mode's recurrences and sums run in one fixed order whatever the number of
+// modes per CTA), so the widths change speed only, never results.  The
+// autotuner keeps the form the size rule chose.
 // ---------------------------------------------------------------------------
 bool tiles_valid(const ch_env* env, int smem_max, int ppc_pre, int ppc_post, int post_batched) {
   const Grid& g = env->g;
@@ -885,9 +886,13 @@ int autotune_tiles(ch_env* env, int smem_max) {
     }
   }
   have = false;
+  // widths of the form the size rule chose: the per-tile and batched forms of
+  // the no-slip solves sum in different orders (four-lane scans against one
+  // thread per system), so timing never switches between them
+  const int form = env->post_batched ? 1 : 0;
   const std::pair<int, int> cands[] = {{0, 8}, {0, 7}, {0, 6}, {0, 5}, {0, 4}, {0, 3}, {0, 2}, {1, 16}, {1, 8}};
   for (const auto& c : cands) {
-    if (!tiles_valid(env, smem_max, env->ppc_pre, c.second, c.first)) continue;
+    if (c.first != form || !tiles_valid(env, smem_max, env->ppc_pre, c.second, c.first)) continue;
     float ms = 0.f;
     RC(time_launches(st, kReps, [&] { return post(c.second, c.first == 1); }, &ms));
     if (!have || ms < best) {

@@ -30,6 +30,7 @@
 #include "common.cuh"
 #include "internal.h"
 #include "stage_launch.h"
+#include "stage_scan.cuh"
 
 namespace chdns {
 
@@ -1265,8 +1266,13 @@ __global__ void __launch_bounds__(128) stage_pre_kernel(Grid g, int B, PencilBuf
 // 1-c, e = 1 v on parity c.  The mean mode solves U at constant flow rate
 // (e = 0) and W (e = 1) on parity c, real component only.
 // ---------------------------------------------------------------------------
+// Lanes per system of the per-tile form: four under the no-slip top (the
+// scan solves of stage_scan.cuh), one under the free-slip top.
+template <int TOP>
+constexpr int post_tile_lanes() { return TOP == 0 ? 4 : 1; }
+
 template <typename RN, int MH, int TOP>
-__global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBufs pb, DevTables t,
+__global__ void __launch_bounds__(64 * post_tile_lanes<TOP>()) stage_post_kernel(Grid g, int B, PencilBufs pb, DevTables t,
                                                         const typename cpx<RN>::T* __restrict__ hn, StageCoef sc,
                                                         int ppc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1339,12 +1345,13 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
     }
   }
   if (!analysed) {
-    // Thread (mode pl, group g of 8) computes the coefficients n = g, g+8, ...
+    // Thread (mode pl, group g of GA) computes the coefficients n = g, g+GA, ...
     // of the three fields of its mode: every pair f_j, f_{N-j} it loads feeds
     // all of its outputs, and the outputs are independent accumulation chains.
     // n and g share their parity, so the folding sign is fixed per thread.
-    constexpr int KN = (2 * MH + 7) / 8;  // n values per thread
-    const int pl = tid % ppc, gq = tid / ppc;  // blockDim = 8 ppc
+    constexpr int GA = 8 * post_tile_lanes<TOP>();
+    constexpr int KN = (2 * MH + GA - 1) / GA;  // n values per thread
+    const int pl = tid % ppc, gq = tid / ppc;  // blockDim = GA ppc
     const RN* cheb = cheb_table<RN>(t);
     const RN sg = (gq & 1) ? (RN)-1.0 : (RN)1.0;
     CN a[3][KN];
@@ -1362,7 +1369,7 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
       for (int f = 0; f < 3; ++f) fold[f] = colf[f][j * ppc] + sg * colf[f][(N - j) * ppc];
 #pragma unroll
       for (int k = 0; k < KN; ++k) {
-        const int n = gq + 8 * k;
+        const int n = gq + GA * k;
         const RN c = cheb[(size_t)min(n, N) * ny + j];
 #pragma unroll
         for (int f = 0; f < 3; ++f) a[f][k] = a[f][k] + c * fold[f];
@@ -1372,7 +1379,7 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
     const RN s0 = (RN)2.0 / (RN)N;
 #pragma unroll
     for (int k = 0; k < KN; ++k) {
-      const int n = gq + 8 * k;
+      const int n = gq + GA * k;
       const RN cbn = (n == 0 || n == N) ? (RN)2.0 : (RN)1.0;
       const RN cH = ((N & 1) == 0) ? cheb[(size_t)min(n, N) * ny + N / 2] : (RN)0.0;
 #pragma unroll
@@ -1385,7 +1392,7 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < KN; ++k) {
-      const int n = gq + 8 * k;
+      const int n = gq + GA * k;
       if (n <= N) {
 #pragma unroll
         for (int f = 0; f < 3; ++f) sN[((size_t)f * ny + n) * ppc + pl] = acc[f][k];
@@ -1395,13 +1402,16 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
   }
 
   if constexpr (TOP == 0) {
-    // ---- implicit solves
-    const int pl = tid % ppc;
-    const int combo = tid / ppc;
+    // ---- implicit solves, system (mode pl, class c, component r, equation
+    // e) on the four lanes q of a group
+    const int q = tid & 3, sys = tid >> 2;
+    const int pl = sys % ppc;
+    const int combo = sys / ppc;
     const int p = p0 + pl;
-    if (p < P && combo < 8) {
-      const int c = combo & 1, r = (combo >> 1) & 1, e = combo >> 2;
-      const int row = p / g.nxh, ix = p % g.nxh;
+    const int c = combo & 1, r = (combo >> 1) & 1, e = combo >> 2;
+    const int row = p / g.nxh, ix = p % g.nxh;
+    // a whole group is live or idle together
+    if (p < P && row != g.nz / 2 && (p != 0 || r == 0)) {
       const double cc = sc.alpha / sc.beta;
       const double* rowc = t.tau.rowc;
       const CN* Hx = reinterpret_cast<const CN*>(sH) + pl;
@@ -1409,15 +1419,10 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
       const CN* Hz = Hy + ny * ppc;
       auto helm = [&](int sig) { return TabSm{sh + sig * 4 * Mh * ppc + pl, Mh, ppc}; };
       auto comp = [](auto z, int qd) { return qd == 0 ? z.x : z.y; };
-      if (row == g.nz / 2) {
-        // Nyquist row stays zero
-      } else if (p == 0) {
-        if (r == 0) {
-          RegArr<MH> f;
-          mean_solve<MH, RN>(f, N, ny, ppc, c, e, (e == 0 ? pb.UM : pb.WM) + (size_t)b * ny,
-                             (e == 0 ? pb.HXP : pb.HZP) + (size_t)b * ny, (e == 0) ? Hx : Hz, cc, sc, helm(c),
-                             ss[(0 * 2 + c) * ppc + pl], rowc, t.tau.u1 + (size_t)sc.k * Mh, t.tau.u1_iflux[sc.k]);
-        }
+      if (p == 0) {
+        mean_scan<MH, RN>(N, ny, ppc, c, e, (e == 0 ? pb.UM : pb.WM) + (size_t)b * ny,
+                          (e == 0 ? pb.HXP : pb.HZP) + (size_t)b * ny, (e == 0) ? Hx : Hz, cc, sc, helm(c),
+                          ss[(0 * 2 + c) * ppc + pl], rowc, t.tau.u1 + (size_t)sc.k * Mh, t.tau.u1_iflux[sc.k], q);
       } else {
         const double kx = t.kx[ix], kz = t.kz[row], k2 = kx * kx + kz * kz;
         const double sgn = (r == 0) ? -1.0 : 1.0;
@@ -1426,9 +1431,8 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
           const int sq = 1 - c;
           const CompS Gc{reinterpret_cast<double*>(sG) + 2 * pl + r, 2 * ppc};
           const CompT<RN> HGc{reinterpret_cast<RN*>(sHG) + 2 * pl + r, 2 * ppc};
-          RegArr<MH> f;
-          omega_solve<MH, RN>(f, N, ny, ppc, sq, Gc, HGc, HGc, Hx, Hz, r, sgn, kx, kz, cc, sc, helm(sq),
-                              ss[(0 * 2 + sq) * ppc + pl], rowc);
+          omega_scan<MH, RN>(N, ny, ppc, sq, Gc, HGc, Hx, Hz, r, sgn, kx, kz, cc, sc, helm(sq),
+                             ss[(0 * 2 + sq) * ppc + pl], rowc, q);
         } else {
           // wall-normal velocity, parity c
           const int sv = c;
@@ -1438,11 +1442,9 @@ __global__ void __launch_bounds__(64) stage_post_kernel(Grid g, int B, PencilBuf
           const double vw =
               fma_rn(sc.theta, comp(pb.vw_new[vo], r) - comp(pb.vw_old[vo], r), comp(pb.vw_old[vo], r));
           const TabSm TP{sp + sv * 4 * Mh * ppc + pl, Mh, ppc};
-          const double* vh = svh + sv * Mh * ppc + pl;
-          RegArr<MH> f;
-          v_solve<MH, RN>(f, N, ny, ppc, sv, Vc, HVc, HVc, Hx, Hy, Hz, r, sgn, kx, kz, k2, cc, sc, helm(sv),
-                          ss[(0 * 2 + sv) * ppc + pl], TP, ss[(1 * 2 + sv) * ppc + pl],
-                          [&](int i) { return vh[i * ppc]; }, ss[(2 * 2 + sv) * ppc + pl], vw, rowc);
+          v_scan<MH, RN>(N, ny, ppc, sv, Vc, HVc, Hx, Hy, Hz, r, sgn, kx, kz, k2, cc, sc, helm(sv),
+                         ss[(0 * 2 + sv) * ppc + pl], TP, ss[(1 * 2 + sv) * ppc + pl], svh + sv * Mh * ppc + pl,
+                         ppc, ss[(2 * 2 + sv) * ppc + pl], vw, rowc, q);
         }
       }
     }
@@ -1939,7 +1941,7 @@ cudaError_t post_mh(const Grid& g, int B, const PencilBufs& pb, const DevTables&
   const cudaError_t e = raise_smem_limit(stage_post_kernel<RN, MH, TOP>, &lim, smem);
   if (e != cudaSuccess) return e;
   return launch_pdl_if<sizeof(RN) == 4>(stage_post_kernel<RN, MH, TOP>, dim3((g.P + ppc - 1) / ppc, B),
-                                        dim3(8 * ppc), smem, st, g, B, pb, t, h, sc, ppc);
+                                        dim3(8 * post_tile_lanes<TOP>() * ppc), smem, st, g, B, pb, t, h, sc, ppc);
 }
 
 template <typename RN, int MH, int TOP>
