@@ -86,6 +86,13 @@ WORKLOADS = {
                             re_bulk=10030.0, dt=0.002), 1, 1,
                        "large channel Re_tau=550, 256x193x256, mixed precision, seeded ZNMF Gaussian actions "
                        "std 0.05 u_tau"),
+    "large395_fp64": (dict(MINIMAL, nx=128, ny=129, nz=128, lx=2 * math.pi, lz=math.pi, re_tau=395.0,
+                           re_bulk=6875.0, dt=0.0025), 1, 0,
+                      "channel Re_tau=395, 128x129x128, all FP64, seeded ZNMF Gaussian actions std 0.05 u_tau"),
+    "large395_mixed": (dict(MINIMAL, nx=128, ny=129, nz=128, lx=2 * math.pi, lz=math.pi, re_tau=395.0,
+                            re_bulk=6875.0, dt=0.0025), 1, 1,
+                       "channel Re_tau=395, 128x129x128, mixed precision, seeded ZNMF Gaussian actions "
+                       "std 0.05 u_tau"),
     "large550_fp64": (dict(MINIMAL, nx=256, ny=193, nz=256, lx=2 * math.pi, lz=math.pi, re_tau=550.0,
                            re_bulk=10030.0, dt=0.002), 1, 0,
                       "large channel Re_tau=550, 256x193x256, all FP64, seeded ZNMF Gaussian actions "
@@ -202,7 +209,6 @@ def measured_peaks() -> dict:
 # the roofline kernel, from one ncu capture of the same workload (summaries
 # under profiles/); absent where no capture of the current kernel exists
 TRAFFIC_BYTES = {
-    ("larger_fp64", "nonlinear_plane"): 12.639232e6,
     ("minimal_batch256_mixed", "stage_post"): (151.877632 + 43.473408) * 1e6,
     # the three passes of one FP64 256x256-mode stage (z inverse + x pass + z forward)
     ("large550_fp64", "nonlinear_plane"): (604.911872 + 852.392448 + 910.863872 + 413.775360 + 455.520000

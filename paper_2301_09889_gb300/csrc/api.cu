@@ -310,11 +310,14 @@ int setup_plane(ch_env* env, PlaneArgs<R>* a, size_t* smem) {
     if ((size_t)6 * (g.mz / S) * g.nxh * csz > 160 * 1024) continue;
     feasible[nf++] = S;
   }
-  // planes of 256 x 256 modes, whose padded z-slab fits no portable cluster
-  // in either precision: three passes through a global scratch array, whose
-  // traffic costs less than the serialisation of a 16-CTA cluster over the
-  // few such clusters the device holds at once
-  if (!nf && two_pass_shape_ok(g.mx, g.mz, g.nxh)) {
+  // three passes through a global scratch array: planes of 256 x 256 modes,
+  // whose padded z-slab fits no portable cluster in either precision (the
+  // traffic costs less than serialising 16-CTA clusters, of which the device
+  // holds few), and the FP64 planes of 64 x 64 and 128 x 128 modes; only in
+  // the precision the handle steps in (the other plane keeps a cluster, for
+  // ch_nonlinear, where one fits)
+  const bool stepping = (sizeof(R) == 8) == (env->prm.precision == 0);
+  if (stepping && two_pass_chosen(g.mx, g.mz, g.nxh, sizeof(R) == 8)) {
     a->two_pass = 1;
     a->S = 1;
     a->Lz = g.mz;
@@ -890,7 +893,7 @@ int autotune_tiles(ch_env* env, int smem_max) {
   // the no-slip solves sum in different orders (four-lane scans against one
   // thread per system), so timing never switches between them
   const int form = env->post_batched ? 1 : 0;
-  const std::pair<int, int> cands[] = {{0, 8}, {0, 7}, {0, 6}, {0, 5}, {0, 4}, {0, 3}, {0, 2}, {1, 16}, {1, 8}};
+  const std::pair<int, int> cands[] = {{0, 8}, {0, 7}, {0, 6}, {0, 5}, {0, 4}, {0, 3}, {0, 2}, {0, 1}, {1, 16}, {1, 8}};
   for (const auto& c : cands) {
     if (c.first != form || !tiles_valid(env, smem_max, env->ppc_pre, c.second, c.first)) continue;
     float ms = 0.f;
@@ -972,7 +975,7 @@ size_t env_footprint(const ch_params_t* p) {
   // planes of 256 x 256 modes: the scratch of the three-pass nonlinear term
   // (complex values of the plane's precision)
   const size_t mx = 3 * (size_t)p->nx / 2, mz = 3 * (size_t)p->nz / 2;
-  const size_t two_pass = two_pass_shape_ok((int)mx, (int)mz, (int)nxh)
+  const size_t two_pass = two_pass_chosen((int)mx, (int)mz, (int)nxh, p->precision == 0)
                               ? B * ny * 6 * mz * nxh * (p->precision == 0 ? 16 : 8) : 0;
   return state + tables + two_pass + ((size_t)4 << 20);  // plus twiddles and rounding slack
 }
@@ -1061,7 +1064,13 @@ int env_create(const ch_params_t* p, ch_env_t** out) {
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
       return fail(CH_ERR_CUDA);
+    // per-tile width: 8 modes per CTA, fewer while that leaves fewer CTAs
+    // than SMs (a single small channel) or exceeds the shared memory
+    int nsm = 152;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     env->ppc_post = 8;
+    while (env->ppc_post > 1 && ((size_t)B * P + env->ppc_post - 1) / env->ppc_post < (size_t)nsm)
+      env->ppc_post /= 2;
     while (env->ppc_post > 1 && stage_post_smem(g, env->tab.tau.Mh, env->ppc_post, p->top_bc) > (size_t)smem_max)
       env->ppc_post /= 2;
     env->ppc_pre = 8;

@@ -17,6 +17,7 @@ template <typename R>
 cudaError_t launch_plane16(const PlaneArgs<R>& a, int B, cudaStream_t st);
 // nonlinear term in three passes through global memory (plane2.cu), FP64
 bool two_pass_shape_ok(int mx, int mz, int nxh);
+bool two_pass_chosen(int mx, int mz, int nxh, bool fp64);
 template <typename R>
 cudaError_t launch_plane_two_pass(const PlaneArgs<R>& a, int B, cudaStream_t st);
 

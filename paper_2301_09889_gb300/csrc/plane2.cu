@@ -172,12 +172,26 @@ static cudaError_t launch_two_pass_ct(const PlaneArgs<R>& a, int B, cudaStream_t
   return launch_pdl_if<pdl>(kc, dim3(NXH / kTwoPassCW, 3 * a.ny, B), dim3(kTwoPassNT), sz, st, a);
 }
 
-// the grids built in two passes: 256 x 256 modes (mx = mz = 384)
-bool two_pass_shape_ok(int mx, int mz, int nxh) { return mx == 384 && mz == 384 && nxh == 128; }
+// The grids built in passes: 256 x 256 modes (mx = mz = 384) in both
+// precisions, whose planes fit no portable cluster; in FP64 also 64 x 64 and
+// 128 x 128 modes, where a cluster per plane leaves the last wave of SMs
+// part-empty and the passes keep every SM on FP64 work.
+bool two_pass_shape_ok(int mx, int mz, int nxh) {
+  return (mx == 384 && mz == 384 && nxh == 128) || (mx == 96 && mz == 96 && nxh == 32) ||
+         (mx == 192 && mz == 192 && nxh == 64);
+}
+bool two_pass_chosen(int mx, int mz, int nxh, bool fp64) {
+  if (mx == 384 && mz == 384 && nxh == 128) return true;
+  return fp64 && two_pass_shape_ok(mx, mz, nxh);
+}
 
 template <typename R>
 cudaError_t launch_plane_two_pass(const PlaneArgs<R>& a, int B, cudaStream_t st) {
   if (a.mx == 384 && a.mz == 384 && a.nxh == 128) return launch_two_pass_ct<R, 384, 384, 128>(a, B, st);
+  if constexpr (sizeof(R) == 8) {
+    if (a.mx == 96 && a.mz == 96 && a.nxh == 32) return launch_two_pass_ct<R, 96, 96, 32>(a, B, st);
+    if (a.mx == 192 && a.mz == 192 && a.nxh == 64) return launch_two_pass_ct<R, 192, 192, 64>(a, B, st);
+  }
   return cudaErrorInvalidValue;
 }
 

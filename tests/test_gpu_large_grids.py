@@ -130,7 +130,8 @@ def _compare(native, grid, precision):
 @pytest.mark.parametrize("precision", [0, 1])
 def test_re395_grid_one_step_against_oracle(native_gpu, oracle_pool, precision):
     info = _compare(native_gpu, RE395, precision)
-    assert info.plane_cluster >= 1
+    # FP64 planes of 128 x 128 modes run in three passes; FP32 ones in a cluster
+    assert (info.plane_cluster == 0) if precision == 0 else (info.plane_cluster >= 1)
 
 
 @pytest.mark.parametrize("precision", [0, 1])
