@@ -209,7 +209,9 @@ def measured_peaks() -> dict:
 # the roofline kernel, from one ncu capture of the same workload (summaries
 # under profiles/); absent where no capture of the current kernel exists
 TRAFFIC_BYTES = {
-    ("minimal_batch256_mixed", "stage_post"): (151.877632 + 43.473408) * 1e6,
+    ("minimal_batch256_mixed", "stage_post"): (152.553984 + 47.812608) * 1e6,
+    # the three passes of one FP64 64x64-mode stage (the scratch stays in L2)
+    ("larger_fp64", "nonlinear_plane"): (12.597248 + 19.201792 + 9.604352) * 1e6,
     # the three passes of one FP64 256x256-mode stage (z inverse + x pass + z forward)
     ("large550_fp64", "nonlinear_plane"): (604.911872 + 852.392448 + 910.863872 + 413.775360 + 455.520000
                                            + 259.116544) * 1e6,
@@ -679,7 +681,7 @@ def served_run(native, workload: str, rate: float, duration: float, warm: float 
     few, so that the host side does not limit the measured server.
     Latencies are the server's own submit-to-completion clock.  linger_us is
     the server's batching window (srv_set_linger; default CH_SERVE_LINGER_US,
-    else 0)."""
+    else 300: the actors of a tick answer within a fraction of a step)."""
     import random
     import threading
 
@@ -687,7 +689,7 @@ def served_run(native, workload: str, rate: float, duration: float, warm: float 
     budget = int(float(os.environ.get("CH_SERVE_BUDGET_GB", "64")) * (1 << 30))
     srv = native.srv_create(budget, slots)
     if linger_us is None:
-        linger_us = int(os.environ.get("CH_SERVE_LINGER_US", "0"))
+        linger_us = int(os.environ.get("CH_SERVE_LINGER_US", "300"))
     envs = []
     try:
         native.srv_set_linger(srv, linger_us)

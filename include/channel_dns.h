@@ -276,10 +276,11 @@ size_t ch_state_bytes(const ch_params_t* p);
  * `slots_per_class` slots and its own CUDA stream, prioritised by the cost
  * of one env-step of the class (cheaper classes first, so that small
  * environments keep their latency next to large ones).  A worker thread runs
- * ticks: for each idle class it takes the oldest pending request of every
- * environment and advances exactly those slots in one masked batched step;
- * ticks of different classes overlap on the device and requests arriving
- * during a tick join the next one.  A slot's result does not depend on the
+ * ticks: for each class with a free tick it takes the oldest pending request
+ * of every environment not already in a running tick and advances exactly
+ * those slots in one masked batched step; a class keeps up to two ticks in
+ * flight, ticks of different classes overlap on the device, and requests
+ * arriving during a tick join a later one.  A slot's result does not depend on the
  * other slots, so an environment steps identically alone and in any mix.
  * All srv_* functions are thread-safe. */
 typedef struct ch_server ch_server_t;

@@ -972,7 +972,7 @@ size_t env_footprint(const ch_params_t* p) {
                             (size_t)p->nz * p->nx * 8 + (2 * (size_t)p->nz * p->nx + 2) * 8);
   const size_t tables = (3 * 2 * 4 * Mh * P + 3 * 2 * P + 2 * 4 * Mh * P + 2 * P + 3 * 2 * Mh * P + 3 * 2 * P +
                          3 * Mh + 3 + 3 * ny + ny + 2 * 3 * 2 * 2 * P) * 8 + ny * ny * 12 + (nxh + p->nz) * 8;
-  // planes of 256 x 256 modes: the scratch of the three-pass nonlinear term
+  // the scratch of the three-pass nonlinear term, where it runs in passes
   // (complex values of the plane's precision)
   const size_t mx = 3 * (size_t)p->nx / 2, mz = 3 * (size_t)p->nz / 2;
   const size_t two_pass = two_pass_chosen((int)mx, (int)mz, (int)nxh, p->precision == 0)

@@ -3,10 +3,12 @@
 // Environments are grouped into classes by their parameters (grid, box,
 // Reynolds numbers, time step, control).  Each class owns one batched handle
 // with a fixed number of slots and its own CUDA stream.  A worker thread runs
-// ticks: for every idle class it gathers the oldest pending request of each
-// environment, launches one masked batched step for exactly those slots, and
-// moves on to the next class, so ticks of different classes overlap on the
-// device.  Requests that arrive while a tick runs join the next one.  A new
+// ticks: for every class with a free tick it gathers the oldest pending
+// request of each environment not already in a running tick, launches one
+// masked batched step for exactly those slots, and moves on to the next
+// class, so ticks of different classes overlap on the device.  A class keeps
+// up to two ticks in flight, the second queued behind the first on its
+// stream, so the GPU does not wait for the host between them.  A new
 // environment is admitted into a free slot of its class; a new class is
 // created only if its device footprint fits the HBM budget.
 //
@@ -55,6 +57,18 @@ struct Request {
   double tau = 0.0, reward = 0.0;
 };
 
+// Host side of one tick.  Its copies read the actions and the mask and write
+// the outputs when they execute, so a class alternates two sets: the next
+// tick is gathered and enqueued while the previous one still runs.
+struct Tick {
+  double* h_act = nullptr;        // pinned [slots][nz][nx]
+  double* h_out = nullptr;        // pinned [slots][out_stride]
+  int* h_active = nullptr;        // pinned [slots]
+  cudaEvent_t ev = nullptr;
+  bool busy = false;
+  std::vector<uint64_t> running;  // request per slot in this tick (0 none)
+};
+
 struct Class {
   ch_params_t key;  // parameters with batch = 0
   ch_env_t* env = nullptr;
@@ -63,15 +77,13 @@ struct Class {
   size_t out_stride = 0;
   size_t footprint = 0;
   std::vector<int> slot_env;  // env id per slot, -1 free
-  double* h_act = nullptr;    // pinned [slots][nz][nx]
-  double* h_out = nullptr;    // pinned [slots][out_stride]
-  int* h_active = nullptr;    // pinned [slots]
-  int* d_active = nullptr;
-  cudaEvent_t ev = nullptr;
+  int* d_active = nullptr;    // device mask, rewritten by each tick in stream order
   cudaStream_t stream = nullptr;  // prioritised stream the class's ticks run on
-  bool busy = false;
+  Tick tick[2];
+  int next_tick = 0;            // the set the class's next tick uses
+  std::vector<char> in_flight;  // slot has a request in a tick not yet completed
   bool stuck = false;   // its stream did not drain after a failed enqueue: no further ticks
-  std::vector<uint64_t> running;  // request per slot in the current tick (0 none)
+  bool busy() const { return tick[0].busy || tick[1].busy; }
 };
 
 struct Env {
@@ -176,22 +188,29 @@ int ch_server::make_class(const ch_params_t& key, int* cls) {
   c->out_stride = chdns::env_out_stride(c->env);
   c->footprint = fp;
   c->slot_env.assign(c->slots, -1);
-  c->running.assign(c->slots, 0);
+  c->in_flight.assign(c->slots, 0);
   const size_t S = c->slots;
-  if (cudaMallocHost(&c->h_act, S * p.nz * p.nx * sizeof(double)) != cudaSuccess ||
-      cudaMallocHost(&c->h_out, S * c->out_stride * sizeof(double)) != cudaSuccess ||
-      cudaMallocHost(&c->h_active, S * sizeof(int)) != cudaSuccess ||
-      cudaMalloc(&c->d_active, S * sizeof(int)) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming) != cudaSuccess) {
-    if (c->h_act) cudaFreeHost(c->h_act);
-    if (c->h_out) cudaFreeHost(c->h_out);
-    if (c->h_active) cudaFreeHost(c->h_active);
+  bool ok = cudaMalloc(&c->d_active, S * sizeof(int)) == cudaSuccess;
+  for (Tick& t : c->tick) {
+    t.running.assign(c->slots, 0);
+    ok = ok && cudaMallocHost(&t.h_act, S * p.nz * p.nx * sizeof(double)) == cudaSuccess &&
+         cudaMallocHost(&t.h_out, S * c->out_stride * sizeof(double)) == cudaSuccess &&
+         cudaMallocHost(&t.h_active, S * sizeof(int)) == cudaSuccess &&
+         cudaEventCreateWithFlags(&t.ev, cudaEventDisableTiming) == cudaSuccess;
+    if (ok) std::memset(t.h_act, 0, S * p.nz * p.nx * sizeof(double));
+  }
+  if (!ok) {
+    for (Tick& t : c->tick) {
+      if (t.h_act) cudaFreeHost(t.h_act);
+      if (t.h_out) cudaFreeHost(t.h_out);
+      if (t.h_active) cudaFreeHost(t.h_active);
+      if (t.ev) cudaEventDestroy(t.ev);
+    }
     if (c->d_active) cudaFree(c->d_active);
     env_destroy(c->env);
     cudaStreamDestroy(c->stream);
     return CH_ERR_OOM;
   }
-  std::memset(c->h_act, 0, S * p.nz * p.nx * sizeof(double));
   used += fp;
   for (size_t i = 0; i < classes.size(); ++i)
     if (!classes[i]) {
@@ -209,11 +228,13 @@ void ch_server::free_class(int ci) {
   if (!c) return;
   env_destroy(c->env);  // synchronises the class stream first
   cudaStreamDestroy(c->stream);
-  cudaFreeHost(c->h_act);
-  cudaFreeHost(c->h_out);
-  cudaFreeHost(c->h_active);
+  for (Tick& t : c->tick) {
+    cudaFreeHost(t.h_act);
+    cudaFreeHost(t.h_out);
+    cudaFreeHost(t.h_active);
+    cudaEventDestroy(t.ev);
+  }
   cudaFree(c->d_active);
-  cudaEventDestroy(c->ev);
   used -= c->footprint;
   classes[ci].reset();
 }
@@ -224,63 +245,67 @@ void ch_server::run() {
   while (!stop) {
     bool launched = false, any_busy = false;
     Clock::time_point wake = Clock::time_point::max();  // earliest end of a batching window
-    // launch a tick on every idle class with pending requests
+    // launch a tick on every class with a free tick set and pending requests
+    // of environments not already in a running tick
     for (size_t ci = 0; ci < classes.size(); ++ci) {
       Class* c = classes[ci].get();
-      if (!c || c->busy) continue;
-      if (linger.count() > 0) {
-        // hold the tick while some of the class's environments have no
-        // request yet and the oldest pending one is younger than the window
-        int nenv = 0, nready = 0;
-        Clock::time_point oldest = Clock::time_point::max();
-        for (int sl = 0; sl < c->slots; ++sl) {
-          const int eid = c->slot_env[sl];
-          if (eid < 0) continue;
-          ++nenv;
-          const Env& e = envs[eid];
-          if (e.queue.empty()) continue;
-          ++nready;
-          oldest = std::min(oldest, reqs[e.queue.front()].submit);
-        }
-        if (nready == 0) continue;
-        if (nready < nenv && Clock::now() < oldest + linger) {
-          wake = std::min(wake, oldest + linger);
-          continue;
-        }
+      if (!c || c->stuck) continue;
+      Tick& T = c->tick[c->next_tick];
+      if (T.busy) continue;
+      int nenv = 0, nready = 0;
+      Clock::time_point oldest = Clock::time_point::max();
+      for (int sl = 0; sl < c->slots; ++sl) {
+        const int eid = c->slot_env[sl];
+        if (eid < 0 || c->in_flight[sl]) continue;
+        ++nenv;
+        const Env& e = envs[eid];
+        if (e.queue.empty()) continue;
+        ++nready;
+        oldest = std::min(oldest, reqs[e.queue.front()].submit);
       }
-      int nact = 0;
+      if (nready == 0) continue;
+      // bounded batching window: hold the tick while some eligible
+      // environments have no request yet and the oldest pending one is
+      // younger than the window
+      if (linger.count() > 0 && nready < nenv && Clock::now() < oldest + linger) {
+        wake = std::min(wake, oldest + linger);
+        continue;
+      }
       const size_t plane = (size_t)c->nz * c->nx;
       for (int sl = 0; sl < c->slots; ++sl) {
-        c->h_active[sl] = 0;
-        c->running[sl] = 0;
+        T.h_active[sl] = 0;
+        T.running[sl] = 0;
         const int eid = c->slot_env[sl];
-        if (eid < 0) continue;
+        if (eid < 0 || c->in_flight[sl]) continue;
         Env& e = envs[eid];
         if (e.queue.empty()) continue;
         Request& r = reqs[e.queue.front()];
         e.queue.pop_front();
         r.state = 1;
-        c->running[sl] = r.id;
-        c->h_active[sl] = 1;
-        if (!r.action.empty()) std::memcpy(c->h_act + sl * plane, r.action.data(), plane * sizeof(double));
-        ++nact;
+        T.running[sl] = r.id;
+        T.h_active[sl] = 1;
+        c->in_flight[sl] = 1;
+        if (!r.action.empty()) std::memcpy(T.h_act + sl * plane, r.action.data(), plane * sizeof(double));
       }
-      if (!nact) continue;
-      c->busy = true;
+      T.busy = true;
+      c->next_tick ^= 1;
       launched = true;
       lk.unlock();
+      // the copies and the step run in stream order after any earlier tick
+      // of the class, so the device mask, action and output buffers are
+      // rewritten only once that tick is done with them
       cudaStream_t st = chdns::env_stream(c->env);
       int rc = CH_OK;
-      if (cudaMemcpyAsync(c->d_active, c->h_active, c->slots * sizeof(int), cudaMemcpyHostToDevice, st) !=
+      if (cudaMemcpyAsync(c->d_active, T.h_active, c->slots * sizeof(int), cudaMemcpyHostToDevice, st) !=
               cudaSuccess ||
-          cudaMemcpyAsync(chdns::env_dact(c->env), c->h_act, c->slots * plane * sizeof(double),
+          cudaMemcpyAsync(chdns::env_dact(c->env), T.h_act, c->slots * plane * sizeof(double),
                           cudaMemcpyHostToDevice, st) != cudaSuccess)
         rc = CH_ERR_CUDA;
-      if (rc == CH_OK) rc = chdns::step_masked(c->env, chdns::env_dact(c->env), c->d_active, c->h_active);
-      if (rc == CH_OK && cudaMemcpyAsync(c->h_out, chdns::env_dout(c->env), c->slots * c->out_stride * sizeof(double),
+      if (rc == CH_OK) rc = chdns::step_masked(c->env, chdns::env_dact(c->env), c->d_active, T.h_active);
+      if (rc == CH_OK && cudaMemcpyAsync(T.h_out, chdns::env_dout(c->env), c->slots * c->out_stride * sizeof(double),
                                          cudaMemcpyDeviceToHost, st) != cudaSuccess)
         rc = CH_ERR_CUDA;
-      if (rc == CH_OK && cudaEventRecord(c->ev, st) != cudaSuccess) rc = CH_ERR_CUDA;
+      if (rc == CH_OK && cudaEventRecord(T.ev, st) != cudaSuccess) rc = CH_ERR_CUDA;
       bool drained = true;
       if (rc != CH_OK) {
         // copies and kernels queued before the failure may still read the
@@ -296,45 +321,51 @@ void ch_server::run() {
       if (rc != CH_OK) {
         worker_error = drained ? rc : CH_ERR_TIMEOUT;
         for (int sl = 0; sl < c->slots; ++sl)
-          if (c->running[sl]) {
-            Request& r = reqs[c->running[sl]];
+          if (T.running[sl]) {
+            Request& r = reqs[T.running[sl]];
             r.state = 2;
             r.status = rc;
             r.done_at = Clock::now();
-            c->running[sl] = 0;
+            T.running[sl] = 0;
+            c->in_flight[sl] = 0;
           }
-        c->busy = !drained;
+        T.busy = !drained;
         c->stuck = !drained;
         cv_done.notify_all();
       }
     }
-    // complete finished ticks
+    // complete finished ticks, oldest first (a class's ticks finish in order)
     for (size_t ci = 0; ci < classes.size(); ++ci) {
       Class* c = classes[ci].get();
-      if (!c || !c->busy || c->stuck) continue;
-      const cudaError_t q = cudaEventQuery(c->ev);
-      if (q == cudaErrorNotReady) {
-        any_busy = true;
-        continue;
+      if (!c || c->stuck) continue;
+      for (int k = 0; k < 2; ++k) {
+        Tick& T = c->tick[c->next_tick ^ (k == 0 ? 0 : 1)];
+        if (!T.busy) continue;
+        const cudaError_t q = cudaEventQuery(T.ev);
+        if (q == cudaErrorNotReady) {
+          any_busy = true;
+          continue;
+        }
+        const auto now = Clock::now();
+        const size_t plane = (size_t)c->nz * c->nx;
+        for (int sl = 0; sl < c->slots; ++sl) {
+          if (!T.running[sl]) continue;
+          Request& r = reqs[T.running[sl]];
+          const double* o = T.h_out + sl * c->out_stride;
+          r.obs.assign(o, o + 2 * plane);
+          r.tau = o[2 * plane];
+          r.reward = o[2 * plane + 1];
+          r.status = (q != cudaSuccess) ? CH_ERR_CUDA : (std::isfinite(r.tau) ? CH_OK : CH_ERR_DIVERGED);
+          r.state = 2;
+          r.done_at = now;
+          record_latency(std::chrono::duration<double, std::micro>(now - r.submit).count());
+          ++completed;
+          T.running[sl] = 0;
+          c->in_flight[sl] = 0;
+        }
+        T.busy = false;
+        cv_done.notify_all();
       }
-      const auto now = Clock::now();
-      const size_t plane = (size_t)c->nz * c->nx;
-      for (int sl = 0; sl < c->slots; ++sl) {
-        if (!c->running[sl]) continue;
-        Request& r = reqs[c->running[sl]];
-        const double* o = c->h_out + sl * c->out_stride;
-        r.obs.assign(o, o + 2 * plane);
-        r.tau = o[2 * plane];
-        r.reward = o[2 * plane + 1];
-        r.status = (q != cudaSuccess) ? CH_ERR_CUDA : (std::isfinite(r.tau) ? CH_OK : CH_ERR_DIVERGED);
-        r.state = 2;
-        r.done_at = now;
-        record_latency(std::chrono::duration<double, std::micro>(now - r.submit).count());
-        ++completed;
-        c->running[sl] = 0;
-      }
-      c->busy = false;
-      cv_done.notify_all();
     }
     if (!launched && !any_busy) {
       // new requests wake the worker; so does the end of a batching window
@@ -354,7 +385,7 @@ namespace {
 // wait (bounded) until class `ci` has no tick in flight
 bool wait_idle(ch_server* s, std::unique_lock<std::mutex>& lk, int ci) {
   return s->cv_done.wait_for(lk, std::chrono::seconds(30), [&] {
-    return !s->classes[ci] || !s->classes[ci]->busy;
+    return !s->classes[ci] || !s->classes[ci]->busy();
   });
 }
 
@@ -627,7 +658,7 @@ int srv_destroy(ch_server_t* s) {
   s->worker.join();
   for (size_t i = 0; i < s->classes.size(); ++i) {
     if (s->classes[i]) {
-      cudaEventSynchronize(s->classes[i]->ev);
+      for (Tick& t : s->classes[i]->tick) cudaEventSynchronize(t.ev);
       s->free_class((int)i);
     }
   }
