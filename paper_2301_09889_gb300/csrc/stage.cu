@@ -21,14 +21,15 @@ size_t stage_pre_smem(const Grid& g, int ppc, size_t node_bytes) {
 }
 // (both with six complex values per mode for the FP64 fast analysis; the
 // coefficient tile is smaller in FP32 node precision, the FP64 size bounds both;
-// a free-slip top adds the exchange slots of the parity closures: six values
-// per thread, two rounds in the batched form)
+// a free-slip top adds the exchange slots of the parity closures to the
+// per-tile form: six values per thread; the batched form exchanges them by
+// shuffles)
 // Above 65 nodes (no-slip top) the batched form runs in two launches and its
 // solve keeps one array of MH doubles per thread in shared memory.
 size_t stage_post_batched_smem(const Grid& g, int ppc, int top, size_t node_bytes) {
   const int mh = mh_bucket(g.N / 2 + 1);
   if (!top && mh > 33) return (size_t)4 * ppc * mh * sizeof(double);
-  return stage_post_batched_tile_bytes(g.ny, ppc, node_bytes) + (top ? (size_t)2 * 4 * ppc * 6 * sizeof(double) : 0);
+  return stage_post_batched_tile_bytes(g.ny, ppc, node_bytes);
 }
 int stage_post_launches(const Grid& g, int top, bool batched) {
   return (batched && !top && mh_bucket(g.N / 2 + 1) > 33) ? 2 : 1;

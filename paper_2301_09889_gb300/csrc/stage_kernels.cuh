@@ -1593,11 +1593,11 @@ __global__ void __launch_bounds__(64 * post_tile_lanes<TOP>()) stage_post_kernel
 // analysis runs field by field with four threads per mode (n = q + 4k); each
 // coefficient is accumulated in the same order as in the per-tile form.
 // ---------------------------------------------------------------------------
-// Five CTAs per SM for the no-slip solve with up to 65 nodes: the register
-// budget (168) holds its one array of coefficients, and the shared tile
-// (41.6 KB at 65 nodes in FP32) allows five.
+// Five CTAs per SM with up to 65 nodes: the register budget (168) holds the
+// solves' one array of coefficients, and the shared tile (41.6 KB at 65
+// nodes in FP32, 44.6 KB with the free-slip exchange slots) allows five.
 template <int MH, int TOP>
-constexpr int post_batched_min_ctas() { return (TOP == 0 && MH <= 33) ? 5 : 1; }
+constexpr int post_batched_min_ctas() { return MH <= 33 ? 5 : 1; }
 
 template <typename RN, int MH, int TOP>
 __global__ void __launch_bounds__(64, post_batched_min_ctas<MH, TOP>()) stage_post_batched_kernel(Grid g, int B, PencilBufs pb, DevTables t,
@@ -1634,7 +1634,13 @@ __global__ void __launch_bounds__(64, post_batched_min_ctas<MH, TOP>()) stage_po
     sN[w] = hn[((size_t)b * 3 * ny + fn) * P + p];
   }
   __syncthreads();
-  const int r = tid & 1, pl = (tid >> 1) % ppc, c = tid / (2 * ppc);
+  // thread (mode pl, class c, component r).  Under the no-slip top each warp
+  // holds one class (16 or more modes per CTA); under the free-slip top the
+  // two classes of a (mode, component) are neighbouring lanes, whose parity
+  // closures exchange their sums by shuffles.
+  const int r = TOP ? (tid >> 1) & 1 : tid & 1;
+  const int pl = TOP ? tid >> 2 : (tid >> 1) % ppc;
+  const int c = TOP ? tid & 1 : tid / (2 * ppc);
 
   // ---- Chebyshev analysis of H_z, H_y, H_x, coefficients in the node
   // precision over the nodal values of the same field (a barrier between
@@ -1699,13 +1705,11 @@ __global__ void __launch_bounds__(64, post_batched_min_ctas<MH, TOP>()) stage_po
     // the mean flow, then v), each closed after a barrier by the pair of class
     // threads (c, 1 - c) of a (mode, component); every thread reaches both
     // barriers
-    double* xch = reinterpret_cast<double*>(smem_raw + stage_post_batched_tile_bytes(ny, ppc, sizeof(CN)));  // [2][4 ppc][6]
     const int p = p0 + pl;
     const int pc = min(p, P - 1);
     const int row = pc / g.nxh, ix = pc % g.nxh;
     const bool live = p < P && row != g.nz / 2;
     const bool mean = p == 0;
-    const int mate = (1 - c) * 2 * ppc + tid % (2 * ppc);
     const double cc = sc.alpha / sc.beta;
     const double* rowc = t.tau.rowc;
     const CN* Hx = sN + pl;
@@ -1724,8 +1728,7 @@ __global__ void __launch_bounds__(64, post_batched_min_ctas<MH, TOP>()) stage_po
     {
       const int sig = mean ? c : 1 - c;
       const int M = (N - sig) / 2 + 1;
-      double* mine = xch + tid * 6;
-      const double* other = xch + mate * 6;
+      double mine[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
       if (live) {
         if (mean) {
           mean_open_affine<MH, RN>(f, N, ny, ppc, sig, (r == 0 ? pb.UM : pb.WM) + (size_t)b * ny,
@@ -1739,10 +1742,15 @@ __global__ void __launch_bounds__(64, post_batched_min_ctas<MH, TOP>()) stage_po
                                     helm(sig), rowc, mine);
         }
       }
-      __syncthreads();
+      // the mate (other class, same mode and component) is the neighbouring lane
+      double se[6], so[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        const double other = __shfl_xor_sync(0xffffffffu, mine[k], 1);
+        se[k] = sig == 0 ? mine[k] : other;
+        so[k] = sig == 0 ? other : mine[k];
+      }
       if (live) {
-        const double* se = sig == 0 ? mine : other;
-        const double* so = sig == 0 ? other : mine;
         double xe, xo, fc = 0.0;
         if (mean && r == 0) {
           const double* u1 = t.tau.u1 + (size_t)sc.k * Mh;
@@ -1786,8 +1794,7 @@ __global__ void __launch_bounds__(64, post_batched_min_ctas<MH, TOP>()) stage_po
     {
       const int sig = c;
       const int M = (N - sig) / 2 + 1;
-      double* mine = xch + (4 * ppc + tid) * 6;
-      const double* other = xch + (4 * ppc + mate) * 6;
+      double mine[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
       const bool on = live && !mean;
       const CompS Vc{reinterpret_cast<double*>(pb.V) + base, 2 * P};
       if (on) {
@@ -1801,10 +1808,14 @@ __global__ void __launch_bounds__(64, post_batched_min_ctas<MH, TOP>()) stage_po
         v_open_part<MH, RN>(f, N, ny, ppc, sig, Vc, HVr, HVc, Hx, Hy, Hz, r, sgn, kx, kz, k2, cc, sc, helm(sig),
                             helm_isq(sig), TP, t.tau.pois_isq[(size_t)sig * P + pc], vw, rowc, mine);
       }
-      __syncthreads();
+      double se[6], so[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        const double other = __shfl_xor_sync(0xffffffffu, mine[k], 1);
+        se[k] = sig == 0 ? mine[k] : other;
+        so[k] = sig == 0 ? other : mine[k];
+      }
       if (on) {
-        const double* se = sig == 0 ? mine : other;
-        const double* so = sig == 0 ? other : mine;
         double ce, co;
         close_free_slip_v(se, so, vs(0, 0), vs(1, 0), vs(0, 1), vs(1, 1), cc, &ce, &co);
         const double cI = sig == 0 ? ce : co;
