@@ -99,6 +99,18 @@ __device__ __forceinline__ void pdl_wait_then_release() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// Asynchronous copy of one 4-, 8- or 16-byte element from global to shared
+// memory (cp.async): no register holds the value, so a thread issues all its
+// copies of a tile before any completes.  cp_async_wait_all() waits for the
+// thread's own copies; a barrier after it publishes the tile to the CTA.
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8 || sizeof(T) == 16, "cp.async copies 4, 8 or 16 bytes");
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(src), "n"(sizeof(T)) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // A kernel's dynamic shared-memory limit (and the non-portable cluster-size
 // opt-in) as configured so far.  raise_smem_limit only ever raises it, under
 // one lock for every kernel, so handles of different sizes driven from

@@ -1294,33 +1294,33 @@ __global__ void __launch_bounds__(64 * post_tile_lanes<TOP>()) stage_post_kernel
   if (pb.active && !pb.active[b]) return;
   const int tid = threadIdx.x, nt = blockDim.x;
 
-  // ---- load the tile
+  // ---- load the tile (asynchronous copies, all in flight before the wait)
   for (int w = tid; w < ny * ppc; w += nt) {
     const int pl = w % ppc, n = w / ppc;
     const int p = min(p0 + pl, P - 1);
     const size_t o = ((size_t)b * ny + n) * P + p;
-    sV[w] = pb.V[o];
-    sG[w] = pb.G[o];
-    sHV[w] = reinterpret_cast<const CN*>(pb.HVP)[o];
-    sHG[w] = reinterpret_cast<const CN*>(pb.HGP)[o];
+    cp_async_elem(sV + w, pb.V + o);
+    cp_async_elem(sG + w, pb.G + o);
+    cp_async_elem(sHV + w, reinterpret_cast<const CN*>(pb.HVP) + o);
+    cp_async_elem(sHG + w, reinterpret_cast<const CN*>(pb.HGP) + o);
   }
   for (int w = tid; w < 2 * 4 * Mh * ppc; w += nt) {
     const int pl = w % ppc, qq = w / ppc;  // qq = (sig * 4 + f) * Mh + i
     const int p = min(p0 + pl, P - 1);
-    sh[w] = t.tau.helm[((size_t)sc.k * 2 * 4 * Mh + qq) * P + p];
-    sp[w] = t.tau.pois[(size_t)qq * P + p];
+    cp_async_elem(sh + w, t.tau.helm + ((size_t)sc.k * 2 * 4 * Mh + qq) * P + p);
+    cp_async_elem(sp + w, t.tau.pois + (size_t)qq * P + p);
   }
   for (int w = tid; w < 2 * Mh * ppc; w += nt) {
     const int pl = w % ppc, qq = w / ppc;
     const int p = min(p0 + pl, P - 1);
-    svh[w] = t.tau.vh[((size_t)sc.k * 2 * Mh + qq) * P + p];
+    cp_async_elem(svh + w, t.tau.vh + ((size_t)sc.k * 2 * Mh + qq) * P + p);
   }
   for (int w = tid; w < 2 * ppc; w += nt) {
     const int pl = w % ppc, sig = w / ppc;
     const int p = min(p0 + pl, P - 1);
-    ss[(0 * 2 + sig) * ppc + pl] = t.tau.helm_isq[(size_t)(sc.k * 2 + sig) * P + p];
-    ss[(1 * 2 + sig) * ppc + pl] = t.tau.pois_isq[(size_t)sig * P + p];
-    ss[(2 * 2 + sig) * ppc + pl] = t.tau.vh_idv[(size_t)(sc.k * 2 + sig) * P + p];
+    cp_async_elem(ss + (0 * 2 + sig) * ppc + pl, t.tau.helm_isq + (size_t)(sc.k * 2 + sig) * P + p);
+    cp_async_elem(ss + (1 * 2 + sig) * ppc + pl, t.tau.pois_isq + (size_t)sig * P + p);
+    cp_async_elem(ss + (2 * 2 + sig) * ppc + pl, t.tau.vh_idv + (size_t)(sc.k * 2 + sig) * P + p);
   }
   // everything above is independent of the nonlinear term; H comes from the
   // preceding kernel
@@ -1330,8 +1330,9 @@ __global__ void __launch_bounds__(64 * post_tile_lanes<TOP>()) stage_post_kernel
   for (int w = tid; w < 3 * ny * ppc; w += nt) {
     const int pl = w % ppc, fn = w / ppc;  // fn = f * ny + n
     const int p = min(p0 + pl, P - 1);
-    sN[w] = hn[((size_t)b * 3 * ny + fn) * P + p];
+    cp_async_elem(sN + w, hn + ((size_t)b * 3 * ny + fn) * P + p);
   }
+  cp_async_wait_all();
   __syncthreads();
 
   // ---- Chebyshev analysis of H_x, H_y, H_z (in place after a barrier)
@@ -1614,8 +1615,8 @@ __global__ void __launch_bounds__(64, post_batched_min_ctas<MH, TOP>()) stage_po
   if (pb.active && !pb.active[b]) return;
   const int tid = threadIdx.x, nt = blockDim.x;
   // FP32 nodes: the previous right-hand sides (FP32 pairs) are staged in shared
-  // memory by one coalesced load behind the node tile, issued before the wait
-  // for H; the new ones go straight to global memory
+  // memory behind the node tile, issued before the wait for H; the new ones go
+  // straight to global memory.  Both tiles arrive by asynchronous copies.
   constexpr bool kStageHV = sizeof(RN) == 4 && kPostStageHV, kStageHG = sizeof(RN) == 4 && kPostStageHG;
   CN* sHVt = sN + 3 * ny * ppc;
   CN* sHGt = sHVt + (kStageHV ? ny * ppc : 0);
@@ -1623,16 +1624,17 @@ __global__ void __launch_bounds__(64, post_batched_min_ctas<MH, TOP>()) stage_po
     for (int w = tid; w < ny * ppc; w += nt) {
       const int pl = w % ppc, n = w / ppc;
       const size_t o = ((size_t)b * ny + n) * P + min(p0 + pl, P - 1);
-      if (kStageHV) sHVt[w] = reinterpret_cast<const CN*>(pb.HVP)[o];
-      if (kStageHG) sHGt[w] = reinterpret_cast<const CN*>(pb.HGP)[o];
+      if (kStageHV) cp_async_elem(sHVt + w, reinterpret_cast<const CN*>(pb.HVP) + o);
+      if (kStageHG) cp_async_elem(sHGt + w, reinterpret_cast<const CN*>(pb.HGP) + o);
     }
   }
   pdl_wait_then_release();  // H comes from the preceding kernel
   for (int w = tid; w < 3 * ny * ppc; w += nt) {
     const int pl = w % ppc, fn = w / ppc;  // fn = f * ny + n
     const int p = min(p0 + pl, P - 1);
-    sN[w] = hn[((size_t)b * 3 * ny + fn) * P + p];
+    cp_async_elem(sN + w, hn + ((size_t)b * 3 * ny + fn) * P + p);
   }
+  cp_async_wait_all();
   __syncthreads();
   // thread (mode pl, class c, component r).  Under the no-slip top each warp
   // holds one class (16 or more modes per CTA); under the free-slip top the
