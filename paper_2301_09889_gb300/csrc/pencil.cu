@@ -151,6 +151,7 @@ __global__ void __launch_bounds__(128) sense_kernel(Grid g, int B, PencilBufs pb
       for (int n = lane; n < ny; n += L) su += cj[n] * pb.UM[(size_t)b * ny + n];
     } else {
       const size_t fo = (size_t)b * ny * P + p;
+#pragma unroll 8
       for (int n = lane; n < ny; n += L) {
         const double2 vn = pb.V[fo + (size_t)n * P];
         const double2 gn = pb.G[fo + (size_t)n * P];
@@ -190,56 +191,56 @@ __global__ void __launch_bounds__(128) sense_kernel(Grid g, int B, PencilBufs pb
 // ---------------------------------------------------------------------------
 // observation planes: unpadded inverse transform of the two sensing-plane
 // spectra, f(x_a, z_b) = Re sum_kz F[kz,0] e^{i kz z} + 2 Re sum_{kx>0} F e^{i(kx x + kz z)}.
-// One CTA per (output row z_b, field, environment).
+// One CTA per (block of zblk output rows, field, environment); each row has
+// nt / zblk threads.  The z sums t[z_b][kx] are split over nq parts (rows
+// q, q + nq, ...) and the x sums of every output over nr parts (kx = 1 + q,
+// 1 + q + nr, ...); the parts are added in ascending order.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) obs_kernel(int nx, int nz, int nxh, const double2* planes,
+__global__ void __launch_bounds__(128) obs_kernel(int nx, int nz, int nxh, int zblk, const double2* planes,
                                                   const double2* tw_nx, const double2* tw_nz, double* out,
                                                   size_t out_stride, const int* active) {
-  // one CTA per (physical row z, field, environment); the sums over kz and
-  // over kx are split across all threads and combined in shared memory
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double2* part = reinterpret_cast<double2*>(smem_raw);  // [max(nt, nxh)] partial sums
-  double2* tmp = part + max((int)blockDim.x, nxh);        // [nxh]
-  const int zb = blockIdx.x, f = blockIdx.y, b = blockIdx.z;
-  if (active && !active[b]) return;
   const int tid = threadIdx.x, nt = blockDim.x;
+  const int tpr = nt / zblk;                 // threads per output row
+  const int nq = max(1, tpr / nxh), nr = max(1, tpr / nx);
+  double2* part = reinterpret_cast<double2*>(smem_raw);  // [zblk][nq][nxh] z partial sums
+  double2* tmp = part + (size_t)zblk * nq * nxh;         // [zblk][nxh]
+  double* pr = reinterpret_cast<double*>(tmp + (size_t)zblk * nxh);  // [zblk][nr][nx] x partial sums
+  const int z0 = blockIdx.x * zblk, f = blockIdx.y, b = blockIdx.z;
+  if (active && !active[b]) return;
   const int P = nz * nxh;
   const double2* F = planes + ((size_t)b * 2 + f) * P;
-  // z sums: thread (kx i, part q) takes the rows q, q + nq, ...
-  const int nq = max(1, nt / nxh);
-  for (int w = tid; w < nxh * nq; w += nt) {
-    const int i = w % nxh, q = w / nxh;
+  for (int w = tid; w < zblk * nq * nxh; w += nt) {
+    const int zl = w / (nq * nxh), q = (w / nxh) % nq, i = w % nxh, zb = min(z0 + zl, nz - 1);
     double2 acc = mk(0.0, 0.0);
-    int e = (q * zb) % nz;             // twiddle index of row q (m = row for row < nz/2)
+    int e = (q * zb) % nz;  // (row zb) mod nz; m = row - nz for row > nz/2 gives the same index
     const int step = (nq * zb) % nz;
+#pragma unroll 4
     for (int row = q; row < nz; row += nq) {
-      if (row != nz / 2) {
-        // m = row - nz for row > nz/2 gives the same index modulo nz
-        acc = acc + cmul(F[row * nxh + i], tw_nz[e]);
-      }
+      if (row != nz / 2) acc = acc + cmul(F[row * nxh + i], tw_nz[e]);
       e += step;
       if (e >= nz) e -= nz;
     }
     part[w] = acc;
   }
   __syncthreads();
-  for (int i = tid; i < nxh; i += nt) {
-    double2 acc = part[i];
-    for (int q = 1; q < nq; ++q) acc = acc + part[q * nxh + i];
-    tmp[i] = acc;
+  for (int w = tid; w < zblk * nxh; w += nt) {
+    const int zl = w / nxh, i = w % nxh;
+    const double2* pz = part + (size_t)zl * nq * nxh + i;
+    double2 acc = pz[0];
+    for (int q = 1; q < nq; ++q) acc = acc + pz[q * nxh];
+    tmp[w] = acc;
   }
   __syncthreads();
-  // x sums: thread (x, part q) takes kx = 1 + q, 1 + q + nr, ...
-  double* pr = reinterpret_cast<double*>(part);
-  const int nr = max(1, nt / nx);
-  for (int w = tid; w < nx * nr; w += nt) {
-    const int xa = w % nx, q = w / nx;
+  for (int w = tid; w < zblk * nr * nx; w += nt) {
+    const int zl = w / (nr * nx), q = (w / nx) % nr, xa = w % nx;
+    const double2* t = tmp + (size_t)zl * nxh;
     double s = 0.0;
-    int e = ((1 + q) * xa) % nx;
+    int e = ((1 + q) * xa) % nx;  // (kx xa) mod nx
     const int step = (nr * xa) % nx;
     for (int i = 1 + q; i < nxh; i += nr) {
       const double2 tw = tw_nx[e];
-      const double2 v = tmp[i];
+      const double2 v = t[i];
       s += v.x * tw.x - v.y * tw.y;
       e += step;
       if (e >= nx) e -= nx;
@@ -247,11 +248,13 @@ __global__ void __launch_bounds__(128) obs_kernel(int nx, int nz, int nxh, const
     pr[w] = s;
   }
   __syncthreads();
-  double* o = out + (size_t)b * out_stride + (size_t)f * nz * nx + (size_t)zb * nx;
-  for (int xa = tid; xa < nx; xa += nt) {
+  for (int w = tid; w < zblk * nx; w += nt) {
+    const int zl = w / nx, xa = w % nx, zb = z0 + zl;
+    if (zb >= nz) continue;
+    const double* px = pr + (size_t)zl * nr * nx + xa;
     double s = 0.0;
-    for (int q = 0; q < nr; ++q) s += pr[q * nx + xa];
-    o[xa] = tmp[0].x + 2.0 * s;
+    for (int q = 0; q < nr; ++q) s += px[q * nx];
+    out[(size_t)b * out_stride + (size_t)f * nz * nx + (size_t)zb * nx + xa] = tmp[zl * nxh].x + 2.0 * s;
   }
 }
 
@@ -260,54 +263,59 @@ __global__ void __launch_bounds__(128) obs_kernel(int nx, int nz, int nxh, const
 // forward transform of the kept modes; the mean mode (zero net mass flux,
 // Sec. 4.1) and the Nyquist row are zero.  Removing the plane mean before the
 // transform changes only the mean mode, which is set to zero, so it is not
-// computed.  Two passes through a scratch plane tx[b][z][kx]:
-//   action_x_kernel: one CTA per (wall row z, environment): x transform of the
-//                    clipped row; also starts the new action (the previous
-//                    spectrum becomes the start of the ramp, the wall-shear
-//                    average restarts);
-//   action_z_kernel: one CTA per (output kz row, environment): z transform.
+// computed.  Two passes through a scratch plane tx[b][z][kx], one thread per
+// output coefficient, each sum in ascending order:
+//   action_x_kernel: x transform of the clipped rows; also starts the new
+//                    action (the previous spectrum becomes the start of the
+//                    ramp, the wall-shear average restarts);
+//   action_z_kernel: z transform.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) action_x_kernel(int nx, int nz, int nxh, const double* act, double u_tau,
-                                                       const double2* tw_nx, double2* tx, double2* vw_old,
-                                                       const double2* vw, double* acc, const int* active) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* a = reinterpret_cast<double*>(smem_raw);  // [nx]
-  const int zb = blockIdx.x, b = blockIdx.y;
+__global__ void __launch_bounds__(128) action_x_kernel(int nx, int nz, int nxh, int B, const double* act,
+                                                       double u_tau, const double2* tw_nx, double2* tx,
+                                                       double2* vw_old, const double2* vw, double* acc,
+                                                       const int* active) {
+  const int P = nz * nxh;
+  const long w = blockIdx.x * (long)blockDim.x + threadIdx.x;  // (b, z, kx), kx fastest
+  if (w >= (long)B * P) return;
+  const int b = (int)(w / P), o = (int)(w % P), zb = o / nxh, i = o % nxh;
   if (active && !active[b]) return;
-  const size_t P = (size_t)nz * nxh;
-  if (zb == 0) {
-    for (size_t w = threadIdx.x; w < P; w += blockDim.x) vw_old[b * P + w] = vw[b * P + w];
-    if (threadIdx.x == 0) acc[b] = 0.0;
-  }
+  const size_t bo = (size_t)b * P + o;
+  vw_old[bo] = vw[bo];
+  if (o == 0) acc[b] = 0.0;
   const double* src = act + ((size_t)b * nz + zb) * nx;
-  for (int xa = threadIdx.x; xa < nx; xa += blockDim.x) a[xa] = fmin(fmax(src[xa], -u_tau), u_tau);
-  __syncthreads();
-  for (int i = threadIdx.x; i < nxh; i += blockDim.x) {
-    double2 s = mk(0.0, 0.0);
-    for (int xa = 0; xa < nx; ++xa) s = s + a[xa] * cconj(tw_nx[(i * xa) % nx]);
-    tx[b * P + (size_t)zb * nxh + i] = s;
+  double2 s = mk(0.0, 0.0);
+  int e = 0;  // (i xa) mod nx
+#pragma unroll 8
+  for (int xa = 0; xa < nx; ++xa) {
+    s = s + fmin(fmax(src[xa], -u_tau), u_tau) * cconj(tw_nx[e]);
+    e += i;
+    if (e >= nx) e -= nx;
   }
+  tx[bo] = s;
 }
 
-__global__ void __launch_bounds__(128) action_z_kernel(int nx, int nz, int nxh, const double2* tx,
+__global__ void __launch_bounds__(128) action_z_kernel(int nx, int nz, int nxh, int B, const double2* tx,
                                                        const double2* tw_nz, double2* vw, const int* active) {
-  const int row = blockIdx.x, b = blockIdx.y;
+  const int P = nz * nxh;
+  const long w = blockIdx.x * (long)blockDim.x + threadIdx.x;  // (b, kz row, kx), kx fastest
+  if (w >= (long)B * P) return;
+  const int b = (int)(w / P), o = (int)(w % P), row = o / nxh, i = o % nxh;
   if (active && !active[b]) return;
-  const size_t P = (size_t)nz * nxh;
   const double sc = 1.0 / ((double)nx * nz);
-  const int m = row < nz / 2 ? row : row - nz;
-  for (int i = threadIdx.x; i < nxh; i += blockDim.x) {
-    double2 s = mk(0.0, 0.0);
-    if (row != nz / 2 && !(row == 0 && i == 0)) {
-      for (int zb = 0; zb < nz; ++zb) {
-        int e = (m * zb) % nz;
-        if (e < 0) e += nz;
-        s = s + cmul(tx[b * P + (size_t)zb * nxh + i], cconj(tw_nz[e]));
-      }
-      s = sc * s;
+  double2 s = mk(0.0, 0.0);
+  if (row != nz / 2 && !(row == 0 && i == 0)) {
+    const int m = row < nz / 2 ? row : row - nz;
+    const int step = m < 0 ? m + nz : m;  // (m zb) mod nz advances by m mod nz
+    int e = 0;
+#pragma unroll 8
+    for (int zb = 0; zb < nz; ++zb) {
+      s = s + cmul(tx[(size_t)b * P + (size_t)zb * nxh + i], cconj(tw_nz[e]));
+      e += step;
+      if (e >= nz) e -= nz;
     }
-    vw[b * P + (size_t)row * nxh + i] = s;
+    s = sc * s;
   }
+  vw[(size_t)b * P + o] = s;
 }
 
 __global__ void finalize_kernel(int B, const double* acc, double inv_steps, double tau_ref, double* out,
@@ -354,9 +362,15 @@ cudaError_t launch_sense(const Grid& g, int B, const PencilBufs& pb, const DevTa
 
 cudaError_t launch_obs(const Grid& g, int B, const double2* planes, const DevTables& t, double* out,
                        size_t out_stride, const int* active, cudaStream_t st) {
-  const size_t smem = (size_t)(std::max(128, g.nxh) + g.nxh) * sizeof(double2);
-  obs_kernel<<<dim3(g.nz, 2, B), 128, smem, st>>>(g.nx, g.nz, g.nxh, planes, t.tw_nx, t.tw_nz, out, out_stride,
-                                                   active);
+  // several output rows per CTA once the batch alone gives 128 or more
+  // (environment, field) CTAs; otherwise one row per CTA, its sums split over
+  // the CTA's threads
+  const int zblk = B >= 64 ? std::max(1, std::min(g.nz, 128 / g.nxh)) : 1;
+  const int tpr = 128 / zblk;
+  const int nq = std::max(1, tpr / g.nxh), nr = std::max(1, tpr / g.nx);
+  const size_t smem = (size_t)zblk * ((nq + 1) * g.nxh * sizeof(double2) + (size_t)nr * g.nx * sizeof(double));
+  obs_kernel<<<dim3((g.nz + zblk - 1) / zblk, 2, B), 128, smem, st>>>(g.nx, g.nz, g.nxh, zblk, planes, t.tw_nx,
+                                                                       t.tw_nz, out, out_stride, active);
   return cudaGetLastError();
 }
 
@@ -364,11 +378,13 @@ cudaError_t launch_action(const Grid& g, int B, const double* act, double u_tau,
                           const PencilBufs& pb, cudaStream_t st) {
   // the sensing-plane buffer is free at this point of the step: it is the scratch plane
   double2* tx = pb.planes;
-  action_x_kernel<<<dim3(g.nz, B), 128, (size_t)g.nx * sizeof(double), st>>>(
-      g.nx, g.nz, g.nxh, act, u_tau, t.tw_nx, tx, pb.vw_old, pb.vw_new, pb.tau_acc, pb.active);
+  const long n = (long)B * g.nz * g.nxh;
+  const unsigned blocks = (unsigned)((n + 127) / 128);
+  action_x_kernel<<<blocks, 128, 0, st>>>(g.nx, g.nz, g.nxh, B, act, u_tau, t.tw_nx, tx, pb.vw_old, pb.vw_new,
+                                          pb.tau_acc, pb.active);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  action_z_kernel<<<dim3(g.nz, B), 128, 0, st>>>(g.nx, g.nz, g.nxh, tx, t.tw_nz, pb.vw_new, pb.active);
+  action_z_kernel<<<blocks, 128, 0, st>>>(g.nx, g.nz, g.nxh, B, tx, t.tw_nz, pb.vw_new, pb.active);
   return cudaGetLastError();
 }
 
