@@ -57,6 +57,19 @@ struct TabSm {
   __device__ double Q(int i) const { return base[(3 * Mh + i) * ppc]; }
 };
 
+// folded tau tables of one (mode, parity) of a no-slip solve: element (f, i)
+// at base[(f * Mh + i) * ppc], f = eA, eB, eC, h, b, W
+struct TabF {
+  const double* base;
+  int Mh, ppc;
+  __device__ double eA(int i) const { return base[(0 * Mh + i) * ppc]; }
+  __device__ double eB(int i) const { return base[(1 * Mh + i) * ppc]; }
+  __device__ double eC(int i) const { return base[(2 * Mh + i) * ppc]; }
+  __device__ double h(int i) const { return base[(3 * Mh + i) * ppc]; }
+  __device__ double b(int i) const { return base[(4 * Mh + i) * ppc]; }
+  __device__ double W(int i) const { return base[(5 * Mh + i) * ppc]; }
+};
+
 // ---------------------------------------------------------------------------
 // Chebyshev-tau Dirichlet solve (D^2 - lam) f = r of one parity of one real
 // component.  For n >= 2 the tau rows are equivalent to the quasi-tridiagonal
@@ -332,6 +345,45 @@ __device__ __forceinline__ void tau_fused(int N, int ny, int sig, Rhs&& rhs, Arr
     if (i < M) f[i] = fma_rn(T.Q(i), f0, f[i]);
 }
 
+// tau_fused on the folded tables (no-slip top).  Row j of the elimination
+// is a_j = eA_j r_{j-1} - eB_j r_j + eC_j r_{j+1} - h_j a_{j+1}: the same
+// rows with the factor e taken into the row constants.  The wall row needs
+// sum_i P_i, the sum of the particular solution P_i = a_i + b_i P_{i-1}
+// (P_0 = 0); it equals sum_i W_i a_i and is accumulated during the
+// elimination.  f_0 = (s - sum_i P_i) / sum_i Q_i then follows at once, and the
+// back substitution f_i = a_i + b_i f_{i-1} gives the solution in one pass
+// (f_i = P_i + Q_i f_0, Q_i the products of b).
+template <int MH, class Arr, class Rhs, class Wall>
+__device__ __forceinline__ void tau_fold(int N, int sig, Rhs&& rhs, Arr& f, const TabF& T, double isq,
+                                         Wall&& wall) {
+  const int M = (N - sig) / 2 + 1;
+  double r1 = 0.0, r2 = 0.0, anext = 0.0, sum = 0.0;  // r_{i+1}, r_{i+2}, a_{i+2}
+#pragma unroll
+  for (int i = MH - 1; i >= 0; --i) {
+    double r0 = 0.0;
+    if (i < M) r0 = rhs(i);
+    const int j = i + 1;  // row j needs r_{j-1} = r0, r_j = r1, r_{j+1} = r2
+    if (j < MH && j < M) {
+      double R = fma_rn(-T.eB(j), r1, mul_rn(T.eA(j), r0));
+      if (j + 1 < M) R = fma_rn(T.eC(j), r2, R);
+      const double a = fma_rn(-T.h(j), anext, R);
+      f[j] = a;
+      anext = a;
+      sum = fma_rn(T.W(j), a, sum);
+    }
+    r2 = r1;
+    r1 = r0;
+  }
+  double fp = mul_rn(isq, wall() - sum);
+  f[0] = fp;
+#pragma unroll
+  for (int i = 1; i < MH; ++i)
+    if (i < M) {
+      fp = fma_rn(T.b(i), fp, f[i]);
+      f[i] = fp;
+    }
+}
+
 // omega_y of parity sq: (D^2 - lam) g' = -((1 + cc) g + dt (gamma h_g + zeta
 // h_g'))/(beta dt nu), the factor -1/(beta dt nu) folded into the table's e;
 // wall row sum g' = cc sum g; g <- g' - cc g.  h_g = sgn (-kx H_z + kz H_x) of
@@ -341,8 +393,7 @@ template <int MH, typename RN, class Arr, class GV, class HR, class HW, class Ta
 __device__ __forceinline__ void omega_solve(Arr& f, int N, int ny, int ppc, int sq, const GV& Gc, const HR& HGr,
                                             const HW& HGw, const typename cpx<RN>::T* Hx,
                                             const typename cpx<RN>::T* Hz, int r, double sgn, double kx, double kz,
-                                            double cc, const StageCoef& sc, const Tab& T, double isq,
-                                            const double* __restrict__ rowc) {
+                                            double cc, const StageCoef& sc, const Tab& T, double isq) {
   using CN = typename cpx<RN>::T;
   const int ra = 1 - r;
   auto comp = [](const CN z, int qd) { return qd == 0 ? z.x : z.y; };
@@ -350,8 +401,8 @@ __device__ __forceinline__ void omega_solve(Arr& f, int N, int ny, int ppc, int 
   const RN dtn = (RN)sc.dt, gan = (RN)sc.gamma, zen = (RN)sc.zeta;
   const int M = (N - sq) / 2 + 1;
   double sum = 0.0;
-  tau_fused<MH>(
-      N, ny, sq,
+  tau_fold<MH>(
+      N, sq,
       [&](int i) {
         const int n = 2 * i + sq;
         const double gn = Gc[n];
@@ -362,7 +413,7 @@ __device__ __forceinline__ void omega_solve(Arr& f, int N, int ny, int ppc, int 
         sum += gn;
         return fma_rn(1.0 + cc, gn, (double)q);
       },
-      f, T, isq, [&] { return mul_rn(cc, sum); }, rowc);
+      f, T, isq, [&] { return mul_rn(cc, sum); });
 #pragma unroll
   for (int i = 0; i < MH; ++i)
     if (i < M) {
@@ -383,8 +434,7 @@ __device__ __forceinline__ void v_solve(Arr& f, int N, int ny, int ppc, int sv, 
                                         const typename cpx<RN>::T* Hx, const typename cpx<RN>::T* Hy,
                                         const typename cpx<RN>::T* Hz, int r, double sgn, double kx, double kz,
                                         double k2, double cc, const StageCoef& sc, const Tab& Th, double isq_h,
-                                        const TabP& Tp, double isq_p, const VH& vh, double idv, double vw,
-                                        const double* __restrict__ rowc) {
+                                        const TabP& Tp, double isq_p, const VH& vh, double idv, double vw) {
   using CN = typename cpx<RN>::T;
   const int ra = 1 - r;
   auto comp = [](const CN z, int qd) { return qd == 0 ? z.x : z.y; };
@@ -395,8 +445,8 @@ __device__ __forceinline__ void v_solve(Arr& f, int N, int ny, int ppc, int sv, 
   const int M = (N - sv) / 2 + 1;
   double dv = 0.0, d2v = 0.0, S0 = 0.0, S2 = 0.0;
   RN tt = 0, dtt = 0;
-  tau_fused<MH>(
-      N, ny, sv,
+  tau_fold<MH>(
+      N, sv,
       [&](int i) {
         const int no = 2 * i + sv + 1;
         if (no <= N) {
@@ -421,9 +471,9 @@ __device__ __forceinline__ void v_solve(Arr& f, int N, int ny, int ppc, int sv, 
         const RN q = mul_rn(dtn, fma_rn(gan, hv, mul_rn(zen, hp)));
         return fma_rn(1.0 + cc, phi, (double)q);
       },
-      f, Th, isq_h, [] { return 0.0; }, rowc);
+      f, Th, isq_h, [] { return 0.0; });
   const double s = fma_rn(cc, S0, ((sv == 0) ? 0.5 : -0.5) * vw);
-  tau_fused<MH>(N, ny, sv, [&](int i) { return f[i]; }, f, Tp, isq_p, [&] { return s; }, rowc);
+  tau_fold<MH>(N, sv, [&](int i) { return f[i]; }, f, Tp, isq_p, [&] { return s; });
   double dp = 0.0;
 #pragma unroll
   for (int i = 0; i < MH; ++i)
@@ -626,12 +676,12 @@ __device__ __forceinline__ void v_open_part(Arr& f, int N, int ny, int ppc, int 
 template <int MH, typename RN, class Arr, class Tab>
 __device__ __forceinline__ void mean_solve(Arr& f, int N, int ny, int ppc, int s, int e, double* X, double* XP,
                                            const typename cpx<RN>::T* Hm, double cc, const StageCoef& sc,
-                                           const Tab& T, double isq, const double* __restrict__ rowc,
+                                           const Tab& T, double isq,
                                            const double* __restrict__ u1, double u1_iflux) {
   const int M = (N - s) / 2 + 1;
   double sum = 0.0, flux_old = 0.0;
-  tau_fused<MH>(
-      N, ny, s,
+  tau_fold<MH>(
+      N, s,
       [&](int i) {
         const int n = 2 * i + s;
         const double xn = X[n];
@@ -642,7 +692,7 @@ __device__ __forceinline__ void mean_solve(Arr& f, int N, int ny, int ppc, int s
         if (s == 0) flux_old = fma_rn(2.0 / (1.0 - (double)n * n), xn, flux_old);
         return fma_rn(1.0 + cc, xn, mul_rn(sc.dt, fma_rn(sc.gamma, hv, mul_rn(sc.zeta, hp))));
       },
-      f, T, isq, [&] { return mul_rn(cc, sum); }, rowc);
+      f, T, isq, [&] { return mul_rn(cc, sum); });
   double fc = 0.0;
   if (e == 0 && s == 0) {
     double flux = 0.0;
@@ -679,9 +729,8 @@ __device__ __forceinline__ void post_solve_noslip(double* col, int cs, Cls cls, 
   const int c = class_of(cls);
   const int P = g.P, ny = g.ny, N = g.N, Mh = t.tau.Mh;
   const double cc = sc.alpha / sc.beta;
-  const double* rowc = t.tau.rowc;
   auto comp = [](auto z, int qq) { return qq == 0 ? z.x : z.y; };
-  auto helm = [&](int sig) { return TabSm{t.tau.helm + (size_t)(sc.k * 2 + sig) * 4 * Mh * P + p, Mh, P}; };
+  auto helm = [&](int sig) { return TabF{t.tau.helm_f + (size_t)(sc.k * 2 + sig) * 6 * Mh * P + p, Mh, P}; };
   auto helm_isq = [&](int sig) { return t.tau.helm_isq[(size_t)(sc.k * 2 + sig) * P + p]; };
   if (p == 0) {
     // mean mode: U (r = 0) at constant flow rate and W (r = 1), parity c
@@ -689,7 +738,7 @@ __device__ __forceinline__ void post_solve_noslip(double* col, int cs, Cls cls, 
     auto run = [&](auto& f) {
       mean_solve<MH, RN>(f, N, ny, hs, c, e, (e == 0 ? pb.UM : pb.WM) + (size_t)b * ny,
                        (e == 0 ? pb.HXP : pb.HZP) + (size_t)b * ny, (e == 0) ? Hx : Hz, cc, sc, helm(c),
-                       helm_isq(c), rowc, t.tau.u1 + (size_t)sc.k * Mh, t.tau.u1_iflux[sc.k]);
+                       helm_isq(c), t.tau.u1 + (size_t)sc.k * Mh, t.tau.u1_iflux[sc.k]);
     };
     if constexpr (SMEM) {
       SmemArr f{col, cs};
@@ -711,8 +760,7 @@ __device__ __forceinline__ void post_solve_noslip(double* col, int cs, Cls cls, 
     const CompS Gc{reinterpret_cast<double*>(pb.G) + base, 2 * P};
     const CompT<RN> HGc{reinterpret_cast<RN*>(pb.HGP) + base, 2 * P};
     auto run = [&](auto& f) {
-      omega_solve<MH, RN>(f, N, ny, hs, sq, Gc, HGr, HGc, Hx, Hz, r, sgn, kx, kz, cc, sc, helm(sq), helm_isq(sq),
-                          rowc);
+      omega_solve<MH, RN>(f, N, ny, hs, sq, Gc, HGr, HGc, Hx, Hz, r, sgn, kx, kz, cc, sc, helm(sq), helm_isq(sq));
     };
     if constexpr (SMEM) {
       SmemArr f{col, cs};
@@ -729,12 +777,12 @@ __device__ __forceinline__ void post_solve_noslip(double* col, int cs, Cls cls, 
     const CompT<RN> HVc{reinterpret_cast<RN*>(pb.HVP) + base, 2 * P};
     const size_t vo = (size_t)b * P + p;
     const double vw = fma_rn(sc.theta, comp(pb.vw_new[vo], r) - comp(pb.vw_old[vo], r), comp(pb.vw_old[vo], r));
-    const TabSm TP{t.tau.pois + (size_t)sv * 4 * Mh * P + p, Mh, P};
+    const TabF TP{t.tau.pois_f + (size_t)sv * 6 * Mh * P + p, Mh, P};
     const double* vh = t.tau.vh + (size_t)(sc.k * 2 + sv) * Mh * P + p;
     auto run = [&](auto& f) {
       v_solve<MH, RN>(f, N, ny, hs, sv, Vc, HVr, HVc, Hx, Hy, Hz, r, sgn, kx, kz, k2, cc, sc, helm(sv),
                       helm_isq(sv), TP, t.tau.pois_isq[(size_t)sv * P + p], [&](int i) { return vh[(size_t)i * P]; },
-                      t.tau.vh_idv[(size_t)(sc.k * 2 + sv) * P + p], vw, rowc);
+                      t.tau.vh_idv[(size_t)(sc.k * 2 + sv) * P + p], vw);
     };
     if constexpr (SMEM) {
       SmemArr f{col, cs};
