@@ -414,10 +414,11 @@ int build_tables(ch_env* env) {
   // free-slip top: sum Q, sum n^2 Q per parity; A, B of vh per parity
   std::vector<double> helm_top((size_t)3 * 2 * 2 * P, 0.0), vh_top((size_t)3 * 2 * 2 * P, 0.0);
   const bool top = p.top_bc == 1;
-  // no-slip top: the folded tables of the per-thread solves, [..][eA, eB, eC, h, b, W][Mh][P]
-  std::vector<double> helm_f(top ? 0 : (size_t)3 * 2 * 6 * Mh * P, 0.0);
+  // no-slip top: the folded tables of the per-thread solves, [..][eA, eB, eC, h, b, W (, E1)][Mh][P];
+  // e1 > 0 adds E1 = e1 e (the Helmholtz tables, e1 = 1 + alpha/beta of the stage)
+  std::vector<double> helm_f(top ? 0 : (size_t)3 * 2 * 7 * Mh * P, 0.0);
   std::vector<double> pois_f(top ? 0 : (size_t)2 * 6 * Mh * P, 0.0);
-  auto put_f = [&](std::vector<double>& tab, size_t base, const Factor& F, int M, int pp, int sig) {
+  auto put_f = [&](std::vector<double>& tab, size_t base, const Factor& F, int M, int pp, int sig, double e1) {
     double w = 1.0;  // W_{M-1}
     for (int i = M - 1; i >= 1; --i) {
       const int n = 2 * i + sig;
@@ -428,6 +429,7 @@ int build_tables(ch_env* env) {
       tab[base + ((size_t)3 * Mh + i) * P + pp] = F.h[i];
       tab[base + ((size_t)4 * Mh + i) * P + pp] = F.b[i];
       tab[base + ((size_t)5 * Mh + i) * P + pp] = w;
+      if (e1 > 0.0) tab[base + ((size_t)6 * Mh + i) * P + pp] = e1 * F.e[i];
     }
   };
   auto put = [&](std::vector<double>& tab, size_t base, const Factor& F, int M, int pp) {
@@ -445,7 +447,7 @@ int build_tables(ch_env* env) {
       const int M = (N - sig) / 2 + 1;
       const Factor Fp = host_factor(N, sig, k2);
       put(pois, (size_t)sig * 4 * Mh * P, Fp, M, pp);
-      if (!top) put_f(pois_f, (size_t)sig * 6 * Mh * P, Fp, M, pp, sig);
+      if (!top) put_f(pois_f, (size_t)sig * 6 * Mh * P, Fp, M, pp, sig, 0.0);
       pois_isq[(size_t)sig * P + pp] = Fp.isq;
       for (int k = 0; k < 3; ++k) {
         const double ibdn = 1.0 / (rk_beta(k) * p.dt * env->nu);
@@ -457,7 +459,7 @@ int build_tables(ch_env* env) {
         Factor Fs = Fh;
         for (double& e : Fs.e) e *= -ibdn;
         put(helm, slot * 4 * Mh * P, Fs, M, pp);
-        if (!top) put_f(helm_f, slot * 6 * Mh * P, Fs, M, pp, sig);
+        if (!top) put_f(helm_f, slot * 7 * Mh * P, Fs, M, pp, sig, 1.0 + rk_alpha(k) / rk_beta(k));
         helm_isq[slot * P + pp] = Fh.isq;
         {
           double sq = 0.0, sq2 = 0.0;
@@ -992,7 +994,7 @@ size_t env_footprint(const ch_params_t* p) {
   const size_t nxh = p->nx / 2, P = nxh * p->nz, ny = p->ny, Mh = (ny - 1) / 2 + 1;
   const size_t state = B * (4 * ny * P * 16 + 4 * ny * 8 + 9 * ny * P * 16 + 3 * P * 16 + 8 +
                             (size_t)p->nz * p->nx * 8 + (2 * (size_t)p->nz * p->nx + 2) * 8);
-  const size_t folded = p->top_bc == 0 ? (3 * 2 * 6 * Mh * P + 2 * 6 * Mh * P) * 8 : 0;
+  const size_t folded = p->top_bc == 0 ? (3 * 2 * 7 * Mh * P + 2 * 6 * Mh * P) * 8 : 0;
   const size_t tables = (3 * 2 * 4 * Mh * P + 3 * 2 * P + 2 * 4 * Mh * P + 2 * P + 3 * 2 * Mh * P + 3 * 2 * P +
                          3 * Mh + 3 + 3 * ny + ny + 2 * 3 * 2 * 2 * P) * 8 + ny * ny * 12 + (nxh + p->nz) * 8 +
                         folded;

@@ -499,10 +499,11 @@ struct TauTables {
   const double* u1_iflux;  // [3]               1 / int u1 dy
   const double* rowc;      // [3][ny]           tau row constants cA_n, cB_n, cC_n
   // no-slip top (top_bc = 0): the same factorisations with the row constants
-  // folded in, eA = e cA_n, eB = e cB_n, eC = e cC_n, then h, b and the wall
+  // folded in, eA = e cA_n, eB = e cB_n, eC = e cC_n, then h, b, the wall
   // weights W (W_{M-1} = 1, W_i = 1 + b_{i+1} W_{i+1}: sum_i P_i = sum_i W_i a_i)
-  const double* helm_f;    // [3][2][6][Mh][P]  eA, eB, eC, h, b, W per stage, parity
-  const double* pois_f;    // [2][6][Mh][P]
+  // and, for the stage's Helmholtz operator, E1 = (1 + alpha/beta) e
+  const double* helm_f;    // [3][2][7][Mh][P]  eA, eB, eC, h, b, W, E1 per stage, parity
+  const double* pois_f;    // [2][6][Mh][P]     eA, eB, eC, h, b, W
   // free-slip top (top_bc = 1): the wall rows couple the parities
   const double* helm_top;  // [3][2][2][P]      sum Q, sum n^2 Q of the stage's factorisation, per parity
   const double* vh_top;    // [3][2][2][P]      A = sum n^2 (n^2 - 1) / 3 vh_n, B = sum n^2 vh_n, per parity

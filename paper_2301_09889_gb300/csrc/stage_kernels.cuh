@@ -58,7 +58,8 @@ struct TabSm {
 };
 
 // folded tau tables of one (mode, parity) of a no-slip solve: element (f, i)
-// at base[(f * Mh + i) * ppc], f = eA, eB, eC, h, b, W
+// at base[(f * Mh + i) * ppc], f = eA, eB, eC, h, b, W, and for the stage's
+// Helmholtz operator E1 = (1 + alpha/beta) e
 struct TabF {
   const double* base;
   int Mh, ppc;
@@ -68,6 +69,11 @@ struct TabF {
   __device__ double h(int i) const { return base[(3 * Mh + i) * ppc]; }
   __device__ double b(int i) const { return base[(4 * Mh + i) * ppc]; }
   __device__ double W(int i) const { return base[(5 * Mh + i) * ppc]; }
+  __device__ double E1(int i) const { return base[(6 * Mh + i) * ppc]; }  // Helmholtz tables only
+};
+// a right-hand side value r and the operand x of a diagonal term E1_j x_j
+struct RhsX {
+  double r, x;
 };
 
 // ---------------------------------------------------------------------------
@@ -352,20 +358,30 @@ __device__ __forceinline__ void tau_fused(int N, int ny, int sig, Rhs&& rhs, Arr
 // (P_0 = 0); it equals sum_i W_i a_i and is accumulated during the
 // elimination.  f_0 = (s - sum_i P_i) / sum_i Q_i then follows at once, and the
 // back substitution f_i = a_i + b_i f_{i-1} gives the solution in one pass
-// (f_i = P_i + Q_i f_0, Q_i the products of b).
-template <int MH, class Arr, class Rhs, class Wall>
+// (f_i = P_i + Q_i f_0, Q_i the products of b).  With DIAG, rhs(i) returns
+// RhsX{r_i, x_i} and row j takes the extra term E1_j x_j.
+template <int MH, bool DIAG = false, class Arr, class Rhs, class Wall>
 __device__ __forceinline__ void tau_fold(int N, int sig, Rhs&& rhs, Arr& f, const TabF& T, double isq,
                                          Wall&& wall) {
   const int M = (N - sig) / 2 + 1;
-  double r1 = 0.0, r2 = 0.0, anext = 0.0, sum = 0.0;  // r_{i+1}, r_{i+2}, a_{i+2}
+  double r1 = 0.0, r2 = 0.0, x1 = 0.0, anext = 0.0, sum = 0.0;  // r_{i+1}, r_{i+2}, x_{i+1}, a_{i+2}
 #pragma unroll
   for (int i = MH - 1; i >= 0; --i) {
-    double r0 = 0.0;
-    if (i < M) r0 = rhs(i);
-    const int j = i + 1;  // row j needs r_{j-1} = r0, r_j = r1, r_{j+1} = r2
+    double r0 = 0.0, x0 = 0.0;
+    if (i < M) {
+      if constexpr (DIAG) {
+        const RhsX v = rhs(i);
+        r0 = v.r;
+        x0 = v.x;
+      } else {
+        r0 = rhs(i);
+      }
+    }
+    const int j = i + 1;  // row j needs r_{j-1} = r0, r_j = r1, r_{j+1} = r2 (and x_j = x1)
     if (j < MH && j < M) {
       double R = fma_rn(-T.eB(j), r1, mul_rn(T.eA(j), r0));
       if (j + 1 < M) R = fma_rn(T.eC(j), r2, R);
+      if constexpr (DIAG) R = fma_rn(T.E1(j), x1, R);
       const double a = fma_rn(-T.h(j), anext, R);
       f[j] = a;
       anext = a;
@@ -373,6 +389,7 @@ __device__ __forceinline__ void tau_fold(int N, int sig, Rhs&& rhs, Arr& f, cons
     }
     r2 = r1;
     r1 = r0;
+    x1 = x0;
   }
   double fp = mul_rn(isq, wall() - sum);
   f[0] = fp;
@@ -422,9 +439,13 @@ __device__ __forceinline__ void omega_solve(Arr& f, int N, int ny, int ppc, int 
     }
 }
 
-// v of parity sv: the walk of v_walk (Dv, D^2 v, t, Dt from n = N down)
-// feeds the phi solve row by row; the wall sums S0 = sum v, S2 = sum n^2 v
-// of the old field are taken on the way down.  Then the Dirichlet solve of
+// v of parity sv.  The phi solve's right-hand side is (1 + cc)(D^2 v - k^2 v)
+// + q; its tau rows apply to it the stencil r -> cA r_{n-2} - cB r_n +
+// cC r_{n+2}, which integrates D^2 twice, so the stencil of D^2 v is v_n
+// itself (n >= 2).  Row j therefore takes (1 + cc) e v_n through E1 plus the
+// stencil of u = -(1 + cc) k^2 v + q, and no D^2 v is formed; only the FP32
+// walk of t and Dt (from n = N down) remains for q.  The wall sums S0 = sum v,
+// S2 = sum n^2 v of the old field are taken on the way down.  Then the Dirichlet solve of
 // (D^2 - k^2) v_p = phi with v_p(+-1) = cc v(+-1) + (wall velocity), reading
 // phi from the same array, and the influence correction c_I vh that fixes
 // Dv at the wall: v <- v_p + c_I vh - cc v.
@@ -438,38 +459,30 @@ __device__ __forceinline__ void v_solve(Arr& f, int N, int ny, int ppc, int sv, 
   using CN = typename cpx<RN>::T;
   const int ra = 1 - r;
   auto comp = [](const CN z, int qd) { return qd == 0 ? z.x : z.y; };
-  const double dsv = 2.0 * sv;
   const RN dsvn = (RN)(2 * sv);
   const RN sgnn = (RN)sgn, kxn = (RN)kx, kzn = (RN)kz, k2n = (RN)k2;
   const RN dtn = (RN)sc.dt, gan = (RN)sc.gamma, zen = (RN)sc.zeta;
   const int M = (N - sv) / 2 + 1;
-  double dv = 0.0, d2v = 0.0, S0 = 0.0, S2 = 0.0;
+  const double ck2 = -(1.0 + cc) * k2;
+  double S0 = 0.0, S2 = 0.0;
   RN tt = 0, dtt = 0;
-  tau_fold<MH>(
+  tau_fold<MH, true>(
       N, sv,
       [&](int i) {
         const int no = 2 * i + sv + 1;
-        if (no <= N) {
-          const double vn1 = (no + 1 <= N) ? Vc[no + 1] : 0.0;
-          dv = fma_rn((double)(4 * i + 4) + dsv, vn1, dv);  // 2 (no + 1)
-          tt = mul_rn(sgnn, fma_rn(kxn, comp(Hx[no * ppc], ra), mul_rn(kzn, comp(Hz[no * ppc], ra))));
-        }
+        if (no <= N) tt = mul_rn(sgnn, fma_rn(kxn, comp(Hx[no * ppc], ra), mul_rn(kzn, comp(Hz[no * ppc], ra))));
         const int n = 2 * i + sv;
-        const double fac = (double)(4 * i + 2) + dsv;  // 2 (n + 1)
-        const RN facn = (RN)(4 * i + 2) + dsvn;
-        const double t1 = fma_rn(fac, dv, d2v);
+        const RN facn = (RN)(4 * i + 2) + dsvn;  // 2 (n + 1)
         const RN t2 = fma_rn(facn, (n + 1 <= N) ? tt : (RN)0, dtt);
-        d2v = (n == 0) ? 0.5 * t1 : t1;
         dtt = (n == 0) ? (RN)0.5 * t2 : t2;
         const double vn = Vc[n];
         S0 += vn;
         S2 = fma_rn((double)n * n, vn, S2);
-        const double phi = fma_rn(-k2, vn, d2v);
         const RN hv = fma_rn(-k2n, comp(Hy[n * ppc], r), -dtt);
         const RN hp = HVr[n];
         HVw[n] = hv;
         const RN q = mul_rn(dtn, fma_rn(gan, hv, mul_rn(zen, hp)));
-        return fma_rn(1.0 + cc, phi, (double)q);
+        return RhsX{fma_rn(ck2, vn, (double)q), vn};
       },
       f, Th, isq_h, [] { return 0.0; });
   const double s = fma_rn(cc, S0, ((sv == 0) ? 0.5 : -0.5) * vw);
@@ -730,7 +743,7 @@ __device__ __forceinline__ void post_solve_noslip(double* col, int cs, Cls cls, 
   const int P = g.P, ny = g.ny, N = g.N, Mh = t.tau.Mh;
   const double cc = sc.alpha / sc.beta;
   auto comp = [](auto z, int qq) { return qq == 0 ? z.x : z.y; };
-  auto helm = [&](int sig) { return TabF{t.tau.helm_f + (size_t)(sc.k * 2 + sig) * 6 * Mh * P + p, Mh, P}; };
+  auto helm = [&](int sig) { return TabF{t.tau.helm_f + (size_t)(sc.k * 2 + sig) * 7 * Mh * P + p, Mh, P}; };
   auto helm_isq = [&](int sig) { return t.tau.helm_isq[(size_t)(sc.k * 2 + sig) * P + p]; };
   if (p == 0) {
     // mean mode: U (r = 0) at constant flow rate and W (r = 1), parity c
