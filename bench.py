@@ -209,7 +209,7 @@ def measured_peaks() -> dict:
 # the roofline kernel, from one ncu capture of the same workload (summaries
 # under profiles/); absent where no capture of the current kernel exists
 TRAFFIC_BYTES = {
-    ("minimal_batch256_mixed", "stage_post"): (152.553984 + 47.812608) * 1e6,
+    ("minimal_batch256_mixed", "stage_post"): (152.163072 + 42.973952) * 1e6,
     # the three passes of one FP64 64x64-mode stage (the scratch stays in L2)
     ("larger_fp64", "nonlinear_plane"): (12.597248 + 19.201792 + 9.604352) * 1e6,
     # the three passes of one FP64 256x256-mode stage (z inverse + x pass + z forward)
