@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <chrono>
 #include <cstring>
@@ -1188,6 +1189,34 @@ int env_step_device(ch_env_t* env, const double* d_action, double* d_out) {
   return run_step(env, d_action, d_out);
 }
 
+// true iff no value is an infinity or a NaN (exponent field all ones); one
+// branch-free pass over the encodings
+static bool all_finite(const double* a, size_t n) {
+  constexpr uint64_t kExp = 0x7ff0000000000000ull;
+  uint64_t bad = 0;
+  for (size_t i = 0; i < n; ++i) {
+    uint64_t u;
+    std::memcpy(&u, a + i, sizeof(u));
+    bad |= (uint64_t)((u & kExp) == kExp);
+  }
+  return bad == 0;
+}
+
+// The observation rows of d_out go straight to the caller's array (one
+// pitched copy); the wall shear and reward of every environment, adjacent in
+// each row, come back as pairs into the pinned h_out and are scattered.
+static cudaError_t fetch_outputs(ch_env* env, double* obs) {
+  const size_t B = env->B, plane = (size_t)env->g.nz * env->g.nx, pitch = env->out_stride * sizeof(double);
+  cudaStream_t st = env->stream;
+  cudaError_t e = cudaSuccess;
+  if (obs) e = cudaMemcpy2DAsync(obs, 2 * plane * sizeof(double), env->d_out, pitch, 2 * plane * sizeof(double), B,
+                                 cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpy2DAsync(env->h_out, 2 * sizeof(double), env->d_out + 2 * plane, pitch, 2 * sizeof(double), B,
+                          cudaMemcpyDeviceToHost, st);
+  return e;
+}
+
 int env_step(ch_env_t* env, const double* action, double* obs, double* wall_shear, double* reward) {
   if (!env) return CH_ERR_ARG;
   if (env->prm.control == 0 && !action) return CH_ERR_ARG;
@@ -1195,20 +1224,18 @@ int env_step(ch_env_t* env, const double* action, double* obs, double* wall_shea
   const size_t B = env->B, plane = (size_t)g.nz * g.nx;
   cudaStream_t st = env->stream;
   if (env->prm.control == 0) {
-    for (size_t i = 0; i < B * plane; ++i)
-      if (!std::isfinite(action[i])) return CH_ERR_ARG;  // poisoned action: reject before any work
+    if (!all_finite(action, B * plane)) return CH_ERR_ARG;  // poisoned action: reject before any work
     CK(cudaMemcpyAsync(env->d_act, action, B * plane * sizeof(double), cudaMemcpyHostToDevice, st));
   }
   RC(run_step(env, env->d_act, env->d_out));
-  CK(cudaMemcpyAsync(env->h_out, env->d_out, B * env->out_stride * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(fetch_outputs(env, obs));
   CK(cudaStreamSynchronize(st));
   int rc = CH_OK;
   for (size_t b = 0; b < B; ++b) {
-    const double* o = env->h_out + b * env->out_stride;
-    if (obs) std::memcpy(obs + b * 2 * plane, o, 2 * plane * sizeof(double));
-    if (wall_shear) wall_shear[b] = o[2 * plane];
-    if (reward) reward[b] = o[2 * plane + 1];
-    if (!std::isfinite(o[2 * plane])) rc = CH_ERR_DIVERGED;
+    const double tau = env->h_out[2 * b], rew = env->h_out[2 * b + 1];
+    if (wall_shear) wall_shear[b] = tau;
+    if (reward) reward[b] = rew;
+    if (!std::isfinite(tau)) rc = CH_ERR_DIVERGED;
   }
   return rc;
 }
@@ -1292,10 +1319,9 @@ int env_observe(ch_env_t* env, double* obs) {
   // spectra, then the observation planes into the output rows
   CK(launch_sense(g, env->B, env->pb, env->tab, env->js, env->prm.alpha, 0, st));
   CK(launch_obs(g, env->B, env->pb.planes, env->tab, env->d_out, env->out_stride, nullptr, st));
-  CK(cudaMemcpyAsync(env->h_out, env->d_out, env->B * env->out_stride * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpy2DAsync(obs, 2 * plane * sizeof(double), env->d_out, env->out_stride * sizeof(double),
+                       2 * plane * sizeof(double), env->B, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  for (int b = 0; b < env->B; ++b)
-    std::memcpy(obs + (size_t)b * 2 * plane, env->h_out + (size_t)b * env->out_stride, 2 * plane * sizeof(double));
   return CH_OK;
 }
 
