@@ -1764,10 +1764,11 @@ __global__ void __launch_bounds__(64, post_batched_min_ctas<MH, TOP>()) stage_po
       solve(c);
     }
   } else {
-    // ---- implicit solves under a free-slip top, in two rounds (omega_y or
-    // the mean flow, then v), each closed after a barrier by the pair of class
-    // threads (c, 1 - c) of a (mode, component); every thread reaches both
-    // barriers
+    // ---- implicit solves under a free-slip top, in two closures (omega_y or
+    // the mean flow, then v), each closed by the pair of class threads
+    // (c, 1 - c) of a (mode, component), neighbouring lanes that exchange
+    // their sums by shuffles; every lane of the warp takes part in both
+    // exchanges
     const int p = p0 + pl;
     const int pc = min(p, P - 1);
     const int row = pc / g.nxh, ix = pc % g.nxh;
@@ -1786,7 +1787,7 @@ __global__ void __launch_bounds__(64, post_batched_min_ctas<MH, TOP>()) stage_po
     const size_t base = 2 * ((size_t)b * ny * P + pc) + r;  // component r of element n at base + 2 P n
     const double sgn = (r == 0) ? -1.0 : 1.0;
     RegArr<MH> f;
-    // round 1: the mean mode (U for r = 0, W for r = 1) on parity c, or
+    // first closure: the mean mode (U for r = 0, W for r = 1) on parity c, or
     // omega_y on parity 1 - c
     {
       const int sig = mean ? c : 1 - c;
@@ -1853,7 +1854,7 @@ __global__ void __launch_bounds__(64, post_batched_min_ctas<MH, TOP>()) stage_po
         }
       }
     }
-    // round 2: v on parity c (every mode but the mean)
+    // second closure: v on parity c (every mode but the mean)
     {
       const int sig = c;
       const int M = (N - sig) / 2 + 1;
