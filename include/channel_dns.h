@@ -149,6 +149,9 @@ int env_reset(ch_env_t* env, uint64_t seed, double amplitude, int kmax);
  *   obs        [B][2][nz][nx] u and v on the sensing plane after the steps;
  *   wall_shear [B] nu dU/dy at the lower wall averaged over the steps;
  *   reward     [B] 1 - wall_shear / tau_ref (Sec. 3.2).
+ * Any of obs, wall_shear, reward may be NULL.  The observations are copied
+ * from the device straight into obs (one pitched copy; pinned memory lets it
+ * run as a DMA, pageable memory is staged by the driver).
  * Synchronises the stream.  Returns CH_ERR_ARG without doing any work if the
  * action holds a non-finite value, and CH_ERR_DIVERGED if any wall shear is
  * not finite (outputs are still written). */
